@@ -1,0 +1,152 @@
+"""CPU oracle for real Schur-form eigenvalue reordering -- TEST INFRASTRUCTURE.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  The GPU library never does; the two
+share no code.
+
+The arithmetic lives in `reorder_oracle.c` (plain C, binary64,
+-ffp-contract=off): the scalar-update reordering of Section 3.2 / Fig. 1a,
+producing the reordered Schur form of Eq. 7.  This module only compiles it
+with gcc and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "reorder_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_llp = ctypes.POINTER(ctypes.c_longlong)
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _SO, extra=()) -> str:
+    """Compile the oracle with gcc (-O2 -ffp-contract=off)."""
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
+           "-o", out + ".tmp", src, "-lm", *extra]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
+def load(path: str | None = None):
+    """Load (building if needed) the oracle library; returns the ctypes CDLL."""
+    global _lib
+    if path is None and _lib is not None:
+        return _lib
+    so = path or build()
+    lib = ctypes.CDLL(so)
+    lib.orc_validate.argtypes = [ctypes.c_int, _dp, ctypes.c_int]
+    lib.orc_validate.restype = ctypes.c_int
+    lib.orc_eigenvalues.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+    lib.orc_eigenvalues.restype = None
+    lib.orc_sylvester.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                  ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int, _dp]
+    lib.orc_sylvester.restype = ctypes.c_int
+    lib.orc_std2.argtypes = [ctypes.c_double] * 4 + [_dp, _dp, _dp]
+    lib.orc_std2.restype = None
+    lib.orc_swap.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.orc_swap.restype = ctypes.c_int
+    lib.orc_reorder.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int, _ip,
+                                _dp, _dp, _ip, ctypes.c_int, ctypes.c_int, _llp, _llp,
+                                ctypes.POINTER(ctypes.c_ubyte)]
+    lib.orc_reorder.restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _f64(a):
+    return np.asfortranarray(np.array(a, dtype=np.float64, copy=True))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def validate(S, lib=None) -> int:
+    S = _f64(S)
+    n = S.shape[0]
+    return (lib or load()).orc_validate(n, _ptr(S), max(n, 1))
+
+
+def eigenvalues(S, lib=None):
+    S = _f64(S)
+    n = S.shape[0]
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    (lib or load()).orc_eigenvalues(n, _ptr(S), max(n, 1), _ptr(wr), _ptr(wi))
+    return wr, wi
+
+
+def sylvester(T11, T22, T12, lib=None):
+    """Solve T11 X - X T22 = gamma T12 (p, q in {1, 2}); returns (X, gamma)."""
+    T11, T22, T12 = _f64(np.atleast_2d(T11)), _f64(np.atleast_2d(T22)), _f64(np.atleast_2d(T12))
+    p, q = T11.shape[0], T22.shape[0]
+    X = np.zeros((2, 2), order="F")
+    g = ctypes.c_double(0.0)
+    (lib or load()).orc_sylvester(p, q, _ptr(T11), p, _ptr(T22), q, _ptr(T12), p,
+                                  _ptr(X), 2, ctypes.byref(g))
+    return X[:p, :q].copy(), g.value
+
+
+def std2(M, lib=None):
+    """Standardize a 2x2 block: returns (c, s, N) with N = Z^T M Z,
+    Z = [[c, -s], [s, c]]."""
+    M = np.asarray(M, dtype=np.float64)
+    c = ctypes.c_double()
+    s = ctypes.c_double()
+    out = np.zeros(4)
+    (lib or load()).orc_std2(M[0, 0], M[0, 1], M[1, 0], M[1, 1],
+                             ctypes.byref(c), ctypes.byref(s), _ptr(out))
+    return c.value, s.value, out.reshape(2, 2, order="F")
+
+
+def swap(S, j, p, q, Q=None, strong=True, lib=None):
+    """Swap the p x p block at j with the q x q block below it.
+    Returns (status, S_new, Q_new); status 0 = applied, 1 = rejected."""
+    S = _f64(S)
+    n = S.shape[0]
+    Qp = None
+    if Q is not None:
+        Q = _f64(Q)
+        Qp = _ptr(Q)
+    st = (lib or load()).orc_swap(n, _ptr(S), n, Qp, n, j, p, q, 1 if strong else 0)
+    return st, S, Q
+
+
+def reorder(S, Q, select, *, abort=False, strong=True, lib=None):
+    """Reorder the Schur form (S, Q) so that the selected eigenvalues lead.
+
+    Returns a dict with S, Q (new arrays), wr, wi, m, status, nswaps, nrej,
+    sel (final per-position selection flags)."""
+    S = _f64(S)
+    n = S.shape[0]
+    Qp = None
+    if Q is not None:
+        Q = _f64(Q)
+        Qp = _ptr(Q)
+    sel_in = np.ascontiguousarray(np.asarray(select, dtype=np.int32))
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    ns = ctypes.c_longlong(0)
+    nr = ctypes.c_longlong(0)
+    selout = np.zeros(max(n, 1), dtype=np.uint8)
+    st = (lib or load()).orc_reorder(n, _ptr(S), max(n, 1), Qp, max(n, 1),
+                                     sel_in.ctypes.data_as(_ip), _ptr(wr), _ptr(wi),
+                                     ctypes.byref(m), 1 if abort else 0, 1 if strong else 0,
+                                     ctypes.byref(ns), ctypes.byref(nr),
+                                     selout.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return dict(S=S, Q=Q, wr=wr, wi=wi, m=m.value, status=st, nswaps=ns.value,
+                nrej=nr.value, sel=selout[:n].astype(bool))
