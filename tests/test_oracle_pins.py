@@ -118,6 +118,19 @@ def test_std2_real_splits(seed):
     assert np.allclose(np.sort([N[0, 0], N[1, 1]]), roots, rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("M", [[[2.0, 1.0], [1e-9, 1.0]], [[1.0, 3.0], [2e-12, -1.0]],
+                               [[-1.0, 1e-8], [4.0, 2.0]], [[0.5, -2.0], [-1e-11, 0.25]]])
+def test_std2_real_nearly_triangular(M):
+    """Real pair with |m12 m21| << ((m11 - m22)/2)^2: the Schur vector must
+    be formed without cancellation, so that the forced zero below the
+    diagonal is a backward error of order eps."""
+    M = np.array(M)
+    c, s, N = oracle.std2(M)
+    Z = np.array([[c, -s], [s, c]])
+    assert N[1, 0] == 0.0
+    assert np.linalg.norm(Z.T @ M @ Z - N) < 8 * EPS * np.linalg.norm(M)
+
+
 def test_std2_special_cases():
     # already triangular: identity rotation, block unchanged
     c, s, N = oracle.std2(np.array([[1.0, 2.0], [0.0, 3.0]]))
@@ -251,7 +264,7 @@ def test_swap_decision_matches_dtrsen():
     LAPACK's dtrsen (an independent implementation of the same test) on
     random hard swaps; both outcomes occur."""
     rng = np.random.default_rng(808)
-    agree = total = rejected = 0
+    agree = total = rejected = weak_rejected = 0
     for _ in range(3000):
         D, p, q = hard_swap_case(rng)
         if oracle.validate(D) != 0:
@@ -269,6 +282,13 @@ def test_swap_decision_matches_dtrsen():
             assert np.linalg.norm(Qn.T @ D @ Qn - Dn) <= 50 * EPS * np.linalg.norm(D)
         else:
             assert np.array_equal(Dn, D)
+        # the weak test alone must already guarantee a small backward error
+        stw, Dw, Qw = oracle.swap(D, 0, p, q, Q=np.eye(k), strong=False)
+        if stw == 0:
+            assert np.linalg.norm(Qw.T @ D @ Qw - Dw) <= 100 * EPS * np.linalg.norm(D)
+        else:
+            weak_rejected += 1
+    assert weak_rejected > 20
     assert total > 2000
     assert rejected > 50
     assert agree >= 0.99 * total
