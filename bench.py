@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark: selected eigenvalues reordered per second on one GB300.
+
+Workload (default): a real Schur form of order n = 4000 from the seeded
+generator (60% of positions in 1x1 blocks, 40% in standardized 2x2 blocks,
+N(0,1) strict upper part), Q = product of 64 seeded Householder reflectors,
+35% of the eigenvalues selected, window 128, chain 64, FP64 DMMA updates.
+
+A step is one full reordering (every planner, window, update and eigenvalue
+kernel of the call).  S and Q (256 MB, larger than L2) are restored from a
+pristine device copy before each step, outside the timed region; that
+rewrite also evicts them from L2.  Each step is timed with CUDA events on the
+library's stream; `value` = selected eigenvalues of all steps (and ranks) /
+summed step time.
+
+Also reported:
+  roofline      the dominant kernel's algorithmic work / its event-timed
+                duration inside the timed steps, against the measured peak;
+  e2e           the same metric through gbr_reorder_host (pinned host
+                buffers, H2D + D2H inside the timed region);
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload;
+  clocks        nvidia-smi samples taken during the timed region.
+
+`--impl reference` times the CPU oracle instead (rank 0 only).
+Multi-GPU: one reordering does not shard; N ranks run N independent
+replicas (`scaling: weak`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import schur_inputs as si  # noqa: E402
+
+WORKLOADS = {
+    "n4000": dict(name="n4000", n=4000, select=0.35, q="64 Householder reflectors", window=128,
+                  chain=64),
+    "n400": dict(name="n400", n=400, select=0.30, q="identity", window=128, chain=64),
+    "n16000c": dict(name="n16000c", n=16000, select=0.50, q="64 Householder reflectors",
+                    window=128, chain=64),
+}
+METRIC = "selected eigenvalues reordered per second"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def make_inputs(wl, seed=0):
+    return si.config(wl["name"], seed)
+
+
+def cpu_oracle_sample(S, Q, sel, budget_s=15.0):
+    """Time the oracle on the first k selected blocks (top to bottom) of the
+    workload, k grown until ~budget_s of work, and extrapolate to the whole
+    workload by the number of adjacent block swaps it needs."""
+    import oracle
+    n = S.shape[0]
+    sub = np.append(np.diag(S, -1) != 0, False)
+    starts, sizes = [], []
+    p = 0
+    while p < n:
+        sz = 2 if sub[p] else 1
+        starts.append(p)
+        sizes.append(sz)
+        p += sz
+    selb = [bool(sel[s] or (sz == 2 and sel[s + 1])) for s, sz in zip(starts, sizes)]
+
+    def swaps_needed(k_blocks):
+        cnt, unsel_above, taken = 0, 0, 0
+        for b, flag in enumerate(selb):
+            if flag:
+                if taken >= k_blocks:
+                    break
+                cnt += unsel_above
+                taken += 1
+            else:
+                unsel_above += 1
+        return cnt
+
+    nsel_blocks = sum(selb)
+    full_swaps = swaps_needed(nsel_blocks)
+    k = max(1, nsel_blocks // 8)
+    while True:
+        sub_sel = np.zeros(n, np.int32)
+        taken = 0
+        for s, sz, flag in zip(starts, sizes, selb):
+            if flag and taken < k:
+                sub_sel[s:s + sz] = 1
+                taken += 1
+        t0 = time.perf_counter()
+        r = oracle.reorder(S, Q, sub_sel)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 3 or k >= nsel_blocks:
+            break
+        k = min(nsel_blocks, int(k * 1.6) + 1)
+    est_full = dt * full_swaps / max(r["nswaps"], 1)
+    nsel = int(np.sum([sz for sz, f in zip(sizes, selb) if f]))
+    return {"value": nsel / est_full, "unit": "eigs/s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {k} of {nsel_blocks} selected blocks of the n={n} workload "
+                       f"({r['nswaps']} of {full_swaps} block swaps) timed {dt:.1f} s on 1 core, "
+                       f"scaled by swap count to the full workload (est. {est_full:.0f} s)")}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    S, Q, sel = make_inputs(wl)
+    nsel = int(expected_selected(S, sel))
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_oracle_sample(S, Q, sel, budget_s=8.0)
+        if i >= args.warmup:
+            times.append(nsel / cb["value"])
+            samples.append(cb["sample"])
+    value = nsel * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "n": wl["n"], "select": wl["select"],
+                       "q": wl["q"], "window": wl["window"], "chain": wl["chain"]},
+            "cpu_baseline": {"value": value, "unit": "eigs/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[-1]},
+            "e2e": {"value": value, "unit": "eigs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def expected_selected(S, sel):
+    n = S.shape[0]
+    cnt = 0
+    p = 0
+    while p < n:
+        if p + 1 < n and S[p + 1, p] != 0:
+            cnt += 2 if (sel[p] or sel[p + 1]) else 0
+            p += 2
+        else:
+            cnt += 1 if sel[p] else 0
+            p += 1
+    return cnt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
+    ap.add_argument("--workload", default="n4000", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import paper_1905_04975_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+
+    S_np, Q_np, sel = make_inputs(wl)
+    n = S_np.shape[0]
+    nsel = expected_selected(S_np, sel)
+    S0, Q0 = g.to_device(S_np), g.to_device(Q_np)
+    S, Q = g.to_device(S_np), g.to_device(Q_np)
+    stream = torch.cuda.Stream()
+    opts = g.make_opts(window=wl["window"], chain=wl["chain"], precision="dmma", timing=True)
+
+    def step():
+        with torch.cuda.stream(stream):
+            S.copy_(S0)
+            Q.copy_(Q0)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = g.reorder(S, Q, sel, opts=opts, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        r, _ = step()
+        assert r.status == 0, r.status
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            r, t = step()
+            ms.append(t)
+            stats.append(r.stats)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = nsel * args.steps * world / (total_ms / 1e3)
+
+    # dominant kernel and its roofline (work per launch from the planner's count)
+    ms_upd = sum(s.ms_update for s in stats) / len(stats)
+    ms_win = sum(s.ms_window for s in stats) / len(stats)
+    nwin = stats[0].windows
+    flops = stats[0].upd_flops
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)   # bf16 measured x nominal FP64/bf16
+    if ms_upd >= ms_win:
+        achieved = flops / (ms_upd / 1e3) / 1e12
+        roof = {"kernel": "update_kernel (DMMA FP64 Y <- Y U)", "bound": "tensor",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 1.25/2250",
+                "launches_per_step": nwin, "avg_launch_ms": ms_upd / max(nwin, 1),
+                "share_of_step": ms_upd / (total_ms / args.steps)}
+    else:
+        roof = {"kernel": "window_kernel (FP64 swaps)", "bound": "alu", "achieved": None,
+                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "launches_per_step": nwin, "avg_launch_ms": ms_win / max(nwin, 1),
+                "share_of_step": ms_win / (total_ms / args.steps)}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        Sp = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Qp = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Sh = Sp.numpy().T  # Fortran-ordered view of the pinned buffer
+        Qh = Qp.numpy().T
+        et = []
+        for i in range(args.e2e_steps + 1):
+            Sh[:] = S_np
+            Qh[:] = Q_np
+            t0 = time.perf_counter()
+            r = g.reorder_host(Sh, Qh, sel, opts=opts, stream=stream)
+            dt = time.perf_counter() - t0
+            if i > 0:
+                et.append(dt)
+        e2e = {"value": nsel * len(et) / sum(et) * world, "unit": "eigs/s",
+               "h2d_bytes_per_step": 2 * n * n * 8 + 4 * n,
+               "d2h_bytes_per_step": 2 * n * n * 8 + 2 * 8 * n}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(S_np, Q_np, sel)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "eigs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "n": n, "select": wl["select"],
+                           "selected_eigs": nsel, "q": wl["q"], "window": wl["window"],
+                           "chain": wl["chain"], "precision": "dmma",
+                           "l2": "S,Q (256 MB > L2) restored from a device copy before each step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+                "clocks": clk.summary(),
+                "gpu_launches": int(sum(s.launches for s in stats)),
+                "detail": {"windows": int(nwin), "chains": int(stats[0].chains),
+                           "swaps": int(stats[0].swaps), "upd_flops": flops,
+                           "ms_window_kernels": ms_win, "ms_update_kernels": ms_upd,
+                           "update_tflops_of_step": flops / (total_ms / args.steps / 1e3) / 1e12}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,164 @@
+/*
+ * gbreorder -- eigenvalue reordering of a real Schur form on one GPU (sm_103a).
+ *
+ * The operation (Section 2, Eq. 7 of Myllykoski & Kjelgaard Mikkelsen,
+ * "Introduction to StarNEig"): given S in standard real Schur form
+ * (Eq. 4: upper quasi-triangular with 1x1 and 2x2 diagonal blocks, each
+ * 2x2 block standardized as [[a, b], [c, a]] with bc < 0), an orthogonal Q
+ * and a selection of eigenvalues, compute an orthogonal Q3 such that
+ *
+ *     S_hat = Q3^T S Q3
+ *
+ * is again in standard real Schur form with the selected eigenvalues in
+ * its leading diagonal blocks; S is overwritten by S_hat and Q by Q Q3.
+ * Selected blocks keep their relative order, and so do unselected ones.
+ *
+ * Method (Section 3.2): chains of adjacent block swaps are applied inside
+ * small diagonal windows and accumulated into an orthogonal matrix U per
+ * window (Fig. 1b); U is then applied to the rest of S and to Q as dense
+ * matrix products (the left/right update tasks of Section 3.2), and the
+ * windows of successive chains are pipelined.
+ *
+ * Conventions for every entry point:
+ *   - matrices are column-major FP64 with a leading dimension (ld >= n),
+ *     as in LAPACK/ScaLAPACK (Section 4.2);
+ *   - `select` has one int per diagonal position; a 2x2 block is selected
+ *     if either of its two positions is;
+ *   - a non-NULL `cuda_stream` is a cudaStream_t; NULL means the legacy
+ *     default stream;
+ *   - calls are synchronous: they return after all GPU work has finished;
+ *   - the library never frees caller memory.  Its own scratch (window
+ *     accumulators, block plan, counters) comes from a per-device pool the
+ *     library owns, grown on demand and kept until gbr_release().
+ *
+ * Return value (int):
+ *     0            success;
+ *     k > 0        k block swaps were rejected by the stability test: the
+ *                  reordering is partial, but S and Q are still an exact
+ *                  orthogonal similarity in standard form (a rejected
+ *                  block stays in place and later selected blocks stop
+ *                  below it);
+ *     -i (1..12)   argument i is invalid (e.g. -1: n < 0, -3: ldS < n,
+ *                  -2: S is not in standard real Schur form);
+ *     GBR_ERR_*    the negative codes below.
+ */
+#ifndef GBREORDER_H
+#define GBREORDER_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBR_ERR_CUDA    (-1001) /* a CUDA call failed (message: gbr_last_error) */
+#define GBR_ERR_NOMEM   (-1002) /* device or host allocation failed */
+#define GBR_ERR_TIMEOUT (-1003) /* a bounded device-side wait gave up */
+#define GBR_ERR_UNSUPPORTED (-1004) /* option value not supported */
+
+#define GBR_PREC_DMMA   0  /* off-diagonal updates on FP64 tensor cores (DMMA) */
+#define GBR_PREC_OZAKI  1  /* off-diagonal updates as split-precision emulated FP64 */
+
+#define GBR_ON_REJECT_CONTINUE 0 /* a rejected block stays; later blocks stop below it */
+
+/* Options; gbr_default_opts() fills the defaults shown. */
+typedef struct gbr_opts {
+    int window;        /* diagonal window size w, 16..128      (default 128) */
+    int chain;         /* selected eigenvalues per chain m, 1..w-2 (default 64) */
+    int precision;     /* GBR_PREC_DMMA                         (default)     */
+    int slices;        /* split-precision slice count (reserved) (default 0)  */
+    int strong_test;   /* 1: weak + strong stability test       (default 1)   */
+    int on_reject;     /* GBR_ON_REJECT_CONTINUE                (default)     */
+    int validate;      /* 1: check the standard-form input      (default 1)   */
+    int timing;        /* 1: time the window and update kernels with CUDA
+                          events into gbr_stats (small overhead) (default 0)  */
+} gbr_opts;
+
+/* Per-call statistics (all optional). */
+typedef struct gbr_stats {
+    long long swaps;      /* accepted block swaps                      */
+    long long rejected;   /* rejected block swaps                      */
+    long long windows;    /* diagonal windows processed                */
+    long long chains;     /* window chains                             */
+    long long launches;   /* kernels launched by the call              */
+    double upd_flops;     /* flops of the off-diagonal updates         */
+    double ms_total;      /* wall time of the call                     */
+    double ms_window;     /* summed window-kernel time (opts.timing)   */
+    double ms_update;     /* summed update-kernel time (opts.timing)   */
+} gbr_stats;
+
+/* Fill *opts with the defaults. */
+void gbr_default_opts(gbr_opts *opts);
+
+/*
+ * Reorder a Schur form resident in device memory (Eq. 7).
+ *
+ *  1 n        order of S (n >= 0)
+ *  2 S        device pointer, n x n column-major, overwritten by S_hat
+ *  3 ldS      leading dimension of S, >= max(1, n)
+ *  4 Q        device pointer or NULL; n x n column-major, overwritten by Q Q3
+ *  5 ldQ      leading dimension of Q, >= max(1, n) when Q != NULL
+ *  6 select   host pointer, n ints; nonzero selects the eigenvalue at that
+ *             diagonal position
+ *  7 eig_re   host pointer or NULL; n doubles: real parts of the
+ *             eigenvalues of S_hat in diagonal order
+ *  8 eig_im   host pointer or NULL; n doubles: imaginary parts (a
+ *             conjugate pair gives +im first, then -im)
+ *  9 m_out    host pointer or NULL; number of selected eigenvalues (the
+ *             dimension of the leading invariant subspace when status 0)
+ * 10 opts     options or NULL for the defaults
+ * 11 stats    host pointer or NULL; filled with per-call statistics
+ * 12 cuda_stream  cudaStream_t or NULL
+ */
+int gbr_reorder(int n, double *S, int ldS, double *Q, int ldQ, const int *select,
+                double *eig_re, double *eig_im, int *m_out, const gbr_opts *opts,
+                gbr_stats *stats, void *cuda_stream);
+
+/*
+ * Same operation with S and Q in HOST memory (pageable or pinned): the
+ * call copies them to the device, reorders, and copies them back.  The
+ * arguments mean what they mean for gbr_reorder, except that S and Q are
+ * host pointers.  Device buffers come from the library's pool.
+ */
+int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *select,
+                     double *eig_re, double *eig_im, int *m_out, const gbr_opts *opts,
+                     gbr_stats *stats, void *cuda_stream);
+
+/*
+ * Window plan of a reordering, on the host only (no GPU work): the diagonal
+ * windows that gbr_reorder launches, in program order, assuming no swap is
+ * rejected (Section 3.2, Fig. 2: one chain of windows per group of at most
+ * `chain` selected eigenvalues, each window at most `window` rows, never
+ * cutting a 2x2 block).
+ *
+ *  n          order of S
+ *  sub        host, n bytes: sub[i] != 0 iff S[i+1, i] != 0 (2x2 block at i)
+ *  select     host, n ints, as for gbr_reorder
+ *  window, chain   as in gbr_opts
+ *  with_q     nonzero to count the flops of the Q update
+ *  windows    host, 2 * max_windows ints or NULL: (s, e) of each window
+ *  max_windows  capacity of `windows`
+ *  chains     host or NULL: number of chains
+ *  upd_flops  host or NULL: flops of all off-diagonal updates,
+ *             sum over windows of 2 w^2 ((n - e) + s + (with_q ? n : 0))
+ * Returns the number of windows (only the first max_windows are written),
+ * or -1 (n < 0), -2 (sub or select NULL), -4/-5 (bad window/chain).
+ */
+int gbr_plan(int n, const unsigned char *sub, const int *select, int window, int chain,
+             int with_q, int *windows, int max_windows, int *chains, double *upd_flops);
+
+/* Human-readable text for a status code (static storage). */
+const char *gbr_status_string(int status);
+
+/* Text of the last CUDA error seen by the calling thread ("" if none). */
+const char *gbr_last_error(void);
+
+/* Release the library's device scratch pool on the current device. */
+void gbr_release(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int gbr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBREORDER_H */

@@ -1,0 +1,243 @@
+"""gbreorder: eigenvalue reordering of a real Schur form on one GB300 GPU.
+
+Thin ctypes binding over the C ABI declared in include/gbreorder.h
+(libgbreorder.so, built in-tree by `build.py`).  It only marshals arguments:
+every step of the reordering runs in the library's CUDA kernels.  PyTorch is
+used for device memory and streams only.
+
+Matrices are FP64 and column-major.  On the device they are torch tensors
+whose memory is column-major: shape (n, n) with strides (1, ld), e.g.
+`torch.from_numpy(S_fortran).cuda()` or `to_device(S)` below.  There is no
+CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "libgbreorder.so")
+
+PREC_DMMA = 0
+PREC_OZAKI = 1
+
+ERR_CUDA = -1001
+ERR_NOMEM = -1002
+ERR_TIMEOUT = -1003
+ERR_UNSUPPORTED = -1004
+
+
+class GbrOpts(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("chain", ctypes.c_int), ("precision", ctypes.c_int),
+                ("slices", ctypes.c_int), ("strong_test", ctypes.c_int),
+                ("on_reject", ctypes.c_int), ("validate", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+class GbrStats(ctypes.Structure):
+    _fields_ = [("swaps", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
+                ("windows", ctypes.c_longlong), ("chains", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong), ("upd_flops", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_window", ctypes.c_double),
+                ("ms_update", ctypes.c_double)]
+
+
+# Every symbol the header declares, with (restype, argtypes).
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_REORDER_ARGS = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _ip,
+                 _dp, _dp, _ip, ctypes.POINTER(GbrOpts), ctypes.POINTER(GbrStats),
+                 ctypes.c_void_p]
+SYMBOLS = {
+    "gbr_default_opts": (None, [ctypes.POINTER(GbrOpts)]),
+    "gbr_reorder": (ctypes.c_int, _REORDER_ARGS),
+    "gbr_reorder_host": (ctypes.c_int, _REORDER_ARGS),
+    "gbr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gbr_last_error": (ctypes.c_char_p, []),
+    "gbr_release": (None, []),
+    "gbr_version": (ctypes.c_int, []),
+    "gbr_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte), _ip, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _ip, _dp]),
+}
+
+_lib = None
+
+
+def load(path: str = SO_PATH):
+    """Load libgbreorder.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path == SO_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m "
+                          "paper_1905_04975_gb300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SYMBOLS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path == SO_PATH:
+        _lib = lib
+    return lib
+
+
+class GbrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gbr status {status}: {msg}")
+        self.status = status
+
+
+def status_string(status: int) -> str:
+    lib = load()
+    s = lib.gbr_status_string(status).decode()
+    if status in (ERR_CUDA, ERR_NOMEM):
+        s += f" ({lib.gbr_last_error().decode()})"
+    return s
+
+
+def default_opts() -> GbrOpts:
+    o = GbrOpts()
+    load().gbr_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(window=None, chain=None, precision=None, slices=None, strong=None,
+              validate=None, timing=None) -> GbrOpts:
+    o = default_opts()
+    if window is not None:
+        o.window = int(window)
+    if chain is not None:
+        o.chain = int(chain)
+    if precision is not None:
+        o.precision = {"dmma": PREC_DMMA, "ozaki": PREC_OZAKI}.get(precision, precision)
+    if slices is not None:
+        o.slices = int(slices)
+    if strong is not None:
+        o.strong_test = 1 if strong else 0
+    if validate is not None:
+        o.validate = 1 if validate else 0
+    if timing is not None:
+        o.timing = 1 if timing else 0
+    return o
+
+
+@dataclass
+class ReorderResult:
+    status: int           # 0, or number of rejected swaps (> 0)
+    m: int                # number of selected eigenvalues
+    eigs: np.ndarray      # complex eigenvalues of the result, diagonal order
+    stats: GbrStats
+
+
+def _colmajor_ld(t) -> int:
+    n0, n1 = t.shape
+    if str(t.dtype) != "torch.float64":
+        raise TypeError("matrices must be float64")
+    if n0 > 1 and t.stride(0) != 1:
+        raise ValueError("matrix must be column-major (stride (1, ld)); use to_device()")
+    return max(t.stride(1), max(n0, 1)) if n1 > 1 else max(n0, 1)
+
+
+def to_device(A: np.ndarray, device="cuda"):
+    """Copy a numpy matrix to a column-major CUDA float64 tensor."""
+    import torch
+    A = np.asfortranarray(A, dtype=np.float64)
+    t = torch.empty((A.shape[1], A.shape[0]), dtype=torch.float64, device=device).t()
+    t.copy_(torch.from_numpy(A))
+    return t
+
+
+def to_host(t) -> np.ndarray:
+    """Copy a column-major CUDA tensor back to a Fortran-ordered numpy array."""
+    return np.asfortranarray(t.cpu().numpy())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def _finish(rc, n, m, wr, wi, stats, allow_partial):
+    if rc < 0 or (rc > 0 and not allow_partial):
+        raise GbrError(rc, status_string(rc))
+    return ReorderResult(status=rc, m=m.value, eigs=wr + 1j * wi, stats=stats)
+
+
+def reorder(S, Q, select, *, opts: GbrOpts | None = None, stream=None, allow_partial=True,
+            **kw) -> ReorderResult:
+    """Reorder (S, Q) in place on the GPU so that the selected eigenvalues lead.
+
+    S, Q: column-major float64 CUDA tensors (Q may be None); select: ints,
+    one per diagonal position.  Keyword options: window, chain, precision,
+    strong, validate."""
+    lib = load()
+    n = int(S.shape[0])
+    ldS = _colmajor_ld(S)
+    qptr, ldQ = None, max(n, 1)
+    if Q is not None:
+        ldQ = _colmajor_ld(Q)
+        qptr = ctypes.c_void_p(Q.data_ptr())
+    sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+    if sel.size != n:
+        raise ValueError("select must have n entries")
+    o = opts if opts is not None else make_opts(**kw)
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    stats = GbrStats()
+    rc = lib.gbr_reorder(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ,
+                         sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
+                         wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
+                         ctypes.byref(stats), _stream_handle(stream))
+    return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+def reorder_host(S: np.ndarray, Q: np.ndarray | None, select, *, opts: GbrOpts | None = None,
+                 stream=None, allow_partial=True, **kw) -> ReorderResult:
+    """Same as reorder() for host (numpy, Fortran-ordered float64) S and Q,
+    updated in place; the library copies them to the GPU and back."""
+    lib = load()
+    if not (S.flags.f_contiguous and S.dtype == np.float64):
+        raise ValueError("S must be a Fortran-ordered float64 array")
+    n = int(S.shape[0])
+    qptr = None
+    if Q is not None:
+        if not (Q.flags.f_contiguous and Q.dtype == np.float64):
+            raise ValueError("Q must be a Fortran-ordered float64 array")
+        qptr = ctypes.c_void_p(Q.ctypes.data)
+    sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+    o = opts if opts is not None else make_opts(**kw)
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    stats = GbrStats()
+    rc = lib.gbr_reorder_host(n, ctypes.c_void_p(S.ctypes.data), max(n, 1), qptr, max(n, 1),
+                              sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
+                              wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
+                              ctypes.byref(stats), _stream_handle(stream))
+    return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+def plan(sub, select, window=128, chain=64, with_q=True):
+    """Host-only window plan: returns (windows (k x 2 int array of [s, e)),
+    chains, update flops)."""
+    lib = load()
+    sub = np.ascontiguousarray(np.asarray(sub, dtype=np.uint8).reshape(-1))
+    sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+    n = sub.size
+    ch = ctypes.c_int(0)
+    fl = ctypes.c_double(0.0)
+    cnt = lib.gbr_plan(n, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), sel.ctypes.data_as(_ip),
+                       window, chain, 1 if with_q else 0, None, 0, None, None)
+    if cnt < 0:
+        raise GbrError(cnt, "invalid plan arguments")
+    out = np.zeros(2 * max(cnt, 1), dtype=np.int32)
+    cnt = lib.gbr_plan(n, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), sel.ctypes.data_as(_ip),
+                       window, chain, 1 if with_q else 0, out.ctypes.data_as(_ip), cnt,
+                       ctypes.byref(ch), ctypes.byref(fl))
+    return out[:2 * cnt].reshape(cnt, 2), ch.value, fl.value

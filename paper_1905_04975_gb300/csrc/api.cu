@@ -1,0 +1,485 @@
+// C-ABI entry points, the window planner and the device scratch pool.
+//
+// Planner (Section 3.2: windows, chains, Fig. 2): selected blocks are
+// grouped top to bottom into chains of at most m eigenvalues.  A chain is
+// moved up by a sequence of diagonal windows of at most w rows: the first
+// window ends at the chain's last block; each window brings the chain's
+// blocks to its top; the next window ends where those blocks now end, until
+// a window starts at the chain's target position.  Window edges never cut a
+// 2x2 block.  The planner simulates every window as the stable partition the
+// window kernel produces (selected blocks first, stuck blocks as barriers),
+// so the whole window list is known before the first launch.  If the device
+// reports rejected swaps, the planner re-runs on the state read back from the
+// device (stuck blocks then act as barriers) until nothing can move.
+#include "../../include/gbreorder.h"
+#include "common.cuh"
+
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace gbr {
+
+static thread_local std::string g_last_error;
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    g_last_error = buf;
+    return e == cudaErrorMemoryAllocation ? GBR_ERR_NOMEM : GBR_ERR_CUDA;
+}
+
+#define GBR_CK(call, what)                              \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device scratch pool: one grow-only allocation per device and purpose.
+// ---------------------------------------------------------------------------
+enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_NSLOTS = 3 };
+struct DevPool {
+    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr};
+    size_t bytes[POOL_NSLOTS] = {0, 0, 0};
+};
+static std::mutex g_mu;  // serializes calls: the pool is shared per device
+static DevPool g_pool[64];
+
+static int pool_get(int slot, size_t bytes, void** out) {
+    int dev = 0;
+    GBR_CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return GBR_ERR_CUDA;
+    DevPool& p = g_pool[dev];
+    if (p.bytes[slot] < bytes) {
+        if (p.ptr[slot]) {
+            GBR_CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+            cudaFree(p.ptr[slot]);
+            p.ptr[slot] = nullptr;
+            p.bytes[slot] = 0;
+        }
+        size_t grow = bytes + bytes / 4;
+        GBR_CK(cudaMalloc(&p.ptr[slot], grow), "cudaMalloc(pool)");
+        p.bytes[slot] = grow;
+    }
+    *out = p.ptr[slot];
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Planner
+// ---------------------------------------------------------------------------
+struct PlanState {
+    int n = 0;
+    std::vector<uint8_t> bsz;  // size of the block starting at a position, else 0
+    std::vector<uint8_t> sel;  // SEL_* per position (uniform inside a block)
+};
+
+static void init_state(PlanState& st, int n, const uint8_t* sub, const uint8_t* sel) {
+    st.n = n;
+    st.bsz.assign(n, 0);
+    st.sel.assign(sel, sel + n);
+    for (int p = 0; p < n;) {
+        int sz = (p + 1 < n && sub[p]) ? 2 : 1;
+        st.bsz[p] = (uint8_t)sz;
+        p += sz;
+    }
+}
+
+// The window kernel's effect on the block order of [s, e): every selected
+// block moves up past the unselected blocks above it, up to the window top or
+// the nearest selected or stuck block; stuck blocks do not move.
+static void sim_window(PlanState& st, int s, int e) {
+    struct B { uint8_t sz, sel; };
+    B out[WMAX], pend[WMAX];
+    int no = 0, np = 0;
+    for (int p = s; p < e;) {
+        B b{st.bsz[p], st.sel[p]};
+        if (b.sel == SEL_YES) {
+            out[no++] = b;
+        } else if (b.sel == SEL_STUCK) {
+            for (int i = 0; i < np; ++i) out[no++] = pend[i];
+            np = 0;
+            out[no++] = b;
+        } else {
+            pend[np++] = b;
+        }
+        p += b.sz;
+    }
+    for (int i = 0; i < np; ++i) out[no++] = pend[i];
+    int p = s;
+    for (int i = 0; i < no; ++i) {
+        for (int t = 0; t < out[i].sz; ++t) {
+            st.bsz[p + t] = t == 0 ? out[i].sz : 0;
+            st.sel[p + t] = out[i].sel;
+        }
+        p += out[i].sz;
+    }
+}
+
+static void plan_pass(PlanState& st, int w, int m, std::vector<Window>& win, int& nchains) {
+    const int n = st.n;
+    int ks = 0;
+    for (;;) {
+        int pos = ks, first = -1;
+        while (pos < n) {
+            int sz = st.bsz[pos];
+            if (st.sel[pos] == SEL_STUCK) {
+                ks = pos + sz;
+            } else if (st.sel[pos] == SEL_YES) {
+                if (pos == ks) {
+                    ks += sz;
+                } else {
+                    first = pos;
+                    break;
+                }
+            }
+            pos += sz;
+        }
+        if (first < 0) break;
+        int cnt = 0, last_end = first;
+        for (int p = first; p < n;) {
+            int sz = st.bsz[p];
+            if (st.sel[p] == SEL_STUCK) break;
+            if (st.sel[p] == SEL_YES) {
+                if (cnt > 0 && cnt + sz > m) break;
+                cnt += sz;
+                last_end = p + sz;
+            }
+            p += sz;
+        }
+        const int top = ks;
+        int e_cur = last_end;
+        for (;;) {
+            int s_cur = e_cur - w > top ? e_cur - w : top;
+            if (s_cur > top && st.bsz[s_cur] == 0) s_cur += 1;
+            int c_in = 0;
+            for (int p = s_cur; p < e_cur; p += st.bsz[p])
+                if (st.sel[p] == SEL_YES) c_in += st.bsz[p];
+            win.push_back(Window{s_cur, e_cur, nchains, 0});
+            sim_window(st, s_cur, e_cur);
+            if (s_cur == top) break;
+            e_cur = s_cur + c_in;
+        }
+        ks = top + cnt;
+        ++nchains;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reorder on device-resident S, Q.
+// ---------------------------------------------------------------------------
+static int check_opts(const gbr_opts* o) {
+    if (o->window < 4 || o->window > WMAX) return -10;
+    if (o->chain < 1 || o->chain > o->window - 2) return -10;
+    if (o->precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
+    if (o->on_reject != GBR_ON_REJECT_CONTINUE) return GBR_ERR_UNSUPPORTED;
+    return 0;
+}
+
+static int reorder_device(int n, double* S, int ldS, double* Q, int ldQ, const int* select,
+                          double* eig_re, double* eig_im, int* m_out, const gbr_opts& o,
+                          gbr_stats* stats, cudaStream_t st) {
+    // scratch layout
+    const int nslots = 1;
+    size_t off_ctr = 0;
+    size_t off_sub = 256;
+    size_t off_sel = off_sub + (((size_t)n + 255) & ~(size_t)255);
+    size_t off_eig = off_sel + (((size_t)n + 255) & ~(size_t)255);
+    size_t off_u = off_eig + (((size_t)2 * n * sizeof(double) + 255) & ~(size_t)255);
+    size_t total = off_u + (size_t)nslots * WMAX * WMAX * sizeof(double);
+    void* base = nullptr;
+    int rc = pool_get(POOL_SCRATCH, total, &base);
+    if (rc) return rc;
+    char* b = (char*)base;
+    DevCounters* d_ctr = (DevCounters*)(b + off_ctr);
+    uint8_t* d_sub = (uint8_t*)(b + off_sub);
+    uint8_t* d_sel = (uint8_t*)(b + off_sel);
+    double* d_eig = (double*)(b + off_eig);
+    double* d_u = (double*)(b + off_u);
+
+    DevCounters h_ctr{0, 0, INT_MAX, 0};
+    GBR_CK(cudaMemcpyAsync(d_ctr, &h_ctr, sizeof h_ctr, cudaMemcpyHostToDevice, st), "H2D counters");
+    if (o.validate) GBR_CK(launch_validate(n, S, ldS, d_ctr, st), "validate kernel");
+    GBR_CK(launch_subdiag(n, S, ldS, d_sub, st), "subdiag kernel");
+    std::vector<uint8_t> sub(n), sel(n);
+    GBR_CK(cudaMemcpyAsync(sub.data(), d_sub, n, cudaMemcpyDeviceToHost, st), "D2H subdiag");
+    GBR_CK(cudaMemcpyAsync(&h_ctr, d_ctr, sizeof h_ctr, cudaMemcpyDeviceToHost, st), "D2H counters");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (h_ctr.bad_column != INT_MAX) return -2;
+
+    // selection per position; a 2x2 block is selected if either row is
+    int msel = 0;
+    for (int p = 0; p < n;) {
+        int sz = (p + 1 < n && sub[p]) ? 2 : 1;
+        uint8_t v = select[p] != 0;
+        if (sz == 2) v |= select[p + 1] != 0;
+        for (int t = 0; t < sz; ++t) sel[p + t] = v;
+        msel += v * sz;
+        p += sz;
+    }
+    GBR_CK(cudaMemcpyAsync(d_sel, sel.data(), n, cudaMemcpyHostToDevice, st), "H2D selection");
+
+    // optional per-kernel event timing: one event pair per launch, read at the end
+    struct Events {
+        std::vector<cudaEvent_t> w, u;
+        ~Events() {
+            for (cudaEvent_t e : w) cudaEventDestroy(e);
+            for (cudaEvent_t e : u) cudaEventDestroy(e);
+        }
+    } evs;
+    std::vector<cudaEvent_t>& evw = evs.w;
+    std::vector<cudaEvent_t>& evu = evs.u;
+    auto mark = [&](std::vector<cudaEvent_t>& v) -> cudaError_t {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        v.push_back(ev);
+        return cudaEventRecord(ev, st);
+    };
+    long long launches = o.validate ? 2 : 1;
+
+    PlanState ps;
+    init_state(ps, n, sub.data(), sel.data());
+    long long nwin = 0;
+    int nchains = 0;
+    double flops = 0.0;
+    unsigned long long seen_rej = 0;
+    for (int pass = 0; pass < 1 + 2 * n; ++pass) {
+        std::vector<Window> win;
+        plan_pass(ps, o.window, o.chain, win, nchains);
+        if (win.empty()) break;
+        for (const Window& wdw : win) {
+            if (o.timing) GBR_CK(mark(evw), "event");
+            GBR_CK(launch_window(n, wdw, S, ldS, d_sel, d_u, o.strong_test, d_ctr, st), "window kernel");
+            if (o.timing) { GBR_CK(mark(evw), "event"); GBR_CK(mark(evu), "event"); }
+            GBR_CK(launch_update(n, wdw, S, ldS, Q, ldQ, d_u, st), "update kernel");
+            if (o.timing) GBR_CK(mark(evu), "event");
+            double ww = (double)(wdw.e - wdw.s);
+            flops += 2.0 * ww * ww * ((double)(n - wdw.e) + wdw.s + (Q ? n : 0));
+            launches += 2;
+        }
+        nwin += (long long)win.size();
+        GBR_CK(cudaMemcpyAsync(&h_ctr, d_ctr, sizeof h_ctr, cudaMemcpyDeviceToHost, st), "D2H counters");
+        GBR_CK(cudaStreamSynchronize(st), "sync");
+        if (h_ctr.rejected == seen_rej) break;  // the simulated plan was exact
+        seen_rej = h_ctr.rejected;
+        // re-plan from the device state: stuck blocks are barriers now
+        GBR_CK(launch_subdiag(n, S, ldS, d_sub, st), "subdiag kernel");
+        GBR_CK(cudaMemcpyAsync(sub.data(), d_sub, n, cudaMemcpyDeviceToHost, st), "D2H subdiag");
+        GBR_CK(cudaMemcpyAsync(sel.data(), d_sel, n, cudaMemcpyDeviceToHost, st), "D2H selection");
+        GBR_CK(cudaStreamSynchronize(st), "sync");
+        init_state(ps, n, sub.data(), sel.data());
+        launches += 1;
+    }
+
+    if (eig_re || eig_im) {
+        GBR_CK(launch_eigs(n, S, ldS, d_eig, d_eig + n, st), "eigenvalue kernel");
+        if (eig_re)
+            GBR_CK(cudaMemcpyAsync(eig_re, d_eig, n * sizeof(double), cudaMemcpyDeviceToHost, st),
+                   "D2H eig_re");
+        if (eig_im)
+            GBR_CK(cudaMemcpyAsync(eig_im, d_eig + n, n * sizeof(double), cudaMemcpyDeviceToHost, st),
+                   "D2H eig_im");
+    }
+    if (eig_re || eig_im) launches += 1;
+    GBR_CK(cudaMemcpyAsync(&h_ctr, d_ctr, sizeof h_ctr, cudaMemcpyDeviceToHost, st), "D2H counters");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    double msw = 0.0, msu = 0.0;
+    for (size_t i = 0; i + 1 < evw.size(); i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, evw[i], evw[i + 1]) == cudaSuccess) msw += t;
+    }
+    for (size_t i = 0; i + 1 < evu.size(); i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, evu[i], evu[i + 1]) == cudaSuccess) msu += t;
+    }
+    if (h_ctr.step_overflow) {
+        g_last_error = "window kernel exceeded its step bound";
+        return GBR_ERR_CUDA;
+    }
+    if (m_out) *m_out = msel;
+    if (stats) {
+        stats->swaps = (long long)h_ctr.swaps;
+        stats->rejected = (long long)h_ctr.rejected;
+        stats->windows = nwin;
+        stats->chains = nchains;
+        stats->launches = launches;
+        stats->upd_flops = flops;
+        stats->ms_window = msw;
+        stats->ms_update = msu;
+    }
+    long long rej = (long long)h_ctr.rejected;
+    return rej > INT_MAX ? INT_MAX : (int)rej;
+}
+
+}  // namespace gbr
+
+using namespace gbr;
+
+extern "C" {
+
+void gbr_default_opts(gbr_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->window = 128;
+    o->chain = 64;
+    o->precision = GBR_PREC_DMMA;
+    o->slices = 0;
+    o->strong_test = 1;
+    o->on_reject = GBR_ON_REJECT_CONTINUE;
+    o->validate = 1;
+    o->timing = 0;
+}
+
+static int common_args(int n, const void* S, int ldS, const void* Q, int ldQ, const int* select) {
+    if (n < 0) return -1;
+    if (n > 0 && !S) return -2;
+    if (ldS < (n > 1 ? n : 1)) return -3;
+    if (Q && ldQ < (n > 1 ? n : 1)) return -5;
+    if (n > 0 && !select) return -6;
+    return 0;
+}
+
+int gbr_reorder(int n, double* S, int ldS, double* Q, int ldQ, const int* select, double* eig_re,
+                double* eig_im, int* m_out, const gbr_opts* opts, gbr_stats* stats,
+                void* cuda_stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = common_args(n, S, ldS, Q, ldQ, select);
+    if (rc) return rc;
+    gbr_opts o;
+    if (opts) o = *opts; else gbr_default_opts(&o);
+    rc = check_opts(&o);
+    if (rc) return rc;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (n == 0) {
+        if (m_out) *m_out = 0;
+        return 0;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    rc = reorder_device(n, S, ldS, Q, ldQ, select, eig_re, eig_im, m_out, o, stats,
+                        (cudaStream_t)cuda_stream);
+    if (stats)
+        stats->ms_total =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int gbr_reorder_host(int n, double* S, int ldS, double* Q, int ldQ, const int* select,
+                     double* eig_re, double* eig_im, int* m_out, const gbr_opts* opts,
+                     gbr_stats* stats, void* cuda_stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = common_args(n, S, ldS, Q, ldQ, select);
+    if (rc) return rc;
+    gbr_opts o;
+    if (opts) o = *opts; else gbr_default_opts(&o);
+    rc = check_opts(&o);
+    if (rc) return rc;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (n == 0) {
+        if (m_out) *m_out = 0;
+        return 0;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(g_mu);
+    size_t mat = (size_t)n * n * sizeof(double);
+    void *dS = nullptr, *dQ = nullptr;
+    rc = pool_get(POOL_HOST_S, mat, &dS);
+    if (rc) return rc;
+    if (Q) {
+        rc = pool_get(POOL_HOST_Q, mat, &dQ);
+        if (rc) return rc;
+    }
+    GBR_CK(cudaMemcpy2DAsync(dS, n * sizeof(double), S, (size_t)ldS * sizeof(double),
+                             n * sizeof(double), n, cudaMemcpyHostToDevice, st), "H2D S");
+    if (Q)
+        GBR_CK(cudaMemcpy2DAsync(dQ, n * sizeof(double), Q, (size_t)ldQ * sizeof(double),
+                                 n * sizeof(double), n, cudaMemcpyHostToDevice, st), "H2D Q");
+    rc = reorder_device(n, (double*)dS, n, (double*)dQ, n, select, eig_re, eig_im, m_out, o, stats, st);
+    if (rc < 0) return rc;
+    GBR_CK(cudaMemcpy2DAsync(S, (size_t)ldS * sizeof(double), dS, n * sizeof(double),
+                             n * sizeof(double), n, cudaMemcpyDeviceToHost, st), "D2H S");
+    if (Q)
+        GBR_CK(cudaMemcpy2DAsync(Q, (size_t)ldQ * sizeof(double), dQ, n * sizeof(double),
+                                 n * sizeof(double), n, cudaMemcpyDeviceToHost, st), "D2H Q");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (stats)
+        stats->ms_total =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int gbr_plan(int n, const unsigned char* sub, const int* select, int window, int chain,
+             int with_q, int* windows, int max_windows, int* chains, double* upd_flops) {
+    if (n < 0) return -1;
+    if (n > 0 && (!sub || !select)) return -2;
+    if (window < 4 || window > WMAX) return -4;
+    if (chain < 1 || chain > window - 2) return -5;
+    std::vector<uint8_t> sb(n), sl(n);
+    for (int p = 0; p < n;) {
+        int sz = (p + 1 < n && sub[p]) ? 2 : 1;
+        uint8_t v = select[p] != 0;
+        if (sz == 2) v |= select[p + 1] != 0;
+        for (int t = 0; t < sz; ++t) {
+            sl[p + t] = v;
+            sb[p + t] = (t == 0 && sz == 2) ? 1 : 0;
+        }
+        p += sz;
+    }
+    PlanState ps;
+    init_state(ps, n, sb.data(), sl.data());
+    std::vector<Window> win;
+    int nch = 0;
+    plan_pass(ps, window, chain, win, nch);
+    double fl = 0.0;
+    for (size_t i = 0; i < win.size(); ++i) {
+        double ww = (double)(win[i].e - win[i].s);
+        fl += 2.0 * ww * ww * ((double)(n - win[i].e) + win[i].s + (with_q ? n : 0));
+        if (windows && (int)i < max_windows) {
+            windows[2 * i] = win[i].s;
+            windows[2 * i + 1] = win[i].e;
+        }
+    }
+    if (chains) *chains = nch;
+    if (upd_flops) *upd_flops = fl;
+    return (int)win.size();
+}
+
+const char* gbr_status_string(int s) {
+    if (s == 0) return "success";
+    if (s > 0) return "partial reorder: some block swaps were rejected by the stability test";
+    switch (s) {
+        case -1: return "invalid argument 1: n < 0";
+        case -2: return "invalid argument 2: S is NULL or not in standard real Schur form";
+        case -3: return "invalid argument 3: ldS < max(1, n)";
+        case -5: return "invalid argument 5: ldQ < max(1, n)";
+        case -6: return "invalid argument 6: select is NULL";
+        case -10: return "invalid argument 10: window must be 4..128 and chain 1..window-2";
+        case GBR_ERR_CUDA: return "CUDA error (see gbr_last_error)";
+        case GBR_ERR_NOMEM: return "out of device memory";
+        case GBR_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case GBR_ERR_UNSUPPORTED: return "unsupported option value";
+        default: return "invalid argument";
+    }
+}
+
+const char* gbr_last_error(void) { return g_last_error.c_str(); }
+
+void gbr_release(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    for (int s = 0; s < POOL_NSLOTS; ++s) {
+        if (g_pool[dev].ptr[s]) cudaFree(g_pool[dev].ptr[s]);
+        g_pool[dev].ptr[s] = nullptr;
+        g_pool[dev].bytes[s] = 0;
+    }
+}
+
+int gbr_version(void) { return 100; }
+
+}  // extern "C"

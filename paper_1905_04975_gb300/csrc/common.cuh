@@ -1,0 +1,48 @@
+// Internal definitions shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace gbr {
+
+// Largest diagonal window handled by the window kernel (shared-memory bound:
+// packed upper-Hessenberg S window + dense accumulator U).
+constexpr int WMAX = 128;
+
+// Column-major element access.
+__host__ __device__ inline size_t cm(int i, int j, int ld) {
+    return (size_t)j * (size_t)ld + (size_t)i;
+}
+
+// Per-position selection state kept on the device during a reorder.
+enum : uint8_t { SEL_NO = 0, SEL_YES = 1, SEL_STUCK = 2 };
+
+// Device-side counters, one set per call.
+struct DevCounters {
+    unsigned long long swaps;
+    unsigned long long rejected;
+    int bad_column;      // validation: first column violating the standard form, or INT_MAX
+    int step_overflow;   // windows that hit the step cap (a logic error if nonzero)
+};
+
+// One diagonal window in program order.
+struct Window {
+    int s, e;            // rows/cols [s, e) of S
+    int chain;           // chain index
+    int u_off;           // offset (in doubles) of this window's U in the U pool
+};
+
+// Launchers (each .cu file owns its kernels).
+cudaError_t launch_validate(int n, const double* S, int ldS, DevCounters* ctr, cudaStream_t st);
+cudaError_t launch_subdiag(int n, const double* S, int ldS, uint8_t* sub, cudaStream_t st);
+cudaError_t launch_eigs(int n, const double* S, int ldS, double* wr, double* wi, cudaStream_t st);
+cudaError_t launch_window(int n, const Window& w, double* S, int ldS, uint8_t* sel, double* U,
+                          int strong, DevCounters* ctr, cudaStream_t st);
+cudaError_t launch_update(int n, const Window& w, double* S, int ldS, double* Q, int ldQ,
+                          const double* U, cudaStream_t st);
+size_t window_smem_bytes(int w);
+size_t update_smem_bytes(int w);
+
+}  // namespace gbr

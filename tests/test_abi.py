@@ -1,0 +1,80 @@
+"""The C-ABI library: builds for sm_103a, exports every symbol the header
+declares, and checks its arguments before touching the GPU (these calls run
+without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1905_04975_gb300 as g
+from paper_1905_04975_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return g.load()
+
+
+def header_functions():
+    with open(os.path.join(ROOT, "include", "gbreorder.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbr_\w+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lib):
+    names = header_functions()
+    assert "gbr_reorder" in names and "gbr_reorder_host" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in the header but not exported"
+        assert name in g.SYMBOLS, f"{name} not bound in the Python layer"
+
+
+def test_defaults_and_strings(lib):
+    o = g.default_opts()
+    assert (o.window, o.chain, o.precision, o.strong_test, o.validate, o.timing) == (128, 64, 0, 1, 1, 0)
+    assert lib.gbr_version() >= 100
+    for code in (0, 3, -1, -2, -3, -5, -6, -10, g.ERR_CUDA, g.ERR_NOMEM, g.ERR_TIMEOUT,
+                 g.ERR_UNSUPPORTED):
+        assert lib.gbr_status_string(code)
+
+
+def call(lib, n, S, ldS, Q, ldQ, sel, opts=None):
+    wr = np.zeros(max(n, 1))
+    wi = np.zeros(max(n, 1))
+    m = ctypes.c_int(-7)
+    st = g.GbrStats()
+    o = opts or g.default_opts()
+    rc = lib.gbr_reorder(n, S, ldS, Q, ldQ,
+                         sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if sel is not None else None,
+                         wr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         wi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(m),
+                         ctypes.byref(o), ctypes.byref(st), None)
+    return rc, m.value
+
+
+def test_argument_errors_before_gpu(lib):
+    dummy = ctypes.c_void_p(0x1000)  # never dereferenced: argument checks come first
+    sel = np.zeros(8, np.int32)
+    assert call(lib, -1, dummy, 8, None, 8, sel)[0] == -1
+    assert call(lib, 8, None, 8, None, 8, sel)[0] == -2
+    assert call(lib, 8, dummy, 7, None, 8, sel)[0] == -3
+    assert call(lib, 8, dummy, 8, dummy, 4, sel)[0] == -5
+    assert call(lib, 8, dummy, 8, None, 8, None)[0] == -6
+    bad = g.default_opts()
+    bad.window = 200
+    assert call(lib, 0, None, 1, None, 1, sel, bad)[0] == -10
+    bad = g.default_opts()
+    bad.chain = 127
+    assert call(lib, 0, None, 1, None, 1, sel, bad)[0] == -10
+    ozk = g.default_opts()
+    ozk.precision = 7
+    assert call(lib, 0, None, 1, None, 1, sel, ozk)[0] == g.ERR_UNSUPPORTED
+    # n = 0 is a no-op that succeeds without a GPU
+    rc, m = call(lib, 0, None, 1, None, 1, sel)
+    assert rc == 0 and m == 0

@@ -1,0 +1,225 @@
+"""GPU reordering vs the CPU oracle (through the C ABI).
+
+Reordered Schur forms are unique only up to the signs of Schur vectors and
+the basis inside each 2x2 block, so parity compares what is unique:
+  * the eigenvalue order on the diagonal (1e-10 relative),
+  * the leading invariant subspace (sine of the largest principal angle
+    <= 1e-10 cond, cond = ||S||_F / sep),
+and checks that the rest is valid: standard form with exact zeros,
+||Q^T Q - I||_F and ||A - Q S Q^T||_F / ||A||_F <= 50 n eps.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import lapack
+from scipy.optimize import linear_sum_assignment
+
+import oracle
+import schur_inputs as si
+from tests.helpers import (EPS, block_eigs, expected_order, is_standard, match_eigs, orth_err,
+                           residual, sin_angle)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gbr():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1905_04975_gb300 as g
+    g.load()  # raises if the library was not built
+    return g
+
+
+def run_gpu(g, S, Q, sel, **kw):
+    Sd = g.to_device(S)
+    Qd = g.to_device(Q) if Q is not None else None
+    r = g.reorder(Sd, Qd, sel, **kw)
+    torch.cuda.synchronize()
+    return r, g.to_host(Sd), (g.to_host(Qd) if Qd is not None else None)
+
+
+def cond_of(S, sel, sel_eigs, unsel_eigs):
+    n = S.shape[0]
+    m = int(np.sum(sel))
+    if 0 < m < n and n <= 600:
+        lw = max(1, 2 * m * (n - m))
+        sep = lapack.dtrsen(np.asarray(sel, np.int32), S, np.eye(n), job="V", lwork=lw,
+                            liwork=max(1, m * (n - m)))[6]
+        if sep > 0:
+            return np.linalg.norm(S) / sep
+    if len(sel_eigs) and len(unsel_eigs):
+        gap = np.min(np.abs(sel_eigs[:, None] - unsel_eigs[None, :]))
+        return np.linalg.norm(S) / max(gap, 1e-300)
+    return 1.0
+
+
+def check(S, Q, sel, r, Sg, Qg, ref=None, order_tol=1e-10):
+    n = S.shape[0]
+    Qin = Q if Q is not None else np.eye(n)
+    A = Qin @ S @ Qin.T
+    want, m = expected_order(S, sel)
+    assert r.m == m
+    got = block_eigs(Sg)
+    assert is_standard(Sg)
+    # eigenvalues returned by the kernel are those of the diagonal blocks
+    assert np.allclose(r.eigs, got, rtol=1e-15, atol=0)
+    if r.status == 0:
+        assert match_eigs(got, want, 0) <= order_tol
+    if Qg is not None:
+        assert orth_err(Qg) <= 50 * n * EPS
+        assert residual(A, Sg, Qg) <= 50 * n * EPS
+    if ref is not None and r.status == 0 and ref["status"] == 0:
+        oe = ref["wr"] + 1j * ref["wi"]
+        assert match_eigs(got, oe, 0) <= order_tol
+        if Qg is not None and 0 < m < n:
+            cond = cond_of(S, sel, want[:m], want[m:])
+            ang = sin_angle(Qg[:, :m], ref["Q"][:, :m])
+            assert ang <= max(1e-10 * cond, 1e-12), (ang, cond)
+    return got
+
+
+def random_small(n, seed, frac):
+    S, Q, sel = si.reorder_problem(n, seed, select_frac=frac, q="householder", reflectors=8)
+    return S, Q, sel
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 11, 12])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_all_windows(gbr, n, seed):
+    S, Q, sel = random_small(n, 10 * n + seed, 0.5)
+    ref = oracle.reorder(S, Q, sel)
+    for w, m in [(4, 2), (8, 3), (128, 64)]:
+        r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=w, chain=m)
+        assert r.status == 0
+        check(S, Q, sel, r, Sg, Qg, ref)
+
+
+@pytest.mark.parametrize("w,m", [(128, 64), (64, 30), (32, 16), (16, 4)])
+def test_n400_workload(gbr, w, m):
+    S, Q, sel = si.config("n400")
+    ref = oracle.reorder(S, Q, sel)
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=w, chain=m)
+    assert r.status == 0 and ref["status"] == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
+    assert r.stats.windows > 0 and r.stats.swaps > 0
+
+
+@pytest.mark.parametrize("n,frac,w,m", [(129, 0.4, 64, 30), (257, 0.3, 128, 64),
+                                        (515, 0.6, 64, 62), (700, 0.1, 128, 100)])
+def test_ragged_sizes_householder_q(gbr, n, frac, w, m):
+    S, Q, sel = si.reorder_problem(n, n, select_frac=frac, q="householder")
+    ref = oracle.reorder(S, Q, sel)
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=w, chain=m)
+    assert r.status == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
+
+
+def test_selection_edge_cases(gbr):
+    S, Q, sel = si.reorder_problem(300, 5, select_frac=0.3, q="householder")
+    n = 300
+    cases = [np.zeros(n, np.int32), np.ones(n, np.int32)]
+    last = np.zeros(n, np.int32)
+    last[-1] = 1
+    first = np.zeros(n, np.int32)
+    first[0] = 1
+    cases += [last, first]
+    for s in cases:
+        ref = oracle.reorder(S, Q, s)
+        r, Sg, Qg = run_gpu(gbr, S, Q, s)
+        assert r.status == 0
+        check(S, Q, s, r, Sg, Qg, ref)
+    for s in cases[:2]:
+        r, Sg, Qg = run_gpu(gbr, S, Q, s)
+        assert np.array_equal(Sg, S) and np.array_equal(Qg, Q)
+
+
+def test_without_q(gbr):
+    S, Q, sel = si.config("n400")
+    r, Sg, _ = run_gpu(gbr, S, None, sel)
+    ref = oracle.reorder(S, None, sel)
+    assert r.status == 0
+    check(S, None, sel, r, Sg, None, ref)
+    # same S as with Q (the Q update does not feed back into S)
+    r2, Sg2, _ = run_gpu(gbr, S, Q, sel)
+    assert np.array_equal(Sg, Sg2)
+
+
+def test_deterministic_and_host_entry(gbr):
+    S, Q, sel = si.reorder_problem(600, 9, select_frac=0.35, q="householder")
+    r1, S1, Q1 = run_gpu(gbr, S, Q, sel)
+    r2, S2, Q2 = run_gpu(gbr, S, Q, sel)
+    assert np.array_equal(S1, S2) and np.array_equal(Q1, Q2)
+    Sh, Qh = np.asfortranarray(S.copy()), np.asfortranarray(Q.copy())
+    r3 = gbr.reorder_host(Sh, Qh, sel)
+    assert r3.status == 0
+    assert np.array_equal(Sh, S1) and np.array_equal(Qh, Q1)
+
+
+def test_rejections_clustered_nonnormal(gbr):
+    """kappa = 1e6 2x2 blocks in tight clusters: some swaps are rejected.
+    Acceptance near the threshold depends on rounding, so the oracle and the
+    GPU may reject different swaps; both must return valid similarities, the
+    eigenvalue order must agree before the first rejection in either, and
+    the counts are reported side by side."""
+    n = 300
+    S, Q, sel = si.reorder_problem(n, 3, select_frac=0.5, clusters=True, spread=1e-6, kappa=1e6)
+    ref = oracle.reorder(S, Q, sel)
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel)
+    print(f"rejections: oracle {ref['nrej']}, gpu {r.status}")
+    assert ref["status"] > 0
+    assert r.status > 0
+    assert is_standard(Sg)
+    A = Q @ S @ Q.T
+    assert residual(A, Sg, Qg) <= 50 * n * EPS
+    assert orth_err(Qg) <= 50 * n * EPS
+    a, b = block_eigs(S), block_eigs(Sg)
+    cost = np.abs(a[:, None] - b[None, :])
+    i, j = linear_sum_assignment(cost)
+    assert cost[i, j].max() <= 1e-3   # attainable accuracy of these eigenvalues
+    # common prefix: positions before the first stuck selected block in either
+    want, m = expected_order(S, sel)
+    got_o = ref["wr"] + 1j * ref["wi"]
+    got_g = block_eigs(Sg)
+    k = 0
+    while k < m and abs(got_o[k] - want[k]) <= 1e-6 * max(1, abs(want[k])) and \
+            abs(got_g[k] - want[k]) <= 1e-6 * max(1, abs(want[k])):
+        k += 1
+    assert k > 0
+    assert match_eigs(got_g[:k], got_o[:k], 0) <= 1e-6
+
+
+def test_invalid_input_rejected(gbr):
+    S, Q, sel = si.config("n400")
+    bad = S.copy(order="F")
+    bad[10, 3] = 1e-3   # below the subdiagonal
+    with pytest.raises(gbr.GbrError) as ei:
+        run_gpu(gbr, bad, Q, sel)
+    assert ei.value.status == -2
+    bad = S.copy(order="F")
+    j = next(i for i in range(399) if S[i + 1, i] != 0)
+    bad[j, j] += 0.5    # 2x2 block not standardized
+    with pytest.raises(gbr.GbrError) as ei:
+        run_gpu(gbr, bad, Q, sel)
+    assert ei.value.status == -2
+
+
+_n4000 = {}
+
+
+def n4000_oracle():
+    if not _n4000:
+        S, Q, sel = si.config("n4000")
+        _n4000["inp"] = (S, Q, sel)
+        _n4000["ref"] = oracle.reorder(S, Q, sel)
+    return _n4000["inp"], _n4000["ref"]
+
+
+def test_n4000_workload_full_parity(gbr):
+    """The benchmark workload (n = 4000, p = 0.35, 64-reflector Q, window
+    128, chain 64, DMMA updates) in the benchmark's launch configuration,
+    against the full oracle run."""
+    (S, Q, sel), ref = n4000_oracle()
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=128, chain=64)
+    assert r.status == 0 and ref["status"] == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
