@@ -1,0 +1,359 @@
+// FP64 math of one adjacent block swap (Section 3.2: Givens rotations and
+// Householder reflectors), shared by the window kernels.  Host-callable too,
+// so the same code can be exercised on the CPU.
+#pragma once
+
+#include <float.h>
+#include <math.h>
+
+#ifdef __CUDACC__
+#define GBR_HD __host__ __device__ __forceinline__
+#else
+#define GBR_HD inline
+#endif
+
+namespace gbr {
+
+// ---------------------------------------------------------------------------
+// Small dense helpers on k x k column-major matrices with leading dim 4.
+// ---------------------------------------------------------------------------
+GBR_HD void mm4(int k, const double* A, bool tA, const double* B, bool tB,
+                                    double* C) {
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < k; ++l) {
+                double a = tA ? A[i * 4 + l] : A[l * 4 + i];
+                double b = tB ? B[l * 4 + j] : B[j * 4 + l];
+                acc = fma(a, b, acc);
+            }
+            C[j * 4 + i] = acc;
+        }
+}
+
+// Rotation (cs, sn) that brings the 2x2 block M = [[a, b], [c, d]] to
+// standard form: equal diagonal with bc < 0 (complex pair, *cplx = true), or
+// upper triangular (real pair, *cplx = false).
+GBR_HD void std_rotation(double a, double b, double c, double d, double* cs, double* sn,
+                             bool* cplx) {
+    *cs = 1.0;
+    *sn = 0.0;
+    *cplx = false;
+    if (c == 0.0) return;
+    double p = 0.5 * (a - d);
+    double disc = fma(p, p, b * c);
+    if (disc >= 0.0) {
+        // Schur vector of the eigenvalue (a + d)/2 + sign(p) sqrt(disc)
+        double x = (p >= 0.0) ? p + sqrt(disc) : p - sqrt(disc);
+        double h = hypot(x, c);
+        *cs = x / h;
+        *sn = c / h;
+        return;
+    }
+    *cplx = true;
+    double sig = b + c;
+    double r = hypot(2.0 * p, sig);
+    if (r == 0.0) return;
+    double sg = (sig >= 0.0) ? 1.0 : -1.0;
+    double c2 = sg * sig / r;          // cos 2t >= 0
+    double s2 = -sg * 2.0 * p / r;     // sin 2t
+    double cc = sqrt(0.5 * (1.0 + c2));
+    *cs = cc;
+    *sn = s2 / (2.0 * cc);
+}
+
+// Applies the rotation to the 2x2 block in place and fixes its structure.
+// Returns the rotation actually used (a second one is composed in when
+// rounding turned a complex pair real).
+GBR_HD void standardize2(double* m /* 2x2, ld 4 */, double* cs, double* sn) {
+    bool cplx;
+    std_rotation(m[0], m[4], m[1], m[5], cs, sn, &cplx);
+    double c = *cs, s = *sn;
+    // N = R^T M R, R = [[c, -s], [s, c]]
+    double a11 = fma(c, m[0], s * m[1]), a12 = fma(c, m[4], s * m[5]);
+    double a21 = fma(c, m[1], -s * m[0]), a22 = fma(c, m[5], -s * m[4]);
+    double n11 = fma(a11, c, a12 * s), n12 = fma(a12, c, -a11 * s);
+    double n21 = fma(a21, c, a22 * s), n22 = fma(a22, c, -a21 * s);
+    if (!cplx) {
+        n21 = 0.0;
+    } else {
+        double avg = 0.5 * (n11 + n22);
+        n11 = n22 = avg;
+        if (!(n12 * n21 < 0.0)) {
+            double c2, s2;
+            bool cx2;
+            std_rotation(n11, n12, n21, n22, &c2, &s2, &cx2);
+            double b11 = fma(c2, n11, s2 * n21), b12 = fma(c2, n12, s2 * n22);
+            double b21 = fma(c2, n21, -s2 * n11), b22 = fma(c2, n22, -s2 * n12);
+            n11 = fma(b11, c2, b12 * s2);
+            n12 = fma(b12, c2, -b11 * s2);
+            n22 = fma(b22, c2, -b21 * s2);
+            n21 = 0.0;
+            double cc = c * c2 - s * s2, ss = s * c2 + c * s2;
+            *cs = cc;
+            *sn = ss;
+        }
+    }
+    m[0] = n11; m[1] = n21; m[4] = n12; m[5] = n22;
+}
+
+// Householder vector for x[0..len): (I - tau v v^T) x = beta e_0, v[0] = 1.
+GBR_HD void house(int len, const double* x, double* v, double* tau) {
+    double alpha = x[0], sig = 0.0;
+    for (int i = 1; i < len; ++i) sig = fma(x[i], x[i], sig);
+    v[0] = 1.0;
+    if (sig == 0.0) {
+        for (int i = 1; i < len; ++i) v[i] = 0.0;
+        *tau = 0.0;
+        return;
+    }
+    double nrm = sqrt(fma(alpha, alpha, sig));
+    double beta = (alpha >= 0.0) ? -nrm : nrm;
+    double inv = 1.0 / (alpha - beta);
+    for (int i = 1; i < len; ++i) v[i] = x[i] * inv;
+    *tau = (beta - alpha) / beta;
+}
+
+// Solves T11 X - X T22 = gamma T12 for the p x q matrix X (Kronecker form,
+// Gaussian elimination with complete pivoting; tiny pivots are raised to
+// eps * max|K|; gamma <= 1 guards against overflow).  D holds the k x k
+// block [[T11, T12], [0, T22]] with leading dimension 4.  X is p x q, ld 2.
+GBR_HD void sylvester(const double* D, int p, int q, double* X, double* gamma) {
+    const int N = p * q;
+    double K[16], b[4];
+    int perm[4];
+    double kmax = 0.0;
+    for (int r = 0; r < N; ++r) {
+        int i = r % p, kk = r / p;
+        b[r] = D[(p + kk) * 4 + i];                 // T12(i, kk)
+        for (int c = 0; c < N; ++c) {
+            int l = c % p, mm = c / p;
+            double v = 0.0;
+            if (kk == mm) v += D[l * 4 + i];        // T11(i, l)
+            if (i == l) v -= D[(p + kk) * 4 + p + mm];  // T22(mm, kk)
+            K[c * 4 + r] = v;
+            kmax = fmax(kmax, fabs(v));
+        }
+    }
+    for (int c = 0; c < 4; ++c) perm[c] = c;
+    double smin = fmax(DBL_EPSILON * kmax, DBL_MIN);
+    for (int st = 0; st < N; ++st) {
+        int pr = st, pc = st;
+        double best = -1.0;
+        for (int c = st; c < N; ++c)
+            for (int r = st; r < N; ++r) {
+                double a = fabs(K[c * 4 + r]);
+                if (a > best) { best = a; pr = r; pc = c; }
+            }
+        if (pr != st) {
+            for (int c = 0; c < N; ++c) {
+                double t = K[c * 4 + st]; K[c * 4 + st] = K[c * 4 + pr]; K[c * 4 + pr] = t;
+            }
+            double t = b[st]; b[st] = b[pr]; b[pr] = t;
+        }
+        if (pc != st) {
+            for (int r = 0; r < N; ++r) {
+                double t = K[st * 4 + r]; K[st * 4 + r] = K[pc * 4 + r]; K[pc * 4 + r] = t;
+            }
+            int t = perm[st]; perm[st] = perm[pc]; perm[pc] = t;
+        }
+        double piv = K[st * 4 + st];
+        if (fabs(piv) < smin) { piv = smin; K[st * 4 + st] = smin; }
+        double ipiv = 1.0 / piv;
+        for (int r = st + 1; r < N; ++r) {
+            double f = K[st * 4 + r] * ipiv;
+            for (int c = st + 1; c < N; ++c) K[c * 4 + r] = fma(-f, K[c * 4 + st], K[c * 4 + r]);
+            b[r] = fma(-f, b[st], b[r]);
+        }
+    }
+    double g = 1.0, y[4];
+    const double big = DBL_MAX / 4.0;
+    for (int st = N - 1; st >= 0; --st) {
+        double acc = b[st];
+        for (int c = st + 1; c < N; ++c) acc = fma(-K[c * 4 + st], y[c], acc);
+        double piv = fabs(K[st * 4 + st]);
+        if (piv < 1.0 && fabs(acc) > big * piv) {
+            double f = big * piv / fabs(acc);
+            for (int c = 0; c < N; ++c) b[c] *= f;
+            for (int c = st + 1; c < N; ++c) y[c] *= f;
+            acc *= f;
+            g *= f;
+        }
+        y[st] = acc / K[st * 4 + st];
+    }
+    for (int c = 0; c < N; ++c) {
+        int u = perm[c];
+        X[(u / p) * 2 + (u % p)] = y[c];
+    }
+    *gamma = g;
+}
+
+// Error-free transformations (Knuth's TwoSum; TwoProduct through fma).
+GBR_HD void two_sum(double a, double b, double* s, double* e) {
+    double x = a + b, bb = x - a;
+    *e = (a - (x - bb)) + (b - bb);
+    *s = x;
+}
+
+// max_ij |(Qs Dt Qs^T - D)_ij| evaluated in compensated arithmetic: each
+// entry is the sum of the k*k triple products Qs_ia Dt_ab Qs_jb and -D_ij,
+// every product split exactly into high and low parts and summed with
+// TwoSum, so the result is accurate to a few units in the last place of the
+// residual itself rather than of the terms.
+GBR_HD double recon_err_compensated(int k, const double* Qs, const double* Dt, const double* D) {
+    double worst = 0.0;
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            double s = -D[j * 4 + i], comp = 0.0;
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b) {
+                    double qa = Qs[a * 4 + i], dab = Dt[b * 4 + a], qb = Qs[b * 4 + j];
+                    double ph = qa * dab, pl = fma(qa, dab, -ph);   // qa dab = ph + pl
+                    double th = ph * qb, tl = fma(ph, qb, -th);     // ph qb = th + tl
+                    double e;
+                    two_sum(s, th, &s, &e);
+                    comp += e + tl + pl * qb;
+                }
+            worst = fmax(worst, fabs(s + comp));
+        }
+    return worst;
+}
+
+// Orthogonal Z (k x k, ld 4) and new block Dn (ld 4) with Z^T D Z = Dn and
+// the blocks exchanged; false if the swap fails the stability test.
+GBR_HD bool swap_transform(const double* D, int p, int q, bool strong, double* Z,
+                               double* Dn) {
+    const int k = p + q;
+    for (int i = 0; i < 16; ++i) { Z[i] = 0.0; Dn[i] = 0.0; }
+    if (k == 2) {
+        double t11 = D[0], t12 = D[4], t22 = D[5];
+        if (t11 == t22) {
+            Z[0] = Z[5] = 1.0;
+            Dn[0] = t11; Dn[4] = t12; Dn[5] = t22;
+            return true;
+        }
+        double d = t22 - t11;
+        double h = hypot(t12, d);
+        double c = t12 / h, s = d / h;
+        Z[0] = c; Z[1] = s; Z[4] = -s; Z[5] = c;
+        // (Z^T D Z)_{12} with row 1 of Z^T D = (c t11, c t12 + s t22)
+        double r12 = fma(c, t12, s * t22);
+        Dn[0] = t22;
+        Dn[4] = fma(r12, c, -(c * t11) * s);
+        Dn[5] = t11;
+        return true;
+    }
+    double dnorm = 0.0;
+    for (int c = 0; c < k; ++c)
+        for (int r = 0; r < k; ++r) dnorm = fmax(dnorm, fabs(D[c * 4 + r]));
+    const double thresh = fmax(10.0 * DBL_EPSILON * dnorm, DBL_MIN);
+
+    double X[4], gamma;
+    sylvester(D, p, q, X, &gamma);
+
+    // Orthogonal Qs whose leading q columns span [-X; gamma I_q].
+    //  p=2, q=1: one 3x3 reflector mapping [-X; gamma] to a multiple of e_1;
+    //  p=1, q=2: one 3x3 reflector mapping u = (gamma, x11, x12), which is
+    //            orthogonal to both columns of [-X; gamma I], to a multiple of
+    //            e_3 (its first two columns then span the subspace);
+    //  p=2, q=2: Householder QR of the 4x2 matrix [-X; gamma I] (two reflectors).
+    double M[8];
+    for (int j = 0; j < q; ++j)
+        for (int i = 0; i < k; ++i)
+            M[j * 4 + i] = (i < p) ? -X[j * 2 + i] : ((i - p == j) ? gamma : 0.0);
+    double v1[4], t1, v2[4] = {0, 0, 0, 0}, t2 = 0.0;
+    if (p == 1 && q == 2) {
+        // reflector for the reversed vector (x12, x11, gamma) -> e_1, then reversed back
+        double ur[3] = {X[2], X[0], gamma}, vr[3];
+        house(3, ur, vr, &t1);
+        v1[0] = vr[2]; v1[1] = vr[1]; v1[2] = vr[0]; v1[3] = 0.0;
+    } else {
+        house(k, &M[0], v1, &t1);
+    }
+    if (p == 2 && q == 2) {
+        // apply H1 to column 2 of M, then reflect its rows 1..k-1
+        double w = 0.0;
+        for (int i = 0; i < k; ++i) w = fma(v1[i], M[4 + i], w);
+        w *= t1;
+        for (int i = 0; i < k; ++i) M[4 + i] = fma(-w, v1[i], M[4 + i]);
+        house(k - 1, &M[5], v2, &t2);
+    }
+    double Qs[16];
+    for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i) Qs[j * 4 + i] = (i == j) ? 1.0 : 0.0;
+    if (p == 2 && q == 2) {  // Qs <- H2 (acting on indices 1..3)
+        for (int j = 1; j < k; ++j) {
+            double w = 0.0;
+            for (int i = 1; i < k; ++i) w = fma(v2[i - 1], Qs[j * 4 + i], w);
+            w *= t2;
+            for (int i = 1; i < k; ++i) Qs[j * 4 + i] = fma(-w, v2[i - 1], Qs[j * 4 + i]);
+        }
+    }
+    for (int j = 0; j < k; ++j) {  // Qs <- H1 Qs
+        double w = 0.0;
+        for (int i = 0; i < k; ++i) w = fma(v1[i], Qs[j * 4 + i], w);
+        w *= t1;
+        for (int i = 0; i < k; ++i) Qs[j * 4 + i] = fma(-w, v1[i], Qs[j * 4 + i]);
+    }
+
+    double T[16], Dt[16];
+    mm4(k, Qs, true, D, false, T);     // Qs^T D
+    mm4(k, T, false, Qs, false, Dt);   // Qs^T D Qs
+
+    double low = 0.0;
+    for (int c = 0; c < q; ++c)
+        for (int r = q; r < k; ++r) low = fmax(low, fabs(Dt[c * 4 + r]));
+    if (!(low <= thresh)) return false;
+    for (int c = 0; c < q; ++c)
+        for (int r = q; r < k; ++r) Dt[c * 4 + r] = 0.0;
+    if (strong) {
+        mm4(k, Qs, false, Dt, false, T);   // Qs Dt0
+        double E[16];
+        mm4(k, T, false, Qs, true, E);     // Qs Dt0 Qs^T
+        double err = 0.0;
+        for (int c = 0; c < k; ++c)
+            for (int r = 0; r < k; ++r) err = fmax(err, fabs(E[c * 4 + r] - D[c * 4 + r]));
+        // Rounding in this check alone can reach the threshold for
+        // well-conditioned swaps; decide on the accurately evaluated residual.
+        if (!(err <= thresh) && !(recon_err_compensated(k, Qs, Dt, D) <= thresh)) return false;
+    }
+
+    // Standardize the new 2x2 blocks: R = diag(R1, R2); Z = Qs R; Dn = R^T Dt0 R.
+    double R[16];
+    for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i) R[j * 4 + i] = (i == j) ? 1.0 : 0.0;
+    double blk1[16], blk2[16];
+    if (q == 2) {
+        blk1[0] = Dt[0]; blk1[1] = Dt[1]; blk1[4] = Dt[4]; blk1[5] = Dt[5];
+        double c, s;
+        standardize2(blk1, &c, &s);
+        R[0] = c; R[1] = s; R[4] = -s; R[5] = c;
+    }
+    if (p == 2) {
+        int o = q;
+        blk2[0] = Dt[o * 4 + o]; blk2[1] = Dt[o * 4 + o + 1];
+        blk2[4] = Dt[(o + 1) * 4 + o]; blk2[5] = Dt[(o + 1) * 4 + o + 1];
+        double c, s;
+        standardize2(blk2, &c, &s);
+        R[o * 4 + o] = c; R[o * 4 + o + 1] = s; R[(o + 1) * 4 + o] = -s; R[(o + 1) * 4 + o + 1] = c;
+    }
+    mm4(k, Qs, false, R, false, Z);
+    mm4(k, R, true, Dt, false, T);
+    mm4(k, T, false, R, false, Dn);
+    // exact structure: zero lower-left block, standardized 2x2 blocks
+    for (int c = 0; c < q; ++c)
+        for (int r = q; r < k; ++r) Dn[c * 4 + r] = 0.0;
+    if (q == 2) { Dn[0] = blk1[0]; Dn[1] = blk1[1]; Dn[4] = blk1[4]; Dn[5] = blk1[5]; }
+    else if (k > 1) { Dn[1] = 0.0; }
+    if (p == 2) {
+        int o = q;
+        Dn[o * 4 + o] = blk2[0]; Dn[o * 4 + o + 1] = blk2[1];
+        Dn[(o + 1) * 4 + o] = blk2[4]; Dn[(o + 1) * 4 + o + 1] = blk2[5];
+    }
+    // entries two or more below the diagonal are structurally zero
+    for (int c = 0; c < k; ++c)
+        for (int r = c + 2; r < k; ++r) Dn[c * 4 + r] = 0.0;
+    return true;
+}
+
+}  // namespace gbr
