@@ -219,10 +219,53 @@ GBR_HD double recon_err_compensated(int k, const double* Qs, const double* Dt, c
     return worst;
 }
 
+// Given the swap's orthogonal Qs and Dt0 = Qs^T D Qs with its lower-left block
+// zeroed: rotations that restore the standard form of the new 2x2 blocks,
+// R = diag(R1, R2), then Z = Qs R and Dn = R^T Dt0 R with exact structure.
+GBR_HD void finish_swap(int p, int q, const double* Qs, const double* Dt, double* Z, double* Dn) {
+    const int k = p + q;
+    double T[16];
+    double R[16];
+    for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i) R[j * 4 + i] = (i == j) ? 1.0 : 0.0;
+    double blk1[16], blk2[16];
+    if (q == 2) {
+        blk1[0] = Dt[0]; blk1[1] = Dt[1]; blk1[4] = Dt[4]; blk1[5] = Dt[5];
+        double c, s;
+        standardize2(blk1, &c, &s);
+        R[0] = c; R[1] = s; R[4] = -s; R[5] = c;
+    }
+    if (p == 2) {
+        int o = q;
+        blk2[0] = Dt[o * 4 + o]; blk2[1] = Dt[o * 4 + o + 1];
+        blk2[4] = Dt[(o + 1) * 4 + o]; blk2[5] = Dt[(o + 1) * 4 + o + 1];
+        double c, s;
+        standardize2(blk2, &c, &s);
+        R[o * 4 + o] = c; R[o * 4 + o + 1] = s; R[(o + 1) * 4 + o] = -s; R[(o + 1) * 4 + o + 1] = c;
+    }
+    mm4(k, Qs, false, R, false, Z);
+    mm4(k, R, true, Dt, false, T);
+    mm4(k, T, false, R, false, Dn);
+    // exact structure: zero lower-left block, standardized 2x2 blocks
+    for (int c = 0; c < q; ++c)
+        for (int r = q; r < k; ++r) Dn[c * 4 + r] = 0.0;
+    if (q == 2) { Dn[0] = blk1[0]; Dn[1] = blk1[1]; Dn[4] = blk1[4]; Dn[5] = blk1[5]; }
+    else if (k > 1) { Dn[1] = 0.0; }
+    if (p == 2) {
+        int o = q;
+        Dn[o * 4 + o] = blk2[0]; Dn[o * 4 + o + 1] = blk2[1];
+        Dn[(o + 1) * 4 + o] = blk2[4]; Dn[(o + 1) * 4 + o + 1] = blk2[5];
+    }
+    // entries two or more below the diagonal are structurally zero
+    for (int c = 0; c < k; ++c)
+        for (int r = c + 2; r < k; ++r) Dn[c * 4 + r] = 0.0;
+}
+
 // Orthogonal Z (k x k, ld 4) and new block Dn (ld 4) with Z^T D Z = Dn and
-// the blocks exchanged; false if the swap fails the stability test.
-GBR_HD bool swap_transform(const double* D, int p, int q, bool strong, double* Z,
-                               double* Dn) {
+// the blocks exchanged, in plain FP64; false if the swap fails the stability
+// test as evaluated here.
+GBR_HD bool swap_transform_fast(const double* D, int p, int q, bool strong, double* Z,
+                                double* Dn) {
     const int k = p + q;
     for (int i = 0; i < 16; ++i) { Z[i] = 0.0; Dn[i] = 0.0; }
     if (k == 2) {
@@ -318,42 +361,184 @@ GBR_HD bool swap_transform(const double* D, int p, int q, bool strong, double* Z
         if (!(err <= thresh) && !(recon_err_compensated(k, Qs, Dt, D) <= thresh)) return false;
     }
 
-    // Standardize the new 2x2 blocks: R = diag(R1, R2); Z = Qs R; Dn = R^T Dt0 R.
-    double R[16];
-    for (int j = 0; j < 4; ++j)
-        for (int i = 0; i < 4; ++i) R[j * 4 + i] = (i == j) ? 1.0 : 0.0;
-    double blk1[16], blk2[16];
-    if (q == 2) {
-        blk1[0] = Dt[0]; blk1[1] = Dt[1]; blk1[4] = Dt[4]; blk1[5] = Dt[5];
-        double c, s;
-        standardize2(blk1, &c, &s);
-        R[0] = c; R[1] = s; R[4] = -s; R[5] = c;
-    }
-    if (p == 2) {
-        int o = q;
-        blk2[0] = Dt[o * 4 + o]; blk2[1] = Dt[o * 4 + o + 1];
-        blk2[4] = Dt[(o + 1) * 4 + o]; blk2[5] = Dt[(o + 1) * 4 + o + 1];
-        double c, s;
-        standardize2(blk2, &c, &s);
-        R[o * 4 + o] = c; R[o * 4 + o + 1] = s; R[(o + 1) * 4 + o] = -s; R[(o + 1) * 4 + o + 1] = c;
-    }
-    mm4(k, Qs, false, R, false, Z);
-    mm4(k, R, true, Dt, false, T);
-    mm4(k, T, false, R, false, Dn);
-    // exact structure: zero lower-left block, standardized 2x2 blocks
-    for (int c = 0; c < q; ++c)
-        for (int r = q; r < k; ++r) Dn[c * 4 + r] = 0.0;
-    if (q == 2) { Dn[0] = blk1[0]; Dn[1] = blk1[1]; Dn[4] = blk1[4]; Dn[5] = blk1[5]; }
-    else if (k > 1) { Dn[1] = 0.0; }
-    if (p == 2) {
-        int o = q;
-        Dn[o * 4 + o] = blk2[0]; Dn[o * 4 + o + 1] = blk2[1];
-        Dn[(o + 1) * 4 + o] = blk2[4]; Dn[(o + 1) * 4 + o + 1] = blk2[5];
-    }
-    // entries two or more below the diagonal are structurally zero
-    for (int c = 0; c < k; ++c)
-        for (int r = c + 2; r < k; ++r) Dn[c * 4 + r] = 0.0;
+    finish_swap(p, q, Qs, Dt, Z, Dn);
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Accurate retry in double-double arithmetic (a value is hi + lo with
+// |lo| <= ulp(hi)/2; Dekker's and Knuth's error-free transformations).
+// For moderately ill-conditioned swaps (||X|| ~ 1e2) the rounding of a
+// plain-FP64 transform alone can reach the 10 eps max|D| threshold; the
+// retry builds the same reflectors and Qs^T D Qs in ~106-bit arithmetic, so
+// that only a genuinely unstable swap (large residual of the Sylvester
+// solution, seen by the weak test) is rejected.
+// ---------------------------------------------------------------------------
+struct dd { double hi, lo; };
+
+GBR_HD dd dd_from(double a) { return dd{a, 0.0}; }
+GBR_HD dd dd_norm(double s, double e) {
+    double h = s + e;
+    return dd{h, e - (h - s)};
+}
+GBR_HD dd dd_add(dd a, dd b) {
+    double s, e;
+    two_sum(a.hi, b.hi, &s, &e);
+    e += a.lo + b.lo;
+    return dd_norm(s, e);
+}
+GBR_HD dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+GBR_HD dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+GBR_HD dd dd_mul(dd a, dd b) {
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);
+    e = fma(a.hi, b.lo, e);
+    e = fma(a.lo, b.hi, e);
+    return dd_norm(p, e);
+}
+GBR_HD dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul(b, dd_from(q1)));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul(b, dd_from(q2)));
+    double q3 = r.hi / b.hi;
+    return dd_add(dd_norm(q1, q2), dd_from(q3));
+}
+GBR_HD dd dd_sqrt(dd a) {
+    if (a.hi <= 0.0) return dd_from(0.0);
+    double x = sqrt(a.hi);
+    dd x2 = dd_mul(dd_from(x), dd_from(x));
+    double corr = (dd_sub(a, x2).hi) / (2.0 * x);
+    return dd_norm(x, corr);
+}
+
+// (I - tau v v^T) x = beta e_0, v[0] = 1, in double-double.
+GBR_HD void house_dd(int len, const dd* x, dd* v, dd* tau) {
+    dd sig = dd_from(0.0);
+    for (int i = 1; i < len; ++i) sig = dd_add(sig, dd_mul(x[i], x[i]));
+    v[0] = dd_from(1.0);
+    if (sig.hi == 0.0) {
+        for (int i = 1; i < len; ++i) v[i] = dd_from(0.0);
+        *tau = dd_from(0.0);
+        return;
+    }
+    dd nrm = dd_sqrt(dd_add(dd_mul(x[0], x[0]), sig));
+    dd beta = (x[0].hi >= 0.0) ? dd_neg(nrm) : nrm;
+    dd den = dd_sub(x[0], beta);
+    for (int i = 1; i < len; ++i) v[i] = dd_div(x[i], den);
+    *tau = dd_div(dd_sub(beta, x[0]), beta);
+}
+
+GBR_HD bool swap_transform_accurate(const double* D, int p, int q, bool strong, double* Z,
+                                    double* Dn) {
+    const int k = p + q;
+    double dnorm = 0.0;
+    for (int c = 0; c < k; ++c)
+        for (int r = 0; r < k; ++r) dnorm = fmax(dnorm, fabs(D[c * 4 + r]));
+    const double thresh = fmax(10.0 * DBL_EPSILON * dnorm, DBL_MIN);
+
+    // X from the FP64 solve, refined once with a double-double residual:
+    // r = gamma T12 - (T11 X - X T22); T11 dX - dX T22 = r.
+    double X[4], gamma;
+    sylvester(D, p, q, X, &gamma);
+    dd Xd[4], R[4];
+    double Rh[16];
+    for (int j = 0; j < q; ++j)
+        for (int i = 0; i < p; ++i) {
+            dd acc = dd_mul(dd_from(gamma), dd_from(D[(p + j) * 4 + i]));
+            for (int l = 0; l < p; ++l)
+                acc = dd_sub(acc, dd_mul(dd_from(D[l * 4 + i]), dd_from(X[j * 2 + l])));
+            for (int l = 0; l < q; ++l)
+                acc = dd_add(acc, dd_mul(dd_from(X[l * 2 + i]), dd_from(D[(p + j) * 4 + p + l])));
+            R[j * 2 + i] = acc;
+        }
+    for (int i = 0; i < 16; ++i) Rh[i] = 0.0;
+    for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i) Rh[j * 4 + i] = D[j * 4 + i];
+    for (int j = 0; j < q; ++j)
+        for (int i = 0; i < p; ++i) Rh[(p + j) * 4 + i] = R[j * 2 + i].hi;
+    double dX[4], g2;
+    sylvester(Rh, p, q, dX, &g2);
+    for (int j = 0; j < q; ++j)
+        for (int i = 0; i < p; ++i)
+            Xd[j * 2 + i] = dd_add(dd_from(X[j * 2 + i]), dd_from(g2 > 0.0 ? dX[j * 2 + i] / g2 : 0.0));
+
+    // reflectors (same construction as the fast path), in double-double
+    dd v1[4], t1, v2[3] = {dd_from(0), dd_from(0), dd_from(0)}, t2 = dd_from(0.0);
+    dd g = dd_from(gamma);
+    if (p == 1 && q == 2) {
+        dd ur[3] = {Xd[2], Xd[0], g}, vr[3];
+        house_dd(3, ur, vr, &t1);
+        v1[0] = vr[2]; v1[1] = vr[1]; v1[2] = vr[0]; v1[3] = dd_from(0.0);
+    } else {
+        dd c0[4];
+        for (int i = 0; i < k; ++i)
+            c0[i] = (i < p) ? dd_neg(Xd[i]) : ((i == p) ? g : dd_from(0.0));
+        house_dd(k, c0, v1, &t1);
+        if (p == 2 && q == 2) {
+            dd c1[4] = {dd_neg(Xd[2]), dd_neg(Xd[3]), dd_from(0.0), g};
+            dd w = dd_from(0.0);
+            for (int i = 0; i < 4; ++i) w = dd_add(w, dd_mul(v1[i], c1[i]));
+            w = dd_mul(w, t1);
+            for (int i = 0; i < 4; ++i) c1[i] = dd_sub(c1[i], dd_mul(w, v1[i]));
+            house_dd(3, &c1[1], v2, &t2);
+        }
+    }
+    // Qs = H1 H2 explicit, double-double
+    dd Qd[16];
+    for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i) Qd[j * 4 + i] = dd_from(i == j ? 1.0 : 0.0);
+    if (p == 2 && q == 2)
+        for (int j = 1; j < 4; ++j) {
+            dd w = dd_from(0.0);
+            for (int i = 1; i < 4; ++i) w = dd_add(w, dd_mul(v2[i - 1], Qd[j * 4 + i]));
+            w = dd_mul(w, t2);
+            for (int i = 1; i < 4; ++i) Qd[j * 4 + i] = dd_sub(Qd[j * 4 + i], dd_mul(w, v2[i - 1]));
+        }
+    for (int j = 0; j < k; ++j) {
+        dd w = dd_from(0.0);
+        for (int i = 0; i < k; ++i) w = dd_add(w, dd_mul(v1[i], Qd[j * 4 + i]));
+        w = dd_mul(w, t1);
+        for (int i = 0; i < k; ++i) Qd[j * 4 + i] = dd_sub(Qd[j * 4 + i], dd_mul(w, v1[i]));
+    }
+    // Dt = Qs^T D Qs
+    dd T[16], Dtd[16];
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            dd acc = dd_from(0.0);
+            for (int l = 0; l < k; ++l) acc = dd_add(acc, dd_mul(Qd[i * 4 + l], dd_from(D[j * 4 + l])));
+            T[j * 4 + i] = acc;
+        }
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            dd acc = dd_from(0.0);
+            for (int l = 0; l < k; ++l) acc = dd_add(acc, dd_mul(T[l * 4 + i], Qd[j * 4 + l]));
+            Dtd[j * 4 + i] = acc;
+        }
+    double Qs[16], Dt[16];
+    for (int i = 0; i < 16; ++i) { Qs[i] = 0.0; Dt[i] = 0.0; }
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            Qs[j * 4 + i] = Qd[j * 4 + i].hi + Qd[j * 4 + i].lo;
+            Dt[j * 4 + i] = Dtd[j * 4 + i].hi + Dtd[j * 4 + i].lo;
+        }
+    double low = 0.0;
+    for (int c = 0; c < q; ++c)
+        for (int r = q; r < k; ++r) low = fmax(low, fabs(Dt[c * 4 + r]));
+    if (!(low <= thresh)) return false;
+    for (int c = 0; c < q; ++c)
+        for (int r = q; r < k; ++r) Dt[c * 4 + r] = 0.0;
+    if (strong && !(recon_err_compensated(k, Qs, Dt, D) <= thresh)) return false;
+    finish_swap(p, q, Qs, Dt, Z, Dn);
+    return true;
+}
+
+// A swap: the fast FP64 transform, and the double-double retry when the fast
+// one fails the stability test.
+GBR_HD bool swap_transform(const double* D, int p, int q, bool strong, double* Z, double* Dn) {
+    if (swap_transform_fast(D, p, q, strong, Z, Dn)) return true;
+    if (p + q == 2) return false;
+    return swap_transform_accurate(D, p, q, strong, Z, Dn);
 }
 
 }  // namespace gbr
