@@ -181,21 +181,42 @@ static int check_opts(const gbr_opts* o) {
     return 0;
 }
 
+// Scratch layout of one reorder call of order n (bytes from a 256-aligned base):
+// counters | subdiagonal flags | selection flags | eigenvalues | U.
+struct ScratchLayout {
+    size_t off_ctr, off_sub, off_sel, off_eig, off_u, total;
+};
+static constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static constexpr ScratchLayout scratch_layout(size_t n) {
+    return ScratchLayout{0,
+                         256,
+                         256 + align256(n),
+                         256 + 2 * align256(n),
+                         256 + 2 * align256(n) + align256(2 * n * sizeof(double)),
+                         256 + 2 * align256(n) + align256(2 * n * sizeof(double)) +
+                             (size_t)WMAX * WMAX * sizeof(double)};
+}
+
+static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int ldQ,
+                             const int* select, double* eig_re, double* eig_im, int* m_out,
+                             const gbr_opts& o, gbr_stats* stats, cudaStream_t st);
+
 static int reorder_device(int n, double* S, int ldS, double* Q, int ldQ, const int* select,
                           double* eig_re, double* eig_im, int* m_out, const gbr_opts& o,
                           gbr_stats* stats, cudaStream_t st) {
-    // scratch layout
-    const int nslots = 1;
-    size_t off_ctr = 0;
-    size_t off_sub = 256;
-    size_t off_sel = off_sub + (((size_t)n + 255) & ~(size_t)255);
-    size_t off_eig = off_sel + (((size_t)n + 255) & ~(size_t)255);
-    size_t off_u = off_eig + (((size_t)2 * n * sizeof(double) + 255) & ~(size_t)255);
-    size_t total = off_u + (size_t)nslots * WMAX * WMAX * sizeof(double);
     void* base = nullptr;
-    int rc = pool_get(POOL_SCRATCH, total, &base);
+    int rc = pool_get(POOL_SCRATCH, scratch_layout(n).total, &base);
     if (rc) return rc;
-    char* b = (char*)base;
+    return reorder_device_at((char*)base, n, S, ldS, Q, ldQ, select, eig_re, eig_im, m_out, o,
+                             stats, st);
+}
+
+static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int ldQ,
+                             const int* select, double* eig_re, double* eig_im, int* m_out,
+                             const gbr_opts& o, gbr_stats* stats, cudaStream_t st) {
+    const ScratchLayout L = scratch_layout(n);
+    const size_t off_ctr = L.off_ctr, off_sub = L.off_sub, off_sel = L.off_sel,
+                 off_eig = L.off_eig, off_u = L.off_u;
     DevCounters* d_ctr = (DevCounters*)(b + off_ctr);
     uint8_t* d_sub = (uint8_t*)(b + off_sub);
     uint8_t* d_sel = (uint8_t*)(b + off_sel);
