@@ -8,8 +8,10 @@
 
 #ifdef __CUDACC__
 #define GBR_HD __host__ __device__ __forceinline__
+#define GBR_HD_NOINLINE __host__ __device__ __noinline__
 #else
 #define GBR_HD inline
+#define GBR_HD_NOINLINE inline
 #endif
 
 namespace gbr {
@@ -429,7 +431,7 @@ GBR_HD void house_dd(int len, const dd* x, dd* v, dd* tau) {
     *tau = dd_div(dd_sub(beta, x[0]), beta);
 }
 
-GBR_HD bool swap_transform_accurate(const double* D, int p, int q, bool strong, double* Z,
+GBR_HD_NOINLINE bool swap_transform_accurate(const double* D, int p, int q, bool strong, double* Z,
                                     double* Dn) {
     const int k = p + q;
     double dnorm = 0.0;
