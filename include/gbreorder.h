@@ -53,6 +53,7 @@ extern "C" {
 #define GBR_ERR_NOMEM   (-1002) /* device or host allocation failed */
 #define GBR_ERR_TIMEOUT (-1003) /* a bounded device-side wait gave up */
 #define GBR_ERR_UNSUPPORTED (-1004) /* option value not supported */
+#define GBR_ERR_NOALLOC_LIMIT (-1005) /* n > GBR_NOALLOC_MAX_N in gbr_reorder_noalloc */
 
 #define GBR_PREC_DMMA   0  /* off-diagonal updates on FP64 tensor cores (DMMA) */
 #define GBR_PREC_OZAKI  1  /* off-diagonal updates as split-precision emulated FP64 */
@@ -121,6 +122,34 @@ int gbr_reorder(int n, double *S, int ldS, double *Q, int ldQ, const int *select
 int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *select,
                      double *eig_re, double *eig_im, int *m_out, const gbr_opts *opts,
                      gbr_stats *stats, void *cuda_stream);
+
+/*
+ * Same operation as gbr_reorder, for callers that must not allocate device
+ * memory (for example code that runs while a stream is being captured into
+ * a CUDA graph, or a program that owns all device memory through its own
+ * arena).  The paper has no counterpart: this is an interface convenience.
+ *
+ * Arguments and return values are those of gbr_reorder, plus
+ * GBR_ERR_NOALLOC_LIMIT when n > GBR_NOALLOC_MAX_N.  The call never calls
+ * cudaMalloc, cudaFree or any other allocating routine, and creates no CUDA
+ * events (opts->timing is ignored).  Its scratch is a fixed array of
+ * GBR_NOALLOC_SCRATCH_BYTES in device global memory, part of the library
+ * image: every GPU that loads the library holds it until the process exits.
+ *
+ * Set-up: the first call on each device looks up the device address of that
+ * array (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * previous call's contents (each call re-initialises what must start at
+ * zero), so calls that overlap on the GPU -- from several host threads or
+ * several streams at once -- race; calls from one process are serialized by
+ * the library, but the caller must not run two such calls concurrently from
+ * separate processes on one device.
+ */
+#define GBR_NOALLOC_MAX_N 16384
+#define GBR_NOALLOC_SCRATCH_BYTES (256 + 2 * 16384 + 2 * 16384 * 8 + 128 * 128 * 8)
+int gbr_reorder_noalloc(int n, double *S, int ldS, double *Q, int ldQ, const int *select,
+                        double *eig_re, double *eig_im, int *m_out, const gbr_opts *opts,
+                        gbr_stats *stats, void *cuda_stream);
 
 /*
  * Window plan of a reordering, on the host only (no GPU work): the diagonal

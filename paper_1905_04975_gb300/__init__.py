@@ -28,6 +28,8 @@ ERR_CUDA = -1001
 ERR_NOMEM = -1002
 ERR_TIMEOUT = -1003
 ERR_UNSUPPORTED = -1004
+ERR_NOALLOC_LIMIT = -1005
+NOALLOC_MAX_N = 16384
 
 
 class GbrOpts(ctypes.Structure):
@@ -55,6 +57,7 @@ SYMBOLS = {
     "gbr_default_opts": (None, [ctypes.POINTER(GbrOpts)]),
     "gbr_reorder": (ctypes.c_int, _REORDER_ARGS),
     "gbr_reorder_host": (ctypes.c_int, _REORDER_ARGS),
+    "gbr_reorder_noalloc": (ctypes.c_int, _REORDER_ARGS),
     "gbr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbr_last_error": (ctypes.c_char_p, []),
     "gbr_release": (None, []),
@@ -194,6 +197,30 @@ def reorder(S, Q, select, *, opts: GbrOpts | None = None, stream=None, allow_par
                          sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
                          wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
                          ctypes.byref(stats), _stream_handle(stream))
+    return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+def reorder_noalloc(S, Q, select, *, opts: GbrOpts | None = None, stream=None,
+                    allow_partial=True, **kw) -> ReorderResult:
+    """Same as reorder(), through gbr_reorder_noalloc: no device allocation;
+    scratch comes from a fixed array in the library image (n <= 16384)."""
+    lib = load()
+    n = int(S.shape[0])
+    ldS = _colmajor_ld(S)
+    qptr, ldQ = None, max(n, 1)
+    if Q is not None:
+        ldQ = _colmajor_ld(Q)
+        qptr = ctypes.c_void_p(Q.data_ptr())
+    sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+    o = opts if opts is not None else make_opts(**kw)
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    stats = GbrStats()
+    rc = lib.gbr_reorder_noalloc(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ,
+                                 sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
+                                 wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
+                                 ctypes.byref(stats), _stream_handle(stream))
     return _finish(rc, n, m, wr, wi, stats, allow_partial)
 
 

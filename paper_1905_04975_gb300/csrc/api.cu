@@ -470,6 +470,69 @@ int gbr_plan(int n, const unsigned char* sub, const int* select, int window, int
     return (int)win.size();
 }
 
+// ---------------------------------------------------------------------------
+// Reordering without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// reorder: code running while a stream is being captured into a CUDA graph,
+// programs whose memory is all handed out by their own arena, or processes
+// where a cudaMalloc would synchronize the device at a bad moment.  For them
+// this entry point takes its scratch (counters, block flags, selection
+// flags, eigenvalue staging and one window accumulator) from a fixed array
+// in device global memory that is part of the library image instead of the
+// library's pool.  Every GPU that loads the library holds this array
+// (GBR_NOALLOC_SCRATCH_BYTES) until the process exits.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoallocBytes = scratch_layout(GBR_NOALLOC_MAX_N).total;
+static_assert(kNoallocBytes == GBR_NOALLOC_SCRATCH_BYTES, "header and layout disagree");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Device address of g_noalloc_scratch for each device, looked up once with
+// that device current (in host code the symbol is only a host-side stand-in).
+static void* g_noalloc_ptr[64];
+
+static int noalloc_scratch(char** out) {
+    int dev = 0;
+    GBR_CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return GBR_ERR_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        GBR_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (char*)g_noalloc_ptr[dev];
+    return 0;
+}
+
+int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int* select,
+                        double* eig_re, double* eig_im, int* m_out, const gbr_opts* opts,
+                        gbr_stats* stats, void* cuda_stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = common_args(n, S, ldS, Q, ldQ, select);
+    if (rc) return rc;
+    if (n > GBR_NOALLOC_MAX_N) return GBR_ERR_NOALLOC_LIMIT;
+    gbr_opts o;
+    if (opts) o = *opts; else gbr_default_opts(&o);
+    rc = check_opts(&o);
+    if (rc) return rc;
+    o.timing = 0;  // event timing would create events; this path creates nothing
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (n == 0) {
+        if (m_out) *m_out = 0;
+        return 0;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    char* base = nullptr;
+    rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    rc = reorder_device_at(base, n, S, ldS, Q, ldQ, select, eig_re, eig_im, m_out, o, stats,
+                           (cudaStream_t)cuda_stream);
+    if (stats)
+        stats->ms_total =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
 const char* gbr_status_string(int s) {
     if (s == 0) return "success";
     if (s > 0) return "partial reorder: some block swaps were rejected by the stability test";
@@ -484,6 +547,8 @@ const char* gbr_status_string(int s) {
         case GBR_ERR_NOMEM: return "out of device memory";
         case GBR_ERR_TIMEOUT: return "a bounded device-side wait timed out";
         case GBR_ERR_UNSUPPORTED: return "unsupported option value";
+        case GBR_ERR_NOALLOC_LIMIT:
+            return "n exceeds GBR_NOALLOC_MAX_N, the size the no-allocation entry point supports";
         default: return "invalid argument";
     }
 }

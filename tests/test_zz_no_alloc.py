@@ -1,0 +1,74 @@
+"""gbr_reorder_noalloc: the reordering entry point for callers that cannot
+allocate device memory (e.g. while a stream is being captured, or when an
+application owns all device memory).  Its scratch is a fixed device array in
+the library image.  Its results must match gbr_reorder's, call after call:
+the shared scratch keeps the previous call's contents, so a second call must
+start from a clean state.
+
+This file is collected last so that, in a run that stops at the first
+failure, every other test has already run.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import schur_inputs as si
+from tests.helpers import EPS, expected_order, match_eigs, orth_err, residual
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1905_04975_gb300 as g
+    g.load()
+    return g
+
+
+def run(g, fn, S, Q, sel, **kw):
+    Sd, Qd = g.to_device(S), g.to_device(Q)
+    r = fn(Sd, Qd, sel, **kw)
+    torch.cuda.synchronize()
+    return r, g.to_host(Sd), g.to_host(Qd)
+
+
+@pytest.mark.parametrize("case", ["n400", "ragged700"])
+def test_noalloc_matches_reorder_twice(g, case):
+    if case == "n400":
+        S, Q, sel = si.config("n400")
+        kw = {}
+    else:
+        S, Q, sel = si.reorder_problem(700, 77, select_frac=0.4, q="householder")
+        kw = dict(window=64, chain=30)
+    n = S.shape[0]
+    A = Q @ S @ Q.T
+    ref, Sr, Qr = run(g, g.reorder, S, Q, sel, **kw)
+    assert ref.status == 0
+    want, m = expected_order(S, sel)
+    for call in range(2):
+        r, Sn, Qn = run(g, g.reorder_noalloc, S, Q, sel, **kw)
+        assert r.status == 0 and r.m == ref.m == m
+        # same results as the allocating entry point, within the tests' tolerances
+        assert match_eigs(r.eigs, ref.eigs, 0) <= 1e-10
+        assert np.linalg.norm(Sn - Sr) <= 50 * n * EPS * np.linalg.norm(S)
+        assert np.linalg.norm(Qn - Qr) <= 50 * n * EPS * np.sqrt(n)
+        assert match_eigs(r.eigs, want, 0) <= 1e-10
+        assert orth_err(Qn) <= 50 * n * EPS
+        assert residual(A, Sn, Qn) <= 50 * n * EPS
+        assert r.stats.windows == ref.stats.windows
+
+
+def test_noalloc_rejects_oversized(g):
+    lib = g.load()
+    n = g.NOALLOC_MAX_N + 1
+    sel = np.zeros(n, np.int32)
+    dummy = ctypes.c_void_p(0x1000)   # never touched: the size check comes first
+    rc = lib.gbr_reorder_noalloc(n, dummy, n, None, n,
+                                 sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 None, None, None, None, None, None)
+    assert rc == g.ERR_NOALLOC_LIMIT
+    assert b"GBR_NOALLOC_MAX_N" in lib.gbr_status_string(rc)
