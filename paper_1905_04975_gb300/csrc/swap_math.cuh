@@ -5,6 +5,7 @@
 
 #include <float.h>
 #include <math.h>
+#include <string.h>
 
 #ifdef __CUDACC__
 #define GBR_HD __host__ __device__ __forceinline__
@@ -364,6 +365,127 @@ GBR_HD bool swap_transform_fast(const double* D, int p, int q, bool strong, doub
     }
 
     finish_swap(p, q, Qs, Dt, Z, Dn);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Fast k = 3 swap without re-standardization (the window kernel restores the
+// standard form of its 2x2 blocks once, at the end of the window).
+//
+// 2|1: D = [[A, c], [0, lam]] with A 2x2.  X solves (A - lam I) X = c; the one
+// reflector H with H (-x0, -x1, 1)^T = beta e_1 gives Dt = H D H with lam first.
+// 1|2 is mapped onto 2|1 by the flip D' = F D^T F (F reverses the indices):
+// if Z'^T D' Z' = Dt' then Z = F Z' F and Dt = F Dt'^T F.
+// Integer comparisons of |x| bit patterns keep the tests off the FP64 pipe.
+// Returns false when the fast path cannot decide (tiny pivot) or the swap
+// fails the weak or strong test; the caller then uses the full transform.
+// ---------------------------------------------------------------------------
+GBR_HD unsigned long long abs_bits(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+#else
+    unsigned long long u;
+    memcpy(&u, &x, 8);
+    return u & 0x7fffffffffffffffULL;
+#endif
+}
+GBR_HD double bits_double(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+
+// D, Z, Dn: 3x3 column-major with leading dimension 4 (entries [c*4 + r]).
+GBR_HD bool swap21_fast(const double* D, bool strong, double* Z, double* Dn) {
+    unsigned long long mx = 0;
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) {
+            unsigned long long b = abs_bits(D[c * 4 + r]);
+            mx = b > mx ? b : mx;
+        }
+    const double thresh = fmax(10.0 * DBL_EPSILON * bits_double(mx), DBL_MIN);
+    const unsigned long long tb = abs_bits(thresh);
+    const double lam = D[10];
+    const double a00 = D[0] - lam, a01 = D[4], a10 = D[1], a11 = D[5] - lam;
+    const double c0 = D[8], c1 = D[9];
+    const double det = fma(a00, a11, -(a01 * a10));
+    // partial-pivoting quality check: |det| must not be tiny against the entries
+    unsigned long long am = abs_bits(a00);
+    am = abs_bits(a01) > am ? abs_bits(a01) : am;
+    am = abs_bits(a10) > am ? abs_bits(a10) : am;
+    am = abs_bits(a11) > am ? abs_bits(a11) : am;
+    const double amax = bits_double(am);
+    if (!(abs_bits(det) > abs_bits(1e-4 * amax * amax))) return false;
+    const double rdet = 1.0 / det;
+    const double x0 = fma(a11, c0, -(a01 * c1)) * rdet;
+    const double x1 = fma(a00, c1, -(a10 * c0)) * rdet;
+    // reflector for u = (-x0, -x1, 1)
+    const double alpha = -x0;
+    const double sig = fma(x1, x1, 1.0);
+    const double nrm = sqrt(fma(alpha, alpha, sig));
+    const double beta = alpha >= 0.0 ? -nrm : nrm;
+    const double dd = alpha - beta;
+    const double rdd = 1.0 / dd;
+    const double v0 = 1.0, v1 = -x1 * rdd, v2 = rdd;
+    const double tau = -dd / beta;
+    // Dt = H D H, H = I - tau v v^T
+    double T[9];
+    for (int c = 0; c < 3; ++c) {
+        double w = fma(v2, D[c * 4 + 2], fma(v1, D[c * 4 + 1], v0 * D[c * 4 + 0])) * tau;
+        T[c * 3 + 0] = fma(-w, v0, D[c * 4 + 0]);
+        T[c * 3 + 1] = fma(-w, v1, D[c * 4 + 1]);
+        T[c * 3 + 2] = fma(-w, v2, D[c * 4 + 2]);
+    }
+    for (int r = 0; r < 3; ++r) {
+        double w = fma(T[6 + r], v2, fma(T[3 + r], v1, T[r] * v0)) * tau;
+        Dn[0 * 4 + r] = fma(-w, v0, T[r]);
+        Dn[1 * 4 + r] = fma(-w, v1, T[3 + r]);
+        Dn[2 * 4 + r] = fma(-w, v2, T[6 + r]);
+    }
+    // weak test: the block that must vanish, rows 1..2 of column 0
+    if (abs_bits(Dn[1]) > tb || abs_bits(Dn[2]) > tb) return false;
+    Dn[1] = 0.0;
+    Dn[2] = 0.0;
+    if (strong) {
+        // E = H Dt0 H - D
+        for (int c = 0; c < 3; ++c) {
+            double w = fma(v2, Dn[c * 4 + 2], fma(v1, Dn[c * 4 + 1], v0 * Dn[c * 4 + 0])) * tau;
+            T[c * 3 + 0] = fma(-w, v0, Dn[c * 4 + 0]);
+            T[c * 3 + 1] = fma(-w, v1, Dn[c * 4 + 1]);
+            T[c * 3 + 2] = fma(-w, v2, Dn[c * 4 + 2]);
+        }
+        for (int r = 0; r < 3; ++r) {
+            double w = fma(T[6 + r], v2, fma(T[3 + r], v1, T[r] * v0)) * tau;
+            double e0 = fma(-w, v0, T[r]) - D[0 * 4 + r];
+            double e1 = fma(-w, v1, T[3 + r]) - D[1 * 4 + r];
+            double e2 = fma(-w, v2, T[6 + r]) - D[2 * 4 + r];
+            if (abs_bits(e0) > tb || abs_bits(e1) > tb || abs_bits(e2) > tb) return false;
+        }
+    }
+    // Z = H (symmetric)
+    const double tv0 = tau * v0, tv1 = tau * v1, tv2 = tau * v2;
+    Z[0] = fma(-tv0, v0, 1.0); Z[1] = -tv0 * v1;          Z[2] = -tv0 * v2;
+    Z[4] = Z[1];               Z[5] = fma(-tv1, v1, 1.0); Z[6] = -tv1 * v2;
+    Z[8] = Z[2];               Z[9] = Z[6];               Z[10] = fma(-tv2, v2, 1.0);
+    return true;
+}
+
+GBR_HD bool swap3_fast(const double* D, int p, bool strong, double* Z, double* Dn) {
+    if (p == 2) return swap21_fast(D, strong, Z, Dn);
+    // 1|2: flip, solve as 2|1, flip back
+    double Df[16], Zf[16], Dnf[16];
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) Df[c * 4 + r] = D[(2 - r) * 4 + (2 - c)];
+    if (!swap21_fast(Df, strong, Zf, Dnf)) return false;
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) {
+            Z[c * 4 + r] = Zf[(2 - c) * 4 + (2 - r)];
+            Dn[c * 4 + r] = Dnf[(2 - r) * 4 + (2 - c)];
+        }
     return true;
 }
 
