@@ -51,7 +51,8 @@ extern "C" {
 
 #define GBR_ERR_CUDA    (-1001) /* a CUDA call failed (message: gbr_last_error) */
 #define GBR_ERR_NOMEM   (-1002) /* device or host allocation failed */
-#define GBR_ERR_TIMEOUT (-1003) /* a bounded device-side wait gave up */
+#define GBR_ERR_TIMEOUT (-1003) /* a bounded device-side wait gave up; S and Q are
+                                   then partially updated and must be discarded */
 #define GBR_ERR_UNSUPPORTED (-1004) /* option value not supported */
 #define GBR_ERR_NOALLOC_LIMIT (-1005) /* n > GBR_NOALLOC_MAX_N in gbr_reorder_noalloc */
 
@@ -71,7 +72,18 @@ typedef struct gbr_opts {
     int validate;      /* 1: check the standard-form input      (default 1)   */
     int timing;        /* 1: time the window and update kernels with CUDA
                           events into gbr_stats (small overhead) (default 0)  */
+    int sched;         /* GBR_SCHED_PERSISTENT (default) or GBR_SCHED_SEQUENTIAL */
+    int inject;        /* fault injection for tests: GBR_INJECT_STALL makes one
+                          scheduler task wait for a predecessor that never
+                          finishes, so the bounded wait runs out (default 0) */
+    long long wait_limit_ms; /* bound on any device-side wait of the persistent
+                          scheduler, milliseconds; 0 = default (60000)   */
 } gbr_opts;
+
+#define GBR_SCHED_PERSISTENT 0 /* one persistent launch runs all window and update
+                                  tasks, several windows in flight (Section 3.2) */
+#define GBR_SCHED_SEQUENTIAL 1 /* one window, then its update, at a time */
+#define GBR_INJECT_STALL 1
 
 /* Per-call statistics (all optional). */
 typedef struct gbr_stats {
@@ -82,8 +94,11 @@ typedef struct gbr_stats {
     long long launches;   /* kernels launched by the call              */
     double upd_flops;     /* flops of the off-diagonal updates         */
     double ms_total;      /* wall time of the call                     */
-    double ms_window;     /* summed window-kernel time (opts.timing)   */
-    double ms_update;     /* summed update-kernel time (opts.timing)   */
+    double ms_window;     /* summed window-kernel time (opts.timing, sequential) */
+    double ms_update;     /* summed update-kernel time (opts.timing, sequential) */
+    double ms_sched;      /* persistent-scheduler kernel time (opts.timing)      */
+    double win_flops;     /* FP64 flops of the in-window updates of accepted swaps */
+    long long tasks;      /* scheduler tasks (window tasks + update tiles)       */
 } gbr_stats;
 
 /* Fill *opts with the defaults. */

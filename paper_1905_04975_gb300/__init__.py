@@ -23,6 +23,9 @@ SO_PATH = os.path.join(_HERE, "libgbreorder.so")
 
 PREC_DMMA = 0
 PREC_OZAKI = 1
+SCHED_PERSISTENT = 0
+SCHED_SEQUENTIAL = 1
+INJECT_STALL = 1
 
 ERR_CUDA = -1001
 ERR_NOMEM = -1002
@@ -36,7 +39,8 @@ class GbrOpts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("chain", ctypes.c_int), ("precision", ctypes.c_int),
                 ("slices", ctypes.c_int), ("strong_test", ctypes.c_int),
                 ("on_reject", ctypes.c_int), ("validate", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("sched", ctypes.c_int), ("inject", ctypes.c_int),
+                ("wait_limit_ms", ctypes.c_longlong)]
 
 
 class GbrStats(ctypes.Structure):
@@ -44,7 +48,8 @@ class GbrStats(ctypes.Structure):
                 ("windows", ctypes.c_longlong), ("chains", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong), ("upd_flops", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_window", ctypes.c_double),
-                ("ms_update", ctypes.c_double)]
+                ("ms_update", ctypes.c_double), ("ms_sched", ctypes.c_double),
+                ("win_flops", ctypes.c_double), ("tasks", ctypes.c_longlong)]
 
 
 # Every symbol the header declares, with (restype, argtypes).
@@ -108,7 +113,7 @@ def default_opts() -> GbrOpts:
 
 
 def make_opts(window=None, chain=None, precision=None, slices=None, strong=None,
-              validate=None, timing=None) -> GbrOpts:
+              validate=None, timing=None, sched=None, inject=None, wait_limit_ms=None) -> GbrOpts:
     o = default_opts()
     if window is not None:
         o.window = int(window)
@@ -124,6 +129,12 @@ def make_opts(window=None, chain=None, precision=None, slices=None, strong=None,
         o.validate = 1 if validate else 0
     if timing is not None:
         o.timing = 1 if timing else 0
+    if sched is not None:
+        o.sched = {"persistent": SCHED_PERSISTENT, "sequential": SCHED_SEQUENTIAL}.get(sched, sched)
+    if inject is not None:
+        o.inject = int(inject)
+    if wait_limit_ms is not None:
+        o.wait_limit_ms = int(wait_limit_ms)
     return o
 
 

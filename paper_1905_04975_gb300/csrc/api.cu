@@ -14,8 +14,10 @@
 #include "../../include/gbreorder.h"
 #include "common.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <climits>
+#include <queue>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -42,10 +44,10 @@ static int cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Device scratch pool: one grow-only allocation per device and purpose.
 // ---------------------------------------------------------------------------
-enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_NSLOTS = 3 };
+enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_NSLOTS = 4 };
 struct DevPool {
-    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr};
-    size_t bytes[POOL_NSLOTS] = {0, 0, 0};
+    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr, nullptr};
+    size_t bytes[POOL_NSLOTS] = {0, 0, 0, 0};
 };
 static std::mutex g_mu;  // serializes calls: the pool is shared per device
 static DevPool g_pool[64];
@@ -171,6 +173,261 @@ static void plan_pass(PlanState& st, int w, int m, std::vector<Window>& win, int
 }
 
 // ---------------------------------------------------------------------------
+// Task graph for the persistent scheduler (Section 3.2, Fig. 2).
+//
+// Program order is the planner's window order; each window i contributes its
+// window task W_i and update tiles of UPD_BM panel rows (left panel columns
+// and right/Q panel rows on a global UPD_BM grid, so tiles of different
+// windows line up).  A task depends on every earlier task whose exact
+// rectangle of S (or of Q) overlaps its own -- not on tiles, so two tasks
+// that touch different parts of a tile do not wait on each other -- and each
+// update tile on its window task (it reads U_i).  Older overlapping tasks are
+// skipped once a newer one covers the whole overlap (they are then
+// predecessors of that newer task already).
+// ---------------------------------------------------------------------------
+struct Rect {
+    int r0, r1, c0, c1;  // rows [r0, r1) x columns [c0, c1)
+};
+static inline bool rects_overlap(const Rect& a, const Rect& b) {
+    return a.r0 < b.r1 && b.r0 < a.r1 && a.c0 < b.c1 && b.c0 < a.c1;
+}
+static inline bool rect_covers(const Rect& a, const Rect& b) {
+    return a.r0 <= b.r0 && a.r1 >= b.r1 && a.c0 <= b.c0 && a.c1 >= b.c1;
+}
+static inline Rect rect_isect(const Rect& a, const Rect& b) {
+    return Rect{std::max(a.r0, b.r0), std::min(a.r1, b.r1), std::max(a.c0, b.c0),
+                std::min(a.c1, b.c1)};
+}
+
+struct HostTask {
+    int kind, win, y0, rows, mat;  // mat 0 = S, 1 = Q
+    Rect rc;
+    double dur;                     // estimated duration (microseconds)
+};
+
+struct TaskGraph {
+    std::vector<HostTask> t;
+    std::vector<int> ndeps;
+    std::vector<int> soff, succ;    // CSR successors, program order
+};
+
+// Duration model for the queue order only (relative values matter): a window
+// task takes about 2.6 ms at w = 128 (measured), an update tile is a DMMA
+// product of rows x w x w at ~6.9 GFLOP/s per SM.
+static double dur_window(int w) { return 2600.0 * (double)w * w / (128.0 * 128.0); }
+static double dur_tile(int rows, int w) { return 2.0 * rows * (double)w * w / 6900.0 + 2.0; }
+
+static void build_graph(int n, const std::vector<Window>& wins, bool withQ, TaskGraph& G) {
+    std::vector<HostTask>& T = G.t;
+    std::vector<std::pair<int, int>> edges;
+    T.clear();
+    for (int i = 0; i < (int)wins.size(); ++i) {
+        const int s = wins[i].s, e = wins[i].e, w = e - s;
+        const int iw = (int)T.size();
+        T.push_back(HostTask{TASK_W, i, 0, 0, 0, Rect{s, e, s, e}, dur_window(w)});
+        for (int c = e; c < n;) {
+            int ce = std::min(n, (c / UPD_BM + 1) * UPD_BM);
+            edges.push_back({iw, (int)T.size()});
+            T.push_back(HostTask{TASK_L, i, c - e, ce - c, 0, Rect{s, e, c, ce}, dur_tile(ce - c, w)});
+            c = ce;
+        }
+        for (int r = 0; r < s;) {
+            int re = std::min(s, (r / UPD_BM + 1) * UPD_BM);
+            edges.push_back({iw, (int)T.size()});
+            T.push_back(HostTask{TASK_R, i, r, re - r, 0, Rect{r, re, s, e}, dur_tile(re - r, w)});
+            r = re;
+        }
+        if (withQ)
+            for (int r = 0; r < n;) {
+                int re = std::min(n, (r / UPD_BM + 1) * UPD_BM);
+                edges.push_back({iw, (int)T.size()});
+                T.push_back(HostTask{TASK_Q, i, r, re - r, 1, Rect{r, re, s, e}, dur_tile(re - r, w)});
+                r = re;
+            }
+    }
+    const int CB = UPD_BM;
+    const int nc = (n + CB - 1) / CB;
+    std::vector<std::vector<int>> cells[2];
+    cells[0].resize((size_t)nc * nc);
+    if (withQ) cells[1].resize((size_t)nc * nc);
+    std::vector<int> stamp(T.size(), -1);
+    for (int t = 0; t < (int)T.size(); ++t) {
+        const Rect R = T[t].rc;
+        const int m = T[t].mat;
+        for (int cr = R.r0 / CB; cr * CB < R.r1; ++cr)
+            for (int cc = R.c0 / CB; cc * CB < R.c1; ++cc) {
+                const Rect cell{cr * CB, std::min(n, (cr + 1) * CB), cc * CB, std::min(n, (cc + 1) * CB)};
+                const Rect X = rect_isect(R, cell);
+                std::vector<int>& L = cells[m][(size_t)cr * nc + cc];
+                for (int k = (int)L.size() - 1; k >= 0; --k) {
+                    const int u = L[k];
+                    const Rect& U = T[u].rc;
+                    if (!rects_overlap(U, X)) continue;
+                    if (stamp[u] != t) {
+                        stamp[u] = t;
+                        edges.push_back({u, t});
+                    }
+                    if (rect_covers(U, X)) break;
+                }
+                L.push_back(t);
+            }
+    }
+    std::sort(edges.begin(), edges.end());
+    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    const int nt = (int)T.size();
+    G.ndeps.assign(nt, 0);
+    G.soff.assign(nt + 1, 0);
+    G.succ.resize(edges.size());
+    for (auto& ed : edges) {
+        G.ndeps[ed.second]++;
+        G.soff[ed.first + 1]++;
+    }
+    for (int i = 0; i < nt; ++i) G.soff[i + 1] += G.soff[i];
+    std::vector<int> fill(G.soff.begin(), G.soff.end() - 1);
+    for (auto& ed : edges) G.succ[fill[ed.first]++] = ed.second;
+}
+
+// Queue order: a list-scheduling simulation on P processors where the ready
+// task with the longest remaining path to the end (bottom level) starts first;
+// the queue is the order of simulated start times.  Every predecessor of a
+// task starts (and finishes) before it, so it sits earlier in the queue.
+static void queue_order(const TaskGraph& G, int P, std::vector<int>& order) {
+    const int nt = (int)G.t.size();
+    std::vector<double> bl(nt, 0.0);
+    for (int t = nt - 1; t >= 0; --t) {
+        double m = 0.0;
+        for (int i = G.soff[t]; i < G.soff[t + 1]; ++i) m = std::max(m, bl[G.succ[i]]);
+        bl[t] = G.t[t].dur + m;
+    }
+    std::vector<int> indeg(G.ndeps);
+    typedef std::pair<double, int> Key;
+    std::priority_queue<std::pair<double, int>> ready;  // (bottom level, -index)
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> running;  // (finish, task)
+    for (int t = 0; t < nt; ++t)
+        if (indeg[t] == 0) ready.push({bl[t], -t});
+    order.clear();
+    order.reserve(nt);
+    int free = P;
+    double now = 0.0;
+    while ((int)order.size() < nt) {
+        while (free > 0 && !ready.empty()) {
+            int t = -ready.top().second;
+            ready.pop();
+            order.push_back(t);
+            running.push({now + G.t[t].dur, t});
+            --free;
+        }
+        if (running.empty()) break;  // cannot happen for an acyclic graph
+        now = running.top().first;
+        while (!running.empty() && running.top().first <= now) {
+            int t = running.top().second;
+            running.pop();
+            ++free;
+            for (int i = G.soff[t]; i < G.soff[t + 1]; ++i)
+                if (--indeg[G.succ[i]] == 0) ready.push({bl[G.succ[i]], -G.succ[i]});
+        }
+    }
+}
+
+static int num_sms() {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
+// Runs one planned pass with the persistent scheduler.  Returns 0 or an error.
+static int run_persistent(int n, const std::vector<Window>& wins, double* S, int ldS, double* Q,
+                          int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
+                          long long* ntasks_out, double* ms_out, cudaStream_t st) {
+    TaskGraph G;
+    build_graph(n, wins, Q != nullptr, G);
+    const int P = num_sms();
+    std::vector<int> order;
+    queue_order(G, P, order);
+    const int nt = (int)G.t.size();
+    if ((int)order.size() != nt) {
+        g_last_error = "scheduler: task graph is not acyclic";
+        return GBR_ERR_CUDA;
+    }
+    std::vector<int> pos(nt);
+    for (int q = 0; q < nt; ++q) pos[order[q]] = q;
+    std::vector<SchedTask> tq(nt);
+    std::vector<int> deps(nt), soff(nt + 1, 0), succ(G.succ.size());
+    for (int q = 0; q < nt; ++q) {
+        const HostTask& h = G.t[order[q]];
+        tq[q] = SchedTask{h.kind, h.win, h.y0, h.rows};
+        deps[q] = G.ndeps[order[q]];
+        soff[q + 1] = soff[q] + (G.soff[order[q] + 1] - G.soff[order[q]]);
+    }
+    for (int q = 0; q < nt; ++q) {
+        int t = order[q], o2 = soff[q];
+        for (int i = G.soff[t]; i < G.soff[t + 1]; ++i) succ[o2++] = pos[G.succ[i]];
+    }
+    if ((o.inject & GBR_INJECT_STALL) && nt > 1) deps[nt - 1] += 1;  // a predecessor that never ends
+    // device buffers (pool): tasks | wins | deps | soff | succ | head,err | U pool
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_tasks = al(sizeof(SchedTask) * nt), b_wins = al(sizeof(Window) * wins.size());
+    const size_t b_deps = al(sizeof(int) * nt), b_soff = al(sizeof(int) * (nt + 1));
+    const size_t b_succ = al(sizeof(int) * std::max<size_t>(1, succ.size())), b_ctl = 256;
+    const size_t b_u = (size_t)wins.size() * WMAX * WMAX * sizeof(double);
+    void* base = nullptr;
+    int rc = pool_get(POOL_SCHED, b_tasks + b_wins + b_deps + b_soff + b_succ + b_ctl + b_u, &base);
+    if (rc) return rc;
+    char* p = (char*)base;
+    SchedTask* d_tasks = (SchedTask*)p; p += b_tasks;
+    Window* d_wins = (Window*)p; p += b_wins;
+    int* d_deps = (int*)p; p += b_deps;
+    int* d_soff = (int*)p; p += b_soff;
+    int* d_succ = (int*)p; p += b_succ;
+    int* d_ctl = (int*)p; p += b_ctl;
+    double* d_u = (double*)p;
+    GBR_CK(cudaMemcpyAsync(d_tasks, tq.data(), sizeof(SchedTask) * nt, cudaMemcpyHostToDevice, st), "H2D tasks");
+    GBR_CK(cudaMemcpyAsync(d_wins, wins.data(), sizeof(Window) * wins.size(), cudaMemcpyHostToDevice, st), "H2D windows");
+    GBR_CK(cudaMemcpyAsync(d_deps, deps.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st), "H2D deps");
+    GBR_CK(cudaMemcpyAsync(d_soff, soff.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice, st), "H2D succ offsets");
+    if (!succ.empty())
+        GBR_CK(cudaMemcpyAsync(d_succ, succ.data(), sizeof(int) * succ.size(), cudaMemcpyHostToDevice, st), "H2D succ");
+    GBR_CK(cudaMemsetAsync(d_ctl, 0, 256, st), "memset control");
+    SchedParams P2;
+    P2.n = n; P2.ldS = ldS; P2.ldQ = ldQ; P2.strong = o.strong_test; P2.ntasks = nt;
+    P2.S = S; P2.Q = Q; P2.sel = d_sel; P2.ctr = d_ctr;
+    P2.tasks = d_tasks; P2.wins = d_wins; P2.deps_left = d_deps; P2.succ_off = d_soff; P2.succ = d_succ;
+    P2.upool = d_u; P2.head = d_ctl; P2.err = d_ctl + 1;
+    const long long lim_ms = o.wait_limit_ms > 0 ? o.wait_limit_ms : 60000;
+    P2.wait_limit = lim_ms * 1000000 / 128;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (o.timing) {
+        GBR_CK(cudaEventCreate(&e0), "event");
+        GBR_CK(cudaEventCreate(&e1), "event");
+        GBR_CK(cudaEventRecord(e0, st), "event");
+    }
+    GBR_CK(launch_sched(P2, P, st), "scheduler kernel");
+    if (o.timing) GBR_CK(cudaEventRecord(e1, st), "event");
+    int h_err = 0;
+    GBR_CK(cudaMemcpyAsync(&h_err, d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H err");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (o.timing) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *ms_out += ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    *ntasks_out += nt;
+    if (h_err) {
+        g_last_error = "persistent scheduler: a task waited longer than wait_limit_ms";
+        return GBR_ERR_TIMEOUT;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Reorder on device-resident S, Q.
 // ---------------------------------------------------------------------------
 static int check_opts(const gbr_opts* o) {
@@ -178,6 +435,8 @@ static int check_opts(const gbr_opts* o) {
     if (o->chain < 1 || o->chain > o->window - 2) return -10;
     if (o->precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
     if (o->on_reject != GBR_ON_REJECT_CONTINUE) return GBR_ERR_UNSUPPORTED;
+    if (o->sched != GBR_SCHED_PERSISTENT && o->sched != GBR_SCHED_SEQUENTIAL) return -10;
+    if (o->wait_limit_ms < 0) return -10;
     return 0;
 }
 
@@ -223,7 +482,7 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
     double* d_eig = (double*)(b + off_eig);
     double* d_u = (double*)(b + off_u);
 
-    DevCounters h_ctr{0, 0, INT_MAX, 0};
+    DevCounters h_ctr{0, 0, INT_MAX, 0, 0};
     GBR_CK(cudaMemcpyAsync(d_ctr, &h_ctr, sizeof h_ctr, cudaMemcpyHostToDevice, st), "H2D counters");
     if (o.validate) GBR_CK(launch_validate(n, S, ldS, d_ctr, st), "validate kernel");
     GBR_CK(launch_subdiag(n, S, ldS, d_sub, st), "subdiag kernel");
@@ -270,10 +529,21 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
     int nchains = 0;
     double flops = 0.0;
     unsigned long long seen_rej = 0;
+    double ms_sched = 0.0;
+    long long ntasks = 0;
     for (int pass = 0; pass < 1 + 2 * n; ++pass) {
         std::vector<Window> win;
         plan_pass(ps, o.window, o.chain, win, nchains);
         if (win.empty()) break;
+        if (o.sched == GBR_SCHED_PERSISTENT && pass == 0) {
+            int rcs = run_persistent(n, win, S, ldS, Q, ldQ, d_sel, d_ctr, o, &ntasks, &ms_sched, st);
+            if (rcs) return rcs;
+            launches += 1;
+            for (const Window& wdw : win) {
+                double ww = (double)(wdw.e - wdw.s);
+                flops += 2.0 * ww * ww * ((double)(n - wdw.e) + wdw.s + (Q ? n : 0));
+            }
+        } else
         for (const Window& wdw : win) {
             if (o.timing) GBR_CK(mark(evw), "event");
             GBR_CK(launch_window(n, wdw, S, ldS, d_sel, d_u, o.strong_test, d_ctr, st), "window kernel");
@@ -333,6 +603,9 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         stats->upd_flops = flops;
         stats->ms_window = msw;
         stats->ms_update = msu;
+        stats->ms_sched = ms_sched;
+        stats->win_flops = (double)h_ctr.win_flops;
+        stats->tasks = ntasks;
     }
     long long rej = (long long)h_ctr.rejected;
     return rej > INT_MAX ? INT_MAX : (int)rej;
@@ -355,6 +628,9 @@ void gbr_default_opts(gbr_opts* o) {
     o->on_reject = GBR_ON_REJECT_CONTINUE;
     o->validate = 1;
     o->timing = 0;
+    o->sched = GBR_SCHED_PERSISTENT;
+    o->inject = 0;
+    o->wait_limit_ms = 0;
 }
 
 static int common_args(int n, const void* S, int ldS, const void* Q, int ldQ, const int* select) {
@@ -516,6 +792,7 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
     rc = check_opts(&o);
     if (rc) return rc;
     o.timing = 0;  // event timing would create events; this path creates nothing
+    o.sched = GBR_SCHED_SEQUENTIAL;  // the persistent schedule needs scratch sized per plan
     if (stats) memset(stats, 0, sizeof *stats);
     if (n == 0) {
         if (m_out) *m_out = 0;

@@ -11,6 +11,9 @@ namespace gbr {
 // packed upper-Hessenberg S window + dense accumulator U).
 constexpr int WMAX = 128;
 
+// Panel rows per update tile (update_body.cuh, scheduler tasks).
+constexpr int UPD_BM = 64;
+
 // Column-major element access.
 __host__ __device__ inline size_t cm(int i, int j, int ld) {
     return (size_t)j * (size_t)ld + (size_t)i;
@@ -25,6 +28,7 @@ struct DevCounters {
     unsigned long long rejected;
     int bad_column;      // validation: first column violating the standard form, or INT_MAX
     int step_overflow;   // windows that hit the step cap (a logic error if nonzero)
+    unsigned long long win_flops;  // FP64 flops of in-window updates of accepted swaps
 };
 
 // One diagonal window in program order.
@@ -32,6 +36,33 @@ struct Window {
     int s, e;            // rows/cols [s, e) of S
     int chain;           // chain index
     int u_off;           // offset (in doubles) of this window's U in the U pool
+};
+
+// Persistent scheduler (sched.cu): task kinds and launch parameters.
+enum : int { TASK_W = 0, TASK_L = 1, TASK_R = 2, TASK_Q = 3 };  // L/R/Q = TASK_L + panel
+
+struct SchedTask {
+    int kind;   // TASK_*
+    int win;    // window index
+    int y0;     // first panel row of an update tile
+    int rows;   // panel rows of an update tile
+};
+
+struct SchedParams {
+    int n, ldS, ldQ, strong, ntasks;
+    double* S;
+    double* Q;
+    uint8_t* sel;
+    DevCounters* ctr;
+    const SchedTask* tasks;   // queue order
+    const Window* wins;
+    int* deps_left;           // unfinished predecessors per task
+    const int* succ_off;      // CSR successors
+    const int* succ;
+    double* upool;            // one WMAX x WMAX accumulator per window
+    int* head;                // next queue position
+    int* err;                 // nonzero: a wait ran out
+    long long wait_limit;     // spins (~128 ns each) before a wait gives up
 };
 
 // Launchers (each .cu file owns its kernels).
@@ -44,5 +75,8 @@ cudaError_t launch_update(int n, const Window& w, double* S, int ldS, double* Q,
                           const double* U, cudaStream_t st);
 size_t window_smem_bytes(int w);
 size_t update_smem_bytes(int w);
+cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st);
+size_t sched_smem_bytes();
+int sched_threads();
 
 }  // namespace gbr

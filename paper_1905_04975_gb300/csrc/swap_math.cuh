@@ -9,10 +9,10 @@
 
 #ifdef __CUDACC__
 #define GBR_HD __host__ __device__ __forceinline__
-#define GBR_HD_NOINLINE __host__ __device__ __noinline__
+#define GBR_HD_NOINLINE static __host__ __device__ __noinline__
 #else
 #define GBR_HD inline
-#define GBR_HD_NOINLINE inline
+#define GBR_HD_NOINLINE static inline
 #endif
 
 namespace gbr {

@@ -1,0 +1,121 @@
+// Off-diagonal updates of one window (Section 3.2: the accumulated
+// transformation U applied to "the relevant sections of the matrix" as
+// level-3 operations -- the left and right update tasks):
+//
+//   left   S[s:e, e:n] <- U^T S[s:e, e:n]
+//   right  S[0:s, s:e] <- S[0:s, s:e] U
+//   Q      Q[:,  s:e]  <- Q[:,  s:e]  U
+//
+// All three are the same product Y <- Y U on a tall panel Y (R x w): for the
+// right and Q updates Y is the column-major panel itself; for the left update
+// Y is its transpose, i.e. the panel read row-major (row c of Y = column c of
+// S[s:e, e:n], contiguous in memory).  A tile is BM whole rows of Y, so the
+// product is done in place.  The contraction runs on the FP64 tensor path
+// (DMMA, mma.sync m8n8k4 f64).
+//
+// Included by the per-window launch (update.cu) and by the persistent
+// scheduler (sched.cu); global loads go through L2 (ld.global.cg).
+#pragma once
+
+#include "common.cuh"
+
+namespace gbr {
+namespace upd {
+
+constexpr int BM = UPD_BM;        // panel rows per tile
+constexpr int UPD_THREADS = 256;  // 8 warps, each owning 16 output columns
+constexpr int LDY = WMAX + 4;     // padded row pitch of the Y tile in shared memory
+constexpr int LDU = WMAX + 8;     // padded row pitch of U (row k holds U[k, :])
+constexpr size_t kUpdateSmem = sizeof(double) * ((size_t)WMAX * LDU + (size_t)BM * LDY);
+
+enum Panel { PANEL_L = 0, PANEL_R = 1, PANEL_Q = 2 };
+
+__device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+// Panel geometry: element (r, k) of Y at base + r*rs + k*ks, R rows.
+__device__ __forceinline__ void panel_geom(int panel, int n, int s, int e, double* S, int ldS,
+                                           double* Q, int ldQ, double** base, long long* rs,
+                                           long long* ks, int* R) {
+    if (panel == PANEL_L) {
+        *base = S + cm(s, e, ldS);  // Y(r, k) = S[s + k, e + r]
+        *rs = ldS; *ks = 1; *R = n - e;
+    } else if (panel == PANEL_R) {
+        *base = S + cm(0, s, ldS);  // Y(r, k) = S[r, s + k]
+        *rs = 1; *ks = ldS; *R = s;
+    } else {
+        *base = Q + cm(0, s, ldQ);  // Y(r, k) = Q[r, s + k]
+        *rs = 1; *ks = ldQ; *R = n;
+    }
+}
+
+// Y rows [r0, r0 + rows) <- (Y U) rows, rows <= BM; nthreads >= UPD_THREADS
+// (warps beyond the first 8 only help loading).  If load_u is false, Us
+// already holds U (a previous tile of the same window in this CTA).
+__device__ __forceinline__ void update_tile(double* base, long long rs, long long ks, int r0,
+                                            int rows, int w, const double* __restrict__ Ug,
+                                            bool load_u, unsigned char* smem_raw) {
+    double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU
+    double* Ys = Us + WMAX * LDU;                        // BM x LDY
+    const int wp = (w + 15) & ~15;  // padded to the warp column width
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (load_u) {
+        for (int i = tid; i < wp * wp; i += nth) {
+            int k = i / wp, c = i % wp;
+            Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+        }
+    }
+    if (rs == 1) {
+        for (int i = tid; i < BM * wp; i += nth) {
+            int r = i % BM, k = i / BM;
+            Ys[r * LDY + k] = (r < rows && k < w) ? __ldcg(&base[(r0 + r) + (long long)k * ks]) : 0.0;
+        }
+    } else {
+        for (int i = tid; i < BM * wp; i += nth) {
+            int k = i % wp, r = i / wp;
+            Ys[r * LDY + k] = (r < rows && k < w) ? __ldcg(&base[(long long)(r0 + r) * rs + k]) : 0.0;
+        }
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int c0 = warp * 16;
+    if (warp < UPD_THREADS / 32 && c0 < wp) {
+        double acc[8][2][2];
+#pragma unroll
+        for (int rt = 0; rt < 8; ++rt)
+#pragma unroll
+            for (int ct = 0; ct < 2; ++ct) acc[rt][ct][0] = acc[rt][ct][1] = 0.0;
+        for (int kk = 0; kk < wp; kk += 4) {
+            double a[8], bb[2];
+#pragma unroll
+            for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LDY + kk + tig];
+#pragma unroll
+            for (int ct = 0; ct < 2; ++ct) bb[ct] = Us[(kk + tig) * LDU + c0 + ct * 8 + gid];
+#pragma unroll
+            for (int rt = 0; rt < 8; ++rt)
+#pragma unroll
+                for (int ct = 0; ct < 2; ++ct) dmma(acc[rt][ct][0], acc[rt][ct][1], a[rt], bb[ct]);
+        }
+        // write back (in place: this CTA read all of its rows before any write)
+#pragma unroll
+        for (int rt = 0; rt < 8; ++rt) {
+            int r = rt * 8 + gid;
+            if (r >= rows) continue;
+#pragma unroll
+            for (int ct = 0; ct < 2; ++ct)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    int k = c0 + ct * 8 + tig * 2 + v;
+                    if (k < w) __stcg(&base[(long long)(r0 + r) * rs + (long long)k * ks], acc[rt][ct][v]);
+                }
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace upd
+}  // namespace gbr

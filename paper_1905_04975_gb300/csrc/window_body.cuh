@@ -1,0 +1,605 @@
+// Window task: reorders the selected blocks inside one diagonal window of
+// S and accumulates the window's orthogonal transformation U (Section 3.2,
+// Fig. 1b; the "window task" that outputs updated tiles and an accumulator).
+//
+// One CTA owns one window [s, e) of width w <= WMAX.  The window of S lives
+// in shared memory in packed upper-Hessenberg column order (column c keeps
+// rows 0..c+1), U (w x w, starting at the identity) in dense column order.
+//
+// The swaps are organised in parallel steps instead of one at a time: in a
+// step, every selected block whose upper neighbour is an unselected block
+// swaps with it.  Such swaps touch disjoint index ranges, so their left
+// transformations (rows) and right transformations (columns) commute and are
+// applied concurrently; the result is the same stable partition as moving
+// blocks one by one, reached in about w steps instead of m (w - m) swaps on
+// the critical path.  A rejected swap leaves the window unchanged and marks
+// the block stuck: it never moves again and later selected blocks stop below
+// it.
+//
+// Included by the per-window launch (window.cu) and by the persistent
+// scheduler (sched.cu).  Global loads go through L2 (ld.global.cg): in a
+// persistent launch other CTAs write S between this CTA's tasks.
+#pragma once
+
+#include "common.cuh"
+#include "swap_math.cuh"
+
+#include <float.h>
+
+namespace gbr {
+namespace win {
+
+constexpr int WIN_THREADS = 512;
+constexpr int MAXSW = WMAX / 2;  // at most one swap per two positions
+
+__device__ __forceinline__ int poff(int c) { return (c * (c + 3)) >> 1; }
+
+
+
+// Edge rows of a window that belong to a 2x2 block cut by the window
+// boundary (possible only after a rejected swap made the plan stale) are
+// walls: nothing swaps with them and they do not move.
+constexpr uint8_t SEL_WALL = 3;
+
+// ---------------------------------------------------------------------------
+// 2|2 swap by 16 lanes.  The sequential part (Sylvester elimination with
+// complete pivoting, the two reflectors) is computed redundantly by every
+// lane -- an FP64 instruction costs the same for 1 or 16 lanes -- and the
+// 4x4 products (Qs, Qs^T D Qs, the strong test) are lane-parallel: lane l of
+// the half-warp owns entry (r, c) = (l & 3, l >> 2).  No re-standardization
+// (done at the end of the window).  Returns false if the fast path cannot
+// decide; the caller then runs the full transform.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sel4(int i, double a0, double a1, double a2, double a3) {
+    return i == 0 ? a0 : (i == 1 ? a1 : (i == 2 ? a2 : a3));
+}
+
+// T11 X - X T22 = T12 for 2x2 blocks of D (ld 4), elimination on the 4x4
+// Kronecker system with complete pivoting; registers only.
+__device__ __forceinline__ bool sylv22_regs(const double* D, double* X) {
+    double K[4][4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = r & 1, kk = r >> 1;
+        b[r] = D[(2 + kk) * 4 + i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int l = c & 1, mm = c >> 1;
+            double v = (kk == mm) ? D[l * 4 + i] : 0.0;
+            if (i == l) v -= D[(2 + kk) * 4 + 2 + mm];
+            K[r][c] = v;
+        }
+    }
+    unsigned long long kmx = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            unsigned long long a = abs_bits(K[r][c]);
+            kmx = a > kmx ? a : kmx;
+        }
+    const double smin = fmax(DBL_EPSILON * bits_double(kmx), DBL_MIN);
+    int perm = 0x3210;  // perm nibble c = original unknown now in column c
+    double rp[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        unsigned long long best = 0;
+        int pr = s, pc = s;
+#pragma unroll
+        for (int r = s; r < 4; ++r)
+#pragma unroll
+            for (int c = s; c < 4; ++c) {
+                unsigned long long a = abs_bits(K[r][c]);
+                if (a > best) { best = a; pr = r; pc = c; }
+            }
+#pragma unroll
+        for (int r = s + 1; r < 4; ++r)
+            if (pr == r) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { double t = K[s][c]; K[s][c] = K[r][c]; K[r][c] = t; }
+                double t = b[s]; b[s] = b[r]; b[r] = t;
+            }
+#pragma unroll
+        for (int c = s + 1; c < 4; ++c)
+            if (pc == c) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) { double t = K[r][s]; K[r][s] = K[r][c]; K[r][c] = t; }
+                int ns = (perm >> (4 * s)) & 15, nc = (perm >> (4 * c)) & 15;
+                perm &= ~((15 << (4 * s)) | (15 << (4 * c)));
+                perm |= (nc << (4 * s)) | (ns << (4 * c));
+            }
+        double piv = K[s][s];
+        if (abs_bits(piv) < abs_bits(smin)) piv = smin;
+        rp[s] = 1.0 / piv;
+#pragma unroll
+        for (int r = s + 1; r < 4; ++r) {
+            const double f = K[r][s] * rp[s];
+#pragma unroll
+            for (int c = s + 1; c < 4; ++c) K[r][c] = fma(-f, K[s][c], K[r][c]);
+            b[r] = fma(-f, b[s], b[r]);
+        }
+    }
+    double y[4];
+#pragma unroll
+    for (int s = 3; s >= 0; --s) {
+        double acc = b[s];
+#pragma unroll
+        for (int c = s + 1; c < 4; ++c) acc = fma(-K[s][c], y[c], acc);
+        y[s] = acc * rp[s];
+    }
+    unsigned long long ym = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ym = abs_bits(y[c]) > ym ? abs_bits(y[c]) : ym;
+    if (!(ym < 0x7ff0000000000000ULL)) return false;  // inf or nan
+    // un-permute: X[perm(c)] = y[c]   (X column-major 2x2, index i + 2k)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        double v = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (((perm >> (4 * c)) & 15) == t) v = y[c];
+        X[t] = v;
+    }
+    return true;
+}
+
+// Returns true (and this lane's Z and Dn entries) if the fast path decided
+// the swap and accepted it; *fallback is set when the full transform must run.
+__device__ __forceinline__ bool swap22_halfwarp(const double* __restrict__ Sp, int ja, int l,
+                                                unsigned hmask, int hbase, bool strong,
+                                                double* zrc, double* dnrc, bool* fallback) {
+    const int r = l & 3, c = l >> 2;
+    double D[16];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+            D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
+    *fallback = false;
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) mx = abs_bits(D[i]) > mx ? abs_bits(D[i]) : mx;
+    const double thresh = fmax(10.0 * DBL_EPSILON * bits_double(mx), DBL_MIN);
+    const unsigned long long tb = abs_bits(thresh);
+    double X[4];
+    if (!sylv22_regs(D, X)) { *fallback = true; return false; }
+    // reflector 1 on column 0 of [-X; I]: (-x00, -x10, 1, 0)
+    const double a0 = -X[0], x1 = -X[1];
+    const double sig1 = fma(x1, x1, 1.0);
+    const double n1 = sqrt(fma(a0, a0, sig1));
+    const double be1 = a0 >= 0.0 ? -n1 : n1;
+    const double d1 = a0 - be1, rd1 = 1.0 / d1;
+    const double v10 = 1.0, v11 = x1 * rd1, v12 = rd1;  // v13 = 0
+    const double t1 = -d1 / be1;
+    // H1 applied to column 1 of [-X; I]: (-x01, -x11, 0, 1)
+    const double m0 = -X[2], m1 = -X[3], m2 = 0.0, m3 = 1.0;
+    const double w1 = fma(v12, m2, fma(v11, m1, v10 * m0)) * t1;
+    const double q1 = fma(-w1, v11, m1), q2 = fma(-w1, v12, m2), q3 = m3;
+    (void)m0;
+    // reflector 2 on (q1, q2, q3)
+    const double sig2 = fma(q3, q3, q2 * q2);
+    double u1 = 1.0, u2 = 0.0, u3 = 0.0, t2 = 0.0;
+    if (sig2 != 0.0) {
+        const double n2 = sqrt(fma(q1, q1, sig2));
+        const double be2 = q1 >= 0.0 ? -n2 : n2;
+        const double d2 = q1 - be2, rd2 = 1.0 / d2;
+        u2 = q2 * rd2;
+        u3 = q3 * rd2;
+        t2 = -d2 / be2;
+    }
+    // Qs = (I - t1 v v^T)(I - t2 u u^T), v = (1, v11, v12, 0), u = (0, 1, u2, u3)
+    const double vu = fma(v12, u2, v11 * u1);
+    const double vr = sel4(r, v10, v11, v12, 0.0), vc = sel4(c, v10, v11, v12, 0.0);
+    const double ur = sel4(r, 0.0, u1, u2, u3), uc = sel4(c, 0.0, u1, u2, u3);
+    double qs = (r == c) ? 1.0 : 0.0;
+    qs = fma(-t1 * vr, vc, qs);
+    qs = fma(-t2 * ur, uc, qs);
+    qs = fma(t1 * t2 * vu * vr, uc, qs);
+    // T = Qs^T D: T[r][c] = sum_a Qs[a][r] D[a][c]
+    double dcol0 = sel4(c, D[0], D[4], D[8], D[12]), dcol1 = sel4(c, D[1], D[5], D[9], D[13]);
+    double dcol2 = sel4(c, D[2], D[6], D[10], D[14]), dcol3 = sel4(c, D[3], D[7], D[11], D[15]);
+    double T = 0.0;
+    T = fma(__shfl_sync(hmask, qs, hbase + 0 + 4 * r), dcol0, T);
+    T = fma(__shfl_sync(hmask, qs, hbase + 1 + 4 * r), dcol1, T);
+    T = fma(__shfl_sync(hmask, qs, hbase + 2 + 4 * r), dcol2, T);
+    T = fma(__shfl_sync(hmask, qs, hbase + 3 + 4 * r), dcol3, T);
+    // Dt = T Qs: Dt[r][c] = sum_b T[r][b] Qs[b][c]
+    double Dt = 0.0;
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb)
+        Dt = fma(__shfl_sync(hmask, T, hbase + r + 4 * bb), __shfl_sync(hmask, qs, hbase + bb + 4 * c),
+                 Dt);
+    // weak test on the lower-left 2x2 block
+    const bool low = (r >= 2 && c < 2);
+    const bool weak_bad = low && abs_bits(Dt) > tb;
+    if (__any_sync(hmask, weak_bad)) { *fallback = true; return false; }
+    const double Dt0 = low ? 0.0 : Dt;
+    if (strong) {
+        // P = Qs Dt0: P[r][b] = sum_a Qs[r][a] Dt0[a][b]
+        double P = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            P = fma(__shfl_sync(hmask, qs, hbase + r + 4 * a), __shfl_sync(hmask, Dt0, hbase + a + 4 * c),
+                    P);
+        // E = P Qs^T - D: E[r][c] = sum_b P[r][b] Qs[c][b] - D[r][c]
+        double E = 0.0;
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb)
+            E = fma(__shfl_sync(hmask, P, hbase + r + 4 * bb), __shfl_sync(hmask, qs, hbase + c + 4 * bb),
+                    E);
+        const double drc = sel4(r, dcol0, dcol1, dcol2, dcol3);
+        E -= drc;
+        if (__any_sync(hmask, abs_bits(E) > tb)) { *fallback = true; return false; }
+    }
+    *zrc = qs;
+    *dnrc = Dt0;
+    return true;
+}
+
+// Swap types of a step, each handled by its own warps (FP64 issue costs the
+// same for 1 or 32 active lanes, so lanes of a warp must share one code path):
+//   T_11: 1x1|1x1 (Givens), T_3: 1x2 or 2x1 (k = 3), T_22: 2x2|2x2 (k = 4).
+constexpr int T_11 = 0, T_3 = 1, T_22 = 2;
+
+// Warps of a CTA are spread over the SM's four sub-partitions by id % 4; the
+// types go to different sub-partitions so their FP64 streams do not queue
+// behind each other: 2x2|2x2 on partitions 0 and 1, k = 3 on 2, 1x1 on 3.
+__device__ __forceinline__ int type_of_warp(int warp) {
+    int part = warp & 3;
+    return part <= 1 ? T_22 : (part == 2 ? T_3 : T_11);
+}
+// rank of this warp among the warps serving its type
+__device__ __forceinline__ int rank_of_warp(int warp) {
+    int part = warp & 3;
+    return part <= 1 ? (warp >> 2) * 2 + part : (warp >> 2);
+}
+
+// Dynamic shared memory needed by window_body.
+constexpr size_t kWindowSmem = sizeof(double) * ((size_t)WMAX * WMAX +
+                                                 (size_t)((WMAX * (WMAX + 3)) / 2) +
+                                                 (size_t)MAXSW * 16) +
+                               sizeof(int) * 3 * MAXSW + 2 * WMAX;
+
+__device__ __forceinline__ void window_body(int n, double* __restrict__ S, int ldS, int s0, int w,
+                                            uint8_t* __restrict__ gsel, double* __restrict__ Ug,
+                                            int strong, DevCounters* __restrict__ ctr,
+                                            unsigned char* smem_raw) {
+    double* U = reinterpret_cast<double*>(smem_raw);           // w*w
+    double* Sp = U + WMAX * WMAX;                               // packed window
+    double* Zs = Sp + poff(WMAX);                               // MAXSW * 16
+    int* swj = reinterpret_cast<int*>(Zs + MAXSW * 16);         // per slot: start j
+    int* swk = swj + MAXSW;                                     // per slot: k (0 = rejected)
+    int* swp = swk + MAXSW;                                     // per slot: p (or stuck block)
+    uint8_t* bst = reinterpret_cast<uint8_t*>(swp + MAXSW);
+    uint8_t* sel = bst + WMAX;
+    __shared__ int nsw, nrej, nacc;
+    unsigned long long wflops = 0;   // meaningful in lanes 0 of warps 0..2, summed below
+    __shared__ int tcnt[3];
+    __shared__ int tlist[3][MAXSW];     // slots per type
+    __shared__ int ksl[3][MAXSW];       // slots with k = 2, 3, 4 (accepted only)
+    __shared__ int kcnt[3];
+    __shared__ int kpre_l[3][MAXSW + 1];  // prefix sums of left-apply columns per k group
+    __shared__ int kpre_r[3][MAXSW + 1];  // prefix sums of right-apply rows (S rows + U rows)
+
+    const int tid = threadIdx.x;
+    const int nth = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    // load: packed window of S, selection, U = I
+    for (int c = 0; c < w; ++c) {
+        int rows = min(c + 2, w);
+        for (int r = tid; r < rows; r += nth)
+            Sp[poff(c) + r] = __ldcg(&S[cm(s0 + r, s0 + c, ldS)]);
+    }
+    for (int i = tid; i < w * w; i += nth) U[i] = ((i % w) == (i / w)) ? 1.0 : 0.0;
+    for (int i = tid; i < w; i += nth) sel[i] = __ldcg(&gsel[s0 + i]);
+    __shared__ int wall_top, wall_bot;
+    if (tid == 0) {
+        nrej = 0;
+        nacc = 0;
+        wall_top = s0 > 0 && __ldcg(&S[cm(s0, s0 - 1, ldS)]) != 0.0;
+        wall_bot = s0 + w < n && __ldcg(&S[cm(s0 + w, s0 + w - 1, ldS)]) != 0.0;
+    }
+    __syncthreads();
+    if (tid == 0 && wall_top) sel[0] = SEL_WALL;
+    if (tid == 0 && wall_bot) sel[w - 1] = SEL_WALL;
+
+    // Every accepted swap moves a selected block up and every rejected one
+    // retires a block, so the loop ends within w * w steps; the cap only
+    // guards against a logic error (reported through the counters).
+    bool final_pass = false;
+    for (int iter = 0;; ++iter) {
+        __syncthreads();
+        if (iter > 4 * WMAX * WMAX) {
+            if (tid == 0) atomicAdd(&ctr->step_overflow, 1);
+            break;
+        }
+        for (int i = tid; i < w; i += nth)
+            bst[i] = (i == 0) || (Sp[poff(i - 1) + i] == 0.0);
+        if (tid < 3) { tcnt[tid] = 0; kcnt[tid] = 0; }
+        if (tid == 0) nsw = 0;
+        __syncthreads();
+        // --- phase A1: find the swaps of this step (integer work only).  After the
+        // last swap, one more pass lists the 2x2 blocks whose standard form
+        // has to be restored (the fast swap paths leave it to this pass).
+        if (!final_pass) {
+            for (int t = tid; t < w; t += nth) {
+                if (t == 0 || !bst[t] || sel[t] != SEL_YES) continue;
+                int ja = bst[t - 1] ? t - 1 : t - 2;
+                if (sel[ja] != SEL_NO) continue;
+                int p = t - ja;
+                int q = (t + 1 < w && !bst[t + 1]) ? 2 : 1;
+                int slot = atomicAdd(&nsw, 1);
+                swj[slot] = ja;
+                swk[slot] = p + q;
+                swp[slot] = p;
+                int ty = (p + q == 2) ? T_11 : (p + q == 3 ? T_3 : T_22);
+                tlist[ty][atomicAdd(&tcnt[ty], 1)] = slot;
+            }
+        } else {
+            for (int t = tid; t + 1 < w; t += nth) {
+                if (!bst[t] || bst[t + 1]) continue;  // 2x2 block at t
+                double m00 = Sp[poff(t) + t], m10 = Sp[poff(t) + t + 1];
+                double m01 = Sp[poff(t + 1) + t], m11 = Sp[poff(t + 1) + t + 1];
+                if (m00 == m11 && m01 * m10 < 0.0) continue;  // already standard
+                int slot = atomicAdd(&nsw, 1);
+                swj[slot] = t;
+                swk[slot] = 2;
+                swp[slot] = -1;   // marks a standardization rotation
+                tlist[T_11][atomicAdd(&tcnt[T_11], 1)] = slot;
+            }
+        }
+        __syncthreads();
+        const int ns = nsw;
+        if (ns == 0) {
+            if (final_pass) break;
+            final_pass = true;
+            continue;
+        }
+        // --- phase A2: transforms, type-uniform warps
+        {
+            const int ty = type_of_warp(warp);
+            const int rank = rank_of_warp(warp);
+            if (ty == T_22) {
+                // two 2|2 swaps per warp, one per half-warp
+                const int h = lane >> 4, l = lane & 15;
+                const unsigned hmask = h ? 0xffff0000u : 0x0000ffffu;
+                const int nw = (WIN_THREADS / 32) / 2;
+                for (int i = rank * 2 + h; i < tcnt[T_22]; i += nw * 2) {
+                    const int slot = tlist[T_22][i];
+                    const int ja = swj[slot];
+                    double zrc = 0.0, dnrc = 0.0;
+                    bool fb = false;
+                    bool ok = swap22_halfwarp(Sp, ja, l, hmask, h * 16, strong != 0, &zrc, &dnrc, &fb);
+                    const int r = l & 3, c = l >> 2;
+                    if (ok) {
+                        Zs[slot * 16 + c * 4 + r] = zrc;
+                        if (r <= c + 1) Sp[poff(ja + c) + ja + r] = dnrc;
+                        if (l == 0) {
+                            ksl[2][atomicAdd(&kcnt[2], 1)] = slot;
+                            atomicAdd(&nacc, 1);
+                        }
+                    } else if (l == 0) {
+                        double D[16], Zl[16], Dn[16];
+                        for (int cc = 0; cc < 4; ++cc)
+                            for (int rr = 0; rr < 4; ++rr)
+                                D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
+                        if (swap_transform(D, 2, 2, strong != 0, Zl, Dn)) {
+                            for (int cc = 0; cc < 4; ++cc)
+                                for (int rr = 0; rr <= min(cc + 1, 3); ++rr)
+                                    Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
+                            for (int e = 0; e < 16; ++e) Zs[slot * 16 + e] = Zl[e];
+                            ksl[2][atomicAdd(&kcnt[2], 1)] = slot;
+                            atomicAdd(&nacc, 1);
+                        } else {
+                            swk[slot] = 0;
+                            swp[slot] = ja + 2;
+                            atomicAdd(&nrej, 1);
+                        }
+                    }
+                    __syncwarp(hmask);
+                }
+            } else {
+                const int nwarps_ty = (WIN_THREADS / 32) / 4;
+                for (int i = rank * 32 + lane; i < tcnt[ty]; i += nwarps_ty * 32) {
+                    const int slot = tlist[ty][i];
+                    const int ja = swj[slot], p = swp[slot], k = swk[slot], q = k - p;
+                    double* Z = &Zs[slot * 16];
+                    bool ok;
+                    if (ty == T_11 && p < 0) {
+                        // restore the standard form of the 2x2 block at ja
+                        double m[16];
+                        m[0] = Sp[poff(ja) + ja];
+                        m[1] = Sp[poff(ja) + ja + 1];
+                        m[4] = Sp[poff(ja + 1) + ja];
+                        m[5] = Sp[poff(ja + 1) + ja + 1];
+                        double cs, sn;
+                        standardize2(m, &cs, &sn);
+                        Sp[poff(ja) + ja] = m[0];
+                        Sp[poff(ja) + ja + 1] = m[1];
+                        Sp[poff(ja + 1) + ja] = m[4];
+                        Sp[poff(ja + 1) + ja + 1] = m[5];
+                        Z[0] = cs; Z[1] = sn; Z[4] = -sn; Z[5] = cs;
+                        ok = true;
+                    } else if (ty == T_11) {
+                        // Givens rotation from (t12, t22 - t11); always accepted
+                        double t11 = Sp[poff(ja) + ja], t12 = Sp[poff(ja + 1) + ja];
+                        double t22 = Sp[poff(ja + 1) + ja + 1];
+                        double c = 1.0, sn = 0.0, n12 = t12;
+                        if (t11 != t22) {
+                            double d = t22 - t11;
+                            double rh = 1.0 / sqrt(fma(t12, t12, d * d));
+                            c = t12 * rh;
+                            sn = d * rh;
+                            double r12 = fma(c, t12, sn * t22);
+                            n12 = fma(r12, c, -(c * t11) * sn);
+                        }
+                        Z[0] = c; Z[1] = sn; Z[4] = -sn; Z[5] = c;
+                        Sp[poff(ja) + ja] = t22;
+                        Sp[poff(ja) + ja + 1] = 0.0;
+                        Sp[poff(ja + 1) + ja] = n12;
+                        Sp[poff(ja + 1) + ja + 1] = t11;
+                        ok = true;
+                    } else {
+                        double D[16], Zl[16], Dn[16];
+                        for (int cc = 0; cc < 3; ++cc)
+                            for (int rr = 0; rr < 3; ++rr)
+                                D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
+                        ok = swap3_fast(D, p, strong != 0, Zl, Dn) ||
+                             swap_transform(D, p, q, strong != 0, Zl, Dn);
+                        if (ok) {
+                            for (int cc = 0; cc < 3; ++cc)
+                                for (int rr = 0; rr <= min(cc + 1, 2); ++rr)
+                                    Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
+                            for (int e = 0; e < 16; ++e) Z[e] = Zl[e];
+                        }
+                    }
+                    if (ok) {
+                        ksl[k - 2][atomicAdd(&kcnt[k - 2], 1)] = slot;
+                        if (p >= 0) atomicAdd(&nacc, 1);
+                    } else {
+                        swk[slot] = 0;
+                        swp[slot] = ja + p;   // the stuck (selected) block
+                        atomicAdd(&nrej, 1);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // prefix sums of the apply work per k group (one warp per group)
+        if (warp < 3) {
+            const int g = warp, cnt = kcnt[g];
+            int runl = 0, runr = 0;
+            for (int base = 0; base < cnt; base += 32) {
+                int i = base + lane;
+                int nl = 0, nr = 0;
+                if (i < cnt) {
+                    int slot = ksl[g][i];
+                    nl = w - swj[slot] - swk[slot];
+                    nr = swj[slot] + w;
+                }
+                int il = nl, ir = nr;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int a = __shfl_up_sync(0xffffffffu, il, o);
+                    int b2 = __shfl_up_sync(0xffffffffu, ir, o);
+                    if (lane >= o) { il += a; ir += b2; }
+                }
+                if (i < cnt) { kpre_l[g][i + 1] = runl + il; kpre_r[g][i + 1] = runr + ir; }
+                runl += __shfl_sync(0xffffffffu, il, 31);
+                runr += __shfl_sync(0xffffffffu, ir, 31);
+            }
+            if (lane == 0) {
+                kpre_l[g][0] = 0;
+                kpre_r[g][0] = 0;
+                wflops += 2ull * (g + 2) * (g + 2) * (unsigned long long)(runl + runr);
+            }
+        }
+        __syncthreads();
+        // --- phase B: left transformations, rows [j, j+k) x columns [j+k, w),
+        // compacted per k so that every lane of a warp runs the same k
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const int k = g + 2, cnt = kcnt[g], total = kpre_l[g][cnt];
+            for (int it = tid; it < total; it += nth) {
+                int lo = 0, hi = cnt - 1;   // last i with kpre_l[g][i] <= it
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (kpre_l[g][mid] <= it) lo = mid; else hi = mid - 1;
+                }
+                const int slot = ksl[g][lo];
+                const int j = swj[slot];
+                const int c = j + k + (it - kpre_l[g][lo]);
+                const double* Z = &Zs[slot * 16];
+                double x[4], y[4];
+#pragma unroll
+                for (int r = 0; r < k; ++r) x[r] = Sp[poff(c) + j + r];
+#pragma unroll
+                for (int r = 0; r < k; ++r) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int i = 0; i < k; ++i) acc = fma(Z[r * 4 + i], x[i], acc);
+                    y[r] = acc;
+                }
+#pragma unroll
+                for (int r = 0; r < k; ++r) Sp[poff(c) + j + r] = y[r];
+            }
+        }
+        __syncthreads();
+        // --- phase C: right transformations, columns [j, j+k) of S rows [0, j)
+        // and of U rows [0, w)
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const int k = g + 2, cnt = kcnt[g], total = kpre_r[g][cnt];
+            for (int it = tid; it < total; it += nth) {
+                int lo = 0, hi = cnt - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (kpre_r[g][mid] <= it) lo = mid; else hi = mid - 1;
+                }
+                const int slot = ksl[g][lo];
+                const int j = swj[slot];
+                const int rr = it - kpre_r[g][lo];
+                const double* Z = &Zs[slot * 16];
+                double x[4], y[4];
+                const bool inS = rr < j;
+                const int r = inS ? rr : rr - j;
+#pragma unroll
+                for (int i = 0; i < k; ++i) x[i] = inS ? Sp[poff(j + i) + r] : U[(j + i) * w + r];
+#pragma unroll
+                for (int c = 0; c < k; ++c) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int i = 0; i < k; ++i) acc = fma(x[i], Z[c * 4 + i], acc);
+                    y[c] = acc;
+                }
+                if (inS) {
+#pragma unroll
+                    for (int c = 0; c < k; ++c) Sp[poff(j + c) + r] = y[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < k; ++c) U[(j + c) * w + r] = y[c];
+                }
+            }
+        }
+        __syncthreads();
+        // --- phase D: move the selection flags with the blocks
+        for (int sw = tid; sw < ns; sw += nth) {
+            int j = swj[sw], k = swk[sw];
+            if (k == 0) {
+                sel[swp[sw]] = SEL_STUCK;
+                continue;
+            }
+            int p = swp[sw], q = k - p;
+            if (p < 0) continue;   // standardization: blocks do not move
+            for (int i = 0; i < q; ++i) sel[j + i] = SEL_YES;
+            for (int i = q; i < k; ++i) sel[j + i] = SEL_NO;
+        }
+        // a stuck 2x2 block is flagged on both of its rows
+        __syncthreads();
+        for (int t = tid; t + 1 < w; t += nth)
+            if (sel[t] == SEL_STUCK && Sp[poff(t) + t + 1] != 0.0) sel[t + 1] = SEL_STUCK;
+    }
+    __shared__ unsigned long long wfl_sum;
+    if (tid == 0) wfl_sum = 0;
+    __syncthreads();
+    if (lane == 0 && warp < 3) atomicAdd(&wfl_sum, wflops);
+    __syncthreads();
+    wflops = wfl_sum;
+    // store: window of S, selection, U
+    for (int c = 0; c < w; ++c) {
+        int rows = min(c + 2, w);
+        for (int r = tid; r < rows; r += nth)
+            S[cm(s0 + r, s0 + c, ldS)] = Sp[poff(c) + r];
+    }
+    for (int i = tid; i < w; i += nth)
+        if (sel[i] != SEL_WALL) gsel[s0 + i] = sel[i];
+    for (int i = tid; i < w * w; i += nth) Ug[i] = U[i];
+    if (tid == 0) {
+        atomicAdd(&ctr->swaps, (unsigned long long)nacc);
+        atomicAdd(&ctr->rejected, (unsigned long long)nrej);
+        atomicAdd(&ctr->win_flops, wflops);
+    }
+}
+
+}  // namespace win
+}  // namespace gbr

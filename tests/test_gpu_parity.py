@@ -223,3 +223,33 @@ def test_n4000_workload_full_parity(gbr):
     r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=128, chain=64)
     assert r.status == 0 and ref["status"] == 0
     check(S, Q, sel, r, Sg, Qg, ref)
+
+
+@pytest.mark.parametrize("name,w,m", [("n400", 128, 64), ("n400", 32, 14), ("ragged", 64, 30)])
+def test_persistent_matches_sequential(gbr, name, w, m):
+    """The persistent scheduler orders every pair of overlapping tasks as the
+    program order does, so it computes exactly what the one-window-at-a-time
+    schedule computes."""
+    if name == "n400":
+        S, Q, sel = si.config("n400")
+    else:
+        S, Q, sel = si.reorder_problem(777, 5, select_frac=0.45, q="householder")
+    rp, Sp_, Qp_ = run_gpu(gbr, S, Q, sel, window=w, chain=m, sched="persistent")
+    rs, Ss_, Qs_ = run_gpu(gbr, S, Q, sel, window=w, chain=m, sched="sequential")
+    assert rp.status == 0 and rs.status == 0
+    assert rp.stats.tasks > rp.stats.windows
+    assert np.array_equal(Sp_, Ss_) and np.array_equal(Qp_, Qs_)
+
+
+def test_scheduler_wait_times_out_and_context_survives(gbr):
+    """A predecessor that never finishes (host-side injection) makes the
+    bounded device wait run out: the call returns GBR_ERR_TIMEOUT instead of
+    hanging, and the next call on the same context works."""
+    S, Q, sel = si.config("n400")
+    with pytest.raises(gbr.GbrError) as ei:
+        run_gpu(gbr, S, Q, sel, inject=gbr.INJECT_STALL, wait_limit_ms=300)
+    assert ei.value.status == gbr.ERR_TIMEOUT
+    ref = oracle.reorder(S, Q, sel)
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel)
+    assert r.status == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
