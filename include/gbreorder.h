@@ -70,8 +70,9 @@ typedef struct gbr_opts {
     int strong_test;   /* 1: weak + strong stability test       (default 1)   */
     int on_reject;     /* GBR_ON_REJECT_CONTINUE                (default)     */
     int validate;      /* 1: check the standard-form input      (default 1)   */
-    int timing;        /* 1: time the window and update kernels with CUDA
-                          events into gbr_stats (small overhead) (default 0)  */
+    int timing;        /* 1: time the kernels with CUDA events into gbr_stats;
+                          2: also record a per-task timeline of the persistent
+                          scheduler (gbr_last_trace)              (default 0)  */
     int sched;         /* GBR_SCHED_PERSISTENT (default) or GBR_SCHED_SEQUENTIAL */
     int inject;        /* fault injection for tests: GBR_INJECT_STALL makes one
                           scheduler task wait for a predecessor that never
@@ -99,6 +100,9 @@ typedef struct gbr_stats {
     double ms_sched;      /* persistent-scheduler kernel time (opts.timing)      */
     double win_flops;     /* FP64 flops of the in-window updates of accepted swaps */
     long long tasks;      /* scheduler tasks (window tasks + update tiles)       */
+    double sched_cp_ms;   /* longest dependence path of the task graph under the
+                             scheduler's duration model                          */
+    double sched_sim_ms;  /* makespan of the scheduler's list-scheduling model   */
 } gbr_stats;
 
 /* Fill *opts with the defaults. */
@@ -188,6 +192,17 @@ int gbr_reorder_noalloc(int n, double *S, int ldS, double *Q, int ldQ, const int
  */
 int gbr_plan(int n, const unsigned char *sub, const int *select, int window, int chain,
              int with_q, int *windows, int max_windows, int *chains, double *upd_flops);
+
+/*
+ * Timeline of the last persistent-scheduler launch made with opts.timing = 2
+ * (tracing; no counterpart in the paper).  Writes up to max_tasks records of
+ * 8 long longs each, in queue order: task kind (0 window, 1 left tile,
+ * 2 right tile, 3 Q tile), window index, first panel row, panel rows, SM id,
+ * time the CTA took the task, time it started executing (its predecessors
+ * had finished), time it ended (nanoseconds of the GPU global timer).
+ * Returns the number of records available.  `out` may be NULL.
+ */
+int gbr_last_trace(long long *out, int max_tasks);
 
 /* Human-readable text for a status code (static storage). */
 const char *gbr_status_string(int status);

@@ -49,7 +49,8 @@ class GbrStats(ctypes.Structure):
                 ("launches", ctypes.c_longlong), ("upd_flops", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_window", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("ms_sched", ctypes.c_double),
-                ("win_flops", ctypes.c_double), ("tasks", ctypes.c_longlong)]
+                ("win_flops", ctypes.c_double), ("tasks", ctypes.c_longlong),
+                ("sched_cp_ms", ctypes.c_double), ("sched_sim_ms", ctypes.c_double)]
 
 
 # Every symbol the header declares, with (restype, argtypes).
@@ -67,6 +68,7 @@ SYMBOLS = {
     "gbr_last_error": (ctypes.c_char_p, []),
     "gbr_release": (None, []),
     "gbr_version": (ctypes.c_int, []),
+    "gbr_last_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "gbr_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte), _ip, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _ip, _dp]),
 }
@@ -128,7 +130,7 @@ def make_opts(window=None, chain=None, precision=None, slices=None, strong=None,
     if validate is not None:
         o.validate = 1 if validate else 0
     if timing is not None:
-        o.timing = 1 if timing else 0
+        o.timing = int(timing) if not isinstance(timing, bool) else int(timing)
     if sched is not None:
         o.sched = {"persistent": SCHED_PERSISTENT, "sequential": SCHED_SEQUENTIAL}.get(sched, sched)
     if inject is not None:
@@ -279,3 +281,14 @@ def plan(sub, select, window=128, chain=64, with_q=True):
                        window, chain, 1 if with_q else 0, out.ctypes.data_as(_ip), cnt,
                        ctypes.byref(ch), ctypes.byref(fl))
     return out[:2 * cnt].reshape(cnt, 2), ch.value, fl.value
+
+
+def last_trace() -> np.ndarray:
+    """Per-task timeline of the last persistent launch made with timing=2:
+    int64 array (tasks x 8): kind, window, y0, rows, sm, take_ns, start_ns, end_ns."""
+    lib = load()
+    nt = lib.gbr_last_trace(None, 0)
+    out = np.zeros((max(nt, 0), 8), dtype=np.int64)
+    if nt > 0:
+        lib.gbr_last_trace(out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt)
+    return out

@@ -27,6 +27,8 @@
 namespace gbr {
 
 static thread_local std::string g_last_error;
+static std::vector<long long> g_trace;  // last traced persistent launch, 8 words per task
+static double g_last_cp_us = 0.0, g_last_sim_us = 0.0;  // last schedule: critical path, simulated
 
 static int cuda_fail(cudaError_t e, const char* what) {
     char buf[256];
@@ -245,31 +247,48 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
                 r = re;
             }
     }
+    // Dependences in program order on exact rectangles.  Each cell keeps two
+    // lists, the tasks that mix rows (window, left) and those that mix columns
+    // (window, right); pruning by coverage stays within one list, where every
+    // older overlapping task precedes the covering one.
     const int CB = UPD_BM;
     const int nc = (n + CB - 1) / CB;
-    std::vector<std::vector<int>> cells[2];
-    cells[0].resize((size_t)nc * nc);
-    if (withQ) cells[1].resize((size_t)nc * nc);
+    std::vector<std::vector<int>> lrow, lcol;   // S cells: row-mixing / column-mixing tasks
+    std::vector<std::vector<int>> lq;           // Q cells
+    lrow.resize((size_t)nc * nc);
+    lcol.resize((size_t)nc * nc);
+    if (withQ) lq.resize((size_t)nc * nc);
     std::vector<int> stamp(T.size(), -1);
+    auto scan = [&](std::vector<int>& L, const Rect& X, int t) {
+        for (int k = (int)L.size() - 1; k >= 0; --k) {
+            const int u = L[k];
+            const Rect& U = T[u].rc;
+            if (!rects_overlap(U, X)) continue;
+            if (stamp[u] != t) {
+                stamp[u] = t;
+                edges.push_back({u, t});
+            }
+            if (rect_covers(U, X)) break;
+        }
+    };
     for (int t = 0; t < (int)T.size(); ++t) {
         const Rect R = T[t].rc;
-        const int m = T[t].mat;
+        const int kind = T[t].kind;
         for (int cr = R.r0 / CB; cr * CB < R.r1; ++cr)
             for (int cc = R.c0 / CB; cc * CB < R.c1; ++cc) {
                 const Rect cell{cr * CB, std::min(n, (cr + 1) * CB), cc * CB, std::min(n, (cc + 1) * CB)};
                 const Rect X = rect_isect(R, cell);
-                std::vector<int>& L = cells[m][(size_t)cr * nc + cc];
-                for (int k = (int)L.size() - 1; k >= 0; --k) {
-                    const int u = L[k];
-                    const Rect& U = T[u].rc;
-                    if (!rects_overlap(U, X)) continue;
-                    if (stamp[u] != t) {
-                        stamp[u] = t;
-                        edges.push_back({u, t});
-                    }
-                    if (rect_covers(U, X)) break;
+                const size_t ci = (size_t)cr * nc + cc;
+                if (kind == TASK_Q) {
+                    scan(lq[ci], X, t);
+                    lq[ci].push_back(t);
+                    continue;
                 }
-                L.push_back(t);
+                // all S tasks order against every overlapping earlier S task
+                scan(lrow[ci], X, t);
+                scan(lcol[ci], X, t);
+                if (kind == TASK_W || kind == TASK_L) lrow[ci].push_back(t);
+                if (kind == TASK_W || kind == TASK_R) lcol[ci].push_back(t);
             }
     }
     std::sort(edges.begin(), edges.end());
@@ -287,17 +306,50 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
     for (auto& ed : edges) G.succ[fill[ed.first]++] = ed.second;
 }
 
+// Program order for the persistent schedule.  Two windows whose row ranges do
+// not overlap conflict only through a left update of one and a right update
+// of the other, and those commute ((U_a^T X) U_b = U_a^T (X U_b)); so any
+// order of whole windows that keeps the planner's order of every pair of
+// overlapping windows computes the same result.  Windows are taken by level
+// in the overlap graph (1 + the highest level of an earlier overlapping
+// window), which interleaves the chains like a pipeline: a chain's early
+// windows come before the previous chain's late ones, and the left/right
+// updates of different chains are ordered by when their windows run instead
+// of by chain.  Without this, each chain's deferred right updates wait for
+// the previous chain's left updates and the chains form a convoy.
+static void pipeline_order(int n, std::vector<Window>& wins) {
+    std::vector<int> cover(n, 0), level(wins.size());
+    for (size_t b = 0; b < wins.size(); ++b) {
+        int lv = 0;
+        for (int p = wins[b].s; p < wins[b].e; ++p) lv = std::max(lv, cover[p]);
+        level[b] = lv + 1;
+        for (int p = wins[b].s; p < wins[b].e; ++p) cover[p] = std::max(cover[p], lv + 1);
+    }
+    std::vector<int> idx(wins.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return level[a] < level[b]; });
+    std::vector<Window> out(wins.size());
+    for (size_t i = 0; i < idx.size(); ++i) out[i] = wins[idx[i]];
+    wins.swap(out);
+}
+
 // Queue order: a list-scheduling simulation on P processors where the ready
 // task with the longest remaining path to the end (bottom level) starts first;
 // the queue is the order of simulated start times.  Every predecessor of a
 // task starts (and finishes) before it, so it sits earlier in the queue.
-static void queue_order(const TaskGraph& G, int P, std::vector<int>& order) {
+static void queue_order(const TaskGraph& G, int P, std::vector<int>& order, double* cp_us = nullptr,
+                        double* sim_us = nullptr) {
     const int nt = (int)G.t.size();
     std::vector<double> bl(nt, 0.0);
     for (int t = nt - 1; t >= 0; --t) {
         double m = 0.0;
         for (int i = G.soff[t]; i < G.soff[t + 1]; ++i) m = std::max(m, bl[G.succ[i]]);
         bl[t] = G.t[t].dur + m;
+    }
+    if (cp_us) {
+        double m = 0.0;
+        for (int t = 0; t < nt; ++t) m = std::max(m, bl[t]);
+        *cp_us = m;
     }
     std::vector<int> indeg(G.ndeps);
     typedef std::pair<double, int> Key;
@@ -319,6 +371,7 @@ static void queue_order(const TaskGraph& G, int P, std::vector<int>& order) {
         }
         if (running.empty()) break;  // cannot happen for an acyclic graph
         now = running.top().first;
+        if (sim_us) *sim_us = now;
         while (!running.empty() && running.top().first <= now) {
             int t = running.top().second;
             running.pop();
@@ -342,14 +395,15 @@ static int num_sms() {
 }
 
 // Runs one planned pass with the persistent scheduler.  Returns 0 or an error.
-static int run_persistent(int n, const std::vector<Window>& wins, double* S, int ldS, double* Q,
+static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, double* Q,
                           int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
                           long long* ntasks_out, double* ms_out, cudaStream_t st) {
+    pipeline_order(n, wins);
     TaskGraph G;
     build_graph(n, wins, Q != nullptr, G);
     const int P = num_sms();
     std::vector<int> order;
-    queue_order(G, P, order);
+    queue_order(G, P, order, &g_last_cp_us, &g_last_sim_us);
     const int nt = (int)G.t.size();
     if ((int)order.size() != nt) {
         g_last_error = "scheduler: task graph is not acyclic";
@@ -376,8 +430,10 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
     const size_t b_deps = al(sizeof(int) * nt), b_soff = al(sizeof(int) * (nt + 1));
     const size_t b_succ = al(sizeof(int) * std::max<size_t>(1, succ.size())), b_ctl = 256;
     const size_t b_u = (size_t)wins.size() * WMAX * WMAX * sizeof(double);
+    const size_t b_tr = (o.timing >= 2) ? al(sizeof(unsigned long long) * 4 * nt) : 0;
     void* base = nullptr;
-    int rc = pool_get(POOL_SCHED, b_tasks + b_wins + b_deps + b_soff + b_succ + b_ctl + b_u, &base);
+    int rc = pool_get(POOL_SCHED, b_tasks + b_wins + b_deps + b_soff + b_succ + b_ctl + b_tr + b_u,
+                      &base);
     if (rc) return rc;
     char* p = (char*)base;
     SchedTask* d_tasks = (SchedTask*)p; p += b_tasks;
@@ -386,6 +442,7 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
     int* d_soff = (int*)p; p += b_soff;
     int* d_succ = (int*)p; p += b_succ;
     int* d_ctl = (int*)p; p += b_ctl;
+    unsigned long long* d_tr = b_tr ? (unsigned long long*)p : nullptr; p += b_tr;
     double* d_u = (double*)p;
     GBR_CK(cudaMemcpyAsync(d_tasks, tq.data(), sizeof(SchedTask) * nt, cudaMemcpyHostToDevice, st), "H2D tasks");
     GBR_CK(cudaMemcpyAsync(d_wins, wins.data(), sizeof(Window) * wins.size(), cudaMemcpyHostToDevice, st), "H2D windows");
@@ -401,6 +458,8 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
     P2.upool = d_u; P2.head = d_ctl; P2.err = d_ctl + 1;
     const long long lim_ms = o.wait_limit_ms > 0 ? o.wait_limit_ms : 60000;
     P2.wait_limit = lim_ms * 1000000 / 128;
+    P2.trace = d_tr;
+    if (d_tr) GBR_CK(cudaMemsetAsync(d_tr, 0, b_tr, st), "memset trace");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (o.timing) {
         GBR_CK(cudaEventCreate(&e0), "event");
@@ -420,6 +479,21 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
         cudaEventDestroy(e1);
     }
     *ntasks_out += nt;
+    if (d_tr) {
+        std::vector<unsigned long long> raw((size_t)4 * nt);
+        GBR_CK(cudaMemcpy(raw.data(), d_tr, sizeof(unsigned long long) * 4 * nt,
+                          cudaMemcpyDeviceToHost), "D2H trace");
+        g_trace.assign((size_t)8 * nt, 0);
+        for (int q = 0; q < nt; ++q) {
+            const SchedTask& k = tq[q];
+            long long* r = &g_trace[(size_t)8 * q];
+            r[0] = k.kind; r[1] = k.win; r[2] = k.y0; r[3] = k.rows;
+            r[4] = (long long)raw[4 * q + 0];
+            r[5] = (long long)raw[4 * q + 1];
+            r[6] = (long long)raw[4 * q + 2];
+            r[7] = (long long)raw[4 * q + 3];
+        }
+    }
     if (h_err) {
         g_last_error = "persistent scheduler: a task waited longer than wait_limit_ms";
         return GBR_ERR_TIMEOUT;
@@ -606,6 +680,8 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         stats->ms_sched = ms_sched;
         stats->win_flops = (double)h_ctr.win_flops;
         stats->tasks = ntasks;
+        stats->sched_cp_ms = ntasks ? g_last_cp_us / 1e3 : 0.0;
+        stats->sched_sim_ms = ntasks ? g_last_sim_us / 1e3 : 0.0;
     }
     long long rej = (long long)h_ctr.rejected;
     return rej > INT_MAX ? INT_MAX : (int)rej;
@@ -808,6 +884,16 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
         stats->ms_total =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return rc;
+}
+
+int gbr_last_trace(long long* out, int max_tasks) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    const int nt = (int)(g_trace.size() / 8);
+    if (out) {
+        const int k = std::min(nt, std::max(0, max_tasks));
+        memcpy(out, g_trace.data(), sizeof(long long) * 8 * (size_t)k);
+    }
+    return nt;
 }
 
 const char* gbr_status_string(int s) {

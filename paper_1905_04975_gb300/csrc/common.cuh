@@ -63,6 +63,8 @@ struct SchedParams {
     int* head;                // next queue position
     int* err;                 // nonzero: a wait ran out
     long long wait_limit;     // spins (~128 ns each) before a wait gives up
+    unsigned long long* trace;  // null, or 4 words per queue position:
+                                // smid | wait start | exec start | end (ns)
 };
 
 // Launchers (each .cu file owns its kernels).

@@ -29,6 +29,18 @@ __device__ __forceinline__ int ld_volatile(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
 __global__ void __launch_bounds__(SCHED_THREADS, 1)
 sched_kernel(SchedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -38,6 +50,10 @@ sched_kernel(SchedParams P) {
     for (;;) {
         if (tid == 0) {
             int t = atomicAdd(P.head, 1);
+            if (P.trace && t < P.ntasks) {
+                P.trace[4 * t + 0] = smid();
+                P.trace[4 * t + 1] = global_ns();
+            }
             if (t < P.ntasks) {
                 long long spins = 0;
                 while (ld_volatile(&P.deps_left[t]) > 0) {
@@ -57,6 +73,7 @@ sched_kernel(SchedParams P) {
         const int t = task_id;
         if (t < 0 || t >= P.ntasks) break;
         __threadfence();
+        if (P.trace && tid == 0) P.trace[4 * t + 2] = global_ns();
         const SchedTask tk = P.tasks[t];
         const Window wd = P.wins[tk.win];
         double* Ug = P.upool + (size_t)tk.win * WMAX * WMAX;
@@ -79,6 +96,7 @@ sched_kernel(SchedParams P) {
         __threadfence();
         __syncthreads();
         if (tid == 0) {
+            if (P.trace) P.trace[4 * t + 3] = global_ns();
             for (int i = P.succ_off[t]; i < P.succ_off[t + 1]; ++i)
                 atomicSub(&P.deps_left[P.succ[i]], 1);
         }

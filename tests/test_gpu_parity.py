@@ -227,9 +227,10 @@ def test_n4000_workload_full_parity(gbr):
 
 @pytest.mark.parametrize("name,w,m", [("n400", 128, 64), ("n400", 32, 14), ("ragged", 64, 30)])
 def test_persistent_matches_sequential(gbr, name, w, m):
-    """The persistent scheduler orders every pair of overlapping tasks as the
-    program order does, so it computes exactly what the one-window-at-a-time
-    schedule computes."""
+    """The persistent schedule keeps the order of every pair of overlapping
+    windows and runs the left and right updates of non-overlapping windows
+    (which commute) in pipeline order, so it agrees with the one-window-at-a-
+    time schedule to rounding; and it is deterministic."""
     if name == "n400":
         S, Q, sel = si.config("n400")
     else:
@@ -238,7 +239,12 @@ def test_persistent_matches_sequential(gbr, name, w, m):
     rs, Ss_, Qs_ = run_gpu(gbr, S, Q, sel, window=w, chain=m, sched="sequential")
     assert rp.status == 0 and rs.status == 0
     assert rp.stats.tasks > rp.stats.windows
-    assert np.array_equal(Sp_, Ss_) and np.array_equal(Qp_, Qs_)
+    n = S.shape[0]
+    assert match_eigs(block_eigs(Sp_), block_eigs(Ss_), 0) <= 1e-10
+    assert np.linalg.norm(Sp_ - Ss_) <= 50 * n * EPS * np.linalg.norm(S)
+    assert np.linalg.norm(Qp_ - Qs_) <= 50 * n * EPS * np.sqrt(n)
+    rp2, Sp2, Qp2 = run_gpu(gbr, S, Q, sel, window=w, chain=m, sched="persistent")
+    assert np.array_equal(Sp_, Sp2) and np.array_equal(Qp_, Qp2)
 
 
 def test_scheduler_wait_times_out_and_context_survives(gbr):
