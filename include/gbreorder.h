@@ -103,6 +103,8 @@ typedef struct gbr_stats {
     double sched_cp_ms;   /* longest dependence path of the task graph under the
                              scheduler's duration model                          */
     double sched_sim_ms;  /* makespan of the scheduler's list-scheduling model   */
+    double ms_graph;      /* host time building the task graph                   */
+    double ms_order;      /* host time computing the queue order                 */
 } gbr_stats;
 
 /* Fill *opts with the defaults. */

@@ -29,6 +29,7 @@ namespace gbr {
 static thread_local std::string g_last_error;
 static std::vector<long long> g_trace;  // last traced persistent launch, 8 words per task
 static double g_last_cp_us = 0.0, g_last_sim_us = 0.0;  // last schedule: critical path, simulated
+static double g_last_graph_ms = 0.0, g_last_order_ms = 0.0;  // host time: task graph, queue order
 
 static int cuda_fail(cudaError_t e, const char* what) {
     char buf[256];
@@ -227,38 +228,49 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
         const int s = wins[i].s, e = wins[i].e, w = e - s;
         const int iw = (int)T.size();
         T.push_back(HostTask{TASK_W, i, 0, 0, 0, Rect{s, e, s, e}, dur_window(w)});
+        // left panel: columns [e, n); 64-column tiles within UPD_NEAR of the
+        // window (the next windows of the chain wait on those), 256-column
+        // tiles beyond, each on a global grid so tiles of windows line up
         for (int c = e; c < n;) {
-            int ce = std::min(n, (c / UPD_BM + 1) * UPD_BM);
+            const int g = (c - e < UPD_NEAR) ? UPD_BM : UPD_FAR;
+            int ce = std::min(n, (c / g + 1) * g);
             edges.push_back({iw, (int)T.size()});
             T.push_back(HostTask{TASK_L, i, c - e, ce - c, 0, Rect{s, e, c, ce}, dur_tile(ce - c, w)});
             c = ce;
         }
+        // right panel: rows [0, s); 64-row tiles within UPD_NEAR above the window
         for (int r = 0; r < s;) {
-            int re = std::min(s, (r / UPD_BM + 1) * UPD_BM);
+            const int g = (s - r <= UPD_NEAR) ? UPD_BM : UPD_FAR;
+            int re = std::min(s, (r / g + 1) * g);
+            if (g == UPD_FAR && re > s - UPD_NEAR) re = std::max(r + 1, s - UPD_NEAR);
             edges.push_back({iw, (int)T.size()});
             T.push_back(HostTask{TASK_R, i, r, re - r, 0, Rect{r, re, s, e}, dur_tile(re - r, w)});
             r = re;
         }
+        // Q panel: no window waits on Q, so 256-row tiles throughout
         if (withQ)
             for (int r = 0; r < n;) {
-                int re = std::min(n, (r / UPD_BM + 1) * UPD_BM);
+                int re = std::min(n, (r / UPD_FAR + 1) * UPD_FAR);
                 edges.push_back({iw, (int)T.size()});
                 T.push_back(HostTask{TASK_Q, i, r, re - r, 1, Rect{r, re, s, e}, dur_tile(re - r, w)});
                 r = re;
             }
     }
-    // Dependences in program order on exact rectangles.  Each cell keeps two
-    // lists, the tasks that mix rows (window, left) and those that mix columns
-    // (window, right); pruning by coverage stays within one list, where every
-    // older overlapping task precedes the covering one.
+    // Dependences in program order on exact rectangles, found through a grid
+    // of CB x CB cells: each cell lists the tasks touching it, newest last.
     const int CB = UPD_BM;
     const int nc = (n + CB - 1) / CB;
-    std::vector<std::vector<int>> lrow, lcol;   // S cells: row-mixing / column-mixing tasks
-    std::vector<std::vector<int>> lq;           // Q cells
-    lrow.resize((size_t)nc * nc);
-    lcol.resize((size_t)nc * nc);
-    if (withQ) lq.resize((size_t)nc * nc);
+    std::vector<std::vector<int>> cellv;        // S cells: tasks touching the cell
+    cellv.resize((size_t)nc * nc);
+    // Q tiles all lie on the UPD_FAR row grid, so within a row block two Q
+    // tasks conflict exactly when their column ranges overlap: the last Q task
+    // per (row block, column) gives the exact, minimal predecessors.
+    const int nqb = (n + UPD_FAR - 1) / UPD_FAR;
+    std::vector<int> lastq(withQ ? (size_t)nqb * n : 0, -1);
     std::vector<int> stamp(T.size(), -1);
+    // Scanning a cell from the newest task back; an older task is implied once
+    // a newer predecessor covers the whole region (it overlaps that one, so it
+    // precedes it), and the scan ends there.
     auto scan = [&](std::vector<int>& L, const Rect& X, int t) {
         for (int k = (int)L.size() - 1; k >= 0; --k) {
             const int u = L[k];
@@ -274,21 +286,38 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
     for (int t = 0; t < (int)T.size(); ++t) {
         const Rect R = T[t].rc;
         const int kind = T[t].kind;
+        if (kind == TASK_Q) {
+            int* last = &lastq[(size_t)(R.r0 / UPD_FAR) * n];
+            int prev = -1;
+            for (int c = R.c0; c < R.c1; ++c) {
+                const int u = last[c];
+                if (u >= 0 && u != prev && stamp[u] != t) {
+                    stamp[u] = t;
+                    edges.push_back({u, t});
+                }
+                prev = u;
+                last[c] = t;
+            }
+            continue;
+        }
         for (int cr = R.r0 / CB; cr * CB < R.r1; ++cr)
             for (int cc = R.c0 / CB; cc * CB < R.c1; ++cc) {
                 const Rect cell{cr * CB, std::min(n, (cr + 1) * CB), cc * CB, std::min(n, (cc + 1) * CB)};
                 const Rect X = rect_isect(R, cell);
                 const size_t ci = (size_t)cr * nc + cc;
-                if (kind == TASK_Q) {
-                    scan(lq[ci], X, t);
-                    lq[ci].push_back(t);
-                    continue;
-                }
+
                 // all S tasks order against every overlapping earlier S task
-                scan(lrow[ci], X, t);
-                scan(lcol[ci], X, t);
-                if (kind == TASK_W || kind == TASK_L) lrow[ci].push_back(t);
-                if (kind == TASK_W || kind == TASK_R) lcol[ci].push_back(t);
+                scan(cellv[ci], X, t);
+                // compaction: an entry whose part of the cell lies inside the new
+                // task's part precedes the new task and can never be needed again
+                std::vector<int>& L = cellv[ci];
+                size_t keep = 0;
+                for (size_t k = 0; k < L.size(); ++k) {
+                    const Rect I = rect_isect(T[L[k]].rc, cell);
+                    if (!rect_covers(X, I)) L[keep++] = L[k];
+                }
+                L.resize(keep);
+                L.push_back(t);
             }
     }
     std::sort(edges.begin(), edges.end());
@@ -398,12 +427,17 @@ static int num_sms() {
 static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, double* Q,
                           int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
                           long long* ntasks_out, double* ms_out, cudaStream_t st) {
+    auto th0 = std::chrono::steady_clock::now();
     pipeline_order(n, wins);
     TaskGraph G;
     build_graph(n, wins, Q != nullptr, G);
+    auto th1 = std::chrono::steady_clock::now();
     const int P = num_sms();
     std::vector<int> order;
     queue_order(G, P, order, &g_last_cp_us, &g_last_sim_us);
+    auto th2 = std::chrono::steady_clock::now();
+    g_last_graph_ms = std::chrono::duration<double, std::milli>(th1 - th0).count();
+    g_last_order_ms = std::chrono::duration<double, std::milli>(th2 - th1).count();
     const int nt = (int)G.t.size();
     if ((int)order.size() != nt) {
         g_last_error = "scheduler: task graph is not acyclic";
@@ -682,6 +716,8 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         stats->tasks = ntasks;
         stats->sched_cp_ms = ntasks ? g_last_cp_us / 1e3 : 0.0;
         stats->sched_sim_ms = ntasks ? g_last_sim_us / 1e3 : 0.0;
+        stats->ms_graph = ntasks ? g_last_graph_ms : 0.0;
+        stats->ms_order = ntasks ? g_last_order_ms : 0.0;
     }
     long long rej = (long long)h_ctr.rejected;
     return rej > INT_MAX ? INT_MAX : (int)rej;

@@ -11,8 +11,12 @@ namespace gbr {
 // packed upper-Hessenberg S window + dense accumulator U).
 constexpr int WMAX = 128;
 
-// Panel rows per update tile (update_body.cuh, scheduler tasks).
+// Panel rows per update tile (update_body.cuh, scheduler tasks): tiles near
+// a window (within UPD_NEAR rows or columns) are UPD_BM rows, the others
+// UPD_FAR rows, processed by one task as UPD_FAR / UPD_BM tiles of UPD_BM.
 constexpr int UPD_BM = 64;
+constexpr int UPD_FAR = 256;
+constexpr int UPD_NEAR = 256;
 
 // Column-major element access.
 __host__ __device__ inline size_t cm(int i, int j, int ld) {

@@ -87,9 +87,13 @@ sched_kernel(SchedParams P) {
             int R;
             upd::panel_geom(tk.kind - TASK_L, P.n, wd.s, wd.e, P.S, P.ldS, P.Q, P.ldQ, &base, &rs,
                             &ks, &R);
-            const bool load_u = (u_win != tk.win);
+            bool load_u = (u_win != tk.win);
             __syncthreads();
-            upd::update_tile(base, rs, ks, tk.y0, tk.rows, wd.e - wd.s, Ug, load_u, smem_raw);
+            for (int r = 0; r < tk.rows; r += upd::BM) {
+                upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s, Ug,
+                                 load_u, smem_raw);
+                load_u = false;
+            }
             if (tid == 0) u_win = tk.win;
         }
         // release: every thread's writes are ordered before the counters drop
