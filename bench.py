@@ -226,6 +226,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sched", default="persistent", choices=["persistent", "sequential"])
+    ap.add_argument("--precision", default="dmma", choices=["dmma", "ozaki"])
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -250,8 +251,8 @@ def main():
     S0, Q0 = g.to_device(S_np), g.to_device(Q_np)
     S, Q = g.to_device(S_np), g.to_device(Q_np)
     stream = torch.cuda.Stream()
-    opts = g.make_opts(window=wl["window"], chain=wl["chain"], precision="dmma", timing=True,
-                       sched=args.sched)
+    opts = g.make_opts(window=wl["window"], chain=wl["chain"], precision=args.precision,
+                       timing=True, sched=args.sched)
 
     def step():
         with torch.cuda.stream(stream):
@@ -351,7 +352,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl["name"], "n": n, "select": wl["select"],
                            "selected_eigs": nsel, "q": wl["q"], "window": wl["window"],
-                           "chain": wl["chain"], "precision": "dmma", "sched": args.sched,
+                           "chain": wl["chain"], "precision": args.precision, "sched": args.sched,
                            "l2": "S,Q (256 MB > L2) restored from a device copy before each step",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,

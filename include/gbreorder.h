@@ -57,7 +57,10 @@ extern "C" {
 #define GBR_ERR_NOALLOC_LIMIT (-1005) /* n > GBR_NOALLOC_MAX_N in gbr_reorder_noalloc */
 
 #define GBR_PREC_DMMA   0  /* off-diagonal updates on FP64 tensor cores (DMMA) */
-#define GBR_PREC_OZAKI  1  /* off-diagonal updates as split-precision emulated FP64 */
+#define GBR_PREC_OZAKI  1  /* off-diagonal updates as split-precision emulated FP64:
+                              7 signed 8-bit digit slices per operand, 28 exact
+                              bf16 tensor-core slice products, integer combination,
+                              one rounding to double; the windows stay in FP64 */
 
 #define GBR_ON_REJECT_CONTINUE 0 /* a rejected block stays; later blocks stop below it */
 
@@ -65,8 +68,9 @@ extern "C" {
 typedef struct gbr_opts {
     int window;        /* diagonal window size w, 16..128      (default 128) */
     int chain;         /* selected eigenvalues per chain m, 1..w-2 (default 64) */
-    int precision;     /* GBR_PREC_DMMA                         (default)     */
-    int slices;        /* split-precision slice count (reserved) (default 0)  */
+    int precision;     /* GBR_PREC_DMMA (default) or GBR_PREC_OZAKI (persistent
+                          schedule only)                                       */
+    int slices;        /* split-precision slices: 0 or 7 (the only count built) */
     int strong_test;   /* 1: weak + strong stability test       (default 1)   */
     int on_reject;     /* GBR_ON_REJECT_CONTINUE                (default)     */
     int validate;      /* 1: check the standard-form input      (default 1)   */

@@ -218,7 +218,10 @@ struct TaskGraph {
 // task takes about 2.6 ms at w = 128 (measured), an update tile is a DMMA
 // product of rows x w x w at ~6.9 GFLOP/s per SM.
 static double dur_window(int w) { return 2600.0 * (double)w * w / (128.0 * 128.0); }
-static double dur_tile(int rows, int w) { return 2.0 * rows * (double)w * w / 6900.0 + 2.0; }
+// flops per microsecond of one SM on an update tile: FP64 DMMA, or the
+// split-precision form (28 bf16 slice products, integer combination)
+static double g_tile_rate = 6900.0;
+static double dur_tile(int rows, int w) { return 2.0 * rows * (double)w * w / g_tile_rate + 2.0; }
 
 static void build_graph(int n, const std::vector<Window>& wins, bool withQ, TaskGraph& G) {
     std::vector<HostTask>& T = G.t;
@@ -427,6 +430,8 @@ static int num_sms() {
 static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, double* Q,
                           int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
                           long long* ntasks_out, double* ms_out, cudaStream_t st) {
+    const bool ozaki = (o.precision == GBR_PREC_OZAKI);
+    g_tile_rate = ozaki ? 60000.0 : 6900.0;
     auto th0 = std::chrono::steady_clock::now();
     pipeline_order(n, wins);
     TaskGraph G;
@@ -465,8 +470,11 @@ static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, d
     const size_t b_succ = al(sizeof(int) * std::max<size_t>(1, succ.size())), b_ctl = 256;
     const size_t b_u = (size_t)wins.size() * WMAX * WMAX * sizeof(double);
     const size_t b_tr = (o.timing >= 2) ? al(sizeof(unsigned long long) * 4 * nt) : 0;
+    const size_t b_us = ozaki ? al(OZ_USLICE_BYTES * wins.size()) : 0;
+    const size_t b_oz = ozaki ? al(sizeof(double) * UPD_FAR * WMAX * (size_t)P) : 0;
     void* base = nullptr;
-    int rc = pool_get(POOL_SCHED, b_tasks + b_wins + b_deps + b_soff + b_succ + b_ctl + b_tr + b_u,
+    int rc = pool_get(POOL_SCHED,
+                      b_tasks + b_wins + b_deps + b_soff + b_succ + b_ctl + b_tr + b_us + b_oz + b_u,
                       &base);
     if (rc) return rc;
     char* p = (char*)base;
@@ -477,6 +485,8 @@ static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, d
     int* d_succ = (int*)p; p += b_succ;
     int* d_ctl = (int*)p; p += b_ctl;
     unsigned long long* d_tr = b_tr ? (unsigned long long*)p : nullptr; p += b_tr;
+    unsigned char* d_us = b_us ? (unsigned char*)p : nullptr; p += b_us;
+    double* d_oz = b_oz ? (double*)p : nullptr; p += b_oz;
     double* d_u = (double*)p;
     GBR_CK(cudaMemcpyAsync(d_tasks, tq.data(), sizeof(SchedTask) * nt, cudaMemcpyHostToDevice, st), "H2D tasks");
     GBR_CK(cudaMemcpyAsync(d_wins, wins.data(), sizeof(Window) * wins.size(), cudaMemcpyHostToDevice, st), "H2D windows");
@@ -493,6 +503,8 @@ static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, d
     const long long lim_ms = o.wait_limit_ms > 0 ? o.wait_limit_ms : 60000;
     P2.wait_limit = lim_ms * 1000000 / 128;
     P2.trace = d_tr;
+    P2.uslices = d_us;
+    P2.ozscratch = d_oz;
     if (d_tr) GBR_CK(cudaMemsetAsync(d_tr, 0, b_tr, st), "memset trace");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (o.timing) {
@@ -541,7 +553,10 @@ static int run_persistent(int n, std::vector<Window> wins, double* S, int ldS, d
 static int check_opts(const gbr_opts* o) {
     if (o->window < 4 || o->window > WMAX) return -10;
     if (o->chain < 1 || o->chain > o->window - 2) return -10;
-    if (o->precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
+    if (o->precision != GBR_PREC_DMMA && o->precision != GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    if (o->precision == GBR_PREC_OZAKI &&
+        (o->sched != GBR_SCHED_PERSISTENT || (o->slices != 0 && o->slices != OZ_SLICES)))
+        return GBR_ERR_UNSUPPORTED;
     if (o->on_reject != GBR_ON_REJECT_CONTINUE) return GBR_ERR_UNSUPPORTED;
     if (o->sched != GBR_SCHED_PERSISTENT && o->sched != GBR_SCHED_SEQUENTIAL) return -10;
     if (o->wait_limit_ms < 0) return -10;
@@ -905,6 +920,7 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
     if (rc) return rc;
     o.timing = 0;  // event timing would create events; this path creates nothing
     o.sched = GBR_SCHED_SEQUENTIAL;  // the persistent schedule needs scratch sized per plan
+    if (o.precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
     if (stats) memset(stats, 0, sizeof *stats);
     if (n == 0) {
         if (m_out) *m_out = 0;

@@ -11,6 +11,13 @@ namespace gbr {
 // packed upper-Hessenberg S window + dense accumulator U).
 constexpr int WMAX = 128;
 
+// Split-precision (Ozaki) updates: OZ_SLICES signed 8-bit digit slices per
+// FP64 operand; one window's U slices take OZ_USLICE_BYTES (bf16 digits
+// [slice][column n][row k], then one int exponent per column).
+constexpr int OZ_SLICES = 7;
+constexpr size_t OZ_UDIG_ELEMS = (size_t)OZ_SLICES * WMAX * WMAX;
+constexpr size_t OZ_USLICE_BYTES = OZ_UDIG_ELEMS * 2 + (size_t)WMAX * 4;
+
 // Panel rows per update tile (update_body.cuh, scheduler tasks): tiles near
 // a window (within UPD_NEAR rows or columns) are UPD_BM rows, the others
 // UPD_FAR rows, processed by one task as UPD_FAR / UPD_BM tiles of UPD_BM.
@@ -64,6 +71,8 @@ struct SchedParams {
     const int* succ_off;      // CSR successors
     const int* succ;
     double* upool;            // one WMAX x WMAX accumulator per window
+    unsigned char* uslices;   // null (DMMA updates) or OZ_USLICE_BYTES per window
+    double* ozscratch;        // split precision: UPD_FAR x WMAX doubles per CTA
     int* head;                // next queue position
     int* err;                 // nonzero: a wait ran out
     long long wait_limit;     // spins (~128 ns each) before a wait gives up

@@ -22,8 +22,8 @@ namespace gbr {
 namespace {
 
 constexpr int SCHED_THREADS = win::WIN_THREADS;
-constexpr size_t kSchedSmem = win::kWindowSmem > upd::kUpdateSmem ? win::kWindowSmem
-                                                                  : upd::kUpdateSmem;
+constexpr size_t kMax2(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kSchedSmem = kMax2(kMax2(win::kWindowSmem, upd::kUpdateSmem), oz::kSmem);
 
 __device__ __forceinline__ int ld_volatile(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
@@ -79,7 +79,8 @@ sched_kernel(SchedParams P) {
         double* Ug = P.upool + (size_t)tk.win * WMAX * WMAX;
         if (tk.kind == TASK_W) {
             win::window_body(P.n, P.S, P.ldS, wd.s, wd.e - wd.s, P.sel, Ug, P.strong, P.ctr,
-                             smem_raw);
+                             smem_raw,
+                             P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr);
             if (tid == 0) u_win = -1;  // shared memory no longer holds a U
         } else {
             double* base;
@@ -89,12 +90,18 @@ sched_kernel(SchedParams P) {
                             &ks, &R);
             bool load_u = (u_win != tk.win);
             __syncthreads();
+            if (P.uslices) {
+                upd::update_tile_ozaki(base, rs, ks, tk.y0, tk.rows, wd.e - wd.s,
+                                       P.uslices + (size_t)tk.win * OZ_USLICE_BYTES,
+                                       P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX, smem_raw);
+                load_u = true;  // shared memory no longer holds U
+            } else
             for (int r = 0; r < tk.rows; r += upd::BM) {
                 upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s, Ug,
                                  load_u, smem_raw);
                 load_u = false;
             }
-            if (tid == 0) u_win = tk.win;
+            if (tid == 0) u_win = P.uslices ? -1 : tk.win;
         }
         // release: every thread's writes are ordered before the counters drop
         __threadfence();

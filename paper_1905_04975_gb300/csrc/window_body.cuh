@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "swap_math.cuh"
 
+#include <cuda_bf16.h>
 #include <float.h>
 
 namespace gbr {
@@ -254,6 +255,54 @@ __device__ __forceinline__ int rank_of_warp(int warp) {
     return part <= 1 ? (warp >> 2) * 2 + part : (warp >> 2);
 }
 
+// Signed 8-bit digits of x relative to the binary exponent field emax of the
+// largest entry of its row or column: |x| / 2^(emax - 1022) < 1 is written in
+// 56 fractional bits F = m 2^(3 + e - emax) (m the 53-bit significand), and
+// digit p (1..7) is bits [56 - 8p, 64 - 8p) of F, carrying the sign of x.
+// Entries below the normal range count as zero.  Integer work only.
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int emax, bool* neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    *neg = (b >> 63) != 0;
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0ull;
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = emax - e;
+    return sh >= 64 ? 0ull : ((m << 3) >> sh);
+}
+
+// Writes U's digit slices (bf16, [slice][n][k], k < WMAX) and the column
+// exponents for the split-precision updates; columns/rows beyond w are zero.
+__device__ __forceinline__ void write_u_slices(const double* U, int w, unsigned char* out) {
+    __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(out);
+    int* cexp = reinterpret_cast<int*>(out + OZ_UDIG_ELEMS * 2);
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int ce[WMAX];
+    for (int n = warp; n < WMAX; n += nth / 32) {
+        int em = 0;
+        if (n < w)
+            for (int k = lane; k < w; k += 32) {
+                int e = (int)((((unsigned long long)__double_as_longlong(U[n * w + k])) >> 52) & 0x7ff);
+                em = e > em ? e : em;
+            }
+        for (int o = 16; o; o >>= 1) {
+            int v = __shfl_xor_sync(0xffffffffu, em, o);
+            em = v > em ? v : em;
+        }
+        if (lane == 0) { ce[n] = em; cexp[n] = em; }
+    }
+    __syncthreads();
+    for (int i = tid; i < WMAX * WMAX; i += nth) {
+        const int n = i / WMAX, k = i % WMAX;
+        bool neg = false;
+        unsigned long long F = (n < w && k < w) ? oz_fixed(U[n * w + k], ce[n], &neg) : 0ull;
+#pragma unroll
+        for (int p = 0; p < OZ_SLICES; ++p) {
+            int d = (int)((F >> (48 - 8 * p)) & 255ull);
+            dig[(size_t)p * WMAX * WMAX + i] = __int2bfloat16_rn(neg ? -d : d);
+        }
+    }
+}
+
 // Dynamic shared memory needed by window_body.
 constexpr size_t kWindowSmem = sizeof(double) * ((size_t)WMAX * WMAX +
                                                  (size_t)((WMAX * (WMAX + 3)) / 2) +
@@ -263,7 +312,8 @@ constexpr size_t kWindowSmem = sizeof(double) * ((size_t)WMAX * WMAX +
 __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int ldS, int s0, int w,
                                             uint8_t* __restrict__ gsel, double* __restrict__ Ug,
                                             int strong, DevCounters* __restrict__ ctr,
-                                            unsigned char* smem_raw) {
+                                            unsigned char* smem_raw,
+                                            unsigned char* __restrict__ uslices = nullptr) {
     double* U = reinterpret_cast<double*>(smem_raw);           // w*w
     double* Sp = U + WMAX * WMAX;                               // packed window
     double* Zs = Sp + poff(WMAX);                               // MAXSW * 16
@@ -594,6 +644,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     for (int i = tid; i < w; i += nth)
         if (sel[i] != SEL_WALL) gsel[s0 + i] = sel[i];
     for (int i = tid; i < w * w; i += nth) Ug[i] = U[i];
+    if (uslices) write_u_slices(U, w, uslices);
     if (tid == 0) {
         atomicAdd(&ctr->swaps, (unsigned long long)nacc);
         atomicAdd(&ctr->rejected, (unsigned long long)nrej);

@@ -259,3 +259,32 @@ def test_scheduler_wait_times_out_and_context_survives(gbr):
     r, Sg, Qg = run_gpu(gbr, S, Q, sel)
     assert r.status == 0
     check(S, Q, sel, r, Sg, Qg, ref)
+
+
+@pytest.mark.parametrize("name,w,m", [("n400", 128, 64), ("n400", 64, 30), ("ragged", 128, 64),
+                                      ("tiny", 16, 6)])
+def test_split_precision_updates(gbr, name, w, m):
+    """Off-diagonal updates in emulated FP64 (7 digit slices, exact bf16
+    tensor-core products): same parity bar as the FP64 DMMA path, and close
+    to the DMMA result."""
+    if name == "n400":
+        S, Q, sel = si.config("n400")
+    elif name == "tiny":
+        S, Q, sel = si.reorder_problem(37, 4, select_frac=0.5, q="householder", reflectors=8)
+    else:
+        S, Q, sel = si.reorder_problem(900, 8, select_frac=0.4, q="householder")
+    ref = oracle.reorder(S, Q, sel)
+    ro, So, Qo = run_gpu(gbr, S, Q, sel, window=w, chain=m, precision="ozaki")
+    assert ro.status == 0
+    check(S, Q, sel, ro, So, Qo, ref)
+    rd, Sd, Qd = run_gpu(gbr, S, Q, sel, window=w, chain=m, precision="dmma")
+    n = S.shape[0]
+    assert np.linalg.norm(So - Sd) <= 50 * n * EPS * np.linalg.norm(S)
+    assert np.linalg.norm(Qo - Qd) <= 50 * n * EPS * np.sqrt(n)
+
+
+def test_split_precision_n4000(gbr):
+    (S, Q, sel), ref = n4000_oracle()
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=128, chain=64, precision="ozaki")
+    assert r.status == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
