@@ -223,7 +223,16 @@ static double dur_window(int w) { return 2600.0 * (double)w * w / (128.0 * 128.0
 static double g_tile_rate = 6900.0;
 static double dur_tile(int rows, int w) { return 2.0 * rows * (double)w * w / g_tile_rate + 2.0; }
 
+// Far-tile height: 256 panel rows up to n = 6000, then growing with n (the
+// task count and the host time to order it grow as n^3 / far), at most 1024.
+static int far_rows(int n) {
+    int f = UPD_FAR;
+    while (f < 1024 && f * 24 < n) f *= 2;
+    return f;
+}
+
 static void build_graph(int n, const std::vector<Window>& wins, bool withQ, TaskGraph& G) {
+    const int FAR = far_rows(n);
     std::vector<HostTask>& T = G.t;
     std::vector<std::pair<int, int>> edges;
     T.clear();
@@ -232,10 +241,10 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
         const int iw = (int)T.size();
         T.push_back(HostTask{TASK_W, i, 0, 0, 0, Rect{s, e, s, e}, dur_window(w)});
         // left panel: columns [e, n); 64-column tiles within UPD_NEAR of the
-        // window (the next windows of the chain wait on those), 256-column
-        // tiles beyond, each on a global grid so tiles of windows line up
+        // window (the next windows of the chain wait on those), far
+        // tiles (FAR columns) beyond, each on a global grid so tiles of windows line up
         for (int c = e; c < n;) {
-            const int g = (c - e < UPD_NEAR) ? UPD_BM : UPD_FAR;
+            const int g = (c - e < UPD_NEAR) ? UPD_BM : FAR;
             int ce = std::min(n, (c / g + 1) * g);
             edges.push_back({iw, (int)T.size()});
             T.push_back(HostTask{TASK_L, i, c - e, ce - c, 0, Rect{s, e, c, ce}, dur_tile(ce - c, w)});
@@ -243,17 +252,17 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
         }
         // right panel: rows [0, s); 64-row tiles within UPD_NEAR above the window
         for (int r = 0; r < s;) {
-            const int g = (s - r <= UPD_NEAR) ? UPD_BM : UPD_FAR;
+            const int g = (s - r <= UPD_NEAR) ? UPD_BM : FAR;
             int re = std::min(s, (r / g + 1) * g);
-            if (g == UPD_FAR && re > s - UPD_NEAR) re = std::max(r + 1, s - UPD_NEAR);
+            if (g == FAR && re > s - UPD_NEAR) re = std::max(r + 1, s - UPD_NEAR);
             edges.push_back({iw, (int)T.size()});
             T.push_back(HostTask{TASK_R, i, r, re - r, 0, Rect{r, re, s, e}, dur_tile(re - r, w)});
             r = re;
         }
-        // Q panel: no window waits on Q, so 256-row tiles throughout
+        // Q panel: no window waits on Q, so far tiles throughout
         if (withQ)
             for (int r = 0; r < n;) {
-                int re = std::min(n, (r / UPD_FAR + 1) * UPD_FAR);
+                int re = std::min(n, (r / FAR + 1) * FAR);
                 edges.push_back({iw, (int)T.size()});
                 T.push_back(HostTask{TASK_Q, i, r, re - r, 1, Rect{r, re, s, e}, dur_tile(re - r, w)});
                 r = re;
@@ -265,10 +274,10 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
     const int nc = (n + CB - 1) / CB;
     std::vector<std::vector<int>> cellv;        // S cells: tasks touching the cell
     cellv.resize((size_t)nc * nc);
-    // Q tiles all lie on the UPD_FAR row grid, so within a row block two Q
+    // Q tiles all lie on the FAR row grid, so within a row block two Q
     // tasks conflict exactly when their column ranges overlap: the last Q task
     // per (row block, column) gives the exact, minimal predecessors.
-    const int nqb = (n + UPD_FAR - 1) / UPD_FAR;
+    const int nqb = (n + FAR - 1) / FAR;
     std::vector<int> lastq(withQ ? (size_t)nqb * n : 0, -1);
     std::vector<int> stamp(T.size(), -1);
     // Scanning a cell from the newest task back; an older task is implied once
@@ -290,7 +299,7 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
         const Rect R = T[t].rc;
         const int kind = T[t].kind;
         if (kind == TASK_Q) {
-            int* last = &lastq[(size_t)(R.r0 / UPD_FAR) * n];
+            int* last = &lastq[(size_t)(R.r0 / FAR) * n];
             int prev = -1;
             for (int c = R.c0; c < R.c1; ++c) {
                 const int u = last[c];
@@ -323,8 +332,8 @@ static void build_graph(int n, const std::vector<Window>& wins, bool withQ, Task
                 L.push_back(t);
             }
     }
-    std::sort(edges.begin(), edges.end());
-    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    // No edge is listed twice: the scans stamp each predecessor once per task,
+    // and a window task overlaps none of its own tiles.
     const int nt = (int)T.size();
     G.ndeps.assign(nt, 0);
     G.soff.assign(nt + 1, 0);
@@ -658,7 +667,7 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         std::vector<Window> win;
         plan_pass(ps, o.window, o.chain, win, nchains);
         if (win.empty()) break;
-        if (o.sched == GBR_SCHED_PERSISTENT && pass == 0) {
+        if (o.sched == GBR_SCHED_PERSISTENT) {
             int rcs = run_persistent(n, win, S, ldS, Q, ldQ, d_sel, d_ctr, o, &ntasks, &ms_sched, st);
             if (rcs) return rcs;
             launches += 1;

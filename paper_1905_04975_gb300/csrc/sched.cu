@@ -91,9 +91,11 @@ sched_kernel(SchedParams P) {
             bool load_u = (u_win != tk.win);
             __syncthreads();
             if (P.uslices) {
-                upd::update_tile_ozaki(base, rs, ks, tk.y0, tk.rows, wd.e - wd.s,
-                                       P.uslices + (size_t)tk.win * OZ_USLICE_BYTES,
-                                       P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX, smem_raw);
+                for (int r = 0; r < tk.rows; r += UPD_FAR)
+                    upd::update_tile_ozaki(base, rs, ks, tk.y0 + r, min(UPD_FAR, tk.rows - r),
+                                           wd.e - wd.s, P.uslices + (size_t)tk.win * OZ_USLICE_BYTES,
+                                           P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX,
+                                           smem_raw);
                 load_u = true;  // shared memory no longer holds U
             } else
             for (int r = 0; r < tk.rows; r += upd::BM) {
