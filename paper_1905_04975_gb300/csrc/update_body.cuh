@@ -286,6 +286,14 @@ __device__ __forceinline__ void update_tile_ozaki(double* base, long long rs, lo
             {
                 const int mt = warp & 1, nt = warp >> 1;
                 const int ra = mt * 16 + g, nb = nt * 8 + g;
+                // R[q - 1][i]: exact int32 sum of the products on diagonal p + q
+                // (at most 7 terms below 2^23).  Diagonal p + 1 is complete once
+                // slice p is done; T takes it by Horner's rule, highest weight first.
+                int R[OZ_SLICES][4];
+#pragma unroll
+                for (int q = 0; q < OZ_SLICES; ++q)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) R[q][i] = 0;
                 long long thi[4] = {0, 0, 0, 0};
                 unsigned long long tlo[4] = {0, 0, 0, 0};
 #pragma unroll 1
@@ -300,26 +308,33 @@ __device__ __forceinline__ void update_tile_ozaki(double* base, long long rs, lo
                         af[kk][2] = ld_u32(A + (size_t)ra * LDK + kk * 16 + 2 * t4 + 8);
                         af[kk][3] = ld_u32(A + (size_t)(ra + 8) * LDK + kk * 16 + 2 * t4 + 8);
                     }
-#pragma unroll 1
-                    for (int q = 1; q <= OZ_SLICES + 1 - p; ++q) {
+#pragma unroll
+                    for (int q = 1; q <= OZ_SLICES; ++q) {
+                        if (q > OZ_SLICES + 1 - p) break;
                         const __nv_bfloat16* B = Bs + (size_t)(q - 1) * NH * LDK + (size_t)nb * LDK;
                         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                         for (int kk = 0; kk < WMAX / 16; ++kk)
                             mma_bf16(c, af[kk][0], af[kk][1], af[kk][2], af[kk][3],
                                      ld_u32(B + kk * 16 + 2 * t4), ld_u32(B + kk * 16 + 2 * t4 + 8));
-                        // T += P 2^(8 (OZ_SLICES + 1 - p - q)), P exact (|P| < 2^23)
-                        const int sh = 8 * (OZ_SLICES + 1 - p - q);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const long long pv = __float2int_rn(c[i]);
-                            const unsigned long long plo = (unsigned long long)pv << sh;
-                            const long long phi = sh ? (pv >> (64 - sh)) : (pv >> 63);
-                            const unsigned long long nlo = tlo[i] + plo;
-                            thi[i] += phi + (nlo < tlo[i] ? 1 : 0);
-                            tlo[i] = nlo;
-                        }
+                        for (int i = 0; i < 4; ++i) R[q - 1][i] += __float2int_rn(c[i]);  // exact
                     }
+                    // T <- T 2^8 + (diagonal p + 1); the other sums move down one slot
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        thi[i] = (long long)(((unsigned long long)thi[i] << 8) | (tlo[i] >> 56));
+                        const unsigned long long sh = tlo[i] << 8;
+                        const unsigned long long add = (unsigned long long)(long long)R[0][i];
+                        tlo[i] = sh + add;
+                        thi[i] += (tlo[i] < sh ? 1 : 0) - (R[0][i] < 0 ? 1 : 0);
+                    }
+#pragma unroll
+                    for (int q = 0; q + 1 < OZ_SLICES; ++q)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) R[q][i] = R[q + 1][i];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) R[OZ_SLICES - 1][i] = 0;
                 }
                 // value = T 2^-64 2^(er - 1022) 2^(en - 1022); c layout: (g, 2t), (g, 2t+1),
                 // (g + 8, 2t), (g + 8, 2t + 1)
