@@ -55,6 +55,9 @@ extern "C" {
                                    then partially updated and must be discarded */
 #define GBR_ERR_UNSUPPORTED (-1004) /* option value not supported */
 #define GBR_ERR_NOALLOC_LIMIT (-1005) /* n > GBR_NOALLOC_MAX_N in gbr_reorder_noalloc */
+#define GBR_ERR_PLAN_MISMATCH (-1006) /* gbr_batch_run: an S no longer has the block
+                                         structure it was planned for; nothing was
+                                         modified */
 
 #define GBR_PREC_DMMA   0  /* off-diagonal updates on FP64 tensor cores (DMMA) */
 #define GBR_PREC_OZAKI  1  /* off-diagonal updates as split-precision emulated FP64:
@@ -66,8 +69,11 @@ extern "C" {
 
 /* Options; gbr_default_opts() fills the defaults shown. */
 typedef struct gbr_opts {
-    int window;        /* diagonal window size w, 16..128      (default 128) */
-    int chain;         /* selected eigenvalues per chain m, 1..w-2 (default 64) */
+    int window;        /* diagonal window size w, 4..128        (default 128);
+                          GBR_AUTO in batched calls: chosen per instance by
+                          the autotuner (gbr_autotune)                        */
+    int chain;         /* selected eigenvalues per chain m, 1..w-2 (default 64);
+                          GBR_AUTO with window = GBR_AUTO                     */
     int precision;     /* GBR_PREC_DMMA (default) or GBR_PREC_OZAKI (persistent
                           schedule only)                                       */
     int slices;        /* split-precision slices: 0 or 7 (the only count built) */
@@ -84,6 +90,8 @@ typedef struct gbr_opts {
     long long wait_limit_ms; /* bound on any device-side wait of the persistent
                           scheduler, milliseconds; 0 = default (60000)   */
 } gbr_opts;
+
+#define GBR_AUTO 0 /* opts.window / opts.chain of batched calls: autotuned */
 
 #define GBR_SCHED_PERSISTENT 0 /* one persistent launch runs all window and update
                                   tasks, several windows in flight (Section 3.2) */
@@ -175,6 +183,87 @@ int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *s
 int gbr_reorder_noalloc(int n, double *S, int ldS, double *Q, int ldQ, const int *select,
                         double *eig_re, double *eig_im, int *m_out, const gbr_opts *opts,
                         gbr_stats *stats, void *cuda_stream);
+
+/*
+ * Batched reordering: many independent problems (Eq. 7 for each), planned
+ * together into one task graph and run by one persistent-scheduler launch
+ * captured in a CUDA graph.  No counterpart in the paper, which reorders one
+ * (distributed) matrix; the window, chain and update tasks of each instance
+ * are those of Section 3.2.
+ *
+ * gbr_batch_create plans a batch and captures its CUDA graph:
+ *  1 count    number of instances (>= 0)
+ *  2 n        host, count ints: order of each instance (>= 0)
+ *  3 S        host array of count device pointers (column-major, ldS[i]);
+ *             the caller keeps them allocated until gbr_batch_destroy
+ *  4 ldS      host, count ints, ldS[i] >= max(1, n[i])
+ *  5 Q        host array of count device pointers (entries may be NULL), or
+ *             NULL for no Schur vectors at all
+ *  6 ldQ      host, count ints (ignored where Q[i] is NULL); may be NULL if Q is
+ *  7 select   host, sum(n) ints: the selections, concatenated in instance order
+ *  8 opts     options or NULL; window/chain = GBR_AUTO picks them per
+ *             instance from the autotuner's table for the current device
+ *             (built-in defaults for sizes it has not tuned); precision,
+ *             strong_test, validate, wait_limit_ms as for gbr_reorder;
+ *             opts.sched must be GBR_SCHED_PERSISTENT
+ *  9 status   host, count ints or NULL: 0, or -2 for an instance not in
+ *             standard form (it is left out of the plan and never touched)
+ * 10 out      receives the batch handle
+ * 11 cuda_stream  stream for the planning work; the handle runs on the
+ *             stream given to gbr_batch_run
+ * Returns 0, -i for an invalid argument i, or GBR_ERR_*.  The handle owns
+ * its device memory (plan, accumulators, staging) until gbr_batch_destroy.
+ *
+ * gbr_batch_run reorders the current contents of the batch's S and Q in
+ * place.  They must have the block structure (positions of the 2x2 blocks)
+ * they had when the batch was planned: the graph checks this first on the
+ * device and, if any instance differs, modifies nothing and the call
+ * returns GBR_ERR_PLAN_MISMATCH.
+ *  eig_re, eig_im  host, sum(n) doubles each, or NULL: eigenvalues of each
+ *             S_hat in diagonal order, concatenated
+ *  m_out      host, count ints or NULL: selected eigenvalues per instance
+ *  status     host, count ints or NULL: 0, +k (k swaps rejected; the
+ *             instance then got further passes outside the graph, as in
+ *             gbr_reorder), or -2 (invalid, untouched)
+ *  stats      host or NULL: totals over the batch (ms_sched = the scheduler
+ *             kernel's time when opts.timing)
+ * Returns 0 if every valid instance returned 0, else the number of
+ * instances with rejected swaps, or GBR_ERR_*.
+ *
+ * gbr_reorder_batched = create + run + destroy.
+ */
+typedef struct gbr_batch gbr_batch;
+
+int gbr_batch_create(int count, const int *n, double *const *S, const int *ldS,
+                     double *const *Q, const int *ldQ, const int *select,
+                     const gbr_opts *opts, int *status, gbr_batch **out, void *cuda_stream);
+int gbr_batch_run(gbr_batch *batch, double *eig_re, double *eig_im, int *m_out, int *status,
+                  gbr_stats *stats, void *cuda_stream);
+void gbr_batch_destroy(gbr_batch *batch);
+int gbr_reorder_batched(int count, const int *n, double *const *S, const int *ldS,
+                        double *const *Q, const int *ldQ, const int *select,
+                        double *eig_re, double *eig_im, int *m_out, int *status,
+                        const gbr_opts *opts, gbr_stats *stats, void *cuda_stream);
+
+/*
+ * Autotuner of the batched path.  For each size class n in (16, 32],
+ * (32, 64], ... up to n_max, it builds a seeded synthetic batch of
+ * `per_class` instances of that class (standard Schur forms with 60% of
+ * positions in 1x1 blocks, 20-60% of the eigenvalues selected, Q present),
+ * runs it under every candidate (window w in {32, 64, 96, 128} not above
+ * the class, chain m in {w/4, w/2, 3w/4}, far update-tile height in
+ * {64, 256}), times the scheduler kernel with CUDA events, and keeps the
+ * fastest candidate per class in a table for the current device.
+ * Returns the number of classes tuned, or GBR_ERR_*.
+ */
+int gbr_autotune(int n_max, int per_class, void *cuda_stream);
+
+/*
+ * The autotuner's choice for an instance of order n on the current device:
+ * window, chain and far update-tile height (NULL outputs are skipped).
+ * Returns 1 if the class was tuned, 0 if these are the built-in defaults.
+ */
+int gbr_tune_get(int n, int *window, int *chain, int *tile);
 
 /*
  * Window plan of a reordering, on the host only (no GPU work): the diagonal

@@ -32,7 +32,9 @@ ERR_NOMEM = -1002
 ERR_TIMEOUT = -1003
 ERR_UNSUPPORTED = -1004
 ERR_NOALLOC_LIMIT = -1005
+ERR_PLAN_MISMATCH = -1006
 NOALLOC_MAX_N = 16384
+AUTO = 0
 
 
 class GbrOpts(ctypes.Structure):
@@ -72,6 +74,19 @@ SYMBOLS = {
     "gbr_last_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "gbr_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte), _ip, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _ip, _dp]),
+    "gbr_batch_create": (ctypes.c_int, [ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_void_p), _ip,
+                                        ctypes.POINTER(ctypes.c_void_p), _ip, _ip,
+                                        ctypes.POINTER(GbrOpts), _ip,
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "gbr_batch_run": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _ip, _ip,
+                                     ctypes.POINTER(GbrStats), ctypes.c_void_p]),
+    "gbr_batch_destroy": (None, [ctypes.c_void_p]),
+    "gbr_reorder_batched": (ctypes.c_int, [ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_void_p), _ip,
+                                           ctypes.POINTER(ctypes.c_void_p), _ip, _ip, _dp, _dp,
+                                           _ip, _ip, ctypes.POINTER(GbrOpts),
+                                           ctypes.POINTER(GbrStats), ctypes.c_void_p]),
+    "gbr_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "gbr_tune_get": (ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip]),
 }
 
 _lib = None
@@ -293,3 +308,137 @@ def last_trace() -> np.ndarray:
     if nt > 0:
         lib.gbr_last_trace(out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), nt)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Batched reordering
+# ---------------------------------------------------------------------------
+@dataclass
+class BatchResult:
+    status: np.ndarray    # per instance: 0, +k rejected swaps, -2 invalid
+    m: np.ndarray         # selected eigenvalues per instance
+    eigs: list            # per instance: complex eigenvalues in diagonal order
+    stats: GbrStats
+    rc: int               # 0, or the number of instances with rejected swaps
+
+
+def _batch_args(S_list, Q_list, selects):
+    count = len(S_list)
+    n = np.array([int(S.shape[0]) for S in S_list], dtype=np.int32)
+    ldS = np.array([_colmajor_ld(S) for S in S_list], dtype=np.int32)
+    Sp = (ctypes.c_void_p * max(count, 1))(*[S.data_ptr() for S in S_list])
+    Qp = None
+    ldQ = None
+    if Q_list is not None:
+        Qp = (ctypes.c_void_p * max(count, 1))(*[(Q.data_ptr() if Q is not None else None)
+                                                 for Q in Q_list])
+        ldQ = np.array([(_colmajor_ld(Q) if Q is not None else 1) for Q in Q_list], dtype=np.int32)
+    sel = [np.asarray(s, dtype=np.int32).reshape(-1) for s in selects]
+    for s_, nn in zip(sel, n):
+        if s_.size != nn:
+            raise ValueError("each selection must have n entries")
+    selc = np.ascontiguousarray(np.concatenate(sel) if sel else np.zeros(1, np.int32))
+    return count, n, ldS, Sp, Qp, ldQ, selc
+
+
+class Batch:
+    """A planned batch (gbr_batch_create): one task graph over all instances
+    and a captured CUDA graph; run() reorders the current contents of the
+    tensors in place (same block structure as at planning)."""
+
+    def __init__(self, S_list, Q_list, selects, *, opts: GbrOpts | None = None, stream=None,
+                 **kw):
+        lib = load()
+        self._args = _batch_args(S_list, Q_list, selects)
+        count, n, ldS, Sp, Qp, ldQ, selc = self._args
+        self._keep = (S_list, Q_list)
+        self.n = n
+        o = opts if opts is not None else make_opts(**kw)
+        self.create_status = np.zeros(max(count, 1), dtype=np.int32)
+        h = ctypes.c_void_p(None)
+        rc = lib.gbr_batch_create(count, n.ctypes.data_as(_ip), Sp, ldS.ctypes.data_as(_ip), Qp,
+                                  ldQ.ctypes.data_as(_ip) if ldQ is not None else None,
+                                  selc.ctypes.data_as(_ip), ctypes.byref(o),
+                                  self.create_status.ctypes.data_as(_ip), ctypes.byref(h),
+                                  _stream_handle(stream))
+        if rc != 0:
+            raise GbrError(rc, status_string(rc))
+        self._h = h
+
+    def run(self, stream=None) -> BatchResult:
+        lib = load()
+        count = len(self.n)
+        tot = int(self.n.sum())
+        wr = np.zeros(max(tot, 1))
+        wi = np.zeros(max(tot, 1))
+        m = np.zeros(max(count, 1), dtype=np.int32)
+        st = np.zeros(max(count, 1), dtype=np.int32)
+        stats = GbrStats()
+        rc = lib.gbr_batch_run(self._h, wr.ctypes.data_as(_dp), wi.ctypes.data_as(_dp),
+                               m.ctypes.data_as(_ip), st.ctypes.data_as(_ip), ctypes.byref(stats),
+                               _stream_handle(stream))
+        if rc < 0:
+            raise GbrError(rc, status_string(rc))
+        off = np.concatenate([[0], np.cumsum(self.n)])
+        eigs = [wr[off[i]:off[i + 1]] + 1j * wi[off[i]:off[i + 1]] for i in range(count)]
+        return BatchResult(status=st[:count], m=m[:count], eigs=eigs, stats=stats, rc=rc)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().gbr_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reorder_batched(S_list, Q_list, selects, *, opts: GbrOpts | None = None, stream=None,
+                    **kw) -> BatchResult:
+    """One-shot batched reorder (gbr_reorder_batched) of lists of column-major
+    CUDA tensors (Q_list may be None, or hold None entries); window/chain
+    AUTO (0) takes the autotuner's choice per instance."""
+    lib = load()
+    count, n, ldS, Sp, Qp, ldQ, selc = _batch_args(S_list, Q_list, selects)
+    o = opts if opts is not None else make_opts(**kw)
+    tot = int(n.sum())
+    wr = np.zeros(max(tot, 1))
+    wi = np.zeros(max(tot, 1))
+    m = np.zeros(max(count, 1), dtype=np.int32)
+    st = np.zeros(max(count, 1), dtype=np.int32)
+    stats = GbrStats()
+    rc = lib.gbr_reorder_batched(count, n.ctypes.data_as(_ip), Sp, ldS.ctypes.data_as(_ip), Qp,
+                                 ldQ.ctypes.data_as(_ip) if ldQ is not None else None,
+                                 selc.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
+                                 wi.ctypes.data_as(_dp), m.ctypes.data_as(_ip),
+                                 st.ctypes.data_as(_ip), ctypes.byref(o), ctypes.byref(stats),
+                                 _stream_handle(stream))
+    if rc < 0:
+        raise GbrError(rc, status_string(rc))
+    off = np.concatenate([[0], np.cumsum(n)])
+    eigs = [wr[off[i]:off[i + 1]] + 1j * wi[off[i]:off[i + 1]] for i in range(count)]
+    return BatchResult(status=st[:count], m=m[:count], eigs=eigs, stats=stats, rc=rc)
+
+
+def autotune(n_max: int, per_class: int = 256, stream=None) -> int:
+    """Run the batched-path autotuner for sizes up to n_max on the current
+    device; returns the number of size classes tuned."""
+    rc = load().gbr_autotune(int(n_max), int(per_class), _stream_handle(stream))
+    if rc < 0:
+        raise GbrError(rc, status_string(rc))
+    return rc
+
+
+def tune_get(n: int):
+    """(window, chain, far tile rows, tuned?) the batched path uses for order n."""
+    w, m, t = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    tuned = load().gbr_tune_get(int(n), ctypes.byref(w), ctypes.byref(m), ctypes.byref(t))
+    return w.value, m.value, t.value, bool(tuned)

@@ -42,11 +42,21 @@ struct DevCounters {
     unsigned long long win_flops;  // FP64 flops of in-window updates of accepted swaps
 };
 
+// One reordering problem on the device: a scheduler launch may carry many.
+struct Inst {
+    double* S;
+    double* Q;           // null: no Schur vectors
+    uint8_t* sel;        // SEL_* per position
+    DevCounters* ctr;
+    int n, ldS, ldQ, pad;
+};
+
 // One diagonal window in program order.
 struct Window {
     int s, e;            // rows/cols [s, e) of S
-    int chain;           // chain index
-    int u_off;           // offset (in doubles) of this window's U in the U pool
+    int chain;           // chain index (within its instance)
+    int inst;            // instance index (scheduler launches)
+    long long u_off;     // offset (in doubles) of this window's U in the U pool
 };
 
 // Persistent scheduler (sched.cu): task kinds and launch parameters.
@@ -60,21 +70,18 @@ struct SchedTask {
 };
 
 struct SchedParams {
-    int n, ldS, ldQ, strong, ntasks;
-    double* S;
-    double* Q;
-    uint8_t* sel;
-    DevCounters* ctr;
+    int strong, ntasks;
+    const Inst* inst;         // instance table
     const SchedTask* tasks;   // queue order
     const Window* wins;
     int* deps_left;           // unfinished predecessors per task
     const int* succ_off;      // CSR successors
     const int* succ;
-    double* upool;            // one WMAX x WMAX accumulator per window
+    double* upool;            // U of every window, at Window::u_off (w x w, column-major)
     unsigned char* uslices;   // null (DMMA updates) or OZ_USLICE_BYTES per window
     double* ozscratch;        // split precision: UPD_FAR x WMAX doubles per CTA
     int* head;                // next queue position
-    int* err;                 // nonzero: a wait ran out
+    int* err;                 // nonzero: a wait ran out (1) or the plan does not fit S (2)
     long long wait_limit;     // spins (~128 ns each) before a wait gives up
     unsigned long long* trace;  // null, or 4 words per queue position:
                                 // smid | wait start | exec start | end (ns)
@@ -91,6 +98,15 @@ cudaError_t launch_update(int n, const Window& w, double* S, int ldS, double* Q,
 size_t window_smem_bytes(int w);
 size_t update_smem_bytes(int w);
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st);
+cudaError_t sched_configure();  // kernel attributes for the current device (once)
+// Batched scans over an instance table: validation (bad_column per instance),
+// the subdiagonal pattern (sub + off[i], or a comparison with it that sets
+// *mismatch), and eigenvalues (wr/wi + off[i]).
+cudaError_t launch_validate_batched(int count, const Inst* inst, cudaStream_t st);
+cudaError_t launch_subdiag_batched(int count, const Inst* inst, const long long* off,
+                                   uint8_t* sub, int* mismatch, cudaStream_t st);
+cudaError_t launch_eigs_batched(int count, const Inst* inst, const long long* off, double* wr,
+                                double* wi, cudaStream_t st);
 size_t sched_smem_bytes();
 int sched_threads();
 

@@ -1,0 +1,119 @@
+// Host-side internals shared by the entry points (api.cu, batch.cu,
+// server.cu): error reporting, the window planner, the task graph and the
+// persistent-scheduler launch image.
+#pragma once
+
+#include "../../include/gbreorder.h"
+#include "common.cuh"
+
+#include <functional>
+#include <string>
+#include <vector>
+
+namespace gbr {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+void set_last_error(const std::string& s);
+const char* last_error_cstr();
+int cuda_fail(cudaError_t e, const char* what);
+
+#define GBR_CK(call, what)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ::gbr::cuda_fail(e_, what); \
+    } while (0)
+
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// Planner (Section 3.2: windows and chains)
+// ---------------------------------------------------------------------------
+struct PlanState {
+    int n = 0;
+    std::vector<uint8_t> bsz;  // size of the block starting at a position, else 0
+    std::vector<uint8_t> sel;  // SEL_* per position (uniform inside a block)
+};
+
+void init_state(PlanState& st, int n, const uint8_t* sub, const uint8_t* sel);
+void sim_window(PlanState& st, int s, int e);
+void plan_pass(PlanState& st, int w, int m, std::vector<Window>& win, int& nchains);
+// Per-position selection from the caller's per-eigenvalue flags (a 2x2 block
+// is selected if either row is); returns the number of selected positions.
+int selection_positions(int n, const uint8_t* sub, const int* select, uint8_t* sel);
+// Update flops of a window list: 2 w^2 (panel rows of L, R and Q).
+double update_flops(int n, const std::vector<Window>& win, bool withQ);
+
+// ---------------------------------------------------------------------------
+// Task graph and queue order (Section 3.2, Fig. 2)
+// ---------------------------------------------------------------------------
+struct Rect {
+    int r0, r1, c0, c1;  // rows [r0, r1) x columns [c0, c1)
+};
+
+struct HostTask {
+    int kind, win, y0, rows, mat;  // mat 0 = S, 1 = Q
+    Rect rc;
+    double dur;                     // estimated duration (microseconds)
+};
+
+struct TaskGraph {
+    std::vector<HostTask> t;
+    std::vector<int> ndeps;
+    std::vector<int> soff, succ;    // CSR successors, program order
+};
+
+// Duration model of the queue order (microseconds).
+struct CostModel {
+    double win_us_128 = 2600.0;  // window task at w = 128 (scales as w^2)
+    double tile_rate = 6900.0;   // update flops per microsecond of one SM
+    double task_us = 2.0;        // fixed cost per update task
+};
+
+int far_rows(int n);
+void pipeline_order(int n, std::vector<Window>& wins);
+// far: panel rows of the update tiles away from the window (0: far_rows(n)).
+void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostModel& cm,
+                 TaskGraph& G, int far = 0);
+void queue_order(const TaskGraph& G, int P, std::vector<int>& order, double* cp_us = nullptr,
+                 double* sim_us = nullptr);
+
+// ---------------------------------------------------------------------------
+// Persistent-scheduler launch over one or more instances
+// ---------------------------------------------------------------------------
+struct InstPlan {
+    Inst d;                    // device pointers and sizes
+    std::vector<Window> wins;  // planner order (pipeline order is applied here)
+    int far = 0;               // far update-tile rows (0: far_rows(n))
+};
+
+struct SchedInfo {
+    long long tasks = 0;
+    double cp_us = 0.0, sim_us = 0.0, graph_ms = 0.0, order_ms = 0.0;
+};
+
+// Device image of a scheduler launch: prepared once, launched one or more
+// times (each launch restores the dependency counters from deps_init).
+struct SchedLaunch {
+    SchedParams P{};
+    int grid = 0;
+    int* deps_init = nullptr;
+    int* ctl = nullptr;               // head, err (and spare words), 256 bytes
+    size_t trace_bytes = 0;
+    std::vector<SchedTask> tq;        // host copy of the queue (trace decoding)
+};
+
+// Plans the task graph of all instances, orders it for `grid` CTAs, and
+// uploads it into device memory obtained from alloc(bytes) (which must
+// return 256-byte aligned memory that outlives the launches, or null).
+int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostModel& cm, int grid,
+                  const std::function<void*(size_t)>& alloc, SchedLaunch* L, SchedInfo* info,
+                  cudaStream_t st);
+// Enqueues one launch: dependency counters restored, control words reset,
+// then pre(st) if given (it may set *P.err to stop the launch early), then
+// the kernel.  Only stream operations: capturable into a CUDA graph.
+int sched_enqueue(const SchedLaunch& L, cudaStream_t st,
+                  const std::function<int(cudaStream_t)>& pre = nullptr);
+
+}  // namespace gbr

@@ -1,7 +1,8 @@
 // Persistent device scheduler for the window and update tasks (Section 3.2,
 // Fig. 2: window tasks W and right/left update tasks, executed in a
 // sequentially consistent order without global synchronization, with several
-// windows in flight).
+// windows in flight).  One launch may carry the tasks of many independent
+// reordering problems (an instance table; each window names its instance).
 //
 // One CTA per SM loops over a task queue that the host has put in a
 // critical-path-first order.  Each task is either a window task (one diagonal
@@ -76,9 +77,10 @@ sched_kernel(SchedParams P) {
         if (P.trace && tid == 0) P.trace[4 * t + 2] = global_ns();
         const SchedTask tk = P.tasks[t];
         const Window wd = P.wins[tk.win];
-        double* Ug = P.upool + (size_t)tk.win * WMAX * WMAX;
+        const Inst I = P.inst[wd.inst];
+        double* Ug = P.upool + wd.u_off;
         if (tk.kind == TASK_W) {
-            win::window_body(P.n, P.S, P.ldS, wd.s, wd.e - wd.s, P.sel, Ug, P.strong, P.ctr,
+            win::window_body(I.n, I.S, I.ldS, wd.s, wd.e - wd.s, I.sel, Ug, P.strong, I.ctr,
                              smem_raw,
                              P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr);
             if (tid == 0) u_win = -1;  // shared memory no longer holds a U
@@ -86,7 +88,7 @@ sched_kernel(SchedParams P) {
             double* base;
             long long rs, ks;
             int R;
-            upd::panel_geom(tk.kind - TASK_L, P.n, wd.s, wd.e, P.S, P.ldS, P.Q, P.ldQ, &base, &rs,
+            upd::panel_geom(tk.kind - TASK_L, I.n, wd.s, wd.e, I.S, I.ldS, I.Q, I.ldQ, &base, &rs,
                             &ks, &R);
             bool load_u = (u_win != tk.win);
             __syncthreads();
@@ -121,17 +123,21 @@ sched_kernel(SchedParams P) {
 size_t sched_smem_bytes() { return kSchedSmem; }
 int sched_threads() { return SCHED_THREADS; }
 
-cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st) {
+cudaError_t sched_configure() {
     static bool configured[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(sched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSchedSmem);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) configured[dev] = true;
-    }
+    if (dev >= 0 && dev < 64 && configured[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(sched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSchedSmem);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = true;
+    return e;
+}
+
+cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st) {
+    cudaError_t e = sched_configure();
+    if (e != cudaSuccess) return e;
     sched_kernel<<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
     return cudaGetLastError();
 }

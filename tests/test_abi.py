@@ -78,3 +78,46 @@ def test_argument_errors_before_gpu(lib):
     # n = 0 is a no-op that succeeds without a GPU
     rc, m = call(lib, 0, None, 1, None, 1, sel)
     assert rc == 0 and m == 0
+
+
+def batch_create(lib, count, n, S, ldS, Q, ldQ, sel, opts=None, want_out=True):
+    ip = ctypes.POINTER(ctypes.c_int)
+    arr = lambda a: a.ctypes.data_as(ip) if a is not None else None
+    h = ctypes.c_void_p(None)
+    o = opts or g.default_opts()
+    st = np.zeros(max(count, 1), dtype=np.int32)
+    return lib.gbr_batch_create(count, arr(n), S, arr(ldS), Q, arr(ldQ), arr(sel), ctypes.byref(o),
+                                arr(st), ctypes.byref(h) if want_out else None, None)
+
+
+def test_batched_argument_checks(lib):
+    """Argument errors of the batched entry point come back before any GPU
+    work (LAPACK-style -i)."""
+    n = np.array([4, 6], dtype=np.int32)
+    ld = np.array([4, 6], dtype=np.int32)
+    fake = (ctypes.c_void_p * 2)(0x1000, 0x2000)
+    sel = np.zeros(10, dtype=np.int32)
+    assert batch_create(lib, -1, n, fake, ld, None, None, sel) == -1
+    assert batch_create(lib, 2, None, fake, ld, None, None, sel) == -2
+    assert batch_create(lib, 2, np.array([4, -1], np.int32), fake, ld, None, None, sel) == -2
+    assert batch_create(lib, 2, n, None, ld, None, None, sel) == -3
+    assert batch_create(lib, 2, n, (ctypes.c_void_p * 2)(0x1000, None), ld, None, None, sel) == -3
+    assert batch_create(lib, 2, n, fake, np.array([4, 5], np.int32), None, None, sel) == -4
+    assert batch_create(lib, 2, n, fake, ld, fake, None, sel) == -6
+    assert batch_create(lib, 2, n, fake, ld, fake, np.array([4, 2], np.int32), sel) == -6
+    assert batch_create(lib, 2, n, fake, ld, None, None, None) == -7
+    assert batch_create(lib, 2, n, fake, ld, None, None, sel, want_out=False) == -10
+    assert batch_create(lib, 2, n, fake, ld, None, None, sel, opts=g.make_opts(window=200)) == -8
+    assert batch_create(lib, 2, n, fake, ld, None, None, sel, opts=g.make_opts(window=16, chain=15)) == -8
+    assert batch_create(lib, 2, n, fake, ld, None, None, sel,
+                        opts=g.make_opts(sched="sequential")) == g.ERR_UNSUPPORTED
+    assert lib.gbr_batch_run(None, None, None, None, None, None, None) == -1
+    lib.gbr_batch_destroy(None)  # no-op
+    assert lib.gbr_status_string(g.ERR_PLAN_MISMATCH)
+
+
+def test_tuner_defaults_without_tuning(lib):
+    w, m, t, tuned = g.tune_get(300)
+    assert not tuned and (w, m) == (128, 64) and t >= 64
+    assert lib.gbr_autotune(0, 10, None) == -1
+    assert lib.gbr_autotune(64, 0, None) == -2
