@@ -49,6 +49,8 @@ WORKLOADS = {
     "n400": dict(name="n400", n=400, select=0.30, q="identity", window=128, chain=64),
     "n16000c": dict(name="n16000c", n=16000, select=0.50, q="64 Householder reflectors",
                     window=128, chain=64),
+    "batch4096": dict(name="batch4096", kind="batch", count=4096, nmin=32, nmax=512,
+                      select="U(0.2, 0.6) per instance", q="min(n, 64) Householder reflectors"),
 }
 METRIC = "selected eigenvalues reordered per second"
 
@@ -177,13 +179,22 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import oracle
-    S, Q, sel = make_inputs(wl)
-    nsel = int(expected_selected(S, sel))
+    if wl.get("kind") == "batch":
+        probs = batch_inputs(wl)
+        nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
+        sample = lambda: batch_cpu_sample(probs, budget_s=6.0)
+        cfg = {"workload": wl["name"], "instances": wl["count"],
+               "n": f"U{{{wl['nmin']}..{wl['nmax']}}}", "select": wl["select"], "q": wl["q"]}
+    else:
+        S, Q, sel = make_inputs(wl)
+        nsel = int(expected_selected(S, sel))
+        sample = lambda: cpu_oracle_sample(S, Q, sel, budget_s=8.0)
+        cfg = {"workload": wl["name"], "n": wl["n"], "select": wl["select"],
+               "q": wl["q"], "window": wl["window"], "chain": wl["chain"]}
     times = []
     samples = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_oracle_sample(S, Q, sel, budget_s=8.0)
+        cb = sample()
         if i >= args.warmup:
             times.append(nsel / cb["value"])
             samples.append(cb["sample"])
@@ -192,8 +203,7 @@ def run_reference(args, wl):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "n": wl["n"], "select": wl["select"],
-                       "q": wl["q"], "window": wl["window"], "chain": wl["chain"]},
+            "config": cfg,
             "cpu_baseline": {"value": value, "unit": "eigs/s", "cores": 1, "kind": "oracle",
                              "sample": samples[-1]},
             "e2e": {"value": value, "unit": "eigs/s", "h2d_bytes_per_step": 0,
@@ -216,6 +226,182 @@ def expected_selected(S, sel):
     return cnt
 
 
+def batch_inputs(wl, seed=0):
+    """The batched workload: per instance (S, Q, select) from the seeded
+    generator, n ~ U{nmin..nmax}, p ~ U(0.2, 0.6)."""
+    out = []
+    for n, p, sd in si.batch_problems(wl["count"], seed, wl["nmin"], wl["nmax"]):
+        out.append(si.reorder_problem(n, sd, select_frac=p, q="householder",
+                                      reflectors=min(n, 64)))
+    return out
+
+
+def batch_cpu_sample(probs, budget_s=12.0):
+    """The oracle on the first instances of the batch until ~budget_s,
+    scaled to the whole batch by selected eigenvalues."""
+    import oracle
+    t0 = time.perf_counter()
+    done = 0
+    eigs = 0
+    while done < len(probs) and time.perf_counter() - t0 < budget_s:
+        S, Q, sel = probs[done]
+        oracle.reorder(S, Q, sel)
+        eigs += expected_selected(S, sel)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": eigs / dt, "unit": "eigs/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of {len(probs)} instances ({eigs} selected eigenvalues) "
+                      f"in {dt:.1f} s on 1 core"}
+
+
+def run_batch(args, wl):
+    import torch
+    import paper_1905_04975_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+    probs = batch_inputs(wl, seed=rank)
+    ns = [S.shape[0] for S, _, _ in probs]
+    sizes = np.array([n * n for n in ns], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    tot = int(off[-1])
+    nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
+    # one flat pinned host buffer per matrix kind, column-major instances back to back
+    hS = torch.empty(tot, dtype=torch.float64).pin_memory()
+    hQ = torch.empty(tot, dtype=torch.float64).pin_memory()
+    hSn, hQn = hS.numpy(), hQ.numpy()
+    for i, (S, Q, _) in enumerate(probs):
+        hSn[off[i]:off[i + 1]] = S.ravel(order="F")
+        hQn[off[i]:off[i + 1]] = Q.ravel(order="F")
+    dS, dQ = hS.cuda(), hQ.cuda()
+    dS0, dQ0 = dS.clone(), dQ.clone()
+
+    def views(buf):
+        return [buf[off[i]:off[i + 1]].view(ns[i], ns[i]).t() for i in range(len(ns))]
+    Sv, Qv = views(dS), views(dQ)
+    sels = [sel for _, _, sel in probs]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    tuned = g.autotune(wl["nmax"], 256, stream=stream)
+    tune_s = time.perf_counter() - t0
+    choices = {c: g.tune_get(2 ** c) for c in range(5, 10)}
+    opts = g.make_opts(window=g.AUTO, chain=g.AUTO, precision=args.precision, timing=True)
+    t0 = time.perf_counter()
+    batch = g.Batch(Sv, Qv, sels, opts=opts, stream=stream)
+    plan_s = time.perf_counter() - t0
+
+    def restore():
+        with torch.cuda.stream(stream):
+            dS.copy_(dS0)
+            dQ.copy_(dQ0)
+        stream.synchronize()
+
+    def step():
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = batch.run(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        r, _ = step()
+        assert r.rc == 0 and np.all(r.status == 0), r.rc
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            r, t = step()
+            ms.append(t)
+            stats.append(r.stats)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = nsel * args.steps * world / (total_ms / 1e3)
+    st0 = stats[0]
+    ms_sched = sum(s.ms_sched for s in stats) / len(stats)
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)
+    work = st0.upd_flops + st0.win_flops
+    achieved = work / (ms_sched / 1e3) / 1e12
+    roof = {"kernel": "sched_kernel (persistent, all instances: window tasks + update tiles)",
+            "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": None,
+            "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 1.25/2250"),
+            "flops_per_launch": work, "launches_per_step": 1, "avg_launch_ms": ms_sched,
+            "share_of_step": ms_sched / (total_ms / args.steps),
+            "critical_path_model_ms": st0.sched_cp_ms}
+
+    # end to end: inputs from pinned host memory, results back, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        oS = torch.empty(tot, dtype=torch.float64).pin_memory()
+        oQ = torch.empty(tot, dtype=torch.float64).pin_memory()
+        et = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                dS.copy_(hS, non_blocking=True)
+                dQ.copy_(hQ, non_blocking=True)
+            rr = batch.run(stream=stream)
+            with torch.cuda.stream(stream):
+                oS.copy_(dS, non_blocking=True)
+                oQ.copy_(dQ, non_blocking=True)
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+            assert rr.rc == 0
+            if i > 0:
+                et.append(dt)
+        e2e = {"value": nsel * len(et) / sum(et) * world, "unit": "eigs/s",
+               "h2d_bytes_per_step": 2 * tot * 8 + 4 * int(sum(ns)),
+               "d2h_bytes_per_step": 2 * tot * 8 + 16 * int(sum(ns))}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = batch_cpu_sample(probs)
+    batch.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "eigs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "instances": len(ns),
+                           "n": f"U{{{wl['nmin']}..{wl['nmax']}}}", "select": wl["select"],
+                           "selected_eigs": nsel, "q": wl["q"], "window": "autotuned",
+                           "chain": "autotuned", "precision": args.precision,
+                           "l2": f"S,Q ({2 * tot * 8 / 1e9:.1f} GB > L2) restored from a device "
+                                 "copy before each step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": int(sum(s.launches for s in stats)),
+                "detail": {"windows": int(st0.windows), "tasks": int(st0.tasks),
+                           "swaps": int(st0.swaps), "upd_flops": st0.upd_flops,
+                           "win_flops": st0.win_flops, "plan_s": plan_s, "autotune_s": tune_s,
+                           "classes_tuned": tuned,
+                           "tuned": {f"n<={2 ** c}": v[:3] for c, v in choices.items()},
+                           "host_graph_ms": st0.ms_graph, "host_order_ms": st0.ms_order}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,6 +417,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if wl.get("kind") == "batch":
+        return run_batch(args, wl)
 
     import torch
     import paper_1905_04975_gb300 as g
