@@ -266,6 +266,79 @@ int gbr_autotune(int n_max, int per_class, void *cuda_stream);
 int gbr_tune_get(int n, int *window, int *chain, int *tile);
 
 /*
+ * Reordering server: continuous batching of requests on one GPU.  No
+ * counterpart in the paper; each request is the reordering of Eq. 7 with
+ * the tasks of Section 3.2.
+ *
+ * One long-lived kernel (one CTA per SM, or cfg.sms of them) runs the tasks
+ * of every request; a server thread feeds it through a ring of (request,
+ * task) entries in device memory, appending a chunk of each request's tasks
+ * in turn, so a request that arrives while others are on the GPU starts
+ * within one chunk of their tasks.  Requests are validated and planned on
+ * the submitting thread, admitted in arrival order while their device
+ * footprint (S, Q, window accumulators, task graph) fits under
+ * mem_cap_bytes and a request slot is free, copied to device memory owned
+ * by the server where they stay until they complete, and copied back to
+ * the caller's buffers at the end.  A request's result does not depend on
+ * the other requests in flight.  While a server exists, its kernel occupies
+ * its SMs: other kernels of the process wait for them.
+ */
+typedef struct gbr_server gbr_server;
+
+typedef struct gbr_server_cfg {
+    long long mem_cap_bytes; /* device memory for admitted requests (default 60e9) */
+    int max_inflight;        /* request slots on the device (default 512)          */
+    int sms;                 /* CTAs of the server kernel, 0 = one per SM (default) */
+    long long ring_entries;  /* task ring capacity (default 4M entries, 32 MB)      */
+    long long idle_limit_ms; /* the kernel gives up after this long with nothing to
+                                do (0: one hour); requests in flight then fail   */
+    int device;              /* CUDA device (default -1: current at create)       */
+    gbr_opts opts;           /* per-request options (gbr_default_opts); window
+                                and chain GBR_AUTO use the autotuner table       */
+} gbr_server_cfg;
+
+typedef struct gbr_server_stats {
+    long long submitted, completed, failed;
+    long long passes;       /* planned passes uploaded (> completed after rejections) */
+    double p50_ms, p99_ms, max_ms;  /* latency: submit to results in the caller's buffers */
+    double mean_ms;
+    double req_per_s;       /* completed / (last completion - first submit) */
+    double eigs_per_s;      /* selected eigenvalues of completed requests, same span */
+    double mean_inflight;   /* requests on the device, averaged over server iterations */
+    double peak_mem_bytes;  /* largest admitted footprint */
+} gbr_server_stats;
+
+void gbr_server_default_cfg(gbr_server_cfg *cfg);
+
+/* Starts a server.  Returns 0, -1 (cfg invalid), or GBR_ERR_*. */
+int gbr_server_create(const gbr_server_cfg *cfg, gbr_server **out);
+
+/*
+ * Submits one request: n, host S (ldS), host Q or NULL (ldQ), host select
+ * (n ints), and optional host eig_re/eig_im (n doubles each).  Every buffer
+ * must stay valid and untouched until the request completes; S and Q are
+ * overwritten with the result then.  Pinned (page-locked) buffers copy
+ * fastest.  Returns a ticket >= 0, or -i / GBR_ERR_* (a request larger than
+ * the memory cap gives GBR_ERR_NOMEM).
+ */
+long long gbr_server_submit(gbr_server *srv, int n, double *S, int ldS, double *Q, int ldQ,
+                            const int *select, double *eig_re, double *eig_im);
+
+/* 1 if the request completed (status and m written, when non-NULL), 0 if
+   not yet, -1 for an unknown ticket.  status as for gbr_reorder. */
+int gbr_server_poll(gbr_server *srv, long long ticket, int *status, int *m_out);
+
+/* Waits up to timeout_ms (< 0: no limit) for a request; returns as poll. */
+int gbr_server_wait(gbr_server *srv, long long ticket, int *status, int *m_out,
+                    long long timeout_ms);
+
+/* Latency and throughput of the requests completed so far. */
+int gbr_server_get_stats(gbr_server *srv, gbr_server_stats *out);
+
+/* Waits for all submitted requests, stops the server and frees it. */
+void gbr_server_destroy(gbr_server *srv);
+
+/*
  * Window plan of a reordering, on the host only (no GPU work): the diagonal
  * windows that gbr_reorder launches, in program order, assuming no swap is
  * rejected (Section 3.2, Fig. 2: one chain of windows per group of at most

@@ -56,6 +56,22 @@ class GbrStats(ctypes.Structure):
                 ("ms_graph", ctypes.c_double), ("ms_order", ctypes.c_double)]
 
 
+class GbrServerCfg(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_longlong), ("max_inflight", ctypes.c_int),
+                ("sms", ctypes.c_int), ("ring_entries", ctypes.c_longlong),
+                ("idle_limit_ms", ctypes.c_longlong), ("device", ctypes.c_int),
+                ("opts", GbrOpts)]
+
+
+class GbrServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("passes", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("req_per_s", ctypes.c_double), ("eigs_per_s", ctypes.c_double),
+                ("mean_inflight", ctypes.c_double), ("peak_mem_bytes", ctypes.c_double)]
+
+
 # Every symbol the header declares, with (restype, argtypes).
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -87,6 +103,16 @@ SYMBOLS = {
                                            ctypes.POINTER(GbrStats), ctypes.c_void_p]),
     "gbr_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "gbr_tune_get": (ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip]),
+    "gbr_server_default_cfg": (None, [ctypes.POINTER(GbrServerCfg)]),
+    "gbr_server_create": (ctypes.c_int, [ctypes.POINTER(GbrServerCfg),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "gbr_server_submit": (ctypes.c_longlong, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                              ctypes.c_int, _ip, _dp, _dp]),
+    "gbr_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, _ip, _ip]),
+    "gbr_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, _ip, _ip,
+                                       ctypes.c_longlong]),
+    "gbr_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GbrServerStats)]),
+    "gbr_server_destroy": (None, [ctypes.c_void_p]),
 }
 
 _lib = None
@@ -442,3 +468,103 @@ def tune_get(n: int):
     w, m, t = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     tuned = load().gbr_tune_get(int(n), ctypes.byref(w), ctypes.byref(m), ctypes.byref(t))
     return w.value, m.value, t.value, bool(tuned)
+
+
+# ---------------------------------------------------------------------------
+# Reordering server (continuous batching)
+# ---------------------------------------------------------------------------
+def server_cfg(mem_cap_bytes=None, max_inflight=None, sms=None, ring_entries=None,
+               idle_limit_ms=None, device=None, opts: GbrOpts | None = None,
+               **kw) -> GbrServerCfg:
+    c = GbrServerCfg()
+    load().gbr_server_default_cfg(ctypes.byref(c))
+    for name, v in (("mem_cap_bytes", mem_cap_bytes), ("max_inflight", max_inflight),
+                    ("sms", sms), ("ring_entries", ring_entries),
+                    ("idle_limit_ms", idle_limit_ms), ("device", device)):
+        if v is not None:
+            setattr(c, name, int(v))
+    c.opts = opts if opts is not None else make_opts(**kw)
+    return c
+
+
+class Server:
+    """gbr_server: submit host (numpy, Fortran-ordered float64) S and Q;
+    they are overwritten in place when the request completes.  The object
+    keeps every buffer of a request alive until it has completed."""
+
+    def __init__(self, cfg: GbrServerCfg | None = None, **kw):
+        lib = load()
+        self._cfg = cfg if cfg is not None else server_cfg(**kw)
+        h = ctypes.c_void_p(None)
+        rc = lib.gbr_server_create(ctypes.byref(self._cfg), ctypes.byref(h))
+        if rc != 0:
+            raise GbrError(rc, status_string(rc))
+        self._h = h
+        self._live = {}
+
+    def submit(self, S: np.ndarray, Q: np.ndarray | None, select, eigs: bool = True) -> int:
+        if not (S.flags.f_contiguous and S.dtype == np.float64):
+            raise ValueError("S must be a Fortran-ordered float64 array")
+        if Q is not None and not (Q.flags.f_contiguous and Q.dtype == np.float64):
+            raise ValueError("Q must be a Fortran-ordered float64 array")
+        n = int(S.shape[0])
+        sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+        if sel.size != n:
+            raise ValueError("select must have n entries")
+        wr = np.zeros(max(n, 1)) if eigs else None
+        wi = np.zeros(max(n, 1)) if eigs else None
+        t = load().gbr_server_submit(
+            self._h, n, S.ctypes.data_as(_dp), max(n, 1),
+            Q.ctypes.data_as(_dp) if Q is not None else None, max(n, 1),
+            sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp) if eigs else None,
+            wi.ctypes.data_as(_dp) if eigs else None)
+        if t < 0:
+            raise GbrError(int(t), status_string(int(t)))
+        self._live[t] = (S, Q, sel, wr, wi)
+        return int(t)
+
+    def _result(self, t, rc, st, m):
+        if rc != 1:
+            return None
+        S, Q, sel, wr, wi = self._live.pop(t)
+        n = S.shape[0]
+        e = (wr[:n] + 1j * wi[:n]) if wr is not None else None
+        return ReorderResult(status=st.value, m=m.value, eigs=e, stats=None)
+
+    def poll(self, ticket: int):
+        st, m = ctypes.c_int(0), ctypes.c_int(0)
+        rc = load().gbr_server_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(m))
+        if rc < 0:
+            raise KeyError(ticket)
+        return self._result(ticket, rc, st, m)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        st, m = ctypes.c_int(0), ctypes.c_int(0)
+        rc = load().gbr_server_wait(self._h, ticket, ctypes.byref(st), ctypes.byref(m),
+                                    int(timeout_ms))
+        if rc < 0:
+            raise KeyError(ticket)
+        return self._result(ticket, rc, st, m)
+
+    def stats(self) -> dict:
+        s = GbrServerStats()
+        load().gbr_server_get_stats(self._h, ctypes.byref(s))
+        return {f: getattr(s, f) for f, _ in GbrServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().gbr_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -60,7 +60,8 @@ struct Window {
 };
 
 // Persistent scheduler (sched.cu): task kinds and launch parameters.
-enum : int { TASK_W = 0, TASK_L = 1, TASK_R = 2, TASK_Q = 3 };  // L/R/Q = TASK_L + panel
+enum : int { TASK_W = 0, TASK_L = 1, TASK_R = 2, TASK_Q = 3,  // L/R/Q = TASK_L + panel
+             TASK_E = 4 };  // server: eigenvalues + completion of a request (its last task)
 
 struct SchedTask {
     int kind;   // TASK_*
@@ -87,6 +88,45 @@ struct SchedParams {
                                 // smid | wait start | exec start | end (ns)
 };
 
+// Server kernel (sched.cu): a ring of (request slot, local task) entries and
+// a table of requests, all in device memory written by the host.
+struct RingEntry {
+    int req;     // request slot
+    int local;   // task index in the request's queue order
+};
+
+struct SrvReq {
+    Inst inst;                  // S, Q, selection, counters, sizes
+    const SchedTask* tasks;     // queue order; the last one is TASK_E
+    const Window* wins;         // u_off: offset of the window's U in upool
+    int* deps;                  // unfinished predecessors per task
+    const int* succ_off;        // CSR successors (local indices)
+    const int* succ;
+    double* upool;
+    unsigned char* uslices;     // null, or OZ_USLICE_BYTES per window
+    double* eig;                // 2n: real parts, imaginary parts
+    int ntasks;
+    int id;                     // unique per admitted pass (written to the completion word)
+    int done_slot;              // completion word index
+    int pad;
+};
+
+struct SrvParams {
+    const RingEntry* ring;
+    long long cap;              // ring entries
+    long long* head;            // next position to take
+    const long long* tail;      // positions below are published
+    const int* stop;            // nonzero: leave when idle
+    int* err;                   // 1: a dependency wait ran out; 3: the ring stayed empty too long
+    const SrvReq* reqs;
+    double* ozscratch;          // UPD_FAR x WMAX doubles per CTA
+    int* done;                  // completion words (host memory, mapped)
+    int strong;
+    int pad;
+    long long wait_limit;       // spins (~128 ns) of a dependency wait
+    long long park_limit;       // spins (~1 us) of a wait for the ring to fill
+};
+
 // Launchers (each .cu file owns its kernels).
 cudaError_t launch_validate(int n, const double* S, int ldS, DevCounters* ctr, cudaStream_t st);
 cudaError_t launch_subdiag(int n, const double* S, int ldS, uint8_t* sub, cudaStream_t st);
@@ -99,6 +139,7 @@ size_t window_smem_bytes(int w);
 size_t update_smem_bytes(int w);
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st);
 cudaError_t sched_configure();  // kernel attributes for the current device (once)
+cudaError_t launch_server(const SrvParams& P, int grid, cudaStream_t st);
 // Batched scans over an instance table: validation (bad_column per instance),
 // the subdiagonal pattern (sub + off[i], or a comparison with it that sets
 // *mismatch), and eigenvalues (wr/wi + off[i]).

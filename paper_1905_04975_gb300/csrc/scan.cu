@@ -1,7 +1,7 @@
 // Block-structure kernels of a real Schur form (Eq. 4): input validation,
 // the subdiagonal pattern that marks the 2x2 blocks, and the eigenvalues read
 // from the diagonal blocks.
-#include "common.cuh"
+#include "scan_body.cuh"
 
 #include <limits.h>
 
@@ -38,20 +38,11 @@ __global__ void subdiag_kernel(int n, const double* __restrict__ S, int ldS,
         sub[i] = (i + 1 < n && S[cm(i + 1, i, ldS)] != 0.0) ? 1 : 0;
 }
 
-// 1x1 block s -> (s, 0); standardized 2x2 [[a, b], [c, a]] -> a +- i sqrt(-bc),
-// positive imaginary part on the first row.
+// Eigenvalues read off the diagonal blocks (eig_at).
 __global__ void eigs_kernel(int n, const double* __restrict__ S, int ldS, double* __restrict__ wr,
                             double* __restrict__ wi) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double re = S[cm(i, i, ldS)], im = 0.0;
-        if (i + 1 < n && S[cm(i + 1, i, ldS)] != 0.0) {
-            im = sqrt(fabs(S[cm(i, i + 1, ldS)])) * sqrt(fabs(S[cm(i + 1, i, ldS)]));
-        } else if (i > 0 && S[cm(i, i - 1, ldS)] != 0.0) {
-            im = -(sqrt(fabs(S[cm(i - 1, i, ldS)])) * sqrt(fabs(S[cm(i, i - 1, ldS)])));
-        }
-        wr[i] = re;
-        wi[i] = im;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        eig_at(n, S, ldS, i, &wr[i], &wi[i]);
 }
 
 // Batched forms: blockIdx.y (strided) picks the instance, the x dimension
@@ -97,18 +88,8 @@ __global__ void eigs_batched_kernel(int count, const Inst* __restrict__ inst,
                                     double* __restrict__ wi) {
     for (int b = blockIdx.y; b < count; b += gridDim.y) {
         const Inst I = inst[b];
-        const double* S = I.S;
-        const int n = I.n, ldS = I.ldS;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-            double re = S[cm(i, i, ldS)], im = 0.0;
-            if (i + 1 < n && S[cm(i + 1, i, ldS)] != 0.0) {
-                im = sqrt(fabs(S[cm(i, i + 1, ldS)])) * sqrt(fabs(S[cm(i + 1, i, ldS)]));
-            } else if (i > 0 && S[cm(i, i - 1, ldS)] != 0.0) {
-                im = -(sqrt(fabs(S[cm(i - 1, i, ldS)])) * sqrt(fabs(S[cm(i, i - 1, ldS)])));
-            }
-            wr[off[b] + i] = re;
-            wi[off[b] + i] = im;
-        }
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.n; i += gridDim.x * blockDim.x)
+            eig_at(I.n, I.S, I.ldS, i, &wr[off[b] + i], &wi[off[b] + i]);
     }
 }
 

@@ -15,6 +15,7 @@
 // waits on tasks already taken by running CTAs: no deadlock, no co-residency
 // requirement.  Every wait is bounded; a wait that runs out sets an error
 // flag, and all CTAs leave the loop at their next check.
+#include "scan_body.cuh"
 #include "update_body.cuh"
 #include "window_body.cuh"
 
@@ -42,12 +43,48 @@ __device__ __forceinline__ unsigned smid() {
     return r;
 }
 
+// Runs one window task or update tile of window wd of instance I.  u_key
+// names the U held in shared memory by the previous task of this CTA (an
+// update tile of the same window reuses it); key names this task's window.
+__device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, const Inst& I,
+                                         double* Ug, unsigned char* uslices, double* ozscratch,
+                                         int strong, unsigned long long key,
+                                         unsigned long long* u_key, unsigned char* smem_raw) {
+    const int tid = threadIdx.x;
+    if (tk.kind == TASK_W) {
+        win::window_body(I.n, I.S, I.ldS, wd.s, wd.e - wd.s, I.sel, Ug, strong, I.ctr, smem_raw,
+                         uslices);
+        if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds a U
+        return;
+    }
+    double* base;
+    long long rs, ks;
+    int R;
+    upd::panel_geom(tk.kind - TASK_L, I.n, wd.s, wd.e, I.S, I.ldS, I.Q, I.ldQ, &base, &rs, &ks, &R);
+    bool load_u = (*u_key != key);
+    __syncthreads();
+    if (uslices) {
+        for (int r = 0; r < tk.rows; r += UPD_FAR)
+            upd::update_tile_ozaki(base, rs, ks, tk.y0 + r, min(UPD_FAR, tk.rows - r), wd.e - wd.s,
+                                   uslices, ozscratch, smem_raw);
+        if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds U
+    } else {
+        for (int r = 0; r < tk.rows; r += upd::BM) {
+            upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s, Ug,
+                             load_u, smem_raw);
+            load_u = false;
+        }
+        if (tid == 0) *u_key = key;
+    }
+}
+
 __global__ void __launch_bounds__(SCHED_THREADS, 1)
 sched_kernel(SchedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int task_id, u_win;
+    __shared__ int task_id;
+    __shared__ unsigned long long u_key;
     const int tid = threadIdx.x;
-    if (tid == 0) u_win = -1;
+    if (tid == 0) u_key = ~0ull;
     for (;;) {
         if (tid == 0) {
             int t = atomicAdd(P.head, 1);
@@ -78,35 +115,10 @@ sched_kernel(SchedParams P) {
         const SchedTask tk = P.tasks[t];
         const Window wd = P.wins[tk.win];
         const Inst I = P.inst[wd.inst];
-        double* Ug = P.upool + wd.u_off;
-        if (tk.kind == TASK_W) {
-            win::window_body(I.n, I.S, I.ldS, wd.s, wd.e - wd.s, I.sel, Ug, P.strong, I.ctr,
-                             smem_raw,
-                             P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr);
-            if (tid == 0) u_win = -1;  // shared memory no longer holds a U
-        } else {
-            double* base;
-            long long rs, ks;
-            int R;
-            upd::panel_geom(tk.kind - TASK_L, I.n, wd.s, wd.e, I.S, I.ldS, I.Q, I.ldQ, &base, &rs,
-                            &ks, &R);
-            bool load_u = (u_win != tk.win);
-            __syncthreads();
-            if (P.uslices) {
-                for (int r = 0; r < tk.rows; r += UPD_FAR)
-                    upd::update_tile_ozaki(base, rs, ks, tk.y0 + r, min(UPD_FAR, tk.rows - r),
-                                           wd.e - wd.s, P.uslices + (size_t)tk.win * OZ_USLICE_BYTES,
-                                           P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX,
-                                           smem_raw);
-                load_u = true;  // shared memory no longer holds U
-            } else
-            for (int r = 0; r < tk.rows; r += upd::BM) {
-                upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s, Ug,
-                                 load_u, smem_raw);
-                load_u = false;
-            }
-            if (tid == 0) u_win = P.uslices ? -1 : tk.win;
-        }
+        run_task(tk, wd, I, P.upool + wd.u_off,
+                 P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
+                 P.ozscratch ? P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX : nullptr,
+                 P.strong, (unsigned long long)tk.win, &u_key, smem_raw);
         // release: every thread's writes are ordered before the counters drop
         __threadfence();
         __syncthreads();
@@ -114,6 +126,121 @@ sched_kernel(SchedParams P) {
             if (P.trace) P.trace[4 * t + 3] = global_ns();
             for (int i = P.succ_off[t]; i < P.succ_off[t + 1]; ++i)
                 atomicSub(&P.deps_left[P.succ[i]], 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Server kernel: one long-lived launch fed through a ring of (request, task)
+// entries that the host appends while it runs.  Positions are taken in ring
+// order; a position beyond the published tail is held until the host
+// publishes it or sets the stop word.  A request's tasks appear in the ring
+// in its own queue order, so every predecessor of a task sits at an earlier
+// position and has been taken by a running CTA: waits end.  The last task of
+// a request (TASK_E) depends on all others: it reads the eigenvalues off the
+// final blocks and writes the request's completion word to host memory.
+// Loads of host-written tables bypass L1 (their memory is reused).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long ld_volatile64(const long long* p) {
+    return *reinterpret_cast<const volatile long long*>(p);
+}
+
+__global__ void __launch_bounds__(SCHED_THREADS, 1)
+server_kernel(SrvParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long pos_s;
+    __shared__ RingEntry ent_s;
+    __shared__ unsigned long long u_key;
+    const int tid = threadIdx.x;
+    if (tid == 0) u_key = ~0ull;
+    for (;;) {
+        if (tid == 0) {
+            long long t = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(P.head), 1ull);
+            long long spins = 0;
+            // hold the position until it is published
+            while (t >= ld_volatile64(P.tail)) {
+                if (ld_volatile(P.stop) != 0 || ld_volatile(P.err) != 0) { t = -1; break; }
+                if (++spins > P.park_limit) {
+                    atomicExch(P.err, 3);
+                    t = -1;
+                    break;
+                }
+                __nanosleep(1024);
+            }
+            RingEntry e{-1, -1};
+            if (t >= 0) {
+                const RingEntry* rp = P.ring + (t % P.cap);
+                e.req = __ldcg(&rp->req);
+                e.local = __ldcg(&rp->local);
+                const int* deps = reinterpret_cast<const int*>(__ldcg(
+                    reinterpret_cast<const unsigned long long*>(&P.reqs[e.req].deps)));
+                spins = 0;
+                while (ld_volatile(&deps[e.local]) > 0) {
+                    if (ld_volatile(P.err) != 0) { t = -1; break; }
+                    if (++spins > P.wait_limit) {
+                        atomicExch(P.err, 1);
+                        t = -1;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            pos_s = t;
+            ent_s = e;
+        }
+        __syncthreads();
+        if (pos_s < 0) break;
+        __threadfence();
+        const RingEntry e = ent_s;
+        const SrvReq* Rg = P.reqs + e.req;
+        SrvReq R;
+        {
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(Rg);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(&R);
+            for (int k = 0; k < (int)(sizeof(SrvReq) / 8); ++k) dst[k] = __ldcg(src + k);
+        }
+        SchedTask tk;
+        {
+            const int4 v = __ldcg(reinterpret_cast<const int4*>(R.tasks + e.local));
+            tk = SchedTask{v.x, v.y, v.z, v.w};
+        }
+        if (tk.kind == TASK_E) {
+            const Inst& I = R.inst;
+            for (int i = tid; i < I.n; i += blockDim.x) {
+                double re, im;
+                eig_at(I.n, I.S, I.ldS, i, &re, &im);
+                R.eig[i] = re;
+                R.eig[I.n + i] = im;
+            }
+        } else {
+            Window wd;
+            {
+                const Window* wp = R.wins + tk.win;
+                wd.s = __ldcg(&wp->s);
+                wd.e = __ldcg(&wp->e);
+                wd.chain = 0;
+                wd.inst = 0;
+                wd.u_off = __ldcg(&wp->u_off);
+            }
+            run_task(tk, wd, R.inst, R.upool + wd.u_off,
+                     R.uslices ? R.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
+                     P.ozscratch ? P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX : nullptr,
+                     P.strong, ((unsigned long long)(unsigned)R.id << 32) | (unsigned)tk.win, &u_key,
+                     smem_raw);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (tk.kind == TASK_E) {
+                __threadfence_system();
+                *reinterpret_cast<volatile int*>(P.done + R.done_slot) = R.id;
+                __threadfence_system();
+            } else {
+                const int* so = R.succ_off;
+                const int a = __ldcg(&so[e.local]), b = __ldcg(&so[e.local + 1]);
+                for (int i = a; i < b; ++i) atomicSub(&R.deps[__ldcg(&R.succ[i])], 1);
+                atomicSub(&R.deps[R.ntasks - 1], 1);  // the request's final task
+            }
         }
     }
 }
@@ -133,6 +260,21 @@ cudaError_t sched_configure() {
                              (int)kSchedSmem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = true;
     return e;
+}
+
+cudaError_t launch_server(const SrvParams& P, int grid, cudaStream_t st) {
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(server_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSchedSmem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    server_kernel<<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st) {

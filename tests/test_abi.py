@@ -121,3 +121,28 @@ def test_tuner_defaults_without_tuning(lib):
     assert not tuned and (w, m) == (128, 64) and t >= 64
     assert lib.gbr_autotune(0, 10, None) == -1
     assert lib.gbr_autotune(64, 0, None) == -2
+
+
+def test_server_argument_checks(lib):
+    cfg = g.GbrServerCfg()
+    lib.gbr_server_default_cfg(ctypes.byref(cfg))
+    assert cfg.mem_cap_bytes == 60_000_000_000 and cfg.max_inflight >= 1 and cfg.sms == 0
+    assert cfg.ring_entries >= 1024 and cfg.device == -1
+    h = ctypes.c_void_p(None)
+    assert lib.gbr_server_create(ctypes.byref(cfg), None) == -2
+    bad = g.GbrServerCfg()
+    lib.gbr_server_default_cfg(ctypes.byref(bad))
+    bad.ring_entries = 10
+    assert lib.gbr_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.ring_entries, bad.mem_cap_bytes = 1 << 20, 0
+    assert lib.gbr_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.mem_cap_bytes, bad.sms = 1 << 30, -1
+    assert lib.gbr_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.sms = 0
+    bad.opts.sched = g.SCHED_SEQUENTIAL
+    assert lib.gbr_server_create(ctypes.byref(bad), ctypes.byref(h)) == g.ERR_UNSUPPORTED
+    assert lib.gbr_server_submit(None, 4, None, 4, None, 4, None, None, None) == -1
+    assert lib.gbr_server_poll(None, 0, None, None) == -1
+    assert lib.gbr_server_wait(None, 0, None, None, 0) == -1
+    assert lib.gbr_server_get_stats(None, None) == -1
+    lib.gbr_server_destroy(None)
