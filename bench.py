@@ -51,6 +51,8 @@ WORKLOADS = {
                     window=128, chain=64),
     "batch4096": dict(name="batch4096", kind="batch", count=4096, nmin=32, nmax=512,
                       select="U(0.2, 0.6) per instance", q="min(n, 64) Householder reflectors"),
+    "serve": dict(name="serve", kind="serve", nmin=64, nmax=8192, select="U(0.1, 0.6)",
+                  q="8 Householder reflectors", mem_cap=60e9),
 }
 METRIC = "selected eigenvalues reordered per second"
 
@@ -179,7 +181,18 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    if wl.get("kind") == "batch":
+    if wl.get("kind") == "serve":
+        base = si.serve_base(wl["nmax"])
+        reqs = si.request_stream(args.requests, seed=1000, nmin=wl["nmin"], nmax=wl["nmax"],
+                                 pmin=0.1, pmax=0.6)
+        # the oracle's cost grows as n^3: its sample takes the requests of
+        # order <= 1024 of the stream, in order
+        probs = [si.serve_request(base, n, p, sd) for _, n, p, sd in reqs if n <= 1024][:200]
+        nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
+        sample = lambda: batch_cpu_sample(probs, budget_s=6.0)
+        cfg = {"workload": "serve", "n": "requests of order <= 1024 of the stream",
+               "select": wl["select"], "q": wl["q"]}
+    elif wl.get("kind") == "batch":
         probs = batch_inputs(wl)
         nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
         sample = lambda: batch_cpu_sample(probs, budget_s=6.0)
@@ -402,6 +415,97 @@ def run_batch(args, wl):
     return 0
 
 
+def run_serve(args, wl):
+    """Serving: a Poisson stream of requests (n log-uniform, see the
+    workload) through the continuous-batching server.  A saturation burst
+    first measures the throughput; the stream then arrives at each --load
+    fraction of it.  Requests are cut from one base form (schur_inputs)."""
+    import torch
+    import paper_1905_04975_gb300 as g
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    g.load()
+    base = si.serve_base(wl["nmax"], seed=rank)
+    reqs = si.request_stream(args.requests, seed=1000 + rank, nmin=wl["nmin"], nmax=wl["nmax"],
+                             pmin=0.1, pmax=0.6, rate=1.0)
+
+    def make(i):
+        _, n, p, sd = reqs[i % len(reqs)]
+        S, Q, sel = si.serve_request(base, n, p, sd)
+        nn = S.shape[0]
+        # pinned host buffers (the caching host allocator reuses them)
+        tS = torch.empty((nn, nn), dtype=torch.float64).pin_memory()
+        tQ = torch.empty((nn, nn), dtype=torch.float64).pin_memory()
+        hS, hQ = tS.numpy().T, tQ.numpy().T      # Fortran-ordered views
+        hS[:] = S
+        hQ[:] = Q
+        return (tS, tQ, hS, hQ, sel, int(expected_selected(S, sel)))
+
+    def run(rate, count, offset):
+        """Submits `count` requests (Poisson arrivals at `rate` per second,
+        or all at once when rate is None) and waits for all of them."""
+        srv = g.Server(mem_cap_bytes=wl["mem_cap"], precision=args.precision)
+        try:
+            gaps = np.random.default_rng(7 + offset).exponential(1.0 / rate, count) if rate else None
+            pending = {}
+            t0 = time.perf_counter()
+            t_next = t0
+            eigs = 0
+            for i in range(count):
+                item = make(offset + i)
+                if gaps is not None:
+                    t_next += gaps[i]
+                    dt = t_next - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                t = srv.submit(item[2], item[3], item[4], eigs=False)
+                pending[t] = item
+                eigs += item[5]
+                for tk in [tk for tk in pending if srv.poll(tk) is not None]:
+                    del pending[tk]
+            for tk in list(pending):
+                r = srv.wait(tk, -1)
+                assert r.status >= 0, r.status
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        finally:
+            srv.close()
+        return st, wall, eigs
+
+    burst = max(20, args.requests // 10)
+    st_b, wall_b, eigs_b = run(None, burst, 0)
+    sat = st_b["req_per_s"]
+    loads = []
+    for load in args.loads:
+        st, wall, eigs = run(load * sat, args.requests, burst)
+        loads.append({"load": load, "rate_req_s": load * sat, "requests": args.requests,
+                      "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                      "mean_ms": st["mean_ms"], "req_per_s": st["req_per_s"],
+                      "eigs_per_s": st["eigs_per_s"], "mean_inflight": st["mean_inflight"],
+                      "peak_mem_gb": st["peak_mem_bytes"] / 1e9, "failed": st["failed"],
+                      "wall_s": wall})
+    if rank == 0:
+        head = loads[-1] if loads else None
+        line = {"metric": "serve p50/p99 latency and throughput",
+                "value": head["eigs_per_s"] if head else st_b["eigs_per_s"], "unit": "eigs/s",
+                "n_gpus": 1, "steps": len(loads), "warmup": 0,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "serve", "n": "log-uniform [64, 8192]",
+                           "select": wl["select"], "q": wl["q"], "precision": args.precision,
+                           "mem_cap_gb": wl["mem_cap"] / 1e9,
+                           "arrivals": "Poisson at load x saturated req/s"},
+                "serve": {"saturated": {"requests": burst, "req_per_s": sat,
+                                        "eigs_per_s": st_b["eigs_per_s"],
+                                        "p50_ms": st_b["p50_ms"], "p99_ms": st_b["p99_ms"],
+                                        "wall_s": wall_b},
+                          "loads": loads}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,12 +517,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sched", default="persistent", choices=["persistent", "sequential"])
     ap.add_argument("--precision", default="dmma", choices=["dmma", "ozaki"])
+    ap.add_argument("--requests", type=int, default=400, help="serve: requests per load")
+    ap.add_argument("--loads", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[0.5, 0.9], help="serve: arrival rates as fractions of saturation")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
     if wl.get("kind") == "batch":
         return run_batch(args, wl)
+    if wl.get("kind") == "serve":
+        return run_serve(args, wl)
 
     import torch
     import paper_1905_04975_gb300 as g

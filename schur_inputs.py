@@ -20,7 +20,12 @@ are this project's synthetic stand-in):
   reflectors H_i = I - 2 v v^T / v^T v with v ~ N(0,1)^n;
 * selection: blocks in seeded random order are selected until the selected
   eigenvalue count reaches round(p n); a 2x2 block (a conjugate pair) is
-  always selected whole.
+  always selected whole;
+* serving requests: a principal diagonal block S[k:k+n, k:k+n] of one large
+  seeded base form, cut at block boundaries (so it is again a standard
+  form), at a seeded offset k; Q of 8 seeded reflectors; the selection is
+  drawn as above from the sub-block's own blocks.  Twenty thousand
+  independent forms of order up to 8192 would not fit in host memory.
 
 All matrices are float64 in column-major (Fortran) order.
 """
@@ -29,7 +34,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["block_sizes", "schur_form", "householder_q", "selection",
-           "reorder_problem", "batch_problems", "request_stream"]
+           "reorder_problem", "batch_problems", "request_stream", "serve_base",
+           "serve_request"]
 
 
 def block_sizes(n: int, rng: np.random.Generator, frac_1x1: float = 0.6) -> np.ndarray:
@@ -189,3 +195,29 @@ def request_stream(count: int, seed: int = 0, nmin: int = 64, nmax: int = 8192,
     ps = rng.uniform(pmin, pmax, count)
     seeds = rng.integers(0, 2**62, count)
     return [(float(t[i]), int(ns[i]), float(ps[i]), int(seeds[i])) for i in range(count)]
+
+
+def serve_base(nmax: int = 8192, seed: int = 0):
+    """Base form of the serving requests: (S, sizes, block starts)."""
+    rng = np.random.default_rng(seed)
+    S, sizes = schur_form(nmax, rng)
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    return S, sizes, starts
+
+
+def serve_request(base, n: int, frac: float, seed: int, reflectors: int = 8):
+    """One serving request of order about n (the block boundary at or after
+    k + n ends it, capped by the base): (S, Q, select), Fortran order."""
+    S0, sizes, starts = base
+    N = S0.shape[0]
+    rng = np.random.default_rng(seed)
+    n = int(min(max(n, 1), N))
+    last = int(np.searchsorted(starts, N - n, side="right")) - 1
+    b0 = int(rng.integers(0, max(last, 0) + 1))
+    k = int(starts[b0])
+    b1 = int(np.searchsorted(starts, k + n, side="left"))
+    e = int(starts[b1]) if b1 < starts.size else N
+    S = np.asfortranarray(S0[k:e, k:e])
+    Q = householder_q(e - k, rng, reflectors)
+    sel = selection(sizes[b0:b1], frac, rng)
+    return S, Q, sel
