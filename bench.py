@@ -239,6 +239,44 @@ def expected_selected(S, sel):
     return cnt
 
 
+def error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream):
+    """Accuracy of one reordering of the workload (after the timed steps):
+    residual ||A - Q S Q^T||_F / ||A||_F and ||Q^T Q - I||_F estimated with 32
+    Gaussian probe vectors on the GPU, eigenvalue order against the stable
+    partition of the input eigenvalues, and for n <= 4000 the difference to
+    the FP64 oracle's result (eigenvalues, leading invariant subspace)."""
+    import oracle
+    from tests.helpers import block_eigs, expected_order, sin_angle
+    with torch.cuda.stream(stream):
+        S.copy_(S0)
+        Q.copy_(Q0)
+    stream.synchronize()
+    r = g.reorder(S, Q, sel, opts=opts, stream=stream)
+    stream.synchronize()
+    n = S_np.shape[0]
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(n, 32, dtype=torch.float64, device="cuda", generator=gen)
+    S0c, Q0c = S0.contiguous(), Q0.contiguous()
+    Sc, Qc = S.contiguous(), Q.contiguous()
+    AX = Q0c @ (S0c @ (Q0c.T @ X))
+    res = (torch.linalg.norm(AX - Qc @ (Sc @ (Qc.T @ X))) / torch.linalg.norm(S0c)).item() / 32 ** 0.5
+    orth = torch.linalg.norm(Qc.T @ (Qc @ X) - X).item() / 32 ** 0.5
+    Sg = g.to_host(S)
+    got = block_eigs(Sg)
+    want, m = expected_order(S_np, sel)
+    out = {"status": r.status, "residual_est": res, "orth_est": orth, "bound_50n_eps": 50 * n * 2.0 ** -52,
+           "eig_order_max_rel_dev": float(np.max(np.abs(got - want) / np.maximum(np.abs(want), 1.0)))}
+    if n <= 4000:
+        t0 = time.perf_counter()
+        ref = oracle.reorder(S_np, Q_np, sel)
+        out["oracle_s"] = time.perf_counter() - t0
+        oe = ref["wr"] + 1j * ref["wi"]
+        out["vs_oracle_eig_max_rel_dev"] = float(np.max(np.abs(got - oe) / np.maximum(np.abs(oe), 1.0)))
+        Qg = g.to_host(Q)
+        out["vs_oracle_sin_angle"] = sin_angle(Qg[:, :m], ref["Q"][:, :m]) if 0 < m < n else 0.0
+    return out
+
+
 def batch_inputs(wl, seed=0):
     """The batched workload: per instance (S, Q, select) from the seeded
     generator, n ~ U{nmin..nmax}, p ~ U(0.2, 0.6)."""
@@ -518,6 +556,8 @@ def main():
     ap.add_argument("--sched", default="persistent", choices=["persistent", "sequential"])
     ap.add_argument("--precision", default="dmma", choices=["dmma", "ozaki"])
     ap.add_argument("--requests", type=int, default=400, help="serve: requests per load")
+    ap.add_argument("--error", action="store_true",
+                    help="report the accuracy of one reordering (and vs the oracle, n <= 4000)")
     ap.add_argument("--loads", type=lambda v: [float(x) for x in v.split(",")],
                     default=[0.5, 0.9], help="serve: arrival rates as fractions of saturation")
     args = ap.parse_args()
@@ -661,6 +701,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(S_np, Q_np, sel)
+    err = error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream) if args.error else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "eigs/s", "n_gpus": world,
@@ -673,7 +714,7 @@ def main():
                            "l2": "S,Q (256 MB > L2) restored from a device copy before each step",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
-                "clocks": clk.summary(),
+                "clocks": clk.summary(), "error": err,
                 "gpu_launches": int(sum(s.launches for s in stats)),
                 "detail": {"windows": int(nwin), "chains": int(st0.chains),
                            "tasks": int(st0.tasks), "swaps": int(st0.swaps),
