@@ -117,6 +117,9 @@ typedef struct gbr_stats {
     double sched_sim_ms;  /* makespan of the scheduler's list-scheduling model   */
     double ms_graph;      /* host time building the task graph                   */
     double ms_order;      /* host time computing the queue order                 */
+    double upd_flops_issued; /* flops the DMMA update tiles issued: upd_flops less
+                             the products with the all-zero rows of U each warp
+                             skips (0 for split precision)                        */
 } gbr_stats;
 
 /* Fill *opts with the defaults. */

@@ -53,7 +53,8 @@ class GbrStats(ctypes.Structure):
                 ("ms_update", ctypes.c_double), ("ms_sched", ctypes.c_double),
                 ("win_flops", ctypes.c_double), ("tasks", ctypes.c_longlong),
                 ("sched_cp_ms", ctypes.c_double), ("sched_sim_ms", ctypes.c_double),
-                ("ms_graph", ctypes.c_double), ("ms_order", ctypes.c_double)]
+                ("ms_graph", ctypes.c_double), ("ms_order", ctypes.c_double),
+                ("upd_flops_issued", ctypes.c_double)]
 
 
 class GbrServerCfg(ctypes.Structure):

@@ -235,7 +235,7 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
             if (o.timing) GBR_CK(mark(evw), "event");
             GBR_CK(launch_window(n, wdw, S, ldS, d_sel, d_u, o.strong_test, d_ctr, st), "window kernel");
             if (o.timing) { GBR_CK(mark(evw), "event"); GBR_CK(mark(evu), "event"); }
-            GBR_CK(launch_update(n, wdw, S, ldS, Q, ldQ, d_u, st), "update kernel");
+            GBR_CK(launch_update(n, wdw, S, ldS, Q, ldQ, d_u, d_ctr, st), "update kernel");
             if (o.timing) GBR_CK(mark(evu), "event");
             launches += 2;
           }
@@ -291,6 +291,7 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         stats->ms_update = msu;
         stats->ms_sched = ms_sched;
         stats->win_flops = (double)h_ctr.win_flops;
+        stats->upd_flops_issued = (double)h_ctr.upd_issued;
         stats->tasks = ntasks;
         stats->sched_cp_ms = ntasks ? g_last_sched.cp_us / 1e3 : 0.0;
         stats->sched_sim_ms = ntasks ? g_last_sched.sim_us / 1e3 : 0.0;

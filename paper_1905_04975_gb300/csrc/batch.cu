@@ -432,7 +432,7 @@ static int batch_run(gbr_batch* b, double* eig_re, double* eig_im, int* m_out, i
     }
     int with_rej = 0;
     long long swaps = 0, rejected = 0;
-    double wfl = 0.0;
+    double wfl = 0.0, iss = 0.0;
     for (int i = 0; i < b->count; ++i) {
         const DevCounters& c = b->h_ctr[i];
         if (c.step_overflow) {
@@ -446,6 +446,7 @@ static int batch_run(gbr_batch* b, double* eig_re, double* eig_im, int* m_out, i
         swaps += b->valid[i] ? (long long)c.swaps : 0;
         rejected += r;
         wfl += b->valid[i] ? (double)c.win_flops : 0.0;
+        iss += b->valid[i] ? (double)c.upd_issued : 0.0;
     }
     if (b->ntot) {
         if (eig_re) memcpy(eig_re, b->h_wr, sizeof(double) * b->ntot);
@@ -460,6 +461,7 @@ static int batch_run(gbr_batch* b, double* eig_re, double* eig_im, int* m_out, i
         stats->upd_flops = flops;
         stats->ms_sched = ms;
         stats->win_flops = wfl;
+        stats->upd_flops_issued = iss;
         stats->tasks = tasks;
         stats->sched_cp_ms = b->info.cp_us / 1e3;
         stats->sched_sim_ms = b->info.sim_us / 1e3;

@@ -40,6 +40,7 @@ struct DevCounters {
     int bad_column;      // validation: first column violating the standard form, or INT_MAX
     int step_overflow;   // windows that hit the step cap (a logic error if nonzero)
     unsigned long long win_flops;  // FP64 flops of in-window updates of accepted swaps
+    unsigned long long upd_issued; // flops issued by the DMMA update tiles (zero rows of U skipped)
 };
 
 // One reordering problem on the device: a scheduler launch may carry many.
@@ -134,7 +135,7 @@ cudaError_t launch_eigs(int n, const double* S, int ldS, double* wr, double* wi,
 cudaError_t launch_window(int n, const Window& w, double* S, int ldS, uint8_t* sel, double* U,
                           int strong, DevCounters* ctr, cudaStream_t st);
 cudaError_t launch_update(int n, const Window& w, double* S, int ldS, double* Q, int ldQ,
-                          const double* U, cudaStream_t st);
+                          const double* U, DevCounters* ctr, cudaStream_t st);
 size_t window_smem_bytes(int w);
 size_t update_smem_bytes(int w);
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st);

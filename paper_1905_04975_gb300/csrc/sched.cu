@@ -43,7 +43,7 @@ __device__ __forceinline__ unsigned smid() {
     return r;
 }
 
-// Runs one window task or update tile of window wd of instance I.  u_key
+// Runs one window task or update task of window wd of instance I.  u_key
 // names the U held in shared memory by the previous task of this CTA (an
 // update tile of the same window reuses it); key names this task's window.
 __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, const Inst& I,
@@ -71,7 +71,7 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
     } else {
         for (int r = 0; r < tk.rows; r += upd::BM) {
             upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s, Ug,
-                             load_u, smem_raw);
+                             load_u, smem_raw, &I.ctr->upd_issued);
             load_u = false;
         }
         if (tid == 0) *u_key = key;

@@ -58,17 +58,51 @@ __device__ __forceinline__ void panel_geom(int panel, int n, int s, int e, doubl
 // Y rows [r0, r0 + rows) <- (Y U) rows, rows <= BM; nthreads >= UPD_THREADS
 // (warps beyond the first 8 only help loading).  If load_u is false, Us
 // already holds U (a previous tile of the same window in this CTA).
+//
+// U is a product of adjacent-block swaps, so the nonzeros of each of its
+// columns form one contiguous run of rows (a staircase: about a quarter of
+// U is zero for a window whose chain enters at the bottom, more for a
+// chain's first window).  When U is loaded, each warp finds the rows
+// [klo, khi) where its 16 output columns have nonzeros and the products run
+// over those rows only.  If issued is not null, the flops issued by the
+// tile are added to it.
 __device__ __forceinline__ void update_tile(double* base, long long rs, long long ks, int r0,
                                             int rows, int w, const double* __restrict__ Ug,
-                                            bool load_u, unsigned char* smem_raw) {
+                                            bool load_u, unsigned char* smem_raw,
+                                            unsigned long long* issued = nullptr) {
     double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU
     double* Ys = Us + WMAX * LDU;                        // BM x LDY
+    __shared__ int k_lo[UPD_THREADS / 32], k_hi[UPD_THREADS / 32];
     const int wp = (w + 15) & ~15;  // padded to the warp column width
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
     if (load_u) {
         for (int i = tid; i < wp * wp; i += nth) {
             int k = i / wp, c = i % wp;
             Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+        }
+        __syncthreads();
+        if (warp < UPD_THREADS / 32) {
+            const int c0 = warp * 16;
+            int lo = wp, hi = 0;
+            if (c0 < wp)
+                for (int k = lane; k < wp; k += 32) {
+                    bool nz = false;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) nz |= Us[k * LDU + c0 + c] != 0.0;
+                    if (nz) {
+                        lo = min(lo, k);
+                        hi = max(hi, k + 1);
+                    }
+                }
+            for (int o = 16; o; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) {
+                k_lo[warp] = lo < hi ? (lo & ~3) : 0;
+                k_hi[warp] = lo < hi ? min(wp, (hi + 3) & ~3) : 0;
+            }
         }
     }
     if (rs == 1) {
@@ -83,16 +117,22 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
         }
     }
     __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
     const int gid = lane >> 2, tig = lane & 3;
     const int c0 = warp * 16;
+    if (issued && tid == 0) {
+        unsigned long long f = 0;
+        for (int v = 0; v < UPD_THREADS / 32 && v * 16 < w; ++v)
+            f += 2ull * rows * (unsigned long long)min(16, w - v * 16) * (k_hi[v] - k_lo[v]);
+        atomicAdd(issued, f);
+    }
     if (warp < UPD_THREADS / 32 && c0 < wp) {
+        const int klo = k_lo[warp], khi = k_hi[warp];
         double acc[8][2][2];
 #pragma unroll
         for (int rt = 0; rt < 8; ++rt)
 #pragma unroll
             for (int ct = 0; ct < 2; ++ct) acc[rt][ct][0] = acc[rt][ct][1] = 0.0;
-        for (int kk = 0; kk < wp; kk += 4) {
+        for (int kk = klo; kk < khi; kk += 4) {
             double a[8], bb[2];
 #pragma unroll
             for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LDY + kk + tig];
