@@ -330,6 +330,11 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     __shared__ int kcnt[3];
     __shared__ int kpre_l[3][MAXSW + 1];  // prefix sums of left-apply columns per k group
     __shared__ int kpre_r[3][MAXSW + 1];  // prefix sums of right-apply rows (S rows + U rows)
+    // Rows [urlo[c], urhi[c]] hold every nonzero of column c of U: U starts as
+    // I and a swap on columns [j, j+k) mixes only those columns, so the rows
+    // outside the union of their ranges stay exactly zero and are skipped.
+    __shared__ short urlo[WMAX], urhi[WMAX];
+    __shared__ short slo[MAXSW], shi[MAXSW];  // per slot: U rows its right transform touches
 
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
@@ -342,7 +347,11 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
             Sp[poff(c) + r] = __ldcg(&S[cm(s0 + r, s0 + c, ldS)]);
     }
     for (int i = tid; i < w * w; i += nth) U[i] = ((i % w) == (i / w)) ? 1.0 : 0.0;
-    for (int i = tid; i < w; i += nth) sel[i] = __ldcg(&gsel[s0 + i]);
+    for (int i = tid; i < w; i += nth) {
+        sel[i] = __ldcg(&gsel[s0 + i]);
+        urlo[i] = (short)i;
+        urhi[i] = (short)i;
+    }
     __shared__ int wall_top, wall_bot;
     if (tid == 0) {
         nrej = 0;
@@ -524,9 +533,16 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                 int i = base + lane;
                 int nl = 0, nr = 0;
                 if (i < cnt) {
-                    int slot = ksl[g][i];
-                    nl = w - swj[slot] - swk[slot];
-                    nr = swj[slot] + w;
+                    const int slot = ksl[g][i], j = swj[slot], k = swk[slot];
+                    int lo = urlo[j], hi = urhi[j];
+                    for (int c = 1; c < k; ++c) {
+                        lo = min(lo, (int)urlo[j + c]);
+                        hi = max(hi, (int)urhi[j + c]);
+                    }
+                    slo[slot] = (short)lo;
+                    shi[slot] = (short)hi;
+                    nl = w - j - k;
+                    nr = j + (hi - lo + 1);
                 }
                 int il = nl, ir = nr;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -592,7 +608,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                 const double* Z = &Zs[slot * 16];
                 double x[4], y[4];
                 const bool inS = rr < j;
-                const int r = inS ? rr : rr - j;
+                const int r = inS ? rr : rr - j + slo[slot];
 #pragma unroll
                 for (int i = 0; i < k; ++i) x[i] = inS ? Sp[poff(j + i) + r] : U[(j + i) * w + r];
 #pragma unroll
@@ -612,12 +628,17 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
             }
         }
         __syncthreads();
-        // --- phase D: move the selection flags with the blocks
+        // --- phase D: move the selection flags with the blocks; widen the U
+        // row ranges of the columns each accepted transform mixed
         for (int sw = tid; sw < ns; sw += nth) {
             int j = swj[sw], k = swk[sw];
             if (k == 0) {
                 sel[swp[sw]] = SEL_STUCK;
                 continue;
+            }
+            for (int c = 0; c < k; ++c) {
+                urlo[j + c] = slo[sw];
+                urhi[j + c] = shi[sw];
             }
             int p = swp[sw], q = k - p;
             if (p < 0) continue;   // standardization: blocks do not move
