@@ -474,17 +474,25 @@ GBR_HD bool swap21_fast(const double* D, bool strong, double* Z, double* Dn) {
     return true;
 }
 
+// 1|2 is solved as 2|1 on the flipped block F D^T F (F the exchange matrix)
+// and flipped back.  The flip is a select between registers, not a branch:
+// the lanes of a warp that serve 1|2 and 2|1 swaps then run one instruction
+// stream (on the GPU every FP64 instruction a warp issues costs the same
+// whether one lane or all of them need it).
 GBR_HD bool swap3_fast(const double* D, int p, bool strong, double* Z, double* Dn) {
-    if (p == 2) return swap21_fast(D, strong, Z, Dn);
-    // 1|2: flip, solve as 2|1, flip back
+    const bool f = (p == 1);
     double Df[16], Zf[16], Dnf[16];
+#pragma unroll
     for (int c = 0; c < 3; ++c)
-        for (int r = 0; r < 3; ++r) Df[c * 4 + r] = D[(2 - r) * 4 + (2 - c)];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Df[c * 4 + r] = f ? D[(2 - r) * 4 + (2 - c)] : D[c * 4 + r];
     if (!swap21_fast(Df, strong, Zf, Dnf)) return false;
+#pragma unroll
     for (int c = 0; c < 3; ++c)
+#pragma unroll
         for (int r = 0; r < 3; ++r) {
-            Z[c * 4 + r] = Zf[(2 - c) * 4 + (2 - r)];
-            Dn[c * 4 + r] = Dnf[(2 - r) * 4 + (2 - c)];
+            Z[c * 4 + r] = f ? Zf[(2 - c) * 4 + (2 - r)] : Zf[c * 4 + r];
+            Dn[c * 4 + r] = f ? Dnf[(2 - r) * 4 + (2 - c)] : Dnf[c * 4 + r];
         }
     return true;
 }
@@ -658,8 +666,10 @@ GBR_HD_NOINLINE bool swap_transform_accurate(const double* D, int p, int q, bool
 }
 
 // A swap: the fast FP64 transform, and the double-double retry when the fast
-// one fails the stability test.
-GBR_HD bool swap_transform(const double* D, int p, int q, bool strong, double* Z, double* Dn) {
+// one fails the stability test.  The window task reaches it only when its
+// specialized paths decline a swap, so it stays out of line: the window
+// task's step loop must fit the instruction caches.
+GBR_HD_NOINLINE bool swap_transform(const double* D, int p, int q, bool strong, double* Z, double* Dn) {
     if (swap_transform_fast(D, p, q, strong, Z, Dn)) return true;
     if (p + q == 2) return false;
     return swap_transform_accurate(D, p, q, strong, Z, Dn);
