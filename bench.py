@@ -57,6 +57,21 @@ WORKLOADS = {
 METRIC = "selected eigenvalues reordered per second"
 
 
+def whole_job_rate(units, local_ms, dist=None, device="cpu"):
+    """Replicas: every rank processed `units` in `local_ms`; the job's time is
+    the slowest rank's (max over ranks), and its rate is all ranks' units over
+    that time.  Returns (rate per second, job time in ms)."""
+    world = 1
+    job_ms = float(local_ms)
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([job_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        job_ms = float(t.item())
+    return units * world / (job_ms / 1e3), job_ms
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -379,12 +394,7 @@ def run_batch(args, wl):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = sum(ms)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = nsel * args.steps * world / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(nsel * args.steps, sum(ms), dist, "cuda")
     st0 = stats[0]
     ms_sched = sum(s.ms_sched for s in stats) / len(stats)
     pk, src = peaks()
@@ -620,12 +630,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = sum(ms)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = nsel * args.steps * world / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(nsel * args.steps, sum(ms), dist, "cuda")
 
     # dominant kernel and its roofline.  With the persistent scheduler one
     # kernel runs every window task and update tile; all of its arithmetic is
