@@ -90,7 +90,7 @@ static TuneChoice tune_lookup(int n, bool* tuned) {
 
 static CostModel batch_cost_model(const gbr_opts& o) {
     CostModel c;
-    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 33000.0 : 6900.0;
+    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0 : 6900.0;
     return c;
 }
 

@@ -81,7 +81,6 @@ struct SchedParams {
     const int* succ;
     double* upool;            // U of every window, at Window::u_off (w x w, column-major)
     unsigned char* uslices;   // null (DMMA updates) or OZ_USLICE_BYTES per window
-    double* ozscratch;        // split precision: UPD_FAR x WMAX doubles per CTA
     int* head;                // next queue position
     int* err;                 // nonzero: a wait ran out (1) or the plan does not fit S (2)
     long long wait_limit;     // spins (~128 ns each) before a wait gives up
@@ -120,10 +119,9 @@ struct SrvParams {
     const int* stop;            // nonzero: leave when idle
     int* err;                   // 1: a dependency wait ran out; 3: the ring stayed empty too long
     const SrvReq* reqs;
-    double* ozscratch;          // UPD_FAR x WMAX doubles per CTA
     int* done;                  // completion words (host memory, mapped)
     int strong;
-    int pad;
+    int ozaki;                  // nonzero: split-precision updates (tensor memory held)
     long long wait_limit;       // spins (~128 ns) of a dependency wait
     long long park_limit;       // spins (~1 us) of a wait for the ring to fill
 };

@@ -507,10 +507,9 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     const size_t b_ctl = 256;
     const size_t b_tr = (o.timing >= 2) ? al(sizeof(unsigned long long) * 4 * std::max(1, nt)) : 0;
     const size_t b_us = ozaki ? al(OZ_USLICE_BYTES * wins.size()) : 0;
-    const size_t b_oz = ozaki ? al(sizeof(double) * UPD_FAR * WMAX * (size_t)grid) : 0;
     const size_t b_u = al(sizeof(double) * std::max<long long>(1, u_total));
     const size_t total = b_inst + b_tasks + b_wins + 2 * b_deps + b_soff + b_succ + b_ctl + b_tr +
-                         b_us + b_oz + b_u;
+                         b_us + b_u;
     char* p = (char*)alloc(total);
     if (!p) return GBR_ERR_NOMEM;
     Inst* d_inst = (Inst*)p; p += b_inst;
@@ -523,7 +522,6 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     int* d_ctl = (int*)p; p += b_ctl;
     unsigned long long* d_tr = b_tr ? (unsigned long long*)p : nullptr; p += b_tr;
     unsigned char* d_us = b_us ? (unsigned char*)p : nullptr; p += b_us;
-    double* d_oz = b_oz ? (double*)p : nullptr; p += b_oz;
     double* d_u = (double*)p;
     GBR_CK(cudaMemcpyAsync(d_inst, itab.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice, st), "H2D instances");
     if (nt) {
@@ -549,7 +547,6 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     P.succ = d_succ;
     P.upool = d_u;
     P.uslices = d_us;
-    P.ozscratch = d_oz;
     P.head = d_ctl;
     P.err = d_ctl + 1;
     const long long lim_ms = o.wait_limit_ms > 0 ? o.wait_limit_ms : 60000;

@@ -16,6 +16,7 @@
 // requirement.  Every wait is bounded; a wait that runs out sets an error
 // flag, and all CTAs leave the loop at their next check.
 #include "scan_body.cuh"
+#include "ozaki.cuh"
 #include "update_body.cuh"
 #include "window_body.cuh"
 
@@ -46,10 +47,13 @@ __device__ __forceinline__ unsigned smid() {
 // Runs one window task or update task of window wd of instance I.  u_key
 // names the U held in shared memory by the previous task of this CTA (an
 // update tile of the same window reuses it); key names this task's window.
+// Split-precision tiles run on the tensor cores with the CTA's tensor memory
+// (tmem); if one of their bounded waits runs out, *err is set.
 __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, const Inst& I,
-                                         double* Ug, unsigned char* uslices, double* ozscratch,
+                                         double* Ug, unsigned char* uslices,
                                          int strong, unsigned long long key,
-                                         unsigned long long* u_key, unsigned char* smem_raw) {
+                                         unsigned long long* u_key, unsigned char* smem_raw,
+                                         uint32_t tmem, int* err) {
     const int tid = threadIdx.x;
     if (tk.kind == TASK_W) {
         win::window_body(I.n, I.S, I.ldS, wd.s, wd.e - wd.s, I.sel, Ug, strong, I.ctr, smem_raw,
@@ -64,9 +68,9 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
     bool load_u = (*u_key != key);
     __syncthreads();
     if (uslices) {
-        for (int r = 0; r < tk.rows; r += UPD_FAR)
-            upd::update_tile_ozaki(base, rs, ks, tk.y0 + r, min(UPD_FAR, tk.rows - r), wd.e - wd.s,
-                                   uslices, ozscratch, smem_raw);
+        if (!oz::update_tile_tc(base, rs, ks, tk.y0, tk.rows, wd.e - wd.s, uslices, smem_raw, tmem) &&
+            tid == 0)
+            atomicExch(err, 1);
         if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds U
     } else {
         for (int r = 0; r < tk.rows; r += upd::BM) {
@@ -78,13 +82,35 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
     }
 }
 
+// Tensor memory for the split-precision tiles: one warp allocates all
+// oz::TMEM_COLS columns at the start of a persistent launch (one CTA per SM,
+// so the allocation never waits) and frees them when the CTA leaves.
+__device__ __forceinline__ uint32_t tmem_acquire(bool need, uint32_t* slot) {
+    if (!need) return 0u;
+    if ((threadIdx.x >> 5) == 0) oz::tmem_alloc(slot, oz::TMEM_COLS);
+    oz::tc_fence_before();
+    __syncthreads();
+    oz::tc_fence_after();
+    return *slot;
+}
+__device__ __forceinline__ void tmem_release(bool need, uint32_t tmem) {
+    if (!need) return;
+    oz::tc_fence_before();
+    __syncthreads();
+    oz::tc_fence_after();
+    if ((threadIdx.x >> 5) == 0) oz::tmem_dealloc(tmem, oz::TMEM_COLS);
+}
+
 __global__ void __launch_bounds__(SCHED_THREADS, 1)
 sched_kernel(SchedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int task_id;
     __shared__ unsigned long long u_key;
+    __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x;
     if (tid == 0) u_key = ~0ull;
+    const bool oz = P.uslices != nullptr;
+    const uint32_t tmem = tmem_acquire(oz, &tmem_slot);
     for (;;) {
         if (tid == 0) {
             int t = atomicAdd(P.head, 1);
@@ -117,8 +143,7 @@ sched_kernel(SchedParams P) {
         const Inst I = P.inst[wd.inst];
         run_task(tk, wd, I, P.upool + wd.u_off,
                  P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
-                 P.ozscratch ? P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX : nullptr,
-                 P.strong, (unsigned long long)tk.win, &u_key, smem_raw);
+                 P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err);
         // release: every thread's writes are ordered before the counters drop
         __threadfence();
         __syncthreads();
@@ -128,6 +153,7 @@ sched_kernel(SchedParams P) {
                 atomicSub(&P.deps_left[P.succ[i]], 1);
         }
     }
+    tmem_release(oz, tmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -151,8 +177,11 @@ server_kernel(SrvParams P) {
     __shared__ long long pos_s;
     __shared__ RingEntry ent_s;
     __shared__ unsigned long long u_key;
+    __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x;
     if (tid == 0) u_key = ~0ull;
+    const bool oz = P.ozaki != 0;
+    const uint32_t tmem = tmem_acquire(oz, &tmem_slot);
     for (;;) {
         if (tid == 0) {
             long long t = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(P.head), 1ull);
@@ -224,9 +253,8 @@ server_kernel(SrvParams P) {
             }
             run_task(tk, wd, R.inst, R.upool + wd.u_off,
                      R.uslices ? R.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
-                     P.ozscratch ? P.ozscratch + (size_t)blockIdx.x * UPD_FAR * WMAX : nullptr,
                      P.strong, ((unsigned long long)(unsigned)R.id << 32) | (unsigned)tk.win, &u_key,
-                     smem_raw);
+                     smem_raw, tmem, P.err);
         }
         __threadfence();
         __syncthreads();
@@ -243,6 +271,7 @@ server_kernel(SrvParams P) {
             }
         }
     }
+    tmem_release(oz, tmem);
 }
 
 }  // namespace

@@ -151,7 +151,7 @@ bool host_standard(int n, const double* S, int ldS) {
 
 CostModel server_cost(const gbr_opts& o) {
     CostModel c;
-    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 33000.0 : 6900.0;
+    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0 : 6900.0;
     return c;
 }
 
@@ -172,7 +172,6 @@ struct gbr_server {
     int* d_err = nullptr;
     gbr::RingEntry* d_ring = nullptr;
     gbr::SrvReq* d_reqs = nullptr;
-    double* d_oz = nullptr;
     long long cap = 0;
     // pinned host
     gbr::RingEntry* h_ring = nullptr;     // staging, same positions as the device ring
@@ -570,15 +569,13 @@ int gbr_server_create(const gbr_server_cfg* cfg, gbr_server** out) {
     GBR_CK(cudaStreamCreateWithFlags(&s->ps, cudaStreamNonBlocking), "stream");
     const size_t b_ctl = 256, b_ring = al256(sizeof(RingEntry) * s->cap);
     const size_t b_reqs = al256(sizeof(SrvReq) * s->slots);
-    const size_t b_oz = s->ozaki ? al256(sizeof(double) * UPD_FAR * WMAX * (size_t)s->grid) : 0;
-    GBR_CK(cudaMalloc((void**)&s->dctl, b_ctl + b_ring + b_reqs + b_oz), "cudaMalloc(server)");
+    GBR_CK(cudaMalloc((void**)&s->dctl, b_ctl + b_ring + b_reqs), "cudaMalloc(server)");
     s->d_head = (long long*)s->dctl;
     s->d_tail = (long long*)(s->dctl + 8);
     s->d_stop = (int*)(s->dctl + 16);
     s->d_err = (int*)(s->dctl + 20);
     s->d_ring = (RingEntry*)(s->dctl + b_ctl);
     s->d_reqs = (SrvReq*)(s->dctl + b_ctl + b_ring);
-    s->d_oz = b_oz ? (double*)(s->dctl + b_ctl + b_ring + b_reqs) : nullptr;
     GBR_CK(cudaMemset(s->dctl, 0, b_ctl), "memset");
     GBR_CK(cudaMemset(s->d_reqs, 0, b_reqs), "memset");
     GBR_CK(cudaMallocHost((void**)&s->h_ring, sizeof(RingEntry) * s->cap), "cudaMallocHost");
@@ -599,7 +596,7 @@ int gbr_server_create(const gbr_server_cfg* cfg, gbr_server** out) {
     P.stop = s->d_stop;
     P.err = s->d_err;
     P.reqs = s->d_reqs;
-    P.ozscratch = s->d_oz;
+    P.ozaki = s->ozaki ? 1 : 0;
     P.done = s->d_done;
     P.strong = c.opts.strong_test;
     const long long lim_ms = c.opts.wait_limit_ms > 0 ? c.opts.wait_limit_ms : 60000;

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "ozaki.cuh"
 #include "swap_math.cuh"
 
 #include <cuda_bf16.h>
@@ -255,25 +256,13 @@ __device__ __forceinline__ int rank_of_warp(int warp) {
     return part <= 1 ? (warp >> 2) * 2 + part : (warp >> 2);
 }
 
-// Signed 8-bit digits of x relative to the binary exponent field emax of the
-// largest entry of its row or column: |x| / 2^(emax - 1022) < 1 is written in
-// 56 fractional bits F = m 2^(3 + e - emax) (m the 53-bit significand), and
-// digit p (1..7) is bits [56 - 8p, 64 - 8p) of F, carrying the sign of x.
-// Entries below the normal range count as zero.  Integer work only.
-__device__ __forceinline__ unsigned long long oz_fixed(double x, int emax, bool* neg) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    *neg = (b >> 63) != 0;
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e == 0) return 0ull;
-    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
-    const int sh = emax - e;
-    return sh >= 64 ? 0ull : ((m << 3) >> sh);
-}
-
-// Writes U's digit slices (bf16, [slice][n][k], k < WMAX) and the column
-// exponents for the split-precision updates; columns/rows beyond w are zero.
+// Writes U's digit slices for the split-precision updates (ozaki.cuh): the
+// balanced base-256 digits of every entry relative to the largest exponent of
+// its column, as bf16, in the tensor cores' 128-byte-swizzled K-major layout
+// [output half][K half][slice][column n mod 64][128 B] (U(k, n) is entry k of
+// column n), then one int exponent per column.  Columns/rows beyond w are
+// zero.
 __device__ __forceinline__ void write_u_slices(const double* U, int w, unsigned char* out) {
-    __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(out);
     int* cexp = reinterpret_cast<int*>(out + OZ_UDIG_ELEMS * 2);
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
     __shared__ int ce[WMAX];
@@ -291,15 +280,29 @@ __device__ __forceinline__ void write_u_slices(const double* U, int w, unsigned 
         if (lane == 0) { ce[n] = em; cexp[n] = em; }
     }
     __syncthreads();
-    for (int i = tid; i < WMAX * WMAX; i += nth) {
-        const int n = i / WMAX, k = i % WMAX;
-        bool neg = false;
-        unsigned long long F = (n < w && k < w) ? oz_fixed(U[n * w + k], ce[n], &neg) : 0ull;
+    // unit (column n, 16-byte chunk c of K half kh): consecutive threads fill
+    // the 8 chunks of one 128-byte row, then the next column, so the global
+    // writes of a warp are 512 contiguous bytes
+    for (int u = tid; u < WMAX * (WMAX / 8); u += nth) {
+        const int c = u & 7, n = (u >> 3) & (WMAX - 1), kh = u >> 10;
+        long long G[8];
 #pragma unroll
-        for (int p = 0; p < OZ_SLICES; ++p) {
-            int d = (int)((F >> (48 - 8 * p)) & 255ull);
-            dig[(size_t)p * WMAX * WMAX + i] = __int2bfloat16_rn(neg ? -d : d);
+        for (int j = 0; j < 8; ++j) {
+            const int k = 64 * kh + 8 * c + j;
+            G[j] = (n < w && k < w) ? oz::oz_balanced(U[n * w + k], ce[n]) : oz::OZ_BIAS;
         }
+        unsigned char* dst = out + ((size_t)((n >> 6) * 2 + kh) * OZ_SLICES * 64 + (n & 63)) * 128 +
+                             (size_t)((c ^ (n & 7)) << 4);
+        unsigned wv[4];
+#define GBR_PUT_SLICE(P)                                                                   \
+        _Pragma("unroll") for (int t = 0; t < 4; ++t) wv[t] = oz::pack_bf16x2(             \
+            oz::oz_digit<P>((unsigned)G[2 * t], (unsigned)(G[2 * t] >> 32)),                 \
+            oz::oz_digit<P>((unsigned)G[2 * t + 1], (unsigned)(G[2 * t + 1] >> 32)));       \
+        *reinterpret_cast<uint4*>(dst + (size_t)((P) - 1) * 64 * 128) =                    \
+            make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        GBR_PUT_SLICE(1) GBR_PUT_SLICE(2) GBR_PUT_SLICE(3) GBR_PUT_SLICE(4) GBR_PUT_SLICE(5)
+        GBR_PUT_SLICE(6) GBR_PUT_SLICE(7)
+#undef GBR_PUT_SLICE
     }
 }
 
