@@ -87,59 +87,45 @@ __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
 // K-major block of 128-byte rows.
 __host__ __device__ constexpr int sw128(int r, int c) { return r * 128 + ((c ^ (r & 7)) << 4); }
 
-// Signed 128-bit integer (hi, lo) times 2^xe, rounded to the nearest double
-// (ties to even).  Results below the normal range flush to zero.
-__device__ __forceinline__ double i128_to_double(long long hi, unsigned long long lo, int xe) {
-    const bool neg = hi < 0;
-    if (neg) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0ull ? 1 : 0);
-    }
-    const unsigned long long uh = (unsigned long long)hi;
-    if (uh == 0ull && lo == 0ull) return 0.0;
-    const int L = uh ? 64 + 63 - __clzll((long long)uh) : 63 - __clzll((long long)lo);
-    unsigned long long m;
-    const int sh = L - 52;
-    if (sh > 0) {
-        // |T| < 2^74 here, so sh < 64
-        m = (uh << (64 - sh)) | (lo >> sh);
-        const unsigned long long rem = lo & ((1ull << sh) - 1ull);
-        const unsigned long long half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (m & 1ull))) ++m;
-    } else {
-        m = lo << (-sh);
-    }
-    int L2 = L;
-    if (m >> 53) {  // rounding carried into a new bit
-        m >>= 1;
-        ++L2;
-    }
-    const int biased = L2 + xe + 1023;
-    if (biased <= 0) return neg ? -0.0 : 0.0;
-    if (biased >= 2047) return neg ? -__longlong_as_double(0x7ff0000000000000ll)
-                                   : __longlong_as_double(0x7ff0000000000000ll);
-    const unsigned long long bits = ((unsigned long long)neg << 63) |
-                                    ((unsigned long long)biased << 52) | (m & 0xfffffffffffffull);
-    return __longlong_as_double((long long)bits);
-}
-
 // The seven accumulators (FP32 bit patterns, diagonals 2..8) of one output ->
-// y u, given the exponent fields of its row (er) and column (ec).
+// y u, given the exponent fields of its row (er) and column (ec).  The
+// accumulators hold exact integers; T = sum_d D_d 256^(8 - d) (|T| < 2^74) is
+// formed in 128-bit integers and rounded once to the nearest double: |T| is
+// shifted right by 0, 7 or 11 bits so that it fits 63 bits with at least 56
+// significant bits whenever bits are dropped, the dropped bits are kept as a
+// sticky bit in bit 0, and the 64-bit integer is converted with
+// round-to-nearest-even.  Results below the normal range flush to zero.
 __device__ __forceinline__ double oz_combine(const unsigned (&a)[7], int er, int ec) {
     if (er == 0 || ec == 0) return 0.0;
     int D[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) D[j] = __float2int_rn(__uint_as_float(a[j]));  // exact
-    // D2..D6 by Horner in 64 bits (|.| < 2^57), then * 2^16 + D7 * 256 + D8
+    // D2..D6 by Horner in 64 bits (|.| < 2^57), then T = th 2^16 + D7 256 + D8
     long long th = D[0];
 #pragma unroll
     for (int j = 1; j <= 4; ++j) th = th * 256 + D[j];
     const long long lowp = (long long)D[5] * 256 + (long long)D[6];
-    const unsigned long long lo = (unsigned long long)th << 16;
-    long long hi = th >> 48;
-    const unsigned long long lo2 = lo + (unsigned long long)lowp;
-    hi += (lo2 < lo ? 1 : 0) - (lowp < 0 ? 1 : 0);
-    return i128_to_double(hi, lo2, -64 + (er - 1021) + (ec - 1021));
+    const unsigned long long lo0 = (unsigned long long)th << 16;
+    unsigned long long lo = lo0 + (unsigned long long)lowp;
+    long long hi = (th >> 48) + (lo < lo0 ? 1 : 0) - (lowp < 0 ? 1 : 0);
+    const bool neg = hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1 : 0);
+    }
+    const unsigned long long uh = (unsigned long long)hi;  // |T| = uh 2^64 + lo
+    const int sh = uh >= 64ull ? 11 : ((uh != 0ull || (long long)lo < 0) ? 7 : 0);
+    unsigned long long t = lo;
+    if (sh) t = (uh << (64 - sh)) | (lo >> sh) | ((lo & ((1ull << sh) - 1ull)) != 0ull ? 1ull : 0ull);
+    if (t == 0ull) return 0.0;
+    long long bits = __double_as_longlong(__ull2double_rn(t));
+    const int xe = sh - 64 + (er - 1021) + (ec - 1021);
+    const int ef = (int)((bits >> 52) & 0x7ff) + xe;
+    if (ef <= 0) return neg ? -0.0 : 0.0;
+    if (ef >= 2047) bits = 0x7ff0000000000000ll;
+    else bits += (long long)xe << 52;
+    if (neg) bits |= (long long)(1ull << 63);
+    return __longlong_as_double(bits);
 }
 
 // ---------------------------------------------------------------------------
