@@ -56,6 +56,13 @@ WORKLOADS = {
 }
 METRIC = "selected eigenvalues reordered per second"
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the current kernels (profiles/sched_kernel_n4000_full.md and
+# profiles/sched_kernel_n4000_ozaki_full.md); None where no capture of the
+# current build exists for that workload.
+NCU_TRAFFIC = {("n4000", "dmma"): 1.912737e9 + 2.634941e9,
+               ("n4000", "ozaki"): 3.080491e9 + 5.505739e9}
+
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
     """Replicas: every rank processed `units` in `local_ms`; the job's time is
@@ -656,7 +663,8 @@ def main():
         roof = {"kernel": "sched_kernel (persistent: FP64 window tasks + bf16 slice-product "
                           "update tiles)",
                 "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": achieved / bf16_peak, "traffic": None,
+                "frac": achieved / bf16_peak,
+                "traffic": NCU_TRAFFIC.get((wl["name"], "ozaki")),
                 "peak_source": f"{src} bf16 {bf16_peak} TF/s",
                 "flops_per_launch": work, "bf16_slice_flops": 28.0 * flops_upd,
                 "fp64_window_flops": flops_win, "launches_per_step": 1,
@@ -669,7 +677,7 @@ def main():
         achieved = (flops_iss + flops_win) / (ms_sched / 1e3) / 1e12
         roof = {"kernel": "sched_kernel (persistent: window tasks + DMMA update tiles)",
                 "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
+                "frac": achieved / fp64_peak, "traffic": NCU_TRAFFIC.get((wl["name"], "dmma")),
                 "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
                                 "1.25/2250 (FP64 DMMA probe: 1.047 TF/s)"),
                 "flops_per_launch": flops_iss + flops_win, "launches_per_step": 1,
