@@ -73,9 +73,10 @@ struct CostModel {
 
 int far_rows(int n);
 void pipeline_order(int n, std::vector<Window>& wins);
-// far: panel rows of the update tiles away from the window (0: far_rows(n)).
+// far: panel rows of the update tiles away from the window (0: far_rows(n));
+// threads: host threads for the dependence search.
 void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostModel& cm,
-                 TaskGraph& G, int far = 0);
+                 TaskGraph& G, int far = 0, int threads = 1);
 void queue_order(const TaskGraph& G, int P, std::vector<int>& order, double* cp_us = nullptr,
                  double* sim_us = nullptr);
 

@@ -179,19 +179,6 @@ double update_flops(int n, const std::vector<Window>& win, bool withQ) {
 // skipped once a newer one covers the whole overlap (they are then
 // predecessors of that newer task already).
 // ---------------------------------------------------------------------------
-static inline bool rects_overlap(const Rect& a, const Rect& b) {
-    return a.r0 < b.r1 && b.r0 < a.r1 && a.c0 < b.c1 && b.c0 < a.c1;
-}
-static inline bool rect_covers(const Rect& a, const Rect& b) {
-    return a.r0 <= b.r0 && a.r1 >= b.r1 && a.c0 <= b.c0 && a.c1 >= b.c1;
-}
-static inline Rect rect_isect(const Rect& a, const Rect& b) {
-    return Rect{std::max(a.r0, b.r0), std::min(a.r1, b.r1), std::max(a.c0, b.c0),
-                std::min(a.c1, b.c1)};
-}
-
-
-
 // Duration model for the queue order only (relative values matter): a window
 // task takes about cm.win_us_128 at w = 128, an update tile is a product of
 // rows x w x w at cm.tile_rate flops per microsecond of one SM.
@@ -209,7 +196,7 @@ int far_rows(int n) {
 }
 
 void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostModel& cm,
-                 TaskGraph& G, int far) {
+                 TaskGraph& G, int far, int threads) {
     const int FAR = far > 0 ? far : far_rows(n);
     std::vector<HostTask>& T = G.t;
     std::vector<std::pair<int, int>> edges;
@@ -248,71 +235,112 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
             }
     }
     // Dependences in program order on exact rectangles, found through a grid
-    // of CB x CB cells: each cell lists the tasks touching it, newest last.
+    // of CB x CB cells: each cell lists the tasks touching it, newest last,
+    // with each task's rectangle clipped to the cell (cell-relative bytes).
+    // Within one cell, every task ends up ordered (directly or through newer
+    // tasks) after every earlier task that overlaps it there.  A pair of
+    // overlapping tasks is therefore looked at only in the first cell row
+    // where their rectangles overlap: the cell rows are split among threads
+    // (row cr to thread cr mod NT), each thread runs the whole task list over
+    // its own rows, and no pair is emitted by two threads.
     const int CB = UPD_BM;
+    static_assert(UPD_BM <= 255, "cell-relative coordinates are bytes");
     const int nc = (n + CB - 1) / CB;
-    std::vector<std::vector<int>> cellv;        // S cells: tasks touching the cell
-    cellv.resize((size_t)nc * nc);
-    // Q tiles all lie on the FAR row grid, so within a row block two Q
-    // tasks conflict exactly when their column ranges overlap: the last Q task
-    // per (row block, column) gives the exact, minimal predecessors.
-    const int nqb = (n + FAR - 1) / FAR;
-    std::vector<int> lastq(withQ ? (size_t)nqb * n : 0, -1);
-    std::vector<int> stamp(T.size(), -1);
-    // Scanning a cell from the newest task back; an older task is implied once
-    // a newer predecessor covers the whole region (it overlaps that one, so it
-    // precedes it), and the scan ends there.
-    auto scan = [&](std::vector<int>& L, const Rect& X, int t) {
-        for (int k = (int)L.size() - 1; k >= 0; --k) {
-            const int u = L[k];
-            const Rect& U = T[u].rc;
-            if (!rects_overlap(U, X)) continue;
-            if (stamp[u] != t) {
-                stamp[u] = t;
-                edges.push_back({u, t});
-            }
-            if (rect_covers(U, X)) break;
+    struct Entry {
+        int task;
+        uint8_t r0, r1, c0, c1;  // clipped rectangle, relative to the cell
+        uint8_t starts;          // the task's rectangle starts in this cell row
+    };
+    constexpr int INLINE = 14;   // entries kept in the cell itself (lists are short)
+    struct Cell {
+        int cnt = 0;
+        Entry e[INLINE];
+        std::vector<Entry> more;  // entries beyond INLINE (rare)
+        Entry& at(int k) { return k < INLINE ? e[k] : more[k - INLINE]; }
+        void push(const Entry& x) {
+            if (cnt < INLINE) e[cnt] = x;
+            else if ((int)more.size() > cnt - INLINE) more[cnt - INLINE] = x;
+            else more.push_back(x);
+            ++cnt;
         }
     };
-    for (int t = 0; t < (int)T.size(); ++t) {
-        const Rect R = T[t].rc;
-        const int kind = T[t].kind;
-        if (kind == TASK_Q) {
-            int* last = &lastq[(size_t)(R.r0 / FAR) * n];
-            int prev = -1;
-            for (int c = R.c0; c < R.c1; ++c) {
-                const int u = last[c];
-                if (u >= 0 && u != prev && stamp[u] != t) {
-                    stamp[u] = t;
-                    edges.push_back({u, t});
+    const int nqb = (n + FAR - 1) / FAR;
+    const int NT = std::max(1, std::min(threads, nc));
+    std::vector<std::vector<std::pair<int, int>>> tedges(NT);
+    auto worker = [&](int k) {
+        std::vector<std::pair<int, int>>& out = tedges[k];
+        const int myrows = (nc - k + NT - 1) / NT;
+        std::vector<Cell> cells((size_t)std::max(0, myrows) * nc);
+        // Q tiles all lie on the FAR row grid, so within a row block two Q
+        // tasks conflict exactly when their column ranges overlap: the last Q
+        // task per (row block, column) gives the exact, minimal predecessors.
+        const int myq = (nqb - k + NT - 1) / NT;
+        std::vector<int> lastq(withQ ? (size_t)std::max(0, myq) * n : 0, -1);
+        std::vector<int> stamp(T.size(), -1);
+        for (int t = 0; t < (int)T.size(); ++t) {
+            const Rect R = T[t].rc;
+            if (T[t].kind == TASK_Q) {
+                const int qb = R.r0 / FAR;
+                if (qb % NT != k) continue;
+                int* last = &lastq[(size_t)(qb / NT) * n];
+                int prev = -1;
+                for (int c = R.c0; c < R.c1; ++c) {
+                    const int u = last[c];
+                    if (u >= 0 && u != prev && stamp[u] != t) {
+                        stamp[u] = t;
+                        out.push_back({u, t});
+                    }
+                    prev = u;
+                    last[c] = t;
                 }
-                prev = u;
-                last[c] = t;
+                continue;
             }
-            continue;
+            int cr = R.r0 / CB;
+            cr += (k - cr % NT + NT) % NT;  // first of this thread's rows
+            for (; cr * CB < R.r1; cr += NT) {
+                const int br = cr * CB;
+                const uint8_t tstarts = R.r0 >= br ? 1 : 0;
+                for (int cc = R.c0 / CB; cc * CB < R.c1; ++cc) {
+                    const int bc = cc * CB;
+                    const Entry X{t, (uint8_t)(std::max(R.r0, br) - br), (uint8_t)(std::min(R.r1, br + CB) - br),
+                                  (uint8_t)(std::max(R.c0, bc) - bc), (uint8_t)(std::min(R.c1, bc + CB) - bc),
+                                  tstarts};
+                    Cell& C = cells[(size_t)(cr / NT) * nc + cc];
+                    // scanning from the newest, an older task is implied once a
+                    // newer predecessor covers the whole region, and the scan ends
+                    for (int j = C.cnt - 1; j >= 0; --j) {
+                        const Entry& U = C.at(j);
+                        if (U.r0 >= X.r1 || X.r0 >= U.r1 || U.c0 >= X.c1 || X.c0 >= U.c1) continue;
+                        if ((tstarts | U.starts) && stamp[U.task] != t) {
+                            stamp[U.task] = t;
+                            out.push_back({U.task, t});
+                        }
+                        if (U.r0 <= X.r0 && U.r1 >= X.r1 && U.c0 <= X.c0 && U.c1 >= X.c1) break;
+                    }
+                    // compaction: an entry whose part of the cell lies inside the
+                    // new task's part precedes it and can never be needed again
+                    int keep = 0;
+                    for (int j = 0; j < C.cnt; ++j) {
+                        const Entry U = C.at(j);
+                        if (!(X.r0 <= U.r0 && X.r1 >= U.r1 && X.c0 <= U.c0 && X.c1 >= U.c1)) C.at(keep++) = U;
+                    }
+                    C.cnt = keep;
+                    C.push(X);
+                }
+            }
         }
-        for (int cr = R.r0 / CB; cr * CB < R.r1; ++cr)
-            for (int cc = R.c0 / CB; cc * CB < R.c1; ++cc) {
-                const Rect cell{cr * CB, std::min(n, (cr + 1) * CB), cc * CB, std::min(n, (cc + 1) * CB)};
-                const Rect X = rect_isect(R, cell);
-                const size_t ci = (size_t)cr * nc + cc;
-
-                // all S tasks order against every overlapping earlier S task
-                scan(cellv[ci], X, t);
-                // compaction: an entry whose part of the cell lies inside the new
-                // task's part precedes the new task and can never be needed again
-                std::vector<int>& L = cellv[ci];
-                size_t keep = 0;
-                for (size_t k = 0; k < L.size(); ++k) {
-                    const Rect I = rect_isect(T[L[k]].rc, cell);
-                    if (!rect_covers(X, I)) L[keep++] = L[k];
-                }
-                L.resize(keep);
-                L.push_back(t);
-            }
+    };
+    if (NT == 1) {
+        worker(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int k = 0; k < NT; ++k) th.emplace_back(worker, k);
+        for (auto& x : th) x.join();
     }
-    // No edge is listed twice: the scans stamp each predecessor once per task,
-    // and a window task overlaps none of its own tiles.
+    for (auto& v : tedges) edges.insert(edges.end(), v.begin(), v.end());
+    // No edge is listed twice: a pair is emitted only in its first common cell
+    // row, where the thread stamps each predecessor once per task, and a
+    // window task overlaps none of its own tiles.
     const int nt = (int)T.size();
     G.ndeps.assign(nt, 0);
     G.soff.assign(nt + 1, 0);
@@ -360,11 +388,12 @@ void pipeline_order(int n, std::vector<Window>& wins) {
 void queue_order(const TaskGraph& G, int P, std::vector<int>& order, double* cp_us,
                  double* sim_us) {
     const int nt = (int)G.t.size();
-    std::vector<double> bl(nt, 0.0);
+    std::vector<double> dur(nt), bl(nt, 0.0);
+    for (int t = 0; t < nt; ++t) dur[t] = G.t[t].dur;
     for (int t = nt - 1; t >= 0; --t) {
         double m = 0.0;
         for (int i = G.soff[t]; i < G.soff[t + 1]; ++i) m = std::max(m, bl[G.succ[i]]);
-        bl[t] = G.t[t].dur + m;
+        bl[t] = dur[t] + m;
     }
     if (cp_us) {
         double m = 0.0;
@@ -372,32 +401,53 @@ void queue_order(const TaskGraph& G, int P, std::vector<int>& order, double* cp_
         *cp_us = m;
     }
     std::vector<int> indeg(G.ndeps);
-    typedef std::pair<double, int> Key;
-    std::priority_queue<std::pair<double, int>> ready;  // (bottom level, -index)
-    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> running;  // (finish, task)
+    // ready: max-heap on (bottom level, lower index first); running: min-heap
+    // on finish time.  Both are plain binary heaps over small structs.
+    struct RK {
+        double key;
+        int t;
+    };
+    auto ready_less = [](const RK& a, const RK& b) {  // a below b in the max-heap
+        return a.key < b.key || (a.key == b.key && a.t > b.t);
+    };
+    auto run_less = [](const RK& a, const RK& b) {  // a below b in the min-heap
+        return a.key > b.key || (a.key == b.key && a.t > b.t);
+    };
+    std::vector<RK> ready, running;
+    ready.reserve(1024);
+    running.reserve((size_t)P + 1);
     for (int t = 0; t < nt; ++t)
-        if (indeg[t] == 0) ready.push({bl[t], -t});
+        if (indeg[t] == 0) ready.push_back({bl[t], t});
+    std::make_heap(ready.begin(), ready.end(), ready_less);
     order.clear();
     order.reserve(nt);
     int free = P;
     double now = 0.0;
     while ((int)order.size() < nt) {
         while (free > 0 && !ready.empty()) {
-            int t = -ready.top().second;
-            ready.pop();
+            std::pop_heap(ready.begin(), ready.end(), ready_less);
+            const int t = ready.back().t;
+            ready.pop_back();
             order.push_back(t);
-            running.push({now + G.t[t].dur, t});
+            running.push_back({now + dur[t], t});
+            std::push_heap(running.begin(), running.end(), run_less);
             --free;
         }
         if (running.empty()) break;  // cannot happen for an acyclic graph
-        now = running.top().first;
+        now = running.front().key;
         if (sim_us) *sim_us = now;
-        while (!running.empty() && running.top().first <= now) {
-            int t = running.top().second;
-            running.pop();
+        while (!running.empty() && running.front().key <= now) {
+            std::pop_heap(running.begin(), running.end(), run_less);
+            const int t = running.back().t;
+            running.pop_back();
             ++free;
-            for (int i = G.soff[t]; i < G.soff[t + 1]; ++i)
-                if (--indeg[G.succ[i]] == 0) ready.push({bl[G.succ[i]], -G.succ[i]});
+            for (int i = G.soff[t]; i < G.soff[t + 1]; ++i) {
+                const int s = G.succ[i];
+                if (--indeg[s] == 0) {
+                    ready.push_back({bl[s], s});
+                    std::push_heap(ready.begin(), ready.end(), ready_less);
+                }
+            }
         }
     }
 }
@@ -413,11 +463,12 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     auto th0 = std::chrono::steady_clock::now();
     // per-instance program order and task graph; instances are independent
     std::vector<TaskGraph> Gs(ni);
+    const unsigned nth = std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()));
     auto work = [&](size_t i) {
         pipeline_order(plans[i].d.n, plans[i].wins);
-        build_graph(plans[i].d.n, plans[i].wins, plans[i].d.Q != nullptr, cm, Gs[i], plans[i].far);
+        build_graph(plans[i].d.n, plans[i].wins, plans[i].d.Q != nullptr, cm, Gs[i], plans[i].far,
+                    ni >= 64 ? 1 : (int)nth);
     };
-    unsigned nth = std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()));
     if (ni >= 64 && nth > 1) {
         std::vector<std::thread> th;
         for (unsigned k = 0; k < nth; ++k)

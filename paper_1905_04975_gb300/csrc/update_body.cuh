@@ -62,17 +62,17 @@ __device__ __forceinline__ void panel_geom(int panel, int n, int s, int e, doubl
 // U is a product of adjacent-block swaps, so the nonzeros of each of its
 // columns form one contiguous run of rows (a staircase: about a quarter of
 // U is zero for a window whose chain enters at the bottom, more for a
-// chain's first window).  When U is loaded, each warp finds the rows
-// [klo, khi) where its 16 output columns have nonzeros and the products run
-// over those rows only.  If issued is not null, the flops issued by the
-// tile are added to it.
+// chain's first window).  When U is loaded, each warp finds, for each of its
+// two groups of 8 output columns, the rows [klo, khi) where they have
+// nonzeros, and the products of a group run over those rows only.  If
+// issued is not null, the flops issued by the tile are added to it.
 __device__ __forceinline__ void update_tile(double* base, long long rs, long long ks, int r0,
                                             int rows, int w, const double* __restrict__ Ug,
                                             bool load_u, unsigned char* smem_raw,
                                             unsigned long long* issued = nullptr) {
     double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU
     double* Ys = Us + WMAX * LDU;                        // BM x LDY
-    __shared__ int k_lo[UPD_THREADS / 32], k_hi[UPD_THREADS / 32];
+    __shared__ int k_lo[UPD_THREADS / 32][2], k_hi[UPD_THREADS / 32][2];
     const int wp = (w + 15) & ~15;  // padded to the warp column width
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -84,24 +84,27 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
         __syncthreads();
         if (warp < UPD_THREADS / 32) {
             const int c0 = warp * 16;
-            int lo = wp, hi = 0;
-            if (c0 < wp)
-                for (int k = lane; k < wp; k += 32) {
-                    bool nz = false;
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) nz |= Us[k * LDU + c0 + c] != 0.0;
-                    if (nz) {
-                        lo = min(lo, k);
-                        hi = max(hi, k + 1);
+            for (int ct = 0; ct < 2; ++ct) {
+                int lo = wp, hi = 0;
+                if (c0 < wp)
+                    for (int k = lane; k < wp; k += 32) {
+                        bool nz = false;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) nz |= Us[k * LDU + c0 + 8 * ct + c] != 0.0;
+                        if (nz) {
+                            lo = min(lo, k);
+                            hi = max(hi, k + 1);
+                        }
                     }
+                for (int o = 16; o; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
                 }
-            for (int o = 16; o; o >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            }
-            if (lane == 0) {
-                k_lo[warp] = lo < hi ? (lo & ~3) : 0;
-                k_hi[warp] = lo < hi ? min(wp, (hi + 3) & ~3) : 0;
+                if (lane == 0) {
+                    k_lo[warp][ct] = lo < hi ? (lo & ~3) : 0;
+                    k_hi[warp][ct] = lo < hi ? min(wp, (hi + 3) & ~3) : 0;
+                }
             }
         }
     }
@@ -122,17 +125,23 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
     if (issued && tid == 0) {
         unsigned long long f = 0;
         for (int v = 0; v < UPD_THREADS / 32 && v * 16 < w; ++v)
-            f += 2ull * rows * (unsigned long long)min(16, w - v * 16) * (k_hi[v] - k_lo[v]);
+            for (int ct = 0; ct < 2 && v * 16 + 8 * ct < w; ++ct)
+                f += 2ull * rows * (unsigned long long)min(8, w - v * 16 - 8 * ct) *
+                     (k_hi[v][ct] - k_lo[v][ct]);
         atomicAdd(issued, f);
     }
     if (warp < UPD_THREADS / 32 && c0 < wp) {
-        const int klo = k_lo[warp], khi = k_hi[warp];
+        const int lo0 = k_lo[warp][0], hi0 = k_hi[warp][0];
+        const int lo1 = k_lo[warp][1], hi1 = k_hi[warp][1];
         double acc[8][2][2];
 #pragma unroll
         for (int rt = 0; rt < 8; ++rt)
 #pragma unroll
             for (int ct = 0; ct < 2; ++ct) acc[rt][ct][0] = acc[rt][ct][1] = 0.0;
-        for (int kk = klo; kk < khi; kk += 4) {
+        // rows where both groups have nonzeros, then the rows of one group
+        // only (the ranges are contiguous, so at most one such run per side)
+        const int blo = max(lo0, lo1), bhi = min(hi0, hi1);
+        for (int kk = blo; kk < bhi; kk += 4) {
             double a[8], bb[2];
 #pragma unroll
             for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LDY + kk + tig];
@@ -142,6 +151,23 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
             for (int rt = 0; rt < 8; ++rt)
 #pragma unroll
                 for (int ct = 0; ct < 2; ++ct) dmma(acc[rt][ct][0], acc[rt][ct][1], a[rt], bb[ct]);
+        }
+#pragma unroll
+        for (int ct = 0; ct < 2; ++ct) {
+            const int lo = ct ? lo1 : lo0, hi = ct ? hi1 : hi0;
+            // rows of group ct outside [blo, bhi): below and above the common run
+            for (int side = 0; side < 2; ++side) {
+                const int a0 = side ? max(lo, max(bhi, blo)) : lo;
+                const int a1 = side ? hi : min(hi, blo);
+                for (int kk = a0; kk < a1; kk += 4) {
+                    double a[8];
+#pragma unroll
+                    for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LDY + kk + tig];
+                    const double bv = Us[(kk + tig) * LDU + c0 + ct * 8 + gid];
+#pragma unroll
+                    for (int rt = 0; rt < 8; ++rt) dmma(acc[rt][ct][0], acc[rt][ct][1], a[rt], bv);
+                }
+            }
         }
         // write back (in place: this CTA read all of its rows before any write)
 #pragma unroll
