@@ -57,11 +57,9 @@ WORKLOADS = {
 METRIC = "selected eigenvalues reordered per second"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the current kernels (profiles/sched_kernel_n4000_full.md and
-# profiles/sched_kernel_n4000_ozaki_full.md); None where no capture of the
-# current build exists for that workload.
-NCU_TRAFFIC = {("n4000", "dmma"): 1.912737e9 + 2.634941e9,
-               ("n4000", "ozaki"): 3.080491e9 + 5.505739e9}
+# capture of the current kernels (the sched_kernel captures under profiles/);
+# a workload has no entry while no capture of the current build exists.
+NCU_TRAFFIC = {}
 
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
