@@ -326,11 +326,9 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     uint8_t* bst = reinterpret_cast<uint8_t*>(swp + MAXSW);
     uint8_t* sel = bst + WMAX;
     __shared__ int nsw, nrej, nacc;
-    unsigned long long wflops = 0;   // meaningful in lanes 0 of warps 0..2, summed below
+    unsigned long long wflops = 0;   // per thread (phase D), summed at the end
     __shared__ int tcnt[3];
-    __shared__ int tlist[3][MAXSW];     // slots per type
-    __shared__ int ksl[3][MAXSW];       // slots with k = 2, 3, 4 (accepted only)
-    __shared__ int kcnt[3];
+    __shared__ int tlist[3][MAXSW];     // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
     __shared__ int kpre_l[3][MAXSW + 1];  // prefix sums of left-apply columns per k group
     __shared__ int kpre_r[3][MAXSW + 1];  // prefix sums of right-apply rows (S rows + U rows)
     // Rows [urlo[c], urhi[c]] hold every nonzero of column c of U: U starts as
@@ -378,7 +376,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
         }
         for (int i = tid; i < w; i += nth)
             bst[i] = (i == 0) || (Sp[poff(i - 1) + i] == 0.0);
-        if (tid < 3) { tcnt[tid] = 0; kcnt[tid] = 0; }
+        if (tid < 3) tcnt[tid] = 0;
         if (tid == 0) nsw = 0;
         __syncthreads();
         // --- phase A1: find the swaps of this step (integer work only).  After the
@@ -437,10 +435,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                     if (ok) {
                         Zs[slot * 16 + c * 4 + r] = zrc;
                         if (r <= c + 1) Sp[poff(ja + c) + ja + r] = dnrc;
-                        if (l == 0) {
-                            ksl[2][atomicAdd(&kcnt[2], 1)] = slot;
-                            atomicAdd(&nacc, 1);
-                        }
+                        if (l == 0) atomicAdd(&nacc, 1);
                     } else if (l == 0) {
                         double D[16], Zl[16], Dn[16];
                         for (int cc = 0; cc < 4; ++cc)
@@ -451,7 +446,6 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                                 for (int rr = 0; rr <= min(cc + 1, 3); ++rr)
                                     Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
                             for (int e = 0; e < 16; ++e) Zs[slot * 16 + e] = Zl[e];
-                            ksl[2][atomicAdd(&kcnt[2], 1)] = slot;
                             atomicAdd(&nacc, 1);
                         } else {
                             swk[slot] = 0;
@@ -517,7 +511,6 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                         }
                     }
                     if (ok) {
-                        ksl[k - 2][atomicAdd(&kcnt[k - 2], 1)] = slot;
                         if (p >= 0) atomicAdd(&nacc, 1);
                     } else {
                         swk[slot] = 0;
@@ -526,41 +519,44 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                     }
                 }
             }
-        }
-        __syncthreads();
-        // prefix sums of the apply work per k group (one warp per group)
-        if (warp < 3) {
-            const int g = warp, cnt = kcnt[g];
-            int runl = 0, runr = 0;
-            for (int base = 0; base < cnt; base += 32) {
-                int i = base + lane;
-                int nl = 0, nr = 0;
-                if (i < cnt) {
-                    const int slot = ksl[g][i], j = swj[slot], k = swk[slot];
-                    int lo = urlo[j], hi = urhi[j];
-                    for (int c = 1; c < k; ++c) {
-                        lo = min(lo, (int)urlo[j + c]);
-                        hi = max(hi, (int)urhi[j + c]);
+            // Prefix sums of the apply work per k group, one warp per group:
+            // the T_11 warps of rank 1..3 (the Givens rotations of a step fit
+            // in rank 0's 32 lanes, so these are otherwise idle), integer
+            // work that overlaps the FP64 transforms of the other warps.  All
+            // listed swaps are counted; a rejected one is skipped when
+            // applied.  k comes from the group (A2 zeroes swk of a rejection).
+            if (ty == T_11 && rank >= 1) {
+                const int g = rank - 1, k = g + 2, cnt = tcnt[g];
+                int runl = 0, runr = 0;
+                for (int base = 0; base < cnt; base += 32) {
+                    int i = base + lane;
+                    int nl = 0, nr = 0;
+                    if (i < cnt) {
+                        const int slot = tlist[g][i], j = swj[slot];
+                        int lo = urlo[j], hi = urhi[j];
+                        for (int c = 1; c < k; ++c) {
+                            lo = min(lo, (int)urlo[j + c]);
+                            hi = max(hi, (int)urhi[j + c]);
+                        }
+                        slo[slot] = (short)lo;
+                        shi[slot] = (short)hi;
+                        nl = w - j - k;
+                        nr = j + (hi - lo + 1);
                     }
-                    slo[slot] = (short)lo;
-                    shi[slot] = (short)hi;
-                    nl = w - j - k;
-                    nr = j + (hi - lo + 1);
+                    int il = nl, ir = nr;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int a = __shfl_up_sync(0xffffffffu, il, o);
+                        int b2 = __shfl_up_sync(0xffffffffu, ir, o);
+                        if (lane >= o) { il += a; ir += b2; }
+                    }
+                    if (i < cnt) { kpre_l[g][i + 1] = runl + il; kpre_r[g][i + 1] = runr + ir; }
+                    runl += __shfl_sync(0xffffffffu, il, 31);
+                    runr += __shfl_sync(0xffffffffu, ir, 31);
                 }
-                int il = nl, ir = nr;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int a = __shfl_up_sync(0xffffffffu, il, o);
-                    int b2 = __shfl_up_sync(0xffffffffu, ir, o);
-                    if (lane >= o) { il += a; ir += b2; }
+                if (lane == 0) {
+                    kpre_l[g][0] = 0;
+                    kpre_r[g][0] = 0;
                 }
-                if (i < cnt) { kpre_l[g][i + 1] = runl + il; kpre_r[g][i + 1] = runr + ir; }
-                runl += __shfl_sync(0xffffffffu, il, 31);
-                runr += __shfl_sync(0xffffffffu, ir, 31);
-            }
-            if (lane == 0) {
-                kpre_l[g][0] = 0;
-                kpre_r[g][0] = 0;
-                wflops += 2ull * (g + 2) * (g + 2) * (unsigned long long)(runl + runr);
             }
         }
         __syncthreads();
@@ -568,14 +564,15 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
         // compacted per k so that every lane of a warp runs the same k
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = kcnt[g], total = kpre_l[g][cnt];
+            const int k = g + 2, cnt = tcnt[g], total = kpre_l[g][cnt];
             for (int it = tid; it < total; it += nth) {
                 int lo = 0, hi = cnt - 1;   // last i with kpre_l[g][i] <= it
                 while (lo < hi) {
                     int mid = (lo + hi + 1) >> 1;
                     if (kpre_l[g][mid] <= it) lo = mid; else hi = mid - 1;
                 }
-                const int slot = ksl[g][lo];
+                const int slot = tlist[g][lo];
+                if (swk[slot] == 0) continue;  // rejected
                 const int j = swj[slot];
                 const int c = j + k + (it - kpre_l[g][lo]);
                 const double* Z = &Zs[slot * 16];
@@ -598,14 +595,15 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
         // and of U rows [0, w)
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = kcnt[g], total = kpre_r[g][cnt];
+            const int k = g + 2, cnt = tcnt[g], total = kpre_r[g][cnt];
             for (int it = tid; it < total; it += nth) {
                 int lo = 0, hi = cnt - 1;
                 while (lo < hi) {
                     int mid = (lo + hi + 1) >> 1;
                     if (kpre_r[g][mid] <= it) lo = mid; else hi = mid - 1;
                 }
-                const int slot = ksl[g][lo];
+                const int slot = tlist[g][lo];
+                if (swk[slot] == 0) continue;  // rejected
                 const int j = swj[slot];
                 const int rr = it - kpre_r[g][lo];
                 const double* Z = &Zs[slot * 16];
@@ -639,6 +637,9 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                 sel[swp[sw]] = SEL_STUCK;
                 continue;
             }
+            // in-window flops of this accepted transform: k x k applied to
+            // w - j - k columns (left) and j rows of S + its U rows (right)
+            wflops += 2ull * k * k * (unsigned long long)((w - j - k) + j + (shi[sw] - slo[sw] + 1));
             for (int c = 0; c < k; ++c) {
                 urlo[j + c] = slo[sw];
                 urhi[j + c] = shi[sw];
@@ -656,7 +657,8 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     __shared__ unsigned long long wfl_sum;
     if (tid == 0) wfl_sum = 0;
     __syncthreads();
-    if (lane == 0 && warp < 3) atomicAdd(&wfl_sum, wflops);
+    for (int o = 16; o; o >>= 1) wflops += __shfl_xor_sync(0xffffffffu, wflops, o);
+    if (lane == 0) atomicAdd(&wfl_sum, wflops);
     __syncthreads();
     wflops = wfl_sum;
     // store: window of S, selection, U
