@@ -188,6 +188,45 @@ int gbr_reorder_noalloc(int n, double *S, int ldS, double *Q, int ldQ, const int
                         gbr_stats *stats, void *cuda_stream);
 
 /*
+ * One off-diagonal update on one panel, in place:
+ *
+ *     Y <- Y U
+ *
+ * This is the level-3 step of Section 3.2 (Fig. 1b): the accumulated
+ * orthogonal transformation U of a diagonal window applied to a section of
+ * the matrix.  gbr_reorder runs it on three panels per window: the left
+ * update S[win, right] <- U^T S[win, right] (Y = that block read
+ * transposed, row-major: rs = ldS, ks = 1), the right update
+ * S[above, win] <- S[above, win] U and the Q update Q[:, win] <- Q[:, win] U
+ * (Y = the column-major block: rs = 1, ks = ld).  Exposed on its own so that
+ * the update arithmetic can be used and checked separately.
+ *
+ *  1 rows       panel rows (>= 0; 0 is a no-op)
+ *  2 w          window size = columns of Y = order of U, 1..128
+ *  3 Y          device: element (r, k) at Y[r * rs + k * ks], updated in place
+ *  4 rs, 5 ks   strides in elements, >= 1, with rs == 1 or ks == 1
+ *                 (-4 if not)
+ *  6 U          device: w x w, column-major, leading dimension ldU; read only
+ *  7 ldU        >= w
+ *  8 precision  GBR_PREC_DMMA: FP64 tensor-core products (DMMA);
+ *               GBR_PREC_OZAKI: emulated FP64 on the bf16 tensor cores (7
+ *               balanced 8-bit digit slices of every entry, relative to
+ *               the largest exponent of its row of Y or column of U; the 28
+ *               slice products with p + q <= 8 summed exactly; one rounding
+ *               to double).  Per product term, the truncation of both
+ *               operands and the dropped digit products are below
+ *               2^-50 |y|max |u|max; results below the normal range are
+ *               flushed to zero.
+ *  9 cuda_stream  as for gbr_reorder
+ * Returns 0, -i for an invalid argument i, GBR_ERR_TIMEOUT if a bounded
+ * tensor-core wait gave up (Y is then partially updated), or GBR_ERR_*.
+ * Scratch (a contiguous copy of U and its digit slices) comes from the
+ * library's pool.
+ */
+int gbr_update_panel(int rows, int w, double *Y, long long rs, long long ks, const double *U,
+                     int ldU, int precision, void *cuda_stream);
+
+/*
  * Batched reordering: many independent problems (Eq. 7 for each), planned
  * together into one task graph and run by one persistent-scheduler launch
  * captured in a CUDA graph.  No counterpart in the paper, which reorders one

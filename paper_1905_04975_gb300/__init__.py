@@ -89,6 +89,9 @@ SYMBOLS = {
     "gbr_release": (None, []),
     "gbr_version": (ctypes.c_int, []),
     "gbr_last_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
+    "gbr_update_panel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "gbr_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte), _ip, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _ip, _dp]),
     "gbr_batch_create": (ctypes.c_int, [ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_void_p), _ip,
@@ -254,6 +257,28 @@ def reorder(S, Q, select, *, opts: GbrOpts | None = None, stream=None, allow_par
                          wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
                          ctypes.byref(stats), _stream_handle(stream))
     return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+def update_panel(Y, U, precision="dmma", *, stream=None) -> None:
+    """Y <- Y U in place on the GPU (one off-diagonal update of a window).
+
+    Y: 2-D float64 CUDA tensor (rows x w) with stride 1 along one dimension
+    (row- or column-major); U: w x w column-major float64 CUDA tensor.
+    precision: "dmma" (FP64 tensor cores) or "ozaki" (emulated FP64 on the
+    bf16 tensor cores)."""
+    lib = load()
+    rows, w = int(Y.shape[0]), int(Y.shape[1])
+    if str(Y.dtype) != "torch.float64" or str(U.dtype) != "torch.float64":
+        raise TypeError("Y and U must be float64")
+    if tuple(U.shape) != (w, w):
+        raise ValueError("U must be w x w")
+    ldU = _colmajor_ld(U)
+    prec = {"dmma": PREC_DMMA, "ozaki": PREC_OZAKI}.get(precision, precision)
+    rc = lib.gbr_update_panel(rows, w, ctypes.c_void_p(Y.data_ptr()), int(Y.stride(0)),
+                              int(Y.stride(1)), ctypes.c_void_p(U.data_ptr()), ldU, int(prec),
+                              _stream_handle(stream))
+    if rc != 0:
+        raise GbrError(rc, status_string(rc))
 
 
 def reorder_noalloc(S, Q, select, *, opts: GbrOpts | None = None, stream=None,

@@ -19,10 +19,11 @@ static std::vector<long long> g_trace;  // last traced persistent launch, 8 word
 // ---------------------------------------------------------------------------
 // Device scratch pool: one grow-only allocation per device and purpose.
 // ---------------------------------------------------------------------------
-enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_NSLOTS = 4 };
+enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_PANEL = 4,
+                POOL_NSLOTS = 5 };
 struct DevPool {
-    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr, nullptr};
-    size_t bytes[POOL_NSLOTS] = {0, 0, 0, 0};
+    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t bytes[POOL_NSLOTS] = {0, 0, 0, 0, 0};
 };
 static std::mutex g_mu;  // serializes calls: the pool is shared per device
 static DevPool g_pool[64];
@@ -500,6 +501,47 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
         stats->ms_total =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return rc;
+}
+
+int gbr_update_panel(int rows, int w, double* Y, long long rs, long long ks, const double* U,
+                     int ldU, int precision, void* cuda_stream) {
+    if (rows < 0) return -1;
+    if (w < 1 || w > WMAX) return -2;
+    if (rows > 0 && !Y) return -3;
+    if (rs < 1 || ks < 1 || (rs != 1 && ks != 1)) return -4;
+    if (!U) return -6;
+    if (ldU < w) return -7;
+    if (precision != GBR_PREC_DMMA && precision != GBR_PREC_OZAKI) return -8;
+    if (rows == 0) return 0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(g_mu);
+    // scratch: U contiguous (w x w), then the digit slices, then an error word
+    const size_t b_u = align256((size_t)w * w * sizeof(double));
+    const size_t b_us = align256(OZ_USLICE_BYTES);
+    char* b = nullptr;
+    int rc = pool_get(POOL_PANEL, b_u + b_us + 256, (void**)&b);
+    if (rc) return rc;
+    double* dU = (double*)b;
+    unsigned char* dUS = (unsigned char*)(b + b_u);
+    int* derr = (int*)(b + b_u + b_us);
+    GBR_CK(cudaMemcpy2DAsync(dU, (size_t)w * sizeof(double), U, (size_t)ldU * sizeof(double),
+                             (size_t)w * sizeof(double), (size_t)w, cudaMemcpyDeviceToDevice, st),
+           "D2D U");
+    if (precision == GBR_PREC_DMMA) {
+        GBR_CK(launch_panel_dmma(rows, w, Y, rs, ks, dU, st), "panel kernel");
+        GBR_CK(cudaStreamSynchronize(st), "sync");
+        return 0;
+    }
+    GBR_CK(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset");
+    GBR_CK(launch_panel_ozaki(rows, w, Y, rs, ks, dU, dUS, derr, num_sms(), st), "panel kernel");
+    int h_err = 0;
+    GBR_CK(cudaMemcpyAsync(&h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H err");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (h_err) {
+        set_last_error("gbr_update_panel: a tensor-core tile waited longer than its limit");
+        return GBR_ERR_TIMEOUT;
+    }
+    return 0;
 }
 
 int gbr_last_trace(long long* out, int max_tasks) {

@@ -149,5 +149,14 @@ cudaError_t launch_eigs_batched(int count, const Inst* inst, const long long* of
                                 double* wi, cudaStream_t st);
 size_t sched_smem_bytes();
 int sched_threads();
+// One panel update Y <- Y U (panel.cu): element (r, k) of Y at Y[r rs + k ks]
+// with rs == 1 or ks == 1; Ug is w x w column-major (ld w).  The split-
+// precision launch writes U's digit slices to us (OZ_USLICE_BYTES) first and
+// sets *err if a tile's bounded wait runs out.
+cudaError_t launch_panel_dmma(int rows, int w, double* Y, long long rs, long long ks,
+                              const double* Ug, cudaStream_t st);
+cudaError_t launch_panel_ozaki(int rows, int w, double* Y, long long rs, long long ks,
+                               const double* Ug, unsigned char* us, int* err, int grid,
+                               cudaStream_t st);
 
 }  // namespace gbr

@@ -80,6 +80,23 @@ def test_argument_errors_before_gpu(lib):
     assert rc == 0 and m == 0
 
 
+def test_update_panel_argument_checks(lib):
+    """gbr_update_panel checks its arguments (LAPACK-style -i) before any GPU
+    work; rows = 0 is a no-op."""
+    d = ctypes.c_void_p(0x1000)  # never dereferenced
+    up = lib.gbr_update_panel
+    assert up(-1, 8, d, 1, 8, d, 8, g.PREC_DMMA, None) == -1
+    assert up(4, 0, d, 1, 8, d, 8, g.PREC_DMMA, None) == -2
+    assert up(4, 129, d, 1, 8, d, 129, g.PREC_DMMA, None) == -2
+    assert up(4, 8, None, 1, 8, d, 8, g.PREC_DMMA, None) == -3
+    assert up(4, 8, d, 2, 8, d, 8, g.PREC_DMMA, None) == -4   # neither stride is 1
+    assert up(4, 8, d, 0, 1, d, 8, g.PREC_DMMA, None) == -4
+    assert up(4, 8, d, 1, 8, None, 8, g.PREC_DMMA, None) == -6
+    assert up(4, 8, d, 1, 8, d, 7, g.PREC_DMMA, None) == -7
+    assert up(4, 8, d, 1, 8, d, 8, 5, None) == -8
+    assert up(0, 8, None, 1, 8, d, 8, g.PREC_OZAKI, None) == 0
+
+
 def batch_create(lib, count, n, S, ldS, Q, ldQ, sel, opts=None, want_out=True):
     ip = ctypes.POINTER(ctypes.c_int)
     arr = lambda a: a.ctypes.data_as(ip) if a is not None else None
