@@ -6,8 +6,11 @@ share no code.
 
 The arithmetic lives in `reorder_oracle.c` (plain C, binary64,
 -ffp-contract=off): the scalar-update reordering of Section 3.2 / Fig. 1a,
-producing the reordered Schur form of Eq. 7.  This module only compiles it
-with gcc and marshals numpy arrays through ctypes.
+producing the reordered Schur form of Eq. 7; and in `eigvec_oracle.c`: the
+eigenvectors of a real Schur form (Eq. 5) by back substitution with
+overflow protection.  This module only compiles them with gcc, marshals
+numpy arrays through ctypes, and back-transforms the eigenvectors with one
+matrix product (Eq. 6).
 """
 from __future__ import annotations
 
@@ -19,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "reorder_oracle.c")
+_SRC_EV = os.path.join(_HERE, "eigvec_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -29,10 +33,12 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 
 def build(force: bool = False, src: str = _SRC, out: str = _SO, extra=()) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off)."""
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+    srcs = [src] + ([_SRC_EV] if src == _SRC else [])
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(x)
+                                                 for x in srcs):
         return out
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
-           "-o", out + ".tmp", src, "-lm", *extra]
+           "-o", out + ".tmp", *srcs, "-lm", *extra]
     subprocess.run(cmd, check=True)
     os.replace(out + ".tmp", out)
     return out
@@ -61,6 +67,9 @@ def load(path: str | None = None):
                                 _dp, _dp, _ip, ctypes.c_int, ctypes.c_int, _llp, _llp,
                                 ctypes.POINTER(ctypes.c_ubyte)]
     lib.orc_reorder.restype = ctypes.c_int
+    if hasattr(lib, "orc_eigvec"):
+        lib.orc_eigvec.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _dp, ctypes.c_int, _ip]
+        lib.orc_eigvec.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -150,3 +159,65 @@ def reorder(S, Q, select, *, abort=False, strong=True, lib=None):
                                      selout.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
     return dict(S=S, Q=Q, wr=wr, wi=wi, m=m.value, status=st, nswaps=ns.value,
                 nrej=nr.value, sel=selout[:n].astype(bool))
+
+
+def eig_columns(S, select=None):
+    """Column kinds of the eigenvector matrix for a selection: 0 = real
+    eigenvector, 1 / 2 = real / imaginary part of a complex one (diagonal
+    order); with the eigenvalue of each column."""
+    S = np.asarray(S, dtype=np.float64)
+    n = S.shape[0]
+    kinds, lams = [], []
+    j = 0
+    while j < n:
+        nb = 2 if (j + 1 < n and S[j + 1, j] != 0.0) else 1
+        sel = True if select is None else (select[j] != 0 or (nb == 2 and select[j + 1] != 0))
+        if sel:
+            if nb == 1:
+                kinds.append(0)
+                lams.append(complex(S[j, j]))
+            else:
+                w = np.sqrt(-S[j, j + 1] * S[j + 1, j])
+                kinds += [1, 2]
+                lams += [complex(S[j, j], w)] * 2
+        j += nb
+    return np.array(kinds, dtype=np.int32), np.array(lams)
+
+
+def normalize_columns(X, kinds):
+    """max |x_i| = 1 per real column; max(|re| + |im|) = 1 per complex pair."""
+    X = np.array(X, dtype=np.float64, copy=True)
+    c = 0
+    while c < X.shape[1]:
+        if kinds[c] == 0:
+            m = np.max(np.abs(X[:, c]))
+            if m > 0:
+                X[:, c] /= m
+            c += 1
+        else:
+            m = np.max(np.abs(X[:, c]) + np.abs(X[:, c + 1]))
+            if m > 0:
+                X[:, c:c + 2] /= m
+            c += 2
+    return X
+
+
+def eigenvectors(S, Q=None, select=None, lib=None):
+    """Eigenvectors (Eq. 5) of the real Schur form S for the selected
+    eigenvalues, back-transformed by Q (Eq. 6) if given, then normalized.
+    Returns (X n x m, column kinds, eigenvalue per column, scalings per column)."""
+    S = _f64(S)
+    n = S.shape[0]
+    kinds, lams = eig_columns(S, select)
+    m = len(kinds)
+    Y = np.zeros((n, max(m, 1)), dtype=np.float64, order="F")
+    ns = np.zeros(max(m, 1), dtype=np.int32)
+    sel = None if select is None else np.ascontiguousarray(np.asarray(select, dtype=np.int32))
+    got = (lib or load()).orc_eigvec(n, _ptr(S), max(n, 1),
+                                     sel.ctypes.data_as(_ip) if sel is not None else None,
+                                     _ptr(Y), max(n, 1), ns.ctypes.data_as(_ip))
+    assert got == m
+    Y = Y[:, :m]
+    if Q is not None:
+        Y = normalize_columns(np.asarray(Q, dtype=np.float64) @ Y, kinds)
+    return Y, kinds, lams, ns[:m]
