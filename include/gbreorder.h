@@ -227,6 +227,45 @@ int gbr_update_panel(int rows, int w, double *Y, long long rs, long long ks, con
                      int ldU, int precision, void *cuda_stream);
 
 /*
+ * Eigenvectors of a real Schur form (Section 2, Eq. 5) and their back-
+ * transformation (Eq. 6):
+ *
+ *     (S - lambda I) y = 0,   x = Q y,
+ *
+ * for the selected eigenvalues, protected against floating-point overflow.
+ * Each y comes from back substitution over the diagonal blocks above its
+ * eigenvalue.  Pivots below max(eps |lambda|, DBL_MIN / eps) are raised to
+ * that value.  The vector is scaled by exact powers of two (2^-512) before
+ * any solve or update that could exceed 2^900.  The result is normalized:
+ * max |x_i| = 1 for a real vector, max (|re x_i| + |im x_i|) = 1 for a
+ * complex one.  The back-transformation runs on the FP64 tensor cores (DMMA).
+ *
+ *  1 n        order of S (>= 0)
+ *  2 S        device, standard real Schur form (-2 if not), column-major; read only
+ *  3 ldS      >= max(1, n)
+ *  4 Q        device, n x n orthogonal factor (column-major), or NULL for x = y
+ *  5 ldQ      >= max(1, n) if Q is given
+ *  6 select   host, n ints (a 2x2 block is selected if either row is), or NULL
+ *             for every eigenvalue
+ *  7 X        device, n x m output (m = number of selected positions), or NULL
+ *             to query m only.  Columns in diagonal order: one per real
+ *             eigenvalue; a conjugate pair gives two, the real and the
+ *             imaginary part of the vector of the eigenvalue with positive
+ *             imaginary part
+ *  8 ldX      >= max(1, n)
+ *  9 m_out    host or NULL: m
+ * 10 nscale   host, m ints or NULL: per column, the number of 2^-512 scalings
+ *             the overflow protection applied
+ * 11 cuda_stream
+ * Returns 0, -i for an invalid argument i, or GBR_ERR_*.  Scratch (the
+ * vectors before back-transformation, bounds, right-hand sides) comes from
+ * the library's pool.
+ */
+int gbr_eigenvectors(int n, const double *S, int ldS, const double *Q, int ldQ,
+                     const int *select, double *X, int ldX, int *m_out, int *nscale,
+                     void *cuda_stream);
+
+/*
  * Batched reordering: many independent problems (Eq. 7 for each), planned
  * together into one task graph and run by one persistent-scheduler launch
  * captured in a CUDA graph.  No counterpart in the paper, which reorders one

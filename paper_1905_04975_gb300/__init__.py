@@ -89,6 +89,9 @@ SYMBOLS = {
     "gbr_release": (None, []),
     "gbr_version": (ctypes.c_int, []),
     "gbr_last_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
+    "gbr_eigenvectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_void_p,
+                                        ctypes.c_int, _ip, _ip, ctypes.c_void_p]),
     "gbr_update_panel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -279,6 +282,44 @@ def update_panel(Y, U, precision="dmma", *, stream=None) -> None:
                               _stream_handle(stream))
     if rc != 0:
         raise GbrError(rc, status_string(rc))
+
+
+def eigenvectors(S, Q=None, select=None, *, stream=None, with_scalings=False):
+    """Eigenvectors of the real Schur form S (column-major float64 CUDA
+    tensor) for the selected eigenvalues (None: all), back-transformed by Q
+    if given, normalized; returns an n x m column-major CUDA tensor (a
+    conjugate pair gives its real and imaginary part as two columns), and
+    with with_scalings also the per-column count of 2^-512 scalings."""
+    import torch
+    lib = load()
+    n = int(S.shape[0])
+    ldS = _colmajor_ld(S)
+    qptr, ldQ = None, max(n, 1)
+    if Q is not None:
+        ldQ = _colmajor_ld(Q)
+        qptr = ctypes.c_void_p(Q.data_ptr())
+    sel = None
+    if select is not None:
+        sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+        if sel.size != n:
+            raise ValueError("select must have n entries")
+    selp = sel.ctypes.data_as(_ip) if sel is not None else None
+    m = ctypes.c_int(0)
+    st = _stream_handle(stream)
+    rc = lib.gbr_eigenvectors(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ, selp, None,
+                              max(n, 1), ctypes.byref(m), None, st)
+    if rc != 0:
+        raise GbrError(rc, status_string(rc))
+    X = torch.zeros((max(m.value, 1), max(n, 1)), dtype=torch.float64, device=S.device).t()
+    X = X[:n, : m.value]
+    ns = np.zeros(max(m.value, 1), dtype=np.int32)
+    if m.value > 0:
+        rc = lib.gbr_eigenvectors(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ, selp,
+                                  ctypes.c_void_p(X.data_ptr()), max(n, 1), ctypes.byref(m),
+                                  ns.ctypes.data_as(_ip), st)
+        if rc != 0:
+            raise GbrError(rc, status_string(rc))
+    return (X, ns[: m.value]) if with_scalings else X
 
 
 def reorder_noalloc(S, Q, select, *, opts: GbrOpts | None = None, stream=None,

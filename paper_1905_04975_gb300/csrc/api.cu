@@ -20,10 +20,10 @@ static std::vector<long long> g_trace;  // last traced persistent launch, 8 word
 // Device scratch pool: one grow-only allocation per device and purpose.
 // ---------------------------------------------------------------------------
 enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_PANEL = 4,
-                POOL_NSLOTS = 5 };
+                POOL_EIGVEC = 5, POOL_NSLOTS = 6 };
 struct DevPool {
-    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t bytes[POOL_NSLOTS] = {0, 0, 0, 0, 0};
+    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t bytes[POOL_NSLOTS] = {0, 0, 0, 0, 0, 0};
 };
 static std::mutex g_mu;  // serializes calls: the pool is shared per device
 static DevPool g_pool[64];
@@ -541,6 +541,93 @@ int gbr_update_panel(int rows, int w, double* Y, long long rs, long long ks, con
         set_last_error("gbr_update_panel: a tensor-core tile waited longer than its limit");
         return GBR_ERR_TIMEOUT;
     }
+    return 0;
+}
+
+int gbr_eigenvectors(int n, const double* S, int ldS, const double* Q, int ldQ,
+                     const int* select, double* X, int ldX, int* m_out, int* nscale,
+                     void* cuda_stream) {
+    if (n < 0) return -1;
+    if (n > 0 && !S) return -2;
+    if (ldS < (n > 1 ? n : 1)) return -3;
+    if (Q && ldQ < (n > 1 ? n : 1)) return -5;
+    if (X && ldX < (n > 1 ? n : 1)) return -8;
+    if (m_out) *m_out = 0;
+    if (n == 0) return 0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(g_mu);
+    // structure: validation and the 2x2 pattern
+    char* b = nullptr;
+    const size_t b_ctr = 256, b_sub = align256((size_t)n);
+    int rc = pool_get(POOL_SCRATCH, b_ctr + b_sub, (void**)&b);
+    if (rc) return rc;
+    DevCounters* d_ctr = (DevCounters*)b;
+    uint8_t* d_sub = (uint8_t*)(b + b_ctr);
+    DevCounters h_ctr{0, 0, INT_MAX, 0, 0};
+    GBR_CK(cudaMemcpyAsync(d_ctr, &h_ctr, sizeof h_ctr, cudaMemcpyHostToDevice, st), "H2D counters");
+    GBR_CK(launch_validate(n, S, ldS, d_ctr, st), "validate kernel");
+    GBR_CK(launch_subdiag(n, S, ldS, d_sub, st), "subdiag kernel");
+    std::vector<uint8_t> sub(n);
+    GBR_CK(cudaMemcpyAsync(sub.data(), d_sub, n, cudaMemcpyDeviceToHost, st), "D2H subdiag");
+    GBR_CK(cudaMemcpyAsync(&h_ctr, d_ctr, sizeof h_ctr, cudaMemcpyDeviceToHost, st), "D2H counters");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (h_ctr.bad_column != INT_MAX) return -2;
+    // selected blocks in diagonal order: output columns; 1x1 blocks first in the launch list
+    std::vector<int4> real, cplx;
+    std::vector<int> col_top;  // per output column: rows [0, top) may be nonzero
+    int m = 0;
+    for (int j = 0; j < n;) {
+        const int nb = (j + 1 < n && sub[j]) ? 2 : 1;
+        const bool on = !select || select[j] != 0 || (nb == 2 && select[j + 1] != 0);
+        if (on) {
+            (nb == 1 ? real : cplx).push_back(make_int4(j, nb, m, 0));
+            for (int t = 0; t < nb; ++t) col_top.push_back(j + nb);
+            m += nb;
+        }
+        j += nb;
+    }
+    if (m_out) *m_out = m;
+    if (!X || m == 0) return 0;  // query of m only
+    const int nreal = (int)real.size(), nblk = nreal + (int)cplx.size();
+    std::vector<int4> blocks(real);
+    blocks.insert(blocks.end(), cplx.begin(), cplx.end());
+    const int GN = evgemm_col_block();
+    const int ncb = (m + GN - 1) / GN;
+    std::vector<int> kmax(ncb);
+    for (int cb = 0; cb < ncb; ++cb) kmax[cb] = col_top[std::min(m, (cb + 1) * GN) - 1];
+    // scratch: blocks, kmax, column bounds, scalings, Y (when back-transformed),
+    // and the right-hand sides of one wave of CTAs when they do not fit shared memory
+    const bool rsm = eigvec_rhs_smem(n) != 0;
+    const int wave = rsm ? nblk : std::min(nblk, 8 * num_sms());
+    const size_t b_blk = align256(sizeof(int4) * nblk), b_km = align256(sizeof(int) * ncb);
+    const size_t b_cm = align256(sizeof(double) * 2 * n), b_ns = align256(sizeof(int) * m);
+    const size_t b_y = Q ? align256(sizeof(double) * (size_t)n * m) : 0;
+    const size_t b_r = rsm ? 0 : align256(sizeof(double) * 2 * (size_t)n * wave);
+    char* e = nullptr;
+    rc = pool_get(POOL_EIGVEC, b_blk + b_km + b_cm + b_ns + b_y + b_r, (void**)&e);
+    if (rc) return rc;
+    int4* d_blk = (int4*)e;
+    int* d_km = (int*)(e + b_blk);
+    double* d_cm = (double*)(e + b_blk + b_km);
+    int* d_ns = (int*)(e + b_blk + b_km + b_cm);
+    double* d_y = Q ? (double*)(e + b_blk + b_km + b_cm + b_ns) : X;
+    const int ldY = Q ? n : ldX;
+    double* d_r = rsm ? nullptr : (double*)(e + b_blk + b_km + b_cm + b_ns + b_y);
+    GBR_CK(cudaMemcpyAsync(d_blk, blocks.data(), sizeof(int4) * nblk, cudaMemcpyHostToDevice, st), "H2D blocks");
+    GBR_CK(cudaMemcpyAsync(d_km, kmax.data(), sizeof(int) * ncb, cudaMemcpyHostToDevice, st), "H2D kmax");
+    GBR_CK(launch_colmax(n, S, ldS, d_cm, d_cm + n, st), "column bounds kernel");
+    // back substitution, in waves when the right-hand sides live in global memory
+    for (int b0 = 0; b0 < nblk; b0 += wave) {
+        const int cnt = std::min(wave, nblk - b0);
+        const int nr = std::max(0, std::min(nreal - b0, cnt));
+        GBR_CK(launch_eigvec(n, S, ldS, d_blk + b0, cnt, nr, d_y, ldY, d_cm, d_cm + n, d_r, d_ns, st),
+               "eigenvector kernel");
+    }
+    if (Q) GBR_CK(launch_evgemm(n, m, Q, ldQ, d_y, ldY, X, ldX, d_km, st), "back-transform kernel");
+    GBR_CK(launch_evnorm(n, d_blk, nblk, X, ldX, st), "normalization kernel");
+    if (nscale)
+        GBR_CK(cudaMemcpyAsync(nscale, d_ns, sizeof(int) * m, cudaMemcpyDeviceToHost, st), "D2H scalings");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
     return 0;
 }
 

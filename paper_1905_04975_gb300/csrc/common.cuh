@@ -158,5 +158,18 @@ cudaError_t launch_panel_dmma(int rows, int w, double* Y, long long rs, long lon
 cudaError_t launch_panel_ozaki(int rows, int w, double* Y, long long rs, long long ks,
                                const double* Ug, unsigned char* us, int* err, int grid,
                                cudaStream_t st);
+// Eigenvectors (eigvec.cu).  blocks: (j, nb, output column, -) per selected
+// diagonal block, the nreal 1x1 blocks first; rscratch: 2 n doubles per CTA
+// of the launch when eigvec_rhs_smem(n) == 0, else unused.
+size_t eigvec_rhs_smem(int n);
+cudaError_t launch_colmax(int n, const double* S, int ldS, double* cmA, double* cmB,
+                          cudaStream_t st);
+cudaError_t launch_eigvec(int n, const double* S, int ldS, const int4* d_blocks, int nblk,
+                          int nreal, double* Y, int ldY, double* cmA, double* cmB,
+                          double* rscratch, int* nscale, cudaStream_t st);
+cudaError_t launch_evgemm(int rows, int cols, const double* A, int ldA, const double* B, int ldB,
+                          double* C, int ldC, const int* d_kmax, cudaStream_t st);
+int evgemm_col_block();
+cudaError_t launch_evnorm(int n, const int4* d_blocks, int nblk, double* X, int ldX, cudaStream_t st);
 
 }  // namespace gbr

@@ -97,6 +97,21 @@ def test_update_panel_argument_checks(lib):
     assert up(0, 8, None, 1, 8, d, 8, g.PREC_OZAKI, None) == 0
 
 
+def test_eigenvectors_argument_checks(lib):
+    """gbr_eigenvectors checks its arguments before any GPU work; n = 0 is a
+    no-op with m = 0."""
+    d = ctypes.c_void_p(0x1000)  # never dereferenced
+    ev = lib.gbr_eigenvectors
+    m = ctypes.c_int(7)
+    assert ev(-1, d, 4, None, 4, None, d, 4, ctypes.byref(m), None, None) == -1
+    assert ev(4, None, 4, None, 4, None, d, 4, ctypes.byref(m), None, None) == -2
+    assert ev(4, d, 3, None, 4, None, d, 4, ctypes.byref(m), None, None) == -3
+    assert ev(4, d, 4, d, 3, None, d, 4, ctypes.byref(m), None, None) == -5
+    assert ev(4, d, 4, None, 4, None, d, 3, ctypes.byref(m), None, None) == -8
+    assert ev(0, None, 1, None, 1, None, None, 1, ctypes.byref(m), None, None) == 0
+    assert m.value == 0
+
+
 def batch_create(lib, count, n, S, ldS, Q, ldQ, sel, opts=None, want_out=True):
     ip = ctypes.POINTER(ctypes.c_int)
     arr = lambda a: a.ctypes.data_as(ip) if a is not None else None
