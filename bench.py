@@ -51,6 +51,8 @@ WORKLOADS = {
                     window=128, chain=64),
     "batch4096": dict(name="batch4096", kind="batch", count=4096, nmin=32, nmax=512,
                       select="U(0.2, 0.6) per instance", q="min(n, 64) Householder reflectors"),
+    "eigvec4000": dict(name="eigvec4000", kind="eigvec", n=4000, select=0.35,
+                       q="64 Householder reflectors", window=128, chain=64),
     "serve": dict(name="serve", kind="serve", nmin=64, nmax=8192, select="U(0.1, 0.6)",
                   q="8 Householder reflectors", mem_cap=60e9),
 }
@@ -142,7 +144,7 @@ class ClockSampler:
 
 
 def make_inputs(wl, seed=0):
-    return si.config(wl["name"], seed)
+    return si.config("n4000" if wl["name"] == "eigvec4000" else wl["name"], seed)
 
 
 def cpu_oracle_sample(S, Q, sel, budget_s=15.0):
@@ -212,6 +214,29 @@ def run_reference(args, wl):
         sample = lambda: batch_cpu_sample(probs, budget_s=6.0)
         cfg = {"workload": "serve", "n": "requests of order <= 1024 of the stream",
                "select": wl["select"], "q": wl["q"]}
+    elif wl.get("kind") == "eigvec":
+        S, Q, _ = make_inputs(wl)
+        n = S.shape[0]
+        times, samples = [], []
+        for i in range(args.warmup + args.steps):
+            cb = eigvec_cpu_sample(S, Q)
+            if i >= args.warmup:
+                times.append(n / cb["value"])
+                samples.append(cb["sample"])
+        value = n * len(times) / sum(times)
+        line = {"impl": "reference", "metric": "eigenvectors computed per second", "value": value,
+                "unit": "eigenvectors/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "n": n, "eigenvectors": f"all ({n})",
+                           "q": wl["q"]},
+                "cpu_baseline": {"value": value, "unit": "eigenvectors/s", "cores": cb["cores"],
+                                 "kind": "oracle", "sample": samples[-1]},
+                "e2e": {"value": value, "unit": "eigenvectors/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     elif wl.get("kind") == "batch":
         probs = batch_inputs(wl)
         nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
@@ -560,6 +585,148 @@ def run_serve(args, wl):
     return 0
 
 
+def eigvec_cpu_sample(S, Q, step=16):
+    """The eigenvector oracle on every step-th eigenvalue of the form: the
+    back substitution (plain C, one core) and the back-transformation (one
+    numpy matrix product, BLAS threads) timed separately and scaled to all
+    eigenvectors by their work (sum of (j + nb)^2 for the back substitution,
+    columns for the back-transformation)."""
+    import oracle
+    n = S.shape[0]
+    pos, j = [], 0
+    while j < n:
+        nb = 2 if (j + 1 < n and S[j + 1, j] != 0) else 1
+        pos.append((j, nb))
+        j += nb
+    chosen = pos[::step]
+    sel = np.zeros(n, dtype=np.int32)
+    for j, nb in chosen:
+        sel[j] = 1
+    t0 = time.perf_counter()
+    Y, kinds, _, _ = oracle.eigenvectors(S, None, sel)
+    t1 = time.perf_counter()
+    X = oracle.normalize_columns(Q @ Y, kinds)
+    t2 = time.perf_counter()
+    work = sum((j + nb) ** 2 * nb for j, nb in chosen)
+    full = sum((j + nb) ** 2 * nb for j, nb in pos)
+    est = (t1 - t0) * full / work + (t2 - t1) * n / X.shape[1]
+    cores = len(os.sched_getaffinity(0))
+    return {"value": n / est, "unit": "eigenvectors/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{X.shape[1]} of {n} eigenvectors (every {step}th eigenvalue): back "
+                       f"substitution {t1 - t0:.2f} s on 1 core, back-transformation "
+                       f"{t2 - t1:.2f} s (numpy/BLAS, up to {cores} threads); scaled by work "
+                       f"to all eigenvectors (est. {est:.1f} s)")}
+
+
+def run_eigvec(args, wl):
+    """Eigenvectors (Eq. 5) of every eigenvalue of the n = 4000 Schur form,
+    back-transformed by its Q (Eq. 6): eigenvectors per second."""
+    import torch
+    import paper_1905_04975_gb300 as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+    S_np, Q_np, _ = make_inputs(wl)
+    n = S_np.shape[0]
+    S, Q = g.to_device(S_np), g.to_device(Q_np)
+    X = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")  # > L2
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st = g.GbrEvStats()
+        e0.record(stream)
+        g.eigenvectors(S, Q, None, stream=stream, stats=st, out=X)
+        e1.record(stream)
+        e1.synchronize()
+        return st, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, sts = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            st, t = step()
+            ms.append(t)
+            sts.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    value, total_ms = whole_job_rate(n * args.steps, sum(ms), dist, "cuda")
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)
+    ms_s = sum(s.ms_solve for s in sts) / len(sts)
+    ms_b = sum(s.ms_backtransform for s in sts) / len(sts)
+    f_s, f_b = sts[0].solve_flops, sts[0].backtransform_flops
+    if ms_b >= ms_s:
+        roof = {"kernel": "evgemm_kernel (X = Q Y, DMMA)", "bound": "tensor",
+                "achieved": f_b / (ms_b / 1e3) / 1e12, "unit": "TFLOP/s",
+                "flops_per_launch": f_b, "avg_launch_ms": ms_b}
+    else:
+        roof = {"kernel": "eigvec_kernel (back substitution, FP64 FMA)", "bound": "alu",
+                "achieved": f_s / (ms_s / 1e3) / 1e12, "unit": "TFLOP/s",
+                "flops_per_launch": f_s, "avg_launch_ms": ms_s}
+    roof.update({"peak": fp64_peak, "frac": roof["achieved"] / fp64_peak, "traffic": None,
+                 "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
+                                 "1.25/2250"),
+                 "share_of_step": roof["avg_launch_ms"] / (total_ms / args.steps),
+                 "other": {"solve_ms": ms_s, "solve_tflops": f_s / (ms_s / 1e3) / 1e12,
+                           "backtransform_ms": ms_b,
+                           "backtransform_tflops": f_b / max(ms_b, 1e-9) / 1e9}})
+    # end to end: S, Q from pinned host memory, X back, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        hS = torch.from_numpy(np.asfortranarray(S_np).T.copy()).pin_memory()
+        hQ = torch.from_numpy(np.asfortranarray(Q_np).T.copy()).pin_memory()
+        hX = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        et = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                S.t().copy_(hS, non_blocking=True)
+                Q.t().copy_(hQ, non_blocking=True)
+            g.eigenvectors(S, Q, None, stream=stream, out=X)
+            with torch.cuda.stream(stream):
+                hX.copy_(X.t(), non_blocking=True)
+            stream.synchronize()
+            if i > 0:
+                et.append(time.perf_counter() - t0)
+        e2e = {"value": n * len(et) / sum(et) * world, "unit": "eigenvectors/s",
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = eigvec_cpu_sample(S_np, Q_np)
+    if rank == 0:
+        line = {"metric": "eigenvectors computed per second", "value": value,
+                "unit": "eigenvectors/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "n": n, "eigenvectors": f"all ({n})",
+                           "q": wl["q"], "l2": "256 MB buffer written before each step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": 4 * args.steps}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,6 +751,8 @@ def main():
         return run_batch(args, wl)
     if wl.get("kind") == "serve":
         return run_serve(args, wl)
+    if wl.get("kind") == "eigvec":
+        return run_eigvec(args, wl)
 
     import torch
     import paper_1905_04975_gb300 as g

@@ -256,14 +256,25 @@ int gbr_update_panel(int rows, int w, double *Y, long long rs, long long ks, con
  *  9 m_out    host or NULL: m
  * 10 nscale   host, m ints or NULL: per column, the number of 2^-512 scalings
  *             the overflow protection applied
- * 11 cuda_stream
+ * 11 stats    host or NULL: kernel times (CUDA events on the stream) and the
+ *             algorithmic flops of the back substitution (the right-hand-side
+ *             updates, 2 per real multiply-add, doubled for complex vectors)
+ *             and of the back-transformation
+ * 12 cuda_stream
  * Returns 0, -i for an invalid argument i, or GBR_ERR_*.  Scratch (the
  * vectors before back-transformation, bounds, right-hand sides) comes from
  * the library's pool.
  */
+typedef struct gbr_ev_stats {
+    double ms_solve;            /* column bounds + back substitution */
+    double ms_backtransform;    /* X = Q Y (0 without Q) */
+    double ms_normalize;
+    double solve_flops;
+    double backtransform_flops;
+} gbr_ev_stats;
 int gbr_eigenvectors(int n, const double *S, int ldS, const double *Q, int ldQ,
                      const int *select, double *X, int ldX, int *m_out, int *nscale,
-                     void *cuda_stream);
+                     gbr_ev_stats *stats, void *cuda_stream);
 
 /*
  * Batched reordering: many independent problems (Eq. 7 for each), planned

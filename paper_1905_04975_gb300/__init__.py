@@ -91,7 +91,8 @@ SYMBOLS = {
     "gbr_last_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "gbr_eigenvectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_void_p,
-                                        ctypes.c_int, _ip, _ip, ctypes.c_void_p]),
+                                        ctypes.c_int, _ip, _ip, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "gbr_update_panel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -284,12 +285,20 @@ def update_panel(Y, U, precision="dmma", *, stream=None) -> None:
         raise GbrError(rc, status_string(rc))
 
 
-def eigenvectors(S, Q=None, select=None, *, stream=None, with_scalings=False):
+class GbrEvStats(ctypes.Structure):
+    _fields_ = [("ms_solve", ctypes.c_double), ("ms_backtransform", ctypes.c_double),
+                ("ms_normalize", ctypes.c_double), ("solve_flops", ctypes.c_double),
+                ("backtransform_flops", ctypes.c_double)]
+
+
+def eigenvectors(S, Q=None, select=None, *, stream=None, with_scalings=False, stats=None,
+                 out=None):
     """Eigenvectors of the real Schur form S (column-major float64 CUDA
     tensor) for the selected eigenvalues (None: all), back-transformed by Q
     if given, normalized; returns an n x m column-major CUDA tensor (a
     conjugate pair gives its real and imaginary part as two columns), and
-    with with_scalings also the per-column count of 2^-512 scalings."""
+    with with_scalings also the per-column count of 2^-512 scalings.  stats:
+    a GbrEvStats to fill with kernel times and algorithmic flops."""
     import torch
     lib = load()
     n = int(S.shape[0])
@@ -306,17 +315,22 @@ def eigenvectors(S, Q=None, select=None, *, stream=None, with_scalings=False):
     selp = sel.ctypes.data_as(_ip) if sel is not None else None
     m = ctypes.c_int(0)
     st = _stream_handle(stream)
-    rc = lib.gbr_eigenvectors(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ, selp, None,
-                              max(n, 1), ctypes.byref(m), None, st)
-    if rc != 0:
-        raise GbrError(rc, status_string(rc))
-    X = torch.zeros((max(m.value, 1), max(n, 1)), dtype=torch.float64, device=S.device).t()
-    X = X[:n, : m.value]
+    if out is None:
+        rc = lib.gbr_eigenvectors(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ, selp, None,
+                                  max(n, 1), ctypes.byref(m), None, None, st)
+        if rc != 0:
+            raise GbrError(rc, status_string(rc))
+        X = torch.zeros((max(m.value, 1), max(n, 1)), dtype=torch.float64, device=S.device).t()
+        X = X[:n, : m.value]
+    else:
+        X = out
+        m.value = int(out.shape[1])
     ns = np.zeros(max(m.value, 1), dtype=np.int32)
     if m.value > 0:
         rc = lib.gbr_eigenvectors(n, ctypes.c_void_p(S.data_ptr()), ldS, qptr, ldQ, selp,
-                                  ctypes.c_void_p(X.data_ptr()), max(n, 1), ctypes.byref(m),
-                                  ns.ctypes.data_as(_ip), st)
+                                  ctypes.c_void_p(X.data_ptr()), _colmajor_ld(X), ctypes.byref(m),
+                                  ns.ctypes.data_as(_ip),
+                                  ctypes.byref(stats) if stats is not None else None, st)
         if rc != 0:
             raise GbrError(rc, status_string(rc))
     return (X, ns[: m.value]) if with_scalings else X

@@ -546,7 +546,8 @@ int gbr_update_panel(int rows, int w, double* Y, long long rs, long long ks, con
 
 int gbr_eigenvectors(int n, const double* S, int ldS, const double* Q, int ldQ,
                      const int* select, double* X, int ldX, int* m_out, int* nscale,
-                     void* cuda_stream) {
+                     gbr_ev_stats* stats, void* cuda_stream) {
+    if (stats) memset(stats, 0, sizeof *stats);
     if (n < 0) return -1;
     if (n > 0 && !S) return -2;
     if (ldS < (n > 1 ? n : 1)) return -3;
@@ -615,6 +616,32 @@ int gbr_eigenvectors(int n, const double* S, int ldS, const double* Q, int ldQ,
     double* d_r = rsm ? nullptr : (double*)(e + b_blk + b_km + b_cm + b_ns + b_y);
     GBR_CK(cudaMemcpyAsync(d_blk, blocks.data(), sizeof(int4) * nblk, cudaMemcpyHostToDevice, st), "H2D blocks");
     GBR_CK(cudaMemcpyAsync(d_km, kmax.data(), sizeof(int) * ncb, cudaMemcpyHostToDevice, st), "H2D kmax");
+    if (stats) {
+        // algorithmic flops: the right-hand-side updates of the back
+        // substitution (2 per real multiply-add, twice for a complex vector)
+        // and the products of the back-transformation
+        std::vector<double> cum(n + 1, 0.0);  // cum[p]: sum of b0 k over blocks ending at or before p
+        for (int p = 0; p < n;) {
+            const int nb = (p + 1 < n && sub[p]) ? 2 : 1;
+            cum[p + nb] = cum[p] + (double)p * nb;
+            if (nb == 2) cum[p + 1] = cum[p];
+            p += nb;
+        }
+        double fs = 0.0;
+        for (const int4& bk : blocks) fs += 2.0 * (bk.y == 2 ? 2.0 : 1.0) * cum[bk.x];
+        stats->solve_flops = fs;
+        double fg = 0.0;
+        if (Q)
+            for (int cb = 0; cb < ncb; ++cb)
+                fg += 2.0 * n * kmax[cb] * (double)(std::min(m, (cb + 1) * GN) - cb * GN);
+        stats->backtransform_flops = fg;
+    }
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (stats)
+        for (int i = 0; i < 4; ++i) {
+            GBR_CK(cudaEventCreate(&ev[i]), "event");
+        }
+    if (stats) GBR_CK(cudaEventRecord(ev[0], st), "event");
     GBR_CK(launch_colmax(n, S, ldS, d_cm, d_cm + n, st), "column bounds kernel");
     // back substitution, in waves when the right-hand sides live in global memory
     for (int b0 = 0; b0 < nblk; b0 += wave) {
@@ -623,11 +650,24 @@ int gbr_eigenvectors(int n, const double* S, int ldS, const double* Q, int ldQ,
         GBR_CK(launch_eigvec(n, S, ldS, d_blk + b0, cnt, nr, d_y, ldY, d_cm, d_cm + n, d_r, d_ns, st),
                "eigenvector kernel");
     }
+    if (stats) GBR_CK(cudaEventRecord(ev[1], st), "event");
     if (Q) GBR_CK(launch_evgemm(n, m, Q, ldQ, d_y, ldY, X, ldX, d_km, st), "back-transform kernel");
+    if (stats) GBR_CK(cudaEventRecord(ev[2], st), "event");
     GBR_CK(launch_evnorm(n, d_blk, nblk, X, ldX, st), "normalization kernel");
+    if (stats) GBR_CK(cudaEventRecord(ev[3], st), "event");
     if (nscale)
         GBR_CK(cudaMemcpyAsync(nscale, d_ns, sizeof(int) * m, cudaMemcpyDeviceToHost, st), "D2H scalings");
     GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (stats) {
+        float a = 0.f, b2 = 0.f, c = 0.f;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b2, ev[1], ev[2]);
+        cudaEventElapsedTime(&c, ev[2], ev[3]);
+        stats->ms_solve = a;
+        stats->ms_backtransform = b2;
+        stats->ms_normalize = c;
+        for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    }
     return 0;
 }
 

@@ -103,12 +103,12 @@ def test_eigenvectors_argument_checks(lib):
     d = ctypes.c_void_p(0x1000)  # never dereferenced
     ev = lib.gbr_eigenvectors
     m = ctypes.c_int(7)
-    assert ev(-1, d, 4, None, 4, None, d, 4, ctypes.byref(m), None, None) == -1
-    assert ev(4, None, 4, None, 4, None, d, 4, ctypes.byref(m), None, None) == -2
-    assert ev(4, d, 3, None, 4, None, d, 4, ctypes.byref(m), None, None) == -3
-    assert ev(4, d, 4, d, 3, None, d, 4, ctypes.byref(m), None, None) == -5
-    assert ev(4, d, 4, None, 4, None, d, 3, ctypes.byref(m), None, None) == -8
-    assert ev(0, None, 1, None, 1, None, None, 1, ctypes.byref(m), None, None) == 0
+    assert ev(-1, d, 4, None, 4, None, d, 4, ctypes.byref(m), None, None, None) == -1
+    assert ev(4, None, 4, None, 4, None, d, 4, ctypes.byref(m), None, None, None) == -2
+    assert ev(4, d, 3, None, 4, None, d, 4, ctypes.byref(m), None, None, None) == -3
+    assert ev(4, d, 4, d, 3, None, d, 4, ctypes.byref(m), None, None, None) == -5
+    assert ev(4, d, 4, None, 4, None, d, 3, ctypes.byref(m), None, None, None) == -8
+    assert ev(0, None, 1, None, 1, None, None, 1, ctypes.byref(m), None, None, None) == 0
     assert m.value == 0
 
 
