@@ -603,7 +603,7 @@ int gbr_eigenvectors(int n, const double* S, int ldS, const double* Q, int ldQ,
     const size_t b_blk = align256(sizeof(int4) * nblk), b_km = align256(sizeof(int) * ncb);
     const size_t b_cm = align256(sizeof(double) * 2 * n), b_ns = align256(sizeof(int) * m);
     const size_t b_y = Q ? align256(sizeof(double) * (size_t)n * m) : 0;
-    const size_t b_r = rsm ? 0 : align256(sizeof(double) * 2 * (size_t)n * wave);
+    const size_t b_r = rsm ? 0 : align256(sizeof(double) * 3 * (size_t)n * wave);
     char* e = nullptr;
     rc = pool_get(POOL_EIGVEC, b_blk + b_km + b_cm + b_ns + b_y + b_r, (void**)&e);
     if (rc) return rc;

@@ -159,7 +159,7 @@ cudaError_t launch_panel_ozaki(int rows, int w, double* Y, long long rs, long lo
                                const double* Ug, unsigned char* us, int* err, int grid,
                                cudaStream_t st);
 // Eigenvectors (eigvec.cu).  blocks: (j, nb, output column, -) per selected
-// diagonal block, the nreal 1x1 blocks first; rscratch: 2 n doubles per CTA
+// diagonal block, the nreal 1x1 blocks first; rscratch: 3 n doubles per CTA
 // of the launch when eigvec_rhs_smem(n) == 0, else unused.
 size_t eigvec_rhs_smem(int n);
 cudaError_t launch_colmax(int n, const double* S, int ldS, double* cmA, double* cmB,

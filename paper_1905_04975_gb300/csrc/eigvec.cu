@@ -94,11 +94,101 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     return m;
 }
 
+// Inverse of the shifted diagonal block B = [b0, b0 + k), S[B,B] - lambda I,
+// with a pivot (the 1x1 denominator or the 2x2 determinant) below smin
+// raised to smin: inv[0..3] = row-major 2x2 (inv[0] alone for k = 1).
+struct BlkInv {
+    int b0, k;
+    cd inv[4];
+};
+
+__device__ __forceinline__ BlkInv block_inverse(const double* __restrict__ S, int ldS, int b0,
+                                                int k, double lr, double li, double smin) {
+    BlkInv B;
+    B.b0 = b0;
+    B.k = k;
+    const cd one{1.0, 0.0};
+    if (k == 1) {
+        const cd d = perturb(cd{__ldg(&S[cm(b0, b0, ldS)]) - lr, -li}, smin);
+        B.inv[0] = cdiv(one, d);
+        B.inv[1] = B.inv[2] = B.inv[3] = cd{0.0, 0.0};
+        return B;
+    }
+    const cd m00 = cd{__ldg(&S[cm(b0, b0, ldS)]) - lr, -li};
+    const cd m01 = cd{__ldg(&S[cm(b0, b0 + 1, ldS)]), 0.0};
+    const cd m10 = cd{__ldg(&S[cm(b0 + 1, b0, ldS)]), 0.0};
+    const cd m11 = cd{__ldg(&S[cm(b0 + 1, b0 + 1, ldS)]) - lr, -li};
+    cd det = csub(cmul(m00, m11), cmul(m01, m10));
+    const double mx = fmax(fmax(cabs1(m00), cabs1(m01)), fmax(cabs1(m10), cabs1(m11)));
+    det = perturb(det, smin * fmax(mx, smin));
+    const cd rd = cdiv(one, det);
+    B.inv[0] = cmul(m11, rd);
+    B.inv[1] = cmul(cd{-m01.re, -m01.im}, rd);
+    B.inv[2] = cmul(cd{-m10.re, -m10.im}, rd);
+    B.inv[3] = cmul(m00, rd);
+    return B;
+}
+
+// x = inv r for one block; real arithmetic for real vectors.
+template <bool CPLX>
+__device__ __forceinline__ void apply_inv(const BlkInv& B, cd r0, cd r1, double f, cd& x0, cd& x1) {
+    r0 = cd{r0.re * f, r0.im * f};
+    r1 = cd{r1.re * f, r1.im * f};
+    if (!CPLX) {
+        x0 = cd{fma(B.inv[1].re, r1.re, B.inv[0].re * r0.re), 0.0};
+        x1 = cd{fma(B.inv[3].re, r1.re, B.inv[2].re * r0.re), 0.0};
+    } else {
+        const cd a = cmul(B.inv[0], r0), b = cmul(B.inv[1], r1);
+        const cd c = cmul(B.inv[2], r0), d = cmul(B.inv[3], r1);
+        x0 = cd{a.re + b.re, a.im + b.im};
+        x1 = cd{c.re + d.re, c.im + d.im};
+    }
+}
+
+// The overflow guards of one block (one thread): scales by 2^-512 while the
+// solution could exceed EV_BIG, then while the bound of the update of r by x
+// could; returns the number of scalings, with x scaled and rb updated.
+template <bool CPLX>
+__device__ __forceinline__ int solve_guarded(const BlkInv& B, cd r0, cd r1, double cmx,
+                                             double& rb, cd& x0, cd& x1) {
+    int s = 0;
+    double f = 1.0;
+    apply_inv<CPLX>(B, r0, r1, 1.0, x0, x1);
+    while (s < 8 && !(fmax(cabs1(x0), cabs1(x1)) <= EV_BIG)) {
+        f *= EV_SHRINK;
+        ++s;
+        apply_inv<CPLX>(B, r0, r1, f, x0, x1);
+    }
+    rb *= f;
+    if (B.b0 > 0) {
+        double xm = fmax(cabs1(x0), cabs1(x1));
+        int s2 = 0;
+        while (s2 < 8 && rb + B.k * cmx * xm > EV_BIG) {
+            x0 = cd{x0.re * EV_SHRINK, x0.im * EV_SHRINK};
+            x1 = cd{x1.re * EV_SHRINK, x1.im * EV_SHRINK};
+            rb *= EV_SHRINK;
+            xm *= EV_SHRINK;
+            ++s2;
+        }
+        rb += B.k * cmx * xm;
+        s += s2;
+    }
+    return s;
+}
+
 // One eigenvector per CTA.  blocks[b] = (j, nb, column of Y, -); Y column-
 // major (ldY), written for every row (zero below the vector's support).
-// rscratch: per-CTA right-hand side in global memory (2 n doubles per CTA),
-// used when rsm == 0; otherwise the right-hand side is in dynamic shared
+// rscratch: per-CTA right-hand side and 2x2 flags in global memory (3 n
+// doubles per CTA), used when rsm == 0; otherwise both are in dynamic shared
 // memory.  nscale[col]: the number of 2^-512 scalings.
+//
+// Pipelined by one block: while warps 1..7 apply the update of block B_t to
+// the rows below the next block, warp 0 applies it to the next block's rows
+// and lane 0 solves the next block (its pending scaling is applied at the
+// start of the following step, before anything else reads the rows).  The
+// inverses of the shifted diagonal blocks are computed 32 blocks at a time
+// by the lanes of warp 0 (one block per lane) into a ring, so that the
+// serial step of lane 0 is a few multiplications and the guards.
 template <bool CPLX>
 __global__ void __launch_bounds__(EV_THREADS)
 eigvec_kernel(int n, const double* __restrict__ S, int ldS, const int4* __restrict__ blocks,
@@ -107,16 +197,21 @@ eigvec_kernel(int n, const double* __restrict__ S, int ldS, const int4* __restri
               int* __restrict__ nscale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[EV_THREADS / 32];
-    __shared__ cd xs[2];
-    __shared__ int sc_step;
+    __shared__ cd xs[2][2];
+    __shared__ int pend[2];
+    __shared__ BlkInv ring[32];
+    __shared__ int ring_b0[33];  // block starts of the ring's blocks (entry 32: one past)
+    __shared__ int ring_first, ring_count;
     const int4 bk = blocks[blockIdx.x];
     const int j = bk.x, nb = bk.y, col = bk.z, top = j + nb;
     if ((nb == 2) != CPLX) return;  // launched per kind
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double* yr = Y + (size_t)col * ldY;
     double* yi = CPLX ? Y + (size_t)(col + 1) * ldY : nullptr;
-    double* rr = rsm ? reinterpret_cast<double*>(smem_raw) : rscratch + (size_t)blockIdx.x * 2 * n;
+    double* rr = rsm ? reinterpret_cast<double*>(smem_raw) : rscratch + (size_t)blockIdx.x * 3 * n;
     double* ri = rr + n;  // imaginary parts (complex vectors)
+    uint8_t* sub = rsm ? smem_raw + sizeof(double) * 2 * (size_t)n
+                       : reinterpret_cast<uint8_t*>(ri + n);  // 2x2 flag of rows i, i+1
     // eigenvalue and start vector
     double lr, li = 0.0, y1i = 0.0;
     if (!CPLX) {
@@ -130,7 +225,7 @@ eigvec_kernel(int n, const double* __restrict__ S, int ldS, const int4* __restri
         y1i = w / b;
     }
     const double smin = fmax(DBL_EPSILON * (fabs(lr) + fabs(li)), DBL_MIN / DBL_EPSILON);
-    // y rows >= j; r = -S[0:j, j:top] y[j:top]
+    // y rows >= j; r = -S[0:j, j:top] y[j:top]; the 2x2 pattern above j
     for (int i = j + tid; i < n; i += EV_THREADS) {
         yr[i] = (i == j) ? 1.0 : 0.0;
         if (CPLX) yi[i] = (i == j + 1) ? y1i : 0.0;
@@ -138,6 +233,7 @@ eigvec_kernel(int n, const double* __restrict__ S, int ldS, const int4* __restri
     double m = 0.0;
     for (int i = tid; i < j; i += EV_THREADS) {
         const double s0 = __ldg(&S[cm(i, j, ldS)]);
+        sub[i] = (i + 1 < j && __ldg(&S[cm(i + 1, i, ldS)]) != 0.0) ? 1 : 0;
         if (!CPLX) {
             rr[i] = -s0;
             m = fmax(m, fabs(s0));
@@ -148,64 +244,50 @@ eigvec_kernel(int n, const double* __restrict__ S, int ldS, const int4* __restri
             m = fmax(m, fabs(s0) + fabs(s1 * y1i));
         }
     }
-    double rb = block_max(m, red);  // thread 0's bound; the others keep a copy
-    int nsc = 0;
-    __syncthreads();
-    int b1 = j;
-    while (b1 > 0) {
-        const int b0 = (b1 >= 2 && __ldg(&S[cm(b1 - 1, b1 - 2, ldS)]) != 0.0) ? b1 - 2 : b1 - 1;
-        const int k = b1 - b0;
-        if (tid == 0) {
-            int s = 0;
-            double f = 1.0;  // 2^-512 s
-            cd x0, x1 = cd{0.0, 0.0};
-            const cd r0 = cd{rr[b0], CPLX ? ri[b0] : 0.0};
-            if (k == 1) {
-                const cd d = perturb(cd{__ldg(&S[cm(b0, b0, ldS)]) - lr, -li}, smin);
-                while (s < 8 && cabs1(r0) * f > EV_BIG * cabs1(d)) { f *= EV_SHRINK; ++s; }
-                x0 = cdiv(cd{r0.re * f, r0.im * f}, d);
-            } else {
-                const cd r1 = cd{rr[b0 + 1], CPLX ? ri[b0 + 1] : 0.0};
-                const cd m00 = cd{__ldg(&S[cm(b0, b0, ldS)]) - lr, -li};
-                const cd m01 = cd{__ldg(&S[cm(b0, b0 + 1, ldS)]), 0.0};
-                const cd m10 = cd{__ldg(&S[cm(b0 + 1, b0, ldS)]), 0.0};
-                const cd m11 = cd{__ldg(&S[cm(b0 + 1, b0 + 1, ldS)]) - lr, -li};
-                cd det = csub(cmul(m00, m11), cmul(m01, m10));
-                const double mx = fmax(fmax(cabs1(m00), cabs1(m01)), fmax(cabs1(m10), cabs1(m11)));
-                det = perturb(det, smin * fmax(mx, smin));
-                for (;;) {
-                    const cd ra = cd{r0.re * f, r0.im * f}, rbv = cd{r1.re * f, r1.im * f};
-                    const cd u0 = csub(cmul(m11, ra), cmul(m01, rbv));
-                    const cd u1 = csub(cmul(m00, rbv), cmul(m10, ra));
-                    if (fmax(cabs1(u0), cabs1(u1)) <= EV_BIG * cabs1(det) || s == 8) {
-                        x0 = cdiv(u0, det);
-                        x1 = cdiv(u1, det);
-                        break;
-                    }
-                    f *= EV_SHRINK;
-                    ++s;
-                }
+    double rb = block_max(m, red);  // maintained by thread 0 only
+    if (j == 0) {
+        if (tid == 0 && nscale) {
+            nscale[col] = 0;
+            if (CPLX) nscale[col + 1] = 0;
+        }
+        return;
+    }
+    auto block_below = [&](int e) { return (e >= 2 && sub[e - 2]) ? e - 2 : e - 1; };
+    auto colbound = [&](int b0, int k) { return (k == 1) ? cmA[b0] : fmax(cmA[b0], cmB[b0 + 1]); };
+    // warp 0: the inverses of the next (up to) 32 blocks below e
+    auto refill = [&](int e, int first) {
+        if (lane == 0) {
+            int cnt = 0, t = e;
+            while (cnt < 32 && t > 0) {
+                const int b = block_below(t);
+                ring_b0[cnt++] = b;
+                t = b;
             }
-            rb *= f;
-            // the update of r by this block must keep the bound below BIG
-            if (b0 > 0) {
-                const double cmx = (k == 1) ? cmA[b0] : fmax(cmA[b0], cmB[b0 + 1]);
-                double xm = fmax(cabs1(x0), cabs1(x1));
-                int s2 = 0;
-                while (s2 < 8 && rb + k * cmx * xm > EV_BIG) {
-                    x0 = cd{x0.re * EV_SHRINK, x0.im * EV_SHRINK};
-                    x1 = cd{x1.re * EV_SHRINK, x1.im * EV_SHRINK};
-                    rb *= EV_SHRINK;
-                    xm *= EV_SHRINK;
-                    ++s2;
-                }
-                rb += k * cmx * xm;
-                s += s2;
-            }
-            xs[0] = x0;
-            xs[1] = x1;
-            sc_step = s;
-            nsc += s;
+            ring_b0[cnt] = t;
+            ring_count = cnt;
+            ring_first = first;
+        }
+        __syncwarp();
+        if (lane < ring_count) {
+            const int b = ring_b0[lane], e2 = lane ? ring_b0[lane - 1] : e;
+            ring[lane] = block_inverse(S, ldS, b, e2 - b, lr, li, smin);
+        }
+        __syncwarp();
+    };
+    int b1 = j, b0 = block_below(j);
+    if (warp == 0) {
+        refill(j, 0);
+        if (lane == 0) {
+            const BlkInv& Bi = ring[0];
+            const int k = Bi.k;
+            cd x0, x1;
+            const int s = solve_guarded<CPLX>(
+                Bi, cd{rr[b0], CPLX ? ri[b0] : 0.0},
+                cd{k == 2 ? rr[b0 + 1] : 0.0, (CPLX && k == 2) ? ri[b0 + 1] : 0.0},
+                b0 > 0 ? colbound(b0, k) : 0.0, rb, x0, x1);
+            xs[0][0] = x0;
+            xs[0][1] = x1;
+            pend[0] = s;
             yr[b0] = x0.re;
             if (CPLX) yi[b0] = x0.im;
             if (k == 2) {
@@ -213,37 +295,105 @@ eigvec_kernel(int n, const double* __restrict__ S, int ldS, const int4* __restri
                 if (CPLX) yi[b0 + 1] = x1.im;
             }
         }
-        __syncthreads();
-        const int s = sc_step;
-        if (s) {  // rare: scale the rest of the vector and of r exactly
-            double f = 1.0;
+    }
+    __syncthreads();
+    int cur = 0, step = 0, nsc = 0;
+    if (tid == 0) nsc = pend[0];
+    while (b0 > 0) {
+        const int k = b1 - b0;
+        const int s = pend[cur];
+        const cd x0 = xs[cur][0], x1 = xs[cur][1];
+        const int c1 = b0, c0 = block_below(b0), kn = c1 - c0;  // next block [c0, c1)
+        double f = 1.0;
+        if (s) {  // rare: the rows already computed move to the new scale
             for (int t = 0; t < s; ++t) f *= EV_SHRINK;
             for (int i = b1 + tid; i < top; i += EV_THREADS) {
                 yr[i] *= f;
                 if (CPLX) yi[i] *= f;
             }
-            for (int i = tid; i < b0; i += EV_THREADS) {
-                rr[i] *= f;
-                if (CPLX) ri[i] *= f;
-            }
         }
-        // r[0:b0] -= S[0:b0, B] x
-        const cd x0 = xs[0], x1 = xs[1];
-        if (k == 1) {
-            for (int i = tid; i < b0; i += EV_THREADS) {
+        if (warp == 0) {
+            // the next block's rows: scale, update by B, then solve (lane 0)
+            if (lane < kn) {
+                const int i = c0 + lane;
+                const double s0 = __ldg(&S[cm(i, b0, ldS)]);
+                const double s1 = (k == 2) ? __ldg(&S[cm(i, b0 + 1, ldS)]) : 0.0;
+                double v = s ? rr[i] * f : rr[i];
+                v = fma(-s0, x0.re, v);
+                if (k == 2) v = fma(-s1, x1.re, v);
+                rr[i] = v;
+                if (CPLX) {
+                    double u = s ? ri[i] * f : ri[i];
+                    u = fma(-s0, x0.im, u);
+                    if (k == 2) u = fma(-s1, x1.im, u);
+                    ri[i] = u;
+                }
+            }
+            const int q = step + 1;  // index of the next block, counted from the eigenvalue
+            if (q - ring_first >= ring_count) refill(c1, q);
+            else __syncwarp();
+            if (lane == 0) {
+                const BlkInv& Bi = ring[q - ring_first];
+                cd y0, y1;
+                const int sn = solve_guarded<CPLX>(
+                    Bi, cd{rr[c0], CPLX ? ri[c0] : 0.0},
+                    cd{kn == 2 ? rr[c0 + 1] : 0.0, (CPLX && kn == 2) ? ri[c0 + 1] : 0.0},
+                    c0 > 0 ? colbound(c0, kn) : 0.0, rb, y0, y1);
+                xs[cur ^ 1][0] = y0;
+                xs[cur ^ 1][1] = y1;
+                pend[cur ^ 1] = sn;
+                nsc += sn;
+                yr[c0] = y0.re;
+                if (CPLX) yi[c0] = y0.im;
+                if (kn == 2) {
+                    yr[c0 + 1] = y1.re;
+                    if (CPLX) yi[c0 + 1] = y1.im;
+                }
+            }
+        } else if (s) {
+            // rows below the next block: scale, update by B
+            for (int i = tid - 32; i < c0; i += EV_THREADS - 32) {
+                const double s0 = __ldg(&S[cm(i, b0, ldS)]);
+                const double s1 = (k == 2) ? __ldg(&S[cm(i, b0 + 1, ldS)]) : 0.0;
+                double v = fma(-s0, x0.re, rr[i] * f);
+                if (k == 2) v = fma(-s1, x1.re, v);
+                rr[i] = v;
+                if (CPLX) {
+                    double u = fma(-s0, x0.im, ri[i] * f);
+                    if (k == 2) u = fma(-s1, x1.im, u);
+                    ri[i] = u;
+                }
+            }
+        } else if (k == 1) {
+            for (int i = tid - 32; i < c0; i += EV_THREADS - 32) {
                 const double sv = __ldg(&S[cm(i, b0, ldS)]);
                 rr[i] = fma(-sv, x0.re, rr[i]);
                 if (CPLX) ri[i] = fma(-sv, x0.im, ri[i]);
             }
         } else {
-            for (int i = tid; i < b0; i += EV_THREADS) {
+            for (int i = tid - 32; i < c0; i += EV_THREADS - 32) {
                 const double s0 = __ldg(&S[cm(i, b0, ldS)]), s1 = __ldg(&S[cm(i, b0 + 1, ldS)]);
                 rr[i] = fma(-s1, x1.re, fma(-s0, x0.re, rr[i]));
                 if (CPLX) ri[i] = fma(-s1, x1.im, fma(-s0, x0.im, ri[i]));
             }
         }
         __syncthreads();
-        b1 = b0;
+        b1 = c1;
+        b0 = c0;
+        cur ^= 1;
+        ++step;
+    }
+    // the last block's pending scaling: the rows already computed below it
+    {
+        const int s = pend[cur];
+        if (s) {
+            double f = 1.0;
+            for (int t = 0; t < s; ++t) f *= EV_SHRINK;
+            for (int i = b1 + tid; i < top; i += EV_THREADS) {
+                yr[i] *= f;
+                if (CPLX) yi[i] *= f;
+            }
+        }
     }
     if (tid == 0 && nscale) {
         nscale[col] = nsc;
@@ -347,7 +497,7 @@ cudaError_t smem_attr(K kernel, size_t bytes) {
 // Shared memory per CTA for the right-hand side of an n x n problem
 // (complex: 2 n doubles); 0 if it does not fit and global scratch is used.
 size_t eigvec_rhs_smem(int n) {
-    const size_t b = sizeof(double) * 2 * (size_t)n;
+    const size_t b = sizeof(double) * 2 * (size_t)n + (size_t)n + 16;
     return b <= 96 * 1024 ? b : 0;
 }
 
@@ -375,7 +525,7 @@ cudaError_t launch_eigvec(int n, const double* S, int ldS, const int4* d_blocks,
     if (nblk > nreal)
         eigvec_kernel<true><<<nblk - nreal, EV_THREADS, sm, st>>>(
             n, S, ldS, d_blocks + nreal, Y, ldY, cmA, cmB,
-            rscratch ? rscratch + (size_t)nreal * 2 * n : nullptr, sm ? 1 : 0, nscale);
+            rscratch ? rscratch + (size_t)nreal * 3 * n : nullptr, sm ? 1 : 0, nscale);
     return cudaGetLastError();
 }
 
