@@ -61,7 +61,9 @@ METRIC = "selected eigenvalues reordered per second"
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the current kernels (the sched_kernel captures under profiles/);
 # a workload has no entry while no capture of the current build exists.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
+               ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
+               ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9}
 
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
@@ -674,12 +676,14 @@ def run_eigvec(args, wl):
     if ms_b >= ms_s:
         roof = {"kernel": "evgemm_kernel (X = Q Y, DMMA)", "bound": "tensor",
                 "achieved": f_b / (ms_b / 1e3) / 1e12, "unit": "TFLOP/s",
-                "flops_per_launch": f_b, "avg_launch_ms": ms_b}
+                "flops_per_launch": f_b, "avg_launch_ms": ms_b,
+                "traffic": NCU_TRAFFIC.get((wl["name"], "evgemm"))}
     else:
         roof = {"kernel": "eigvec_kernel (back substitution, FP64 FMA)", "bound": "alu",
                 "achieved": f_s / (ms_s / 1e3) / 1e12, "unit": "TFLOP/s",
                 "flops_per_launch": f_s, "avg_launch_ms": ms_s}
-    roof.update({"peak": fp64_peak, "frac": roof["achieved"] / fp64_peak, "traffic": None,
+    roof.setdefault("traffic", None)
+    roof.update({"peak": fp64_peak, "frac": roof["achieved"] / fp64_peak,
                  "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
                                  "1.25/2250"),
                  "share_of_step": roof["avg_launch_ms"] / (total_ms / args.steps),
