@@ -8,7 +8,8 @@ The arithmetic lives in `reorder_oracle.c` (plain C, binary64,
 -ffp-contract=off): the scalar-update reordering of Section 3.2 / Fig. 1a,
 producing the reordered Schur form of Eq. 7; and in `eigvec_oracle.c`: the
 eigenvectors of a real Schur form (Eq. 5) by back substitution with
-overflow protection.  This module only compiles them with gcc, marshals
+overflow protection; and in `gen_oracle.c`: the reordering of a generalized
+real Schur form (S, T) with Q and Z (Eq. 7, second form).  This module only compiles them with gcc, marshals
 numpy arrays through ctypes, and back-transforms the eigenvectors with one
 matrix product (Eq. 6).
 """
@@ -23,6 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "reorder_oracle.c")
 _SRC_EV = os.path.join(_HERE, "eigvec_oracle.c")
+_SRC_GEN = os.path.join(_HERE, "gen_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -33,7 +35,7 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 
 def build(force: bool = False, src: str = _SRC, out: str = _SO, extra=()) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off)."""
-    srcs = [src] + ([_SRC_EV] if src == _SRC else [])
+    srcs = [src] + ([_SRC_EV, _SRC_GEN] if src == _SRC else [])
     if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(x)
                                                  for x in srcs):
         return out
@@ -70,6 +72,21 @@ def load(path: str | None = None):
     if hasattr(lib, "orc_eigvec"):
         lib.orc_eigvec.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _dp, ctypes.c_int, _ip]
         lib.orc_eigvec.restype = ctypes.c_int
+    if hasattr(lib, "orc_gen_reorder"):
+        lib.orc_gen_validate.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int]
+        lib.orc_gen_validate.restype = ctypes.c_int
+        lib.orc_gen_eigenvalues.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                            _dp, _dp]
+        lib.orc_gen_eigenvalues.restype = None
+        lib.orc_gen_sylvester.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        lib.orc_gen_sylvester.restype = ctypes.c_double
+        lib.orc_gen_swap_local.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int,
+                                           _dp, _dp, _dp, _dp]
+        lib.orc_gen_swap_local.restype = ctypes.c_int
+        lib.orc_gen_reorder.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                        _dp, ctypes.c_int, _dp, ctypes.c_int, _ip, _dp, _dp,
+                                        _ip, ctypes.c_int, _llp, _llp]
+        lib.orc_gen_reorder.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -221,3 +238,78 @@ def eigenvectors(S, Q=None, select=None, lib=None):
     if Q is not None:
         Y = normalize_columns(np.asarray(Q, dtype=np.float64) @ Y, kinds)
     return Y, kinds, lams, ns[:m]
+
+
+# ---------------------------------------------------------------------------
+# Generalized real Schur form (S, T)
+# ---------------------------------------------------------------------------
+def gen_validate(S, T, lib=None) -> int:
+    S, T = _f64(S), _f64(T)
+    n = S.shape[0]
+    return (lib or load()).orc_gen_validate(n, _ptr(S), max(n, 1), _ptr(T), max(n, 1))
+
+
+def gen_eigenvalues(S, T, lib=None):
+    """Generalized eigenvalues of the diagonal blocks, diagonal order."""
+    S, T = _f64(S), _f64(T)
+    n = S.shape[0]
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    (lib or load()).orc_gen_eigenvalues(n, _ptr(S), max(n, 1), _ptr(T), max(n, 1), _ptr(wr),
+                                        _ptr(wi))
+    return wr + 1j * wi
+
+
+def gen_sylvester(A, B, p, q, lib=None):
+    """Solve A11 R - L A22 = -gamma A12, B11 R - L B22 = -gamma B12 for the
+    (p + q) x (p + q) pair (A, B); returns (R, L, gamma)."""
+    k = p + q
+    DA = np.zeros((4, 4), order="F")
+    DB = np.zeros((4, 4), order="F")
+    DA[:k, :k] = A
+    DB[:k, :k] = B
+    R = np.zeros(4)
+    L = np.zeros(4)
+    g = (lib or load()).orc_gen_sylvester(p, q, _ptr(DA), _ptr(DB), _ptr(R), _ptr(L))
+    return (R[:p * q].reshape((p, q), order="F"), L[:p * q].reshape((p, q), order="F"), g)
+
+
+def gen_swap_local(A, B, p, q, strong=True, lib=None):
+    """Swap on a (p + q) x (p + q) pair alone: (status, Qs, Zs, A_new, B_new)."""
+    k = p + q
+    DA = np.zeros((4, 4), order="F")
+    DB = np.zeros((4, 4), order="F")
+    DA[:k, :k] = A
+    DB[:k, :k] = B
+    out = [np.zeros((4, 4), order="F") for _ in range(4)]
+    st = (lib or load()).orc_gen_swap_local(p, q, _ptr(DA), _ptr(DB), 1 if strong else 0,
+                                            *[_ptr(o) for o in out])
+    return (st,) + tuple(o[:k, :k].copy() for o in out)
+
+
+def gen_reorder(S, T, Q, Z, select, *, strong=True, lib=None):
+    """Reorder the generalized Schur form (S, T) with Q, Z so that the
+    selected eigenvalues lead.  Returns a dict with S, T, Q, Z (new arrays),
+    eigs (complex), m, status, nswaps, nrej."""
+    S, T = _f64(S), _f64(T)
+    n = S.shape[0]
+    Qp = Zp = None
+    if Q is not None:
+        Q = _f64(Q)
+        Qp = _ptr(Q)
+    if Z is not None:
+        Z = _f64(Z)
+        Zp = _ptr(Z)
+    sel_in = np.ascontiguousarray(np.asarray(select, dtype=np.int32))
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    ns = ctypes.c_longlong(0)
+    nr = ctypes.c_longlong(0)
+    ld = max(n, 1)
+    st = (lib or load()).orc_gen_reorder(n, _ptr(S), ld, _ptr(T), ld, Qp, ld, Zp, ld,
+                                         sel_in.ctypes.data_as(_ip), _ptr(wr), _ptr(wi),
+                                         ctypes.byref(m), 1 if strong else 0,
+                                         ctypes.byref(ns), ctypes.byref(nr))
+    return dict(S=S, T=T, Q=Q, Z=Z, eigs=wr + 1j * wi, m=m.value, status=st,
+                nswaps=ns.value, nrej=nr.value)

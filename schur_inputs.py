@@ -27,6 +27,18 @@ are this project's synthetic stand-in):
   drawn as above from the sub-block's own blocks.  Twenty thousand
   independent forms of order up to 8192 would not fit in host memory.
 
+Generalized real Schur form (S, T) (the pair case of Eq. 7):
+
+* block sizes and selection as above;
+* T upper triangular: diagonal ~ U(0.5, 2), strict upper triangle ~ N(0,1);
+* a 1x1 block of S is lambda t_jj with lambda ~ N(0,1) (so the generalized
+  eigenvalue is lambda); a 2x2 block of S is T_b M with T_b the 2x2 diagonal
+  block of T and M = [[a, b], [c, a]] drawn as for the standard form, so the
+  pair's eigenvalues are a +- i sqrt(-bc); strict upper triangle of S
+  (outside the blocks) ~ N(0,1);
+* Q and Z: products of seeded Householder reflectors (as Q above), drawn
+  one after the other from the same generator.
+
 All matrices are float64 in column-major (Fortran) order.
 """
 from __future__ import annotations
@@ -35,7 +47,7 @@ import numpy as np
 
 __all__ = ["block_sizes", "schur_form", "householder_q", "selection",
            "reorder_problem", "batch_problems", "request_stream", "serve_base",
-           "serve_request"]
+           "serve_request", "gen_schur_pair", "gen_problem", "gen_config"]
 
 
 def block_sizes(n: int, rng: np.random.Generator, frac_1x1: float = 0.6) -> np.ndarray:
@@ -221,3 +233,60 @@ def serve_request(base, n: int, frac: float, seed: int, reflectors: int = 8):
     Q = householder_q(e - k, rng, reflectors)
     sel = selection(sizes[b0:b1], frac, rng)
     return S, Q, sel
+
+
+def gen_schur_pair(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6):
+    """Random generalized real Schur form (S, T). Returns (S, T, sizes)."""
+    sizes = block_sizes(n, rng, frac_1x1)
+    S = np.zeros((n, n), dtype=np.float64, order="F")
+    T = np.zeros((n, n), dtype=np.float64, order="F")
+    if n == 0:
+        return S, T, sizes
+    S[:] = np.triu(rng.standard_normal((n, n)), k=1)
+    T[:] = np.triu(rng.standard_normal((n, n)), k=1)
+    T[np.diag_indices(n)] = rng.uniform(0.5, 2.0, n)
+    nb1 = int(np.sum(sizes == 1))
+    nb2 = int(np.sum(sizes == 2))
+    lam = rng.standard_normal(nb1)
+    a = rng.standard_normal(nb2)
+    b = rng.uniform(0.1, 2.0, nb2) * rng.choice([-1.0, 1.0], nb2)
+    c = -np.sign(b) * rng.uniform(0.1, 2.0, nb2)
+    i1 = i2 = 0
+    pos = 0
+    for sz in sizes:
+        if sz == 1:
+            S[pos, pos] = lam[i1] * T[pos, pos]
+            i1 += 1
+        else:
+            Tb = T[pos:pos + 2, pos:pos + 2]
+            M = np.array([[a[i2], b[i2]], [c[i2], a[i2]]])
+            S[pos:pos + 2, pos:pos + 2] = Tb @ M
+            i2 += 1
+        pos += int(sz)
+    return S, T, sizes
+
+
+def gen_problem(n: int, seed: int = 0, *, select_frac: float = 0.3, qz: str = "householder",
+                reflectors: int = 64):
+    """One generalized reordering instance: (S, T, Q, Z, select)."""
+    rng = np.random.default_rng(seed)
+    S, T, sizes = gen_schur_pair(n, rng)
+    if qz == "identity":
+        Q = np.asfortranarray(np.eye(n))
+        Z = np.asfortranarray(np.eye(n))
+    elif qz == "householder":
+        Q = householder_q(n, rng, reflectors)
+        Z = householder_q(n, rng, reflectors)
+    else:
+        raise ValueError(f"unknown Q/Z kind {qz!r}")
+    sel = selection(sizes, select_frac, rng)
+    return S, T, Q, Z, sel
+
+
+def gen_config(name: str, seed: int = 0):
+    """Named generalized workloads: 'g400', 'g4000'."""
+    if name == "g400":
+        return gen_problem(400, seed, select_frac=0.30, qz="householder", reflectors=16)
+    if name == "g4000":
+        return gen_problem(4000, seed, select_frac=0.35, qz="householder")
+    raise ValueError(name)

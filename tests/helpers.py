@@ -88,3 +88,48 @@ def match_eigs(got, want, rtol):
     """Elementwise eigenvalue order check with relative tolerance."""
     scale = np.maximum(np.abs(want), 1.0)
     return float(np.max(np.abs(got - want) / scale)) if got.size else 0.0
+
+
+# --- generalized Schur form (S, T) --------------------------------------
+def is_gen_schur(S, T):
+    """Exact zeros below the quasi-diagonal of S and below the diagonal of
+    T, no adjacent 2x2 overlap in S."""
+    n = S.shape[0]
+    if n and (np.any(np.tril(S, -2) != 0.0) or np.any(np.tril(T, -1) != 0.0)):
+        return False
+    for j, sz in blocks(S):
+        if sz == 2 and j + 2 < n and S[j + 2, j + 1] != 0.0:
+            return False
+    return True
+
+
+def gen_block_eigs(S, T):
+    """Generalized eigenvalues of the diagonal blocks (LAPACK through
+    scipy.linalg.eigvals), diagonal order, positive imaginary part first."""
+    from scipy.linalg import eigvals
+    ev = []
+    for j, sz in blocks(S):
+        if sz == 1:
+            ev.append(complex(S[j, j] / T[j, j], 0.0))
+        else:
+            w = eigvals(S[j:j + 2, j:j + 2], T[j:j + 2, j:j + 2])
+            w = sorted(w, key=lambda z: -z.imag)
+            ev += [complex(w[0]), complex(w[1])]
+    return np.array(ev)
+
+
+def gen_expected_order(S, T, select):
+    """Stable partition of the input's generalized eigenvalues."""
+    ev = gen_block_eigs(S, T)
+    sel = np.asarray(select).astype(bool).copy()
+    for j, sz in blocks(S):
+        if sz == 2:
+            sel[j] = sel[j + 1] = sel[j] or sel[j + 1]
+    return np.concatenate([ev[sel], ev[~sel]]), int(sel.sum())
+
+
+def pair_residual(A, B, S, T, Q, Z):
+    """max of ||A - Q S Z^T|| / ||A|| and ||B - Q T Z^T|| / ||B|| (Frobenius)."""
+    ra = np.linalg.norm(A - Q @ S @ Z.T) / max(np.linalg.norm(A), 1e-300)
+    rb = np.linalg.norm(B - Q @ T @ Z.T) / max(np.linalg.norm(B), 1e-300)
+    return float(max(ra, rb))
