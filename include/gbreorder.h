@@ -160,6 +160,51 @@ int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *s
                      gbr_stats *stats, void *cuda_stream);
 
 /*
+ * Reorder a generalized real Schur form (S, T) resident in device memory
+ * (Section 2, Eq. 7, second form): orthogonal Q3, Z3 with
+ * (S_hat, T_hat) = Q3^T (S, T) Z3 again in generalized real Schur form and
+ * the selected generalized eigenvalues in its leading diagonal blocks.
+ *
+ * Input form: S upper quasi-triangular (1x1 and 2x2 diagonal blocks, a 2x2
+ * block marked by S[j+1][j] != 0 and carrying a complex-conjugate pair of
+ * the 2x2 pencil), T upper triangular (also inside the 2x2 blocks).  The
+ * output keeps that form; the 2x2 blocks of S are not standardized further.
+ *
+ *  1 n          order (n >= 0)
+ *  2 S, 3 ldS   device, n x n column-major, overwritten by S_hat
+ *  4 T, 5 ldT   device, n x n column-major, overwritten by T_hat
+ *  6 Q, 7 ldQ   device or NULL; overwritten by Q Q3
+ *  8 Z, 9 ldZ   device or NULL; overwritten by Z Z3
+ * 10 select     host, n ints, as for gbr_reorder
+ * 11 eig_re, 12 eig_im  host or NULL: generalized eigenvalues lambda =
+ *               alpha / beta of (S_hat, T_hat) in diagonal order (a 1x1
+ *               block gives s/t, +-inf if t = 0; a 2x2 block its conjugate
+ *               pair, +im first)
+ * 13 m_out      host or NULL: number of selected eigenvalues
+ * 14 opts       options or NULL.  window > 64 is reduced to 64 and chain
+ *               then to at most 32 (both factors of a window live in shared
+ *               memory); precision GBR_PREC_DMMA and sched
+ *               GBR_SCHED_SEQUENTIAL only (others: GBR_ERR_UNSUPPORTED);
+ *               NULL means the defaults with the sequential schedule
+ * 15 stats      host or NULL (upd_flops counts S, T, Q and Z panels)
+ * 16 cuda_stream  cudaStream_t or NULL
+ *
+ * Returns the number of rejected swaps (>= 0) or a negative error: -1 bad
+ * n, -2 (S, T) not in generalized real Schur form (also a NULL S or T),
+ * -3 bad ldS/ldT, -5 bad ldQ/ldZ, -6 NULL select, -10 bad window/chain.
+ */
+int gbr_reorder_gen(int n, double *S, int ldS, double *T, int ldT, double *Q, int ldQ,
+                    double *Z, int ldZ, const int *select, double *eig_re, double *eig_im,
+                    int *m_out, const gbr_opts *opts, gbr_stats *stats, void *cuda_stream);
+
+/* gbr_reorder_gen with S, T, Q, Z in HOST memory (copied to the device and
+ * back inside the call; device buffers from the library's pool). */
+int gbr_reorder_gen_host(int n, double *S, int ldS, double *T, int ldT, double *Q, int ldQ,
+                         double *Z, int ldZ, const int *select, double *eig_re,
+                         double *eig_im, int *m_out, const gbr_opts *opts,
+                         gbr_stats *stats, void *cuda_stream);
+
+/*
  * Same operation as gbr_reorder, for callers that must not allocate device
  * memory (for example code that runs while a stream is being captured into
  * a CUDA graph, or a program that owns all device memory through its own

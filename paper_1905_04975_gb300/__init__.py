@@ -79,8 +79,12 @@ _ip = ctypes.POINTER(ctypes.c_int)
 _REORDER_ARGS = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _ip,
                  _dp, _dp, _ip, ctypes.POINTER(GbrOpts), ctypes.POINTER(GbrStats),
                  ctypes.c_void_p]
+_REORDER_GEN_ARGS = [ctypes.c_int] + [ctypes.c_void_p, ctypes.c_int] * 4 + [
+    _ip, _dp, _dp, _ip, ctypes.POINTER(GbrOpts), ctypes.POINTER(GbrStats), ctypes.c_void_p]
 SYMBOLS = {
     "gbr_default_opts": (None, [ctypes.POINTER(GbrOpts)]),
+    "gbr_reorder_gen": (ctypes.c_int, _REORDER_GEN_ARGS),
+    "gbr_reorder_gen_host": (ctypes.c_int, _REORDER_GEN_ARGS),
     "gbr_reorder": (ctypes.c_int, _REORDER_ARGS),
     "gbr_reorder_host": (ctypes.c_int, _REORDER_ARGS),
     "gbr_reorder_noalloc": (ctypes.c_int, _REORDER_ARGS),
@@ -383,6 +387,69 @@ def reorder_host(S: np.ndarray, Q: np.ndarray | None, select, *, opts: GbrOpts |
                               sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
                               wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
                               ctypes.byref(stats), _stream_handle(stream))
+    return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+def _gen_opts(opts, kw):
+    if opts is not None:
+        return opts
+    kw = dict(kw)
+    kw.setdefault("sched", "sequential")
+    return make_opts(**kw)
+
+
+def reorder_gen(S, T, Q, Z, select, *, opts: GbrOpts | None = None, stream=None,
+                allow_partial=True, **kw) -> ReorderResult:
+    """Reorder the generalized Schur form (S, T) in place on the GPU so that
+    the selected generalized eigenvalues lead; Q <- Q Q3, Z <- Z Z3.
+
+    S, T, Q, Z: column-major float64 CUDA tensors (Q, Z may be None).
+    Keyword options as for reorder(); window is capped at 64."""
+    lib = load()
+    n = int(S.shape[0])
+    ptrs = []
+    for X in (S, T, Q, Z):
+        if X is None:
+            ptrs += [None, max(n, 1)]
+        else:
+            ptrs += [ctypes.c_void_p(X.data_ptr()), _colmajor_ld(X)]
+    sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+    if sel.size != n:
+        raise ValueError("select must have n entries")
+    o = _gen_opts(opts, kw)
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    stats = GbrStats()
+    rc = lib.gbr_reorder_gen(n, *ptrs, sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
+                             wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
+                             ctypes.byref(stats), _stream_handle(stream))
+    return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+def reorder_gen_host(S, T, Q, Z, select, *, opts: GbrOpts | None = None, stream=None,
+                     allow_partial=True, **kw) -> ReorderResult:
+    """reorder_gen() for host (numpy, Fortran-ordered float64) matrices,
+    updated in place; the library copies them to the GPU and back."""
+    lib = load()
+    n = int(S.shape[0])
+    ptrs = []
+    for X in (S, T, Q, Z):
+        if X is None:
+            ptrs += [None, max(n, 1)]
+            continue
+        if not (X.flags.f_contiguous and X.dtype == np.float64):
+            raise ValueError("matrices must be Fortran-ordered float64 arrays")
+        ptrs += [ctypes.c_void_p(X.ctypes.data), max(n, 1)]
+    sel = np.ascontiguousarray(np.asarray(select, dtype=np.int32).reshape(-1))
+    o = _gen_opts(opts, kw)
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    m = ctypes.c_int(0)
+    stats = GbrStats()
+    rc = lib.gbr_reorder_gen_host(n, *ptrs, sel.ctypes.data_as(_ip), wr.ctypes.data_as(_dp),
+                                  wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
+                                  ctypes.byref(stats), _stream_handle(stream))
     return _finish(rc, n, m, wr, wi, stats, allow_partial)
 
 

@@ -20,15 +20,19 @@ static std::vector<long long> g_trace;  // last traced persistent launch, 8 word
 // Device scratch pool: one grow-only allocation per device and purpose.
 // ---------------------------------------------------------------------------
 enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_PANEL = 4,
-                POOL_EIGVEC = 5, POOL_NSLOTS = 6 };
+                POOL_EIGVEC = 5 };
+static_assert(POOL_GEN_SCRATCH == 6 && POOL_GEN_HOST == 7 && POOL_NSLOTS == 8,
+              "pool slots of the generalized entry points");
 struct DevPool {
-    void* ptr[POOL_NSLOTS] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t bytes[POOL_NSLOTS] = {0, 0, 0, 0, 0, 0};
+    void* ptr[POOL_NSLOTS] = {};
+    size_t bytes[POOL_NSLOTS] = {};
 };
 static std::mutex g_mu;  // serializes calls: the pool is shared per device
 static DevPool g_pool[64];
 
-static int pool_get(int slot, size_t bytes, void** out) {
+std::mutex& api_mutex() { return g_mu; }
+
+int pool_get(int slot, size_t bytes, void** out) {
     int dev = 0;
     GBR_CK(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= 64) return GBR_ERR_CUDA;

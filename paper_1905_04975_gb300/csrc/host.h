@@ -7,6 +7,7 @@
 #include "common.cuh"
 
 #include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,12 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 int num_sms();
+
+// Device scratch pool (api.cu): one grow-only allocation per device and slot;
+// callers hold api_mutex() while they use it.
+constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_NSLOTS = 8;
+int pool_get(int slot, size_t bytes, void** out);
+std::mutex& api_mutex();
 
 // ---------------------------------------------------------------------------
 // Planner (Section 3.2: windows and chains)

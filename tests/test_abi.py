@@ -112,6 +112,34 @@ def test_eigenvectors_argument_checks(lib):
     assert m.value == 0
 
 
+def test_reorder_gen_argument_checks(lib):
+    """gbr_reorder_gen checks its arguments before any GPU work; options
+    the pair path does not build are refused; n = 0 is a no-op."""
+    d = ctypes.c_void_p(0x1000)  # never dereferenced
+    sel = np.zeros(4, dtype=np.int32)
+    ip = sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    m = ctypes.c_int(7)
+    seq = g.make_opts(sched="sequential")
+
+    def call(n, S, ldS, T, ldT, Q, ldQ, Z, ldZ, sel_p, opts):
+        return lib.gbr_reorder_gen(n, S, ldS, T, ldT, Q, ldQ, Z, ldZ, sel_p, None, None,
+                                   ctypes.byref(m), ctypes.byref(opts) if opts else None, None, None)
+
+    assert call(-1, d, 4, d, 4, None, 4, None, 4, ip, seq) == -1
+    assert call(4, d, 4, None, 4, None, 4, None, 4, ip, seq) == -2
+    assert call(4, d, 3, d, 4, None, 4, None, 4, ip, seq) == -3
+    assert call(4, d, 4, d, 3, None, 4, None, 4, ip, seq) == -3
+    assert call(4, d, 4, d, 4, d, 3, None, 4, ip, seq) == -5
+    assert call(4, d, 4, d, 4, None, 4, d, 2, ip, seq) == -5
+    assert call(4, d, 4, d, 4, None, 4, None, 4, None, seq) == -6
+    assert call(4, d, 4, d, 4, None, 4, None, 4, ip, g.make_opts(window=16, chain=15,
+                                                                  sched="sequential")) == -10
+    assert call(4, d, 4, d, 4, None, 4, None, 4, ip, g.make_opts(precision="ozaki",
+                                                                  sched="sequential")) == g.ERR_UNSUPPORTED
+    assert call(0, None, 1, None, 1, None, 1, None, 1, None, None) == 0
+    assert m.value == 0
+
+
 def batch_create(lib, count, n, S, ldS, Q, ldQ, sel, opts=None, want_out=True):
     ip = ctypes.POINTER(ctypes.c_int)
     arr = lambda a: a.ctypes.data_as(ip) if a is not None else None

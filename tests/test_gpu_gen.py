@@ -1,0 +1,175 @@
+"""GPU reordering of a generalized Schur form (S, T) with Q and Z (Eq. 7,
+second form) through gbr_reorder_gen, against the CPU oracle.
+
+As for the standard form, the reordered pair is unique only up to the signs
+of the Schur vectors and the basis inside each 2x2 block, so parity compares
+what is unique:
+  * the generalized eigenvalue order on the diagonal (1e-10 relative),
+  * the leading left and right deflating subspaces (span Q[:, :m] and
+    span Z[:, :m]) against the oracle's: sine of the largest principal angle
+    <= 1e-10 cond, cond = ||(S, T)||_F / Dif (LAPACK's estimate),
+and checks that the rest is valid: exact zeros below the quasi-diagonal of
+S and below the diagonal of T, ||Q^T Q - I||, ||Z^T Z - I|| and the
+backward errors ||A - Q S Z^T|| / ||A||, ||B - Q T Z^T|| / ||B|| within
+50 n eps.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import lapack
+
+import oracle
+import schur_inputs as si
+from tests.helpers import (EPS, gen_block_eigs, gen_expected_order, is_gen_schur, match_eigs,
+                           orth_err, pair_residual, sin_angle)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gbr():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1905_04975_gb300 as g
+    g.load()
+    return g
+
+
+def run_gpu(g, S, T, Q, Z, sel, **kw):
+    d = [g.to_device(X) if X is not None else None for X in (S, T, Q, Z)]
+    r = g.reorder_gen(*d, sel, **kw)
+    torch.cuda.synchronize()
+    return (r,) + tuple(g.to_host(X) if X is not None else None for X in d)
+
+
+def dif_cond(S, T, sel, m):
+    n = S.shape[0]
+    if not (0 < m < n) or n > 600:
+        return None
+    lw = max(4 * n + 16, 2 * m * (n - m) + 1)
+    out = lapack.dtgsen(np.asarray(sel, np.int32), S, T, np.eye(n), np.eye(n), ijob=2,
+                        lwork=lw, liwork=max(n + 6, 2 * m * (n - m) + 1))
+    dif, info = out[-2], out[-1]
+    if info != 0 or np.min(dif) <= 0:
+        return None
+    return np.sqrt(np.linalg.norm(S) ** 2 + np.linalg.norm(T) ** 2) / np.min(dif)
+
+
+def check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg, ref=None, order_tol=1e-10):
+    n = S.shape[0]
+    want, m = gen_expected_order(S, T, sel)
+    assert r.m == m
+    assert is_gen_schur(Sg, Tg)
+    got = gen_block_eigs(Sg, Tg)
+    assert match_eigs(r.eigs, got, 0) <= 1e-12
+    if r.status == 0:
+        assert match_eigs(got, want, 0) <= order_tol
+    Qi = Q if Q is not None else np.eye(n)
+    Zi = Z if Z is not None else np.eye(n)
+    Qo = Qg if Qg is not None else None
+    if Qg is not None and Zg is not None:
+        assert orth_err(Qg) <= 50 * n * EPS and orth_err(Zg) <= 50 * n * EPS
+        assert pair_residual(Qi @ S @ Zi.T, Qi @ T @ Zi.T, Sg, Tg, Qg, Zg) <= 50 * n * EPS
+    if ref is not None and r.status == 0 and ref["status"] == 0:
+        assert match_eigs(got, ref["eigs"], 0) <= order_tol
+        if Qo is not None and 0 < m < n:
+            cond = dif_cond(S, T, [1 if x else 0 for x in _pos_sel(S, sel)], m)
+            bound = max(1e-10 * cond, 1e-12) if cond else 1e-8
+            assert sin_angle(Qg[:, :m], ref["Q"][:, :m]) <= bound
+            assert sin_angle(Zg[:, :m], ref["Z"][:, :m]) <= bound
+
+
+def _pos_sel(S, sel):
+    """Per-position selection with 2x2 blocks selected whole."""
+    n = S.shape[0]
+    s = np.asarray(sel).astype(bool).copy()
+    j = 0
+    while j < n:
+        if j + 1 < n and S[j + 1, j] != 0.0:
+            s[j] = s[j + 1] = s[j] or s[j + 1]
+            j += 2
+        else:
+            j += 1
+    return s
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 11, 12])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_all_windows(gbr, n, seed):
+    S, T, Q, Z, sel = si.gen_problem(n, 10 * n + seed, select_frac=0.5, reflectors=4)
+    ref = oracle.gen_reorder(S, T, Q, Z, sel)
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel, window=8, chain=3)
+    assert r.status == 0
+    check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg, ref)
+
+
+@pytest.mark.parametrize("name,n,w,m", [("n60", 60, 16, 6), ("n200", 200, 64, 32),
+                                        ("n200-narrow", 200, 24, 10), ("g400", 400, 64, 32),
+                                        ("ragged515", 515, 64, 30)])
+def test_matches_oracle(gbr, name, n, w, m):
+    if name == "g400":
+        S, T, Q, Z, sel = si.gen_config("g400")
+    else:
+        S, T, Q, Z, sel = si.gen_problem(n, n + 3, select_frac=0.4, reflectors=16)
+    ref = oracle.gen_reorder(S, T, Q, Z, sel)
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m)
+    assert r.status == 0 and r.stats.swaps == ref["nswaps"]
+    check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg, ref)
+
+
+def test_default_window_is_capped(gbr):
+    """Default options ask for w = 128; the pair path runs w = 64, m = 32."""
+    S, T, Q, Z, sel = si.gen_problem(300, 5, select_frac=0.5, reflectors=8)
+    ref = oracle.gen_reorder(S, T, Q, Z, sel)
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel)
+    assert r.status == 0
+    check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg, ref)
+
+
+def test_without_q_and_z(gbr):
+    """Q and Z are optional: S and T come out as with them."""
+    S, T, Q, Z, sel = si.gen_problem(150, 4, select_frac=0.5, reflectors=8)
+    r1, S1, T1, _, _ = run_gpu(gbr, S, T, Q, Z, sel, window=32, chain=12)
+    r2, S2, T2, _, _ = run_gpu(gbr, S, T, None, None, sel, window=32, chain=12)
+    assert np.array_equal(S1, S2) and np.array_equal(T1, T2)
+    assert r1.status == r2.status == 0
+
+
+def test_host_entry_matches_device_entry(gbr):
+    S, T, Q, Z, sel = si.gen_problem(180, 6, select_frac=0.3, reflectors=8)
+    r1, S1, T1, Q1, Z1 = run_gpu(gbr, S, T, Q, Z, sel, window=48, chain=20)
+    Sh, Th, Qh, Zh = (np.asfortranarray(X.copy()) for X in (S, T, Q, Z))
+    r2 = gbr.reorder_gen_host(Sh, Th, Qh, Zh, sel, window=48, chain=20)
+    assert np.array_equal(S1, Sh) and np.array_equal(T1, Th)
+    assert np.array_equal(Q1, Qh) and np.array_equal(Z1, Zh)
+    assert r1.m == r2.m and np.array_equal(r1.eigs, r2.eigs)
+
+
+def test_rejected_swap_leaves_pair_unchanged(gbr):
+    """The ill-conditioned 2x2|2x2 pair the oracle's pin rejects: the GPU
+    rejects it too and leaves (S, T, Q, Z) untouched."""
+    from tests.test_oracle_gen import ill_conditioned_pair
+    S, T = ill_conditioned_pair()
+    I4 = np.asfortranarray(np.eye(4))
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, I4, I4, [0, 0, 1, 1], window=8, chain=3)
+    assert r.status == 1 and r.stats.rejected == 1
+    assert np.array_equal(Sg, S) and np.array_equal(Tg, T)
+    assert np.array_equal(Qg, I4) and np.array_equal(Zg, I4)
+
+
+def test_invalid_pair_is_refused(gbr):
+    S, T, Q, Z, sel = si.gen_problem(40, 2, reflectors=4)
+    T[5, 2] = 1e-3   # below the diagonal of T
+    with pytest.raises(gbr.GbrError) as ei:
+        run_gpu(gbr, S, T, Q, Z, sel, allow_partial=False)
+    assert ei.value.status == -2
+
+
+def test_g4000_workload(gbr):
+    """The n = 4000 pair workload: eigenvalue order against the input's
+    blocks, exact structure, orthogonality and backward error of the whole
+    result (the oracle takes minutes at this size)."""
+    S, T, Q, Z, sel = si.gen_config("g4000")
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel)
+    assert r.status == 0
+    check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg)
