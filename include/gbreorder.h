@@ -181,11 +181,10 @@ int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *s
  *               block gives s/t, +-inf if t = 0; a 2x2 block its conjugate
  *               pair, +im first)
  * 13 m_out      host or NULL: number of selected eigenvalues
- * 14 opts       options or NULL.  window > 64 is reduced to 64 and chain
- *               then to at most 32 (both factors of a window live in shared
- *               memory); precision GBR_PREC_DMMA and sched
- *               GBR_SCHED_SEQUENTIAL only (others: GBR_ERR_UNSUPPORTED);
- *               NULL means the defaults with the sequential schedule
+ * 14 opts       options or NULL for the defaults.  window > 64 is reduced
+ *               to 64 and chain then to at most 32 (both factors of a window
+ *               live in shared memory); precision GBR_PREC_DMMA only
+ *               (GBR_PREC_OZAKI: GBR_ERR_UNSUPPORTED); both schedules
  * 15 stats      host or NULL (upd_flops counts S, T, Q and Z panels)
  * 16 cuda_stream  cudaStream_t or NULL
  *

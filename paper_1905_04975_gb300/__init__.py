@@ -391,11 +391,7 @@ def reorder_host(S: np.ndarray, Q: np.ndarray | None, select, *, opts: GbrOpts |
 
 
 def _gen_opts(opts, kw):
-    if opts is not None:
-        return opts
-    kw = dict(kw)
-    kw.setdefault("sched", "sequential")
-    return make_opts(**kw)
+    return opts if opts is not None else make_opts(**kw)
 
 
 def reorder_gen(S, T, Q, Z, select, *, opts: GbrOpts | None = None, stream=None,

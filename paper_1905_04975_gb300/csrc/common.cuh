@@ -50,6 +50,9 @@ struct Inst {
     uint8_t* sel;        // SEL_* per position
     DevCounters* ctr;
     int n, ldS, ldQ, pad;
+    double* T;           // generalized form (S, T): T, else null
+    double* Z;           // generalized form: right factor Z, or null
+    int ldT, ldZ;
 };
 
 // One diagonal window in program order.
@@ -62,7 +65,8 @@ struct Window {
 
 // Persistent scheduler (sched.cu): task kinds and launch parameters.
 enum : int { TASK_W = 0, TASK_L = 1, TASK_R = 2, TASK_Q = 3,  // L/R/Q = TASK_L + panel
-             TASK_E = 4 };  // server: eigenvalues + completion of a request (its last task)
+             TASK_E = 4,    // server: eigenvalues + completion of a request (its last task)
+             TASK_Z = 5 };  // generalized form: a tile of Z's panel (Z <- Z UZ)
 
 struct SchedTask {
     int kind;   // TASK_*
@@ -73,13 +77,15 @@ struct SchedTask {
 
 struct SchedParams {
     int strong, ntasks;
+    int pair;                 // nonzero: generalized instances (S, T) with Q and Z
     const Inst* inst;         // instance table
     const SchedTask* tasks;   // queue order
     const Window* wins;
     int* deps_left;           // unfinished predecessors per task
     const int* succ_off;      // CSR successors
     const int* succ;
-    double* upool;            // U of every window, at Window::u_off (w x w, column-major)
+    double* upool;            // U of every window, at Window::u_off (w x w, column-major;
+                              // a generalized instance's window has UQ then UZ there)
     unsigned char* uslices;   // null (DMMA updates) or OZ_USLICE_BYTES per window
     int* head;                // next queue position
     int* err;                 // nonzero: a wait ran out (1) or the plan does not fit S (2)

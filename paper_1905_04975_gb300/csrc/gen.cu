@@ -186,6 +186,10 @@ namespace {
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Duration model of the queue order: a pair window task at w = 128
+// equivalent (the model scales it as w^2), in microseconds.
+constexpr double kGenWinUs128 = 4.0 * 2000.0;
+
 // Window and chain of a generalized call: the window is capped at gen::GW
 // (the factors UQ and UZ both live in shared memory), and with the cap the
 // chain at half of it.
@@ -196,6 +200,59 @@ void gen_window(const gbr_opts& o, int* w, int* m) {
         *w = gen::GW;
         *m = std::min(*m, gen::GW / 2);
     }
+}
+
+// One planned pass through the persistent scheduler: the generalized
+// instance's window tasks run window_gen_body, its tiles update S and T
+// (left by UQ, right by UZ), Q (UQ) and Z (UZ).
+int run_persistent_gen(int n, const std::vector<Window>& wins, double* S, int ldS, double* T,
+                       int ldT, double* Q, int ldQ, double* Z, int ldZ, uint8_t* d_sel,
+                       DevCounters* d_ctr, const gbr_opts& o, long long* ntasks_out,
+                       double* ms_out, SchedInfo* info, cudaStream_t st) {
+    std::vector<InstPlan> plans(1);
+    plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0, T, Z, ldT, ldZ};
+    plans[0].wins = wins;
+    CostModel cm;
+    cm.lr_mats = 2.0;
+    cm.win_us_128 = kGenWinUs128;
+    SchedLaunch L;
+    int rc = sched_prepare(
+        plans, o, cm, num_sms(),
+        [](size_t b) -> void* {
+            void* p = nullptr;
+            return pool_get(POOL_GEN_SCHED, b, &p) ? nullptr : p;
+        },
+        &L, info, st);
+    if (rc) return rc;
+    L.P.pair = 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (o.timing) {
+        GBR_CK(cudaEventCreate(&e0), "event");
+        GBR_CK(cudaEventCreate(&e1), "event");
+        GBR_CK(cudaEventRecord(e0, st), "event");
+    }
+    rc = sched_enqueue(L, st);
+    if (rc) return rc;
+    if (o.timing) GBR_CK(cudaEventRecord(e1, st), "event");
+    int h_err = 0;
+    GBR_CK(cudaMemcpyAsync(&h_err, L.P.err, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H err");
+    GBR_CK(cudaStreamSynchronize(st), "sync");
+    if (o.timing) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            ms = 0.f;
+            (void)cudaGetLastError();
+        }
+        *ms_out += ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    *ntasks_out += L.P.ntasks;
+    if (h_err) {
+        set_last_error("persistent scheduler (pair): a task waited longer than wait_limit_ms");
+        return GBR_ERR_TIMEOUT;
+    }
+    return 0;
 }
 
 int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q, int ldQ, double* Z,
@@ -248,6 +305,9 @@ int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q,
     int nchains = 0;
     double flops = 0.0;
     unsigned long long seen_rej = 0;
+    long long ntasks = 0;
+    double ms_sched = 0.0;
+    SchedInfo info_all;
     PlanState ps;
     init_state(ps, n, sub.data(), sel.data());
     for (int pass = 0; pass < 1 + 2 * n; ++pass) {
@@ -259,6 +319,17 @@ int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q,
             const double ww = (double)(wd.e - wd.s) * (wd.e - wd.s);
             flops += 2.0 * ww * (2.0 * (n - wd.e) + 2.0 * wd.s + (Q ? n : 0) + (Z ? n : 0));
         }
+        if (o.sched == GBR_SCHED_PERSISTENT) {
+            SchedInfo inf;
+            rc = run_persistent_gen(n, win, S, ldS, T, ldT, Q, ldQ, Z, ldZ, d_sel, d_ctr, o, &ntasks,
+                                    &ms_sched, &inf, st);
+            if (rc) return rc;
+            info_all.cp_us = inf.cp_us;
+            info_all.sim_us = inf.sim_us;
+            info_all.graph_ms += inf.graph_ms;
+            info_all.order_ms += inf.order_ms;
+            launches += 1;
+        } else
         for (const Window& wd : win) {
             if (o.timing) GBR_CK(mark(evw), "event");
             GBR_CK(launch_window_gen(n, wd, S, ldS, T, ldT, d_sel, d_uq, d_uz, o.strong_test, d_ctr, st),
@@ -318,6 +389,12 @@ int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q,
         stats->ms_update = msu;
         stats->win_flops = (double)h_ctr.win_flops;
         stats->upd_flops_issued = (double)h_ctr.upd_issued;
+        stats->ms_sched = ms_sched;
+        stats->tasks = ntasks;
+        stats->sched_cp_ms = ntasks ? info_all.cp_us / 1e3 : 0.0;
+        stats->sched_sim_ms = ntasks ? info_all.sim_us / 1e3 : 0.0;
+        stats->ms_graph = info_all.graph_ms;
+        stats->ms_order = info_all.order_ms;
     }
     const long long rej = (long long)h_ctr.rejected;
     return rej > INT_MAX ? INT_MAX : (int)rej;
@@ -332,7 +409,9 @@ int gen_args(int n, const void* S, int ldS, const void* T, int ldT, const void* 
     if ((Q && ldQ < ld1) || (Z && ldZ < ld1)) return -5;
     if (n > 0 && !select) return -6;
     if (o.window < 4 || o.window > WMAX || o.chain < 1 || o.chain > o.window - 2) return -10;
-    if (o.precision != GBR_PREC_DMMA || o.sched != GBR_SCHED_SEQUENTIAL) return GBR_ERR_UNSUPPORTED;
+    if (o.precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
+    if (o.sched != GBR_SCHED_PERSISTENT && o.sched != GBR_SCHED_SEQUENTIAL) return -10;
+    if (o.wait_limit_ms < 0) return -10;
     if (o.on_reject != GBR_ON_REJECT_CONTINUE) return GBR_ERR_UNSUPPORTED;
     return 0;
 }
@@ -350,7 +429,7 @@ int gbr_reorder_gen(int n, double* S, int ldS, double* T, int ldT, double* Q, in
                     const gbr_opts* opts, gbr_stats* stats, void* cuda_stream) {
     auto t0 = std::chrono::steady_clock::now();
     gbr_opts o;
-    if (opts) o = *opts; else { gbr_default_opts(&o); o.sched = GBR_SCHED_SEQUENTIAL; }
+    if (opts) o = *opts; else gbr_default_opts(&o);
     int rc = gen_args(n, S, ldS, T, ldT, Q, ldQ, Z, ldZ, select, o);
     if (rc) return rc;
     if (stats) memset(stats, 0, sizeof *stats);
@@ -372,7 +451,7 @@ int gbr_reorder_gen_host(int n, double* S, int ldS, double* T, int ldT, double* 
                          int* m_out, const gbr_opts* opts, gbr_stats* stats, void* cuda_stream) {
     auto t0 = std::chrono::steady_clock::now();
     gbr_opts o;
-    if (opts) o = *opts; else { gbr_default_opts(&o); o.sched = GBR_SCHED_SEQUENTIAL; }
+    if (opts) o = *opts; else gbr_default_opts(&o);
     int rc = gen_args(n, S, ldS, T, ldT, Q, ldQ, Z, ldZ, select, o);
     if (rc) return rc;
     if (stats) memset(stats, 0, sizeof *stats);

@@ -224,7 +224,7 @@ __device__ __forceinline__ void mm_nn(const double* X, const double* Y, double* 
 // Swap on the k x k pair (DA, DB; ld 4, zero beyond k).  On acceptance
 // writes Qs, Zs (identity beyond k) and the new parts NA, NB and returns
 // true; false if a stability test rejects it.
-__device__ __noinline__ bool gen_swap(int p, int q, const double* DA, const double* DB, bool strong,
+static __device__ __noinline__ bool gen_swap(int p, int q, const double* DA, const double* DB, bool strong,
                                       double* Qs, double* Zs, double* NA, double* NB) {
     const int k = p + q;
     double na = 0.0, nb = 0.0;

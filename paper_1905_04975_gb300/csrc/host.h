@@ -30,7 +30,7 @@ int num_sms();
 
 // Device scratch pool (api.cu): one grow-only allocation per device and slot;
 // callers hold api_mutex() while they use it.
-constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_NSLOTS = 8;
+constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_NSLOTS = 9;
 int pool_get(int slot, size_t bytes, void** out);
 std::mutex& api_mutex();
 
@@ -60,7 +60,7 @@ struct Rect {
 };
 
 struct HostTask {
-    int kind, win, y0, rows, mat;  // mat 0 = S, 1 = Q
+    int kind, win, y0, rows, mat;  // mat 0 = S (and T), 1 = Q, 2 = Z
     Rect rc;
     double dur;                     // estimated duration (microseconds)
 };
@@ -76,6 +76,7 @@ struct CostModel {
     double win_us_128 = 2600.0;  // window task at w = 128 (scales as w^2)
     double tile_rate = 6900.0;   // update flops per microsecond of one SM
     double task_us = 2.0;        // fixed cost per update task
+    double lr_mats = 1.0;        // matrices a left/right tile updates (2 for (S, T))
 };
 
 int far_rows(int n);
@@ -83,7 +84,7 @@ void pipeline_order(int n, std::vector<Window>& wins);
 // far: panel rows of the update tiles away from the window (0: far_rows(n));
 // threads: host threads for the dependence search.
 void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostModel& cm,
-                 TaskGraph& G, int far = 0, int threads = 1);
+                 TaskGraph& G, int far = 0, int threads = 1, bool withZ = false);
 void queue_order(const TaskGraph& G, int P, std::vector<int>& order, double* cp_us = nullptr,
                  double* sim_us = nullptr);
 

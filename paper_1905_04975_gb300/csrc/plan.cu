@@ -196,7 +196,7 @@ int far_rows(int n) {
 }
 
 void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostModel& cm,
-                 TaskGraph& G, int far, int threads) {
+                 TaskGraph& G, int far, int threads, bool withZ) {
     const int FAR = far > 0 ? far : far_rows(n);
     std::vector<HostTask>& T = G.t;
     std::vector<std::pair<int, int>> edges;
@@ -212,7 +212,8 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
             const int g = (c - e < UPD_NEAR) ? UPD_BM : FAR;
             int ce = std::min(n, (c / g + 1) * g);
             edges.push_back({iw, (int)T.size()});
-            T.push_back(HostTask{TASK_L, i, c - e, ce - c, 0, Rect{s, e, c, ce}, dur_tile(cm, ce - c, w)});
+            T.push_back(HostTask{TASK_L, i, c - e, ce - c, 0, Rect{s, e, c, ce},
+                                 cm.lr_mats * dur_tile(cm, ce - c, w)});
             c = ce;
         }
         // right panel: rows [0, s); 64-row tiles within UPD_NEAR above the window
@@ -222,7 +223,8 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
             int re = std::min(s, (r / g + 1) * g);
             if (!near && re > s - UPD_NEAR) re = std::max(r + 1, s - UPD_NEAR);
             edges.push_back({iw, (int)T.size()});
-            T.push_back(HostTask{TASK_R, i, r, re - r, 0, Rect{r, re, s, e}, dur_tile(cm, re - r, w)});
+            T.push_back(HostTask{TASK_R, i, r, re - r, 0, Rect{r, re, s, e},
+                                 cm.lr_mats * dur_tile(cm, re - r, w)});
             r = re;
         }
         // Q panel: no window waits on Q, so far tiles throughout
@@ -231,6 +233,14 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
                 int re = std::min(n, (r / FAR + 1) * FAR);
                 edges.push_back({iw, (int)T.size()});
                 T.push_back(HostTask{TASK_Q, i, r, re - r, 1, Rect{r, re, s, e}, dur_tile(cm, re - r, w)});
+                r = re;
+            }
+        // Z panel of a generalized form: like Q, on its own matrix
+        if (withZ)
+            for (int r = 0; r < n;) {
+                int re = std::min(n, (r / FAR + 1) * FAR);
+                edges.push_back({iw, (int)T.size()});
+                T.push_back(HostTask{TASK_Z, i, r, re - r, 2, Rect{r, re, s, e}, dur_tile(cm, re - r, w)});
                 r = re;
             }
     }
@@ -274,15 +284,17 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
         // Q tiles all lie on the FAR row grid, so within a row block two Q
         // tasks conflict exactly when their column ranges overlap: the last Q
         // task per (row block, column) gives the exact, minimal predecessors.
+        // (the same for the Z tiles of a generalized form, in lastz)
         const int myq = (nqb - k + NT - 1) / NT;
         std::vector<int> lastq(withQ ? (size_t)std::max(0, myq) * n : 0, -1);
+        std::vector<int> lastz(withZ ? (size_t)std::max(0, myq) * n : 0, -1);
         std::vector<int> stamp(T.size(), -1);
         for (int t = 0; t < (int)T.size(); ++t) {
             const Rect R = T[t].rc;
-            if (T[t].kind == TASK_Q) {
+            if (T[t].kind == TASK_Q || T[t].kind == TASK_Z) {
                 const int qb = R.r0 / FAR;
                 if (qb % NT != k) continue;
-                int* last = &lastq[(size_t)(qb / NT) * n];
+                int* last = &(T[t].kind == TASK_Q ? lastq : lastz)[(size_t)(qb / NT) * n];
                 int prev = -1;
                 for (int c = R.c0; c < R.c1; ++c) {
                     const int u = last[c];
@@ -467,7 +479,7 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     auto work = [&](size_t i) {
         pipeline_order(plans[i].d.n, plans[i].wins);
         build_graph(plans[i].d.n, plans[i].wins, plans[i].d.Q != nullptr, cm, Gs[i], plans[i].far,
-                    ni >= 64 ? 1 : (int)nth);
+                    ni >= 64 ? 1 : (int)nth, plans[i].d.T != nullptr && plans[i].d.Z != nullptr);
     };
     if (ni >= 64 && nth > 1) {
         std::vector<std::thread> th;
@@ -498,7 +510,8 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
         for (Window w : plans[i].wins) {
             w.inst = (int)i;
             w.u_off = u_total;
-            u_total += (long long)(w.e - w.s) * (w.e - w.s);
+            // a generalized instance keeps UQ and UZ per window
+            u_total += (long long)(w.e - w.s) * (w.e - w.s) * (plans[i].d.T ? 2 : 1);
             wins.push_back(w);
         }
         const TaskGraph& G = Gs[i];

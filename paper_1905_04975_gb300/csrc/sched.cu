@@ -16,6 +16,7 @@
 // requirement.  Every wait is bounded; a wait that runs out sets an error
 // flag, and all CTAs leave the loop at their next check.
 #include "scan_body.cuh"
+#include "gen_body.cuh"
 #include "ozaki.cuh"
 #include "update_body.cuh"
 #include "window_body.cuh"
@@ -27,6 +28,8 @@ namespace {
 constexpr int SCHED_THREADS = win::WIN_THREADS;
 constexpr size_t kMax2(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kSchedSmem = kMax2(kMax2(win::kWindowSmem, upd::kUpdateSmem), oz::kSmem);
+// the generalized (pair) instance of the kernel
+constexpr size_t kSchedSmemPair = kMax2(gen::kGenWindowSmem, upd::kUpdateSmem);
 
 __device__ __forceinline__ int ld_volatile(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
@@ -48,17 +51,51 @@ __device__ __forceinline__ unsigned smid() {
 // names the U held in shared memory by the previous task of this CTA (an
 // update tile of the same window reuses it); key names this task's window.
 // Split-precision tiles run on the tensor cores with the CTA's tensor memory
-// (tmem); if one of their bounded waits runs out, *err is set.
+// (tmem); if one of their bounded waits runs out, *err is set.  PAIR: the
+// instance is a generalized form (S, T) (its own kernel instance, so that the
+// standard path's code and register allocation are untouched).
+template <bool PAIR>
 __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, const Inst& I,
                                          double* Ug, unsigned char* uslices,
                                          int strong, unsigned long long key,
                                          unsigned long long* u_key, unsigned char* smem_raw,
                                          uint32_t tmem, int* err) {
     const int tid = threadIdx.x;
+    const int w = wd.e - wd.s;
     if (tk.kind == TASK_W) {
-        win::window_body(I.n, I.S, I.ldS, wd.s, wd.e - wd.s, I.sel, Ug, strong, I.ctr, smem_raw,
-                         uslices);
+        if constexpr (PAIR)
+            gen::window_gen_body(I.n, I.S, I.ldS, I.T, I.ldT, wd.s, w, I.sel, Ug, Ug + w * w, strong,
+                                 I.ctr, smem_raw);
+        else
+            win::window_body(I.n, I.S, I.ldS, wd.s, w, I.sel, Ug, strong, I.ctr, smem_raw, uslices);
         if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds a U
+        return;
+    }
+    if constexpr (PAIR) {
+        // generalized form: left tiles of S and T by UQ, right tiles of S and
+        // T by UZ, Q by UQ, Z by UZ (UQ then UZ at the window's U offset)
+        const bool byZ = (tk.kind == TASK_R || tk.kind == TASK_Z);
+        const double* U = byZ ? Ug + w * w : Ug;
+        const unsigned long long k2 = (key << 1) | (byZ ? 1ull : 0ull);
+        bool load_u = (*u_key != k2);
+        __syncthreads();
+        const int nm = (tk.kind == TASK_L || tk.kind == TASK_R) ? 2 : 1;
+        for (int mi = 0; mi < nm; ++mi) {
+            double* base;
+            long long rs, ks;
+            int R;
+            const int panel = tk.kind == TASK_Z ? upd::PANEL_Q : tk.kind - TASK_L;
+            double* X = mi ? I.T : I.S;
+            const int ldX = mi ? I.ldT : I.ldS;
+            upd::panel_geom(panel, I.n, wd.s, wd.e, X, ldX, tk.kind == TASK_Z ? I.Z : I.Q,
+                            tk.kind == TASK_Z ? I.ldZ : I.ldQ, &base, &rs, &ks, &R);
+            for (int r = 0; r < tk.rows; r += upd::BM) {
+                upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w, U, load_u,
+                                 smem_raw, &I.ctr->upd_issued);
+                load_u = false;
+            }
+        }
+        if (tid == 0) *u_key = k2;
         return;
     }
     double* base;
@@ -101,6 +138,7 @@ __device__ __forceinline__ void tmem_release(bool need, uint32_t tmem) {
     if ((threadIdx.x >> 5) == 0) oz::tmem_dealloc(tmem, oz::TMEM_COLS);
 }
 
+template <bool PAIR>
 __global__ void __launch_bounds__(SCHED_THREADS, 1)
 sched_kernel(SchedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,7 +179,7 @@ sched_kernel(SchedParams P) {
         const SchedTask tk = P.tasks[t];
         const Window wd = P.wins[tk.win];
         const Inst I = P.inst[wd.inst];
-        run_task(tk, wd, I, P.upool + wd.u_off,
+        run_task<PAIR>(tk, wd, I, P.upool + wd.u_off,
                  P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
                  P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err);
         // release: every thread's writes are ordered before the counters drop
@@ -251,7 +289,7 @@ server_kernel(SrvParams P) {
                 wd.inst = 0;
                 wd.u_off = __ldcg(&wp->u_off);
             }
-            run_task(tk, wd, R.inst, R.upool + wd.u_off,
+            run_task<false>(tk, wd, R.inst, R.upool + wd.u_off,
                      R.uslices ? R.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
                      P.strong, ((unsigned long long)(unsigned)R.id << 32) | (unsigned)tk.win, &u_key,
                      smem_raw, tmem, P.err);
@@ -285,8 +323,11 @@ cudaError_t sched_configure() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && configured[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(sched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSchedSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSchedSmemPair);
     if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = true;
     return e;
 }
@@ -309,7 +350,10 @@ cudaError_t launch_server(const SrvParams& P, int grid, cudaStream_t st) {
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st) {
     cudaError_t e = sched_configure();
     if (e != cudaSuccess) return e;
-    sched_kernel<<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
+    if (P.pair)
+        sched_kernel<true><<<grid, SCHED_THREADS, kSchedSmemPair, st>>>(P);
+    else
+        sched_kernel<false><<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
     return cudaGetLastError();
 }
 

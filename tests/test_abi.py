@@ -114,7 +114,8 @@ def test_eigenvectors_argument_checks(lib):
 
 def test_reorder_gen_argument_checks(lib):
     """gbr_reorder_gen checks its arguments before any GPU work; options
-    the pair path does not build are refused; n = 0 is a no-op."""
+    the pair path does not build (split precision) are refused; n = 0 is a
+    no-op."""
     d = ctypes.c_void_p(0x1000)  # never dereferenced
     sel = np.zeros(4, dtype=np.int32)
     ip = sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int))

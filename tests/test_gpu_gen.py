@@ -106,13 +106,14 @@ def test_tiny_all_windows(gbr, n, seed):
 @pytest.mark.parametrize("name,n,w,m", [("n60", 60, 16, 6), ("n200", 200, 64, 32),
                                         ("n200-narrow", 200, 24, 10), ("g400", 400, 64, 32),
                                         ("ragged515", 515, 64, 30)])
-def test_matches_oracle(gbr, name, n, w, m):
+@pytest.mark.parametrize("sched", ["persistent", "sequential"])
+def test_matches_oracle(gbr, name, n, w, m, sched):
     if name == "g400":
         S, T, Q, Z, sel = si.gen_config("g400")
     else:
         S, T, Q, Z, sel = si.gen_problem(n, n + 3, select_frac=0.4, reflectors=16)
     ref = oracle.gen_reorder(S, T, Q, Z, sel)
-    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m)
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m, sched=sched)
     assert r.status == 0 and r.stats.swaps == ref["nswaps"]
     check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg, ref)
 
@@ -153,6 +154,8 @@ def test_rejected_swap_leaves_pair_unchanged(gbr):
     I4 = np.asfortranarray(np.eye(4))
     r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, I4, I4, [0, 0, 1, 1], window=8, chain=3)
     assert r.status == 1 and r.stats.rejected == 1
+    r2, *_ = run_gpu(gbr, S, T, I4, I4, [0, 0, 1, 1], window=8, chain=3, sched="sequential")
+    assert r2.status == 1
     assert np.array_equal(Sg, S) and np.array_equal(Tg, T)
     assert np.array_equal(Qg, I4) and np.array_equal(Zg, I4)
 
@@ -173,3 +176,18 @@ def test_g4000_workload(gbr):
     r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel)
     assert r.status == 0
     check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg)
+
+
+@pytest.mark.parametrize("n,w,m", [(300, 64, 32), (515, 32, 12)])
+def test_persistent_matches_sequential(gbr, n, w, m):
+    """The persistent schedule (one launch, tasks ordered by dependences on
+    exact rectangles of S/T, Q and Z) and the per-window launch pairs compute
+    the same reordering up to the rounding of commuting updates."""
+    S, T, Q, Z, sel = si.gen_problem(n, 31 + n, select_frac=0.45, reflectors=16)
+    rp, Sp, Tp, Qp, Zp = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m, sched="persistent")
+    rs, Ss, Ts, Qs, Zs = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m, sched="sequential")
+    assert rp.status == rs.status == 0
+    assert rp.stats.tasks > 0 and rs.stats.tasks == 0
+    for a, b, ref in ((Sp, Ss, S), (Tp, Ts, T), (Qp, Qs, Q), (Zp, Zs, Z)):
+        assert np.linalg.norm(a - b) <= 50 * n * EPS * np.linalg.norm(ref)
+    check(S, T, Q, Z, sel, rp, Sp, Tp, Qp, Zp)
