@@ -55,6 +55,8 @@ WORKLOADS = {
                        q="64 Householder reflectors", window=128, chain=64),
     "serve": dict(name="serve", kind="serve", nmin=64, nmax=8192, select="U(0.1, 0.6)",
                   q="8 Householder reflectors", mem_cap=60e9),
+    "g4000": dict(name="g4000", kind="gen", n=4000, select=0.35,
+                  q="Q and Z: 64 Householder reflectors each", window=64, chain=32),
 }
 METRIC = "selected eigenvalues reordered per second"
 
@@ -149,11 +151,15 @@ def make_inputs(wl, seed=0):
     return si.config("n4000" if wl["name"] == "eigvec4000" else wl["name"], seed)
 
 
-def cpu_oracle_sample(S, Q, sel, budget_s=15.0):
+def cpu_oracle_sample(S, Q, sel, budget_s=15.0, run=None, what="workload"):
     """Time the oracle on the first k selected blocks (top to bottom) of the
     workload, k grown until ~budget_s of work, and extrapolate to the whole
-    workload by the number of adjacent block swaps it needs."""
+    workload by the number of adjacent block swaps it needs.  run(sub_sel)
+    runs the oracle and returns its result dict (default: the standard-form
+    reordering of (S, Q))."""
     import oracle
+    if run is None:
+        run = lambda sub_sel: oracle.reorder(S, Q, sub_sel)
     n = S.shape[0]
     sub = np.append(np.diag(S, -1) != 0, False)
     starts, sizes = [], []
@@ -188,7 +194,7 @@ def cpu_oracle_sample(S, Q, sel, budget_s=15.0):
                 sub_sel[s:s + sz] = 1
                 taken += 1
         t0 = time.perf_counter()
-        r = oracle.reorder(S, Q, sub_sel)
+        r = run(sub_sel)
         dt = time.perf_counter() - t0
         if dt >= budget_s / 3 or k >= nsel_blocks:
             break
@@ -196,7 +202,7 @@ def cpu_oracle_sample(S, Q, sel, budget_s=15.0):
     est_full = dt * full_swaps / max(r["nswaps"], 1)
     nsel = int(np.sum([sz for sz, f in zip(sizes, selb) if f]))
     return {"value": nsel / est_full, "unit": "eigs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"first {k} of {nsel_blocks} selected blocks of the n={n} workload "
+            "sample": (f"first {k} of {nsel_blocks} selected blocks of the n={n} {what} "
                        f"({r['nswaps']} of {full_swaps} block swaps) timed {dt:.1f} s on 1 core, "
                        f"scaled by swap count to the full workload (est. {est_full:.0f} s)")}
 
@@ -239,6 +245,15 @@ def run_reference(args, wl):
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
+    elif wl.get("kind") == "gen":
+        import oracle
+        S, T, Q, Z, sel = si.gen_config(wl["name"])
+        nsel = int(expected_selected(S, sel))
+        sample = lambda: cpu_oracle_sample(
+            S, Q, sel, budget_s=8.0, what="pair workload",
+            run=lambda ss: oracle.gen_reorder(S, T, Q, Z, ss))
+        cfg = {"workload": wl["name"], "n": wl["n"], "select": wl["select"], "q": wl["q"],
+               "window": wl["window"], "chain": wl["chain"]}
     elif wl.get("kind") == "batch":
         probs = batch_inputs(wl)
         nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
@@ -620,6 +635,125 @@ def eigvec_cpu_sample(S, Q, step=16):
                        f"to all eigenvectors (est. {est:.1f} s)")}
 
 
+def run_gen(args, wl):
+    """Generalized reordering of the n = 4000 pair (S, T) with Q and Z
+    (Eq. 7, second form): selected eigenvalues reordered per second."""
+    import torch
+    import paper_1905_04975_gb300 as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+    mats = si.gen_config(wl["name"])
+    sel = mats[4]
+    S_np = mats[0]
+    n = S_np.shape[0]
+    nsel = expected_selected(S_np, sel)
+    pristine = [g.to_device(X) for X in mats[:4]]
+    work = [g.to_device(X) for X in mats[:4]]
+    stream = torch.cuda.Stream()
+    opts = g.make_opts(window=wl["window"], chain=wl["chain"], timing=True, sched=args.sched)
+
+    def step():
+        with torch.cuda.stream(stream):
+            for a, b in zip(work, pristine):
+                a.copy_(b)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = g.reorder_gen(*work, sel, opts=opts, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        r, _ = step()
+        assert r.status == 0, r.status
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            r, t = step()
+            ms.append(t)
+            stats.append(r.stats)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    value, total_ms = whole_job_rate(nsel * args.steps, sum(ms), dist, "cuda")
+    st0 = stats[0]
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)
+    flops_iss = st0.upd_flops_issued if st0.upd_flops_issued > 0 else st0.upd_flops
+    if args.sched == "persistent":
+        ms_k = sum(s.ms_sched for s in stats) / len(stats)
+        kern = "sched_kernel<pair> (persistent: pair window tasks + DMMA tiles of S, T, Q, Z)"
+        work_fl = flops_iss + st0.win_flops
+    else:
+        ms_k = sum(s.ms_update for s in stats) / len(stats)
+        kern = "update_gen_kernel (DMMA FP64 Y <- Y U on S, T, Q, Z)"
+        work_fl = flops_iss
+    achieved = work_fl / (ms_k / 1e3) / 1e12
+    roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "traffic": NCU_TRAFFIC.get((wl["name"], args.sched)),
+            "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
+                            "1.25/2250 (FP64 DMMA probe: 1.047 TF/s)"),
+            "flops_per_launch": work_fl, "update_flops_dense": st0.upd_flops,
+            "update_flops_issued": flops_iss, "window_flops": st0.win_flops,
+            "avg_launch_ms": ms_k,
+            "critical_path_model_ms": sum(s.sched_cp_ms for s in stats) / len(stats),
+            "share_of_step": ms_k / (total_ms / args.steps)}
+    e2e = None
+    if args.e2e_steps > 0:
+        pins = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
+        views = [p.numpy().T for p in pins]  # Fortran-ordered views of the pinned buffers
+        et = []
+        for i in range(args.e2e_steps + 1):
+            for v, X in zip(views, mats[:4]):
+                v[:] = X
+            t0 = time.perf_counter()
+            g.reorder_gen_host(*views, sel, opts=opts, stream=stream)
+            dt = time.perf_counter() - t0
+            if i > 0:
+                et.append(dt)
+        e2e = {"value": nsel * len(et) / sum(et) * world, "unit": "eigs/s",
+               "h2d_bytes_per_step": 4 * n * n * 8 + 4 * n,
+               "d2h_bytes_per_step": 4 * n * n * 8 + 2 * 8 * n}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        cpu = cpu_oracle_sample(S_np, mats[2], sel, what="pair workload",
+                                run=lambda ss: oracle.gen_reorder(*mats[:4], ss))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "eigs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "n": n, "select": wl["select"],
+                           "selected_eigs": nsel, "q": wl["q"], "window": wl["window"],
+                           "chain": wl["chain"], "precision": "dmma", "sched": args.sched,
+                           "l2": "S, T, Q, Z (512 MB > L2) restored from device copies before "
+                                 "each step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": int(sum(s.launches for s in stats)),
+                "detail": {"windows": int(st0.windows), "chains": int(st0.chains),
+                           "tasks": int(st0.tasks), "swaps": int(st0.swaps),
+                           "ms_graph": st0.ms_graph, "ms_order": st0.ms_order}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_eigvec(args, wl):
     """Eigenvectors (Eq. 5) of every eigenvalue of the n = 4000 Schur form,
     back-transformed by its Q (Eq. 6): eigenvectors per second."""
@@ -757,6 +891,8 @@ def main():
         return run_serve(args, wl)
     if wl.get("kind") == "eigvec":
         return run_eigvec(args, wl)
+    if wl.get("kind") == "gen":
+        return run_gen(args, wl)
 
     import torch
     import paper_1905_04975_gb300 as g

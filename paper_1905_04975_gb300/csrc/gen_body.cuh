@@ -40,9 +40,11 @@ constexpr uint8_t GSEL_WALL = 3;       // window edge row of a 2x2 block cut by 
 __host__ __device__ constexpr int gpoff(int c) { return (c * (c + 3)) / 2; }
 
 // Shared memory of window_gen_body: UQ, UZ (GW x GW each), packed windows
-// of S and T (column c keeps rows 0..c+1), Qs and Zs per swap slot.
+// of S and T (column c keeps rows 0..c+1), a 128-double scratch per swap
+// slot (gen_swap_octet: its Qs and Zs stay there for the updates).
+constexpr int GSLOT = 128;
 constexpr size_t kGenWindowSmem =
-    sizeof(double) * (2 * (size_t)GW * GW + 2 * (size_t)gpoff(GW) + (size_t)GMAXSW * 32) +
+    sizeof(double) * (2 * (size_t)GW * GW + 2 * (size_t)gpoff(GW) + (size_t)GMAXSW * GSLOT) +
     sizeof(int) * 3 * GMAXSW + 2 * GW;
 
 // |x| order through the bit pattern: for non-negative doubles the integer
@@ -51,17 +53,48 @@ __device__ __forceinline__ unsigned long long mag(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
+// ---------------------------------------------------------------------------
+// Swap of one pair of adjacent blocks by an octet: 8 lanes of a warp.
+//
+// An FP64 instruction costs the same issue slot for 1 or 32 active lanes, so
+// the swap's arithmetic is spread over 8 lanes instead of running on one:
+//   - the Kronecker system (N = 2pq <= 8 unknowns): lane r owns row r;
+//     complete pivoting by an octet arg-max (integer compares on the bit
+//     patterns), row and column exchanges by shuffles, one division per
+//     elimination step; back substitution column by column;
+//   - the two QR factors: lanes 0-3 build column l of Qs, lanes 4-7 column
+//     l - 4 of Zs (each half from its own reflectors);
+//   - the 4 x 4 products, the tests and the rotations of T's new 2x2 blocks:
+//     lane l owns entries 2l, 2l + 1 (column l / 2) of each k x k result,
+//     exchanged through the slot's shared-memory scratch.
+// All loops have the same trip counts on the 8 lanes; shuffles and
+// __syncwarp name the octet's lanes only.
+// ---------------------------------------------------------------------------
+
+// Per-slot scratch (doubles, column-major 4 x 4 each, zero / identity beyond
+// k): DA DB Qs Zs WA WB NA NB.
+constexpr int SC_DA = 0, SC_DB = 16, SC_Q = 32, SC_Z = 48, SC_WA = 64, SC_WB = 80, SC_NA = 96,
+              SC_NB = 112;
+static_assert(SC_NB + 16 <= GSLOT, "slot scratch");
+
+__device__ __forceinline__ double pick8(const double (&v)[8], int i) {
+    double r = v[0];
+#pragma unroll
+    for (int c = 1; c < 8; ++c) r = (i == c) ? v[c] : r;
+    return r;
+}
+
 // Reflector (I - tau v v^T) on 4-vectors mapping x onto beta e_0, v[0] = 1;
 // tau = 0 when x is a multiple of e_0 already.
 __device__ __forceinline__ void house4(const double x[4], double v[4], double* tau) {
-    const double sigma = x[1] * x[1] + x[2] * x[2] + x[3] * x[3];
+    const double sigma = fma(x[1], x[1], fma(x[2], x[2], x[3] * x[3]));
     v[0] = 1.0;
     v[1] = x[1];
     v[2] = x[2];
     v[3] = x[3];
     *tau = 0.0;
     if (sigma != 0.0) {
-        const double nrm = sqrt(x[0] * x[0] + sigma);
+        const double nrm = sqrt(fma(x[0], x[0], sigma));
         const double beta = x[0] >= 0.0 ? -nrm : nrm;
         const double inv = 1.0 / (x[0] - beta);
         v[1] *= inv;
@@ -71,243 +104,293 @@ __device__ __forceinline__ void house4(const double x[4], double v[4], double* t
     }
 }
 
-// Orthogonal factor Qo (4 x 4, column-major, identity beyond k) of the QR
-// factorization of the k x q matrix [X; gamma I], X p x q (column-major,
-// ld p): reflector H1 for column 0 on rows 0..3 (rows >= k are zero), H2 for
-// column 1 on rows 1..3 when q == 2; Qo = H1 diag(1, H2).
-__device__ __forceinline__ void qr_orth(int p, int q, const double* X, double gamma, double Qo[16]) {
-    double M0[4], M1[4];
+// Returns true (on all 8 lanes) if the swap of the p x p block at ja with the
+// q x q block below it is accepted; sc (the slot's scratch) then holds Qs,
+// Zs and the new diagonal parts NA, NB.  l: lane in the octet; ob: lane of
+// the octet's lane 0 in the warp; om: the octet's lane mask.
+__device__ __forceinline__ bool gen_swap_octet(int p, int q, const double* __restrict__ Sp,
+                                               const double* __restrict__ Tp, int ja, bool strong,
+                                               int l, int ob, unsigned om, double* __restrict__ sc) {
+    const int k = p + q, pq = p * q, N = 2 * pq;
+    // own entries e = 2l, 2l+1: column c0 = l / 2, rows r0, r0 + 1
+    const int ec = l >> 1, er = (l & 1) * 2;
+    double pa = 0.0, pb = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        M0[i] = i < p ? X[i] : (i == p ? gamma : 0.0);
-        M1[i] = (q == 2) ? (i < p ? X[i + p] : (i == p + 1 ? gamma : 0.0)) : 0.0;
+    for (int t = 0; t < 2; ++t) {
+        const int r = er + t;
+        const bool in = ec < k && r < k && r <= ec + 1;
+        const double a = in ? Sp[gpoff(ja + ec) + ja + r] : 0.0;
+        const double b = in ? Tp[gpoff(ja + ec) + ja + r] : 0.0;
+        sc[SC_DA + ec * 4 + r] = a;
+        sc[SC_DB + ec * 4 + r] = b;
+        pa = fma(a, a, pa);
+        pb = fma(b, b, pb);
     }
-    double v1[4], v2[4], t1, t2 = 0.0;
-    house4(M0, v1, &t1);
-    v2[0] = 1.0; v2[1] = v2[2] = v2[3] = 0.0;
-    if (q == 2) {
-        double d = 0.0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) d = fma(v1[i], M1[i], d);
-        d *= t1;
-        double x2[4];
-#pragma unroll
-        for (int i = 1; i < 4; ++i) x2[i - 1] = fma(-d, v1[i], M1[i]);
-        x2[3] = 0.0;
-        house4(x2, v2, &t2);
+    for (int o = 1; o < 8; o <<= 1) {
+        pa += __shfl_xor_sync(om, pa, o);
+        pb += __shfl_xor_sync(om, pb, o);
     }
-    // H1 explicitly, then the right product with diag(1, H2) on columns 1..3
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) Qo[c * 4 + r] = (r == c ? 1.0 : 0.0) - t1 * v1[r] * v1[c];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        double d = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d = fma(Qo[(i + 1) * 4 + r], v2[i], d);
-        d *= t2;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) Qo[(i + 1) * 4 + r] = fma(-d, v2[i], Qo[(i + 1) * 4 + r]);
-    }
-}
-
-// Generalized Sylvester solve (see the file comment) on the Kronecker
-// system of N = 2pq unknowns x = [vec R; vec L]; Gaussian elimination with
-// complete pivoting, pivots below max(eps max|K|, DBL_MIN) raised to that
-// value, and gamma <= 1 scaling the right-hand side so that no division in
-// the back substitution overflows.  DA, DB: k x k (ld 4).  R, L: p x q
-// (column-major, ld p).  Returns gamma.
-__device__ __forceinline__ double gen_sylvester(int p, int q, const double* DA, const double* DB,
-                                                double* R, double* L) {
-    const int pq = p * q, N = 2 * pq;
-    double K[64], b[8], y[8];
-    int perm[8];
-    for (int i = 0; i < 64; ++i) K[i] = 0.0;
-    for (int e = 0; e < 2; ++e) {
-        const double* D = e ? DB : DA;
-        for (int c = 0; c < q; ++c)
-            for (int i = 0; i < p; ++i) {
-                const int row = e * pq + i + p * c;
-                b[row] = -D[(p + c) * 4 + i];
-                for (int l = 0; l < p; ++l) K[row * 8 + l + p * c] += D[l * 4 + i];
-                for (int m = 0; m < q; ++m) K[row * 8 + pq + i + p * m] -= D[(p + c) * 4 + p + m];
-            }
-    }
-    unsigned long long km = 0;
-    for (int r = 0; r < N; ++r)
-        for (int c = 0; c < N; ++c) km = max(km, mag(K[r * 8 + c]));
-    double smin = DBL_EPSILON * __longlong_as_double((long long)km);
-    smin = smin < DBL_MIN ? DBL_MIN : smin;
-    for (int c = 0; c < N; ++c) perm[c] = c;
-    for (int s = 0; s < N; ++s) {
-        int pr = s, pc = s;
-        unsigned long long best = 0;
-        bool any = false;
-        for (int r = s; r < N; ++r)
-            for (int c = s; c < N; ++c) {
-                const unsigned long long v = mag(K[r * 8 + c]);
-                if (!any || v > best) { best = v; pr = r; pc = c; any = true; }
-            }
-        if (pr != s) {
-            for (int c = 0; c < N; ++c) {
-                const double t = K[s * 8 + c];
-                K[s * 8 + c] = K[pr * 8 + c];
-                K[pr * 8 + c] = t;
-            }
-            const double t = b[s]; b[s] = b[pr]; b[pr] = t;
-        }
-        if (pc != s) {
-            for (int r = 0; r < N; ++r) {
-                const double t = K[r * 8 + s];
-                K[r * 8 + s] = K[r * 8 + pc];
-                K[r * 8 + pc] = t;
-            }
-            const int t = perm[s]; perm[s] = perm[pc]; perm[pc] = t;
-        }
-        if (fabs(K[s * 8 + s]) < smin) K[s * 8 + s] = smin;
-        const double piv = K[s * 8 + s];
-        for (int r = s + 1; r < N; ++r) {
-            const double f = K[r * 8 + s] / piv;
-            K[r * 8 + s] = 0.0;
-            for (int c = s + 1; c < N; ++c) K[r * 8 + c] = fma(-f, K[s * 8 + c], K[r * 8 + c]);
-            b[r] = fma(-f, b[s], b[r]);
-        }
-    }
-    double g = 1.0;
-    const double big = DBL_MAX / 4.0;
-    for (int s = N - 1; s >= 0; --s) {
-        double acc = b[s];
-        for (int c = s + 1; c < N; ++c) acc = fma(-K[s * 8 + c], y[c], acc);
-        const double pv = fabs(K[s * 8 + s]);
-        if (pv < 1.0 && fabs(acc) > big * pv) {
-            const double f = (big * pv) / fabs(acc);
-            for (int c = 0; c < N; ++c) b[c] *= f;
-            for (int c = s + 1; c < N; ++c) y[c] *= f;
-            acc *= f;
-            g *= f;
-        }
-        y[s] = acc / K[s * 8 + s];
-    }
-    for (int c = 0; c < N; ++c) {
-        const int u = perm[c];
-        if (u < pq) R[u] = y[c];
-        else L[u - pq] = y[c];
-    }
-    return g;
-}
-
-// C = X^T Y and C = X Y (4 x 4, column-major).
-__device__ __forceinline__ void mm_tn(const double* X, const double* Y, double* C) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            double s = 0.0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) s = fma(X[r * 4 + t], Y[c * 4 + t], s);
-            C[c * 4 + r] = s;
-        }
-}
-__device__ __forceinline__ void mm_nn(const double* X, const double* Y, double* C) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            double s = 0.0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) s = fma(X[t * 4 + r], Y[c * 4 + t], s);
-            C[c * 4 + r] = s;
-        }
-}
-
-// Swap on the k x k pair (DA, DB; ld 4, zero beyond k).  On acceptance
-// writes Qs, Zs (identity beyond k) and the new parts NA, NB and returns
-// true; false if a stability test rejects it.
-static __device__ __noinline__ bool gen_swap(int p, int q, const double* DA, const double* DB, bool strong,
-                                      double* Qs, double* Zs, double* NA, double* NB) {
-    const int k = p + q;
-    double na = 0.0, nb = 0.0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        na = fma(DA[i], DA[i], na);
-        nb = fma(DB[i], DB[i], nb);
-    }
-    const double tha = fmax(20.0 * DBL_EPSILON * sqrt(na), DBL_MIN);
-    const double thb = fmax(20.0 * DBL_EPSILON * sqrt(nb), DBL_MIN);
+    const double tha = fmax(20.0 * DBL_EPSILON * sqrt(pa), DBL_MIN);
+    const double thb = fmax(20.0 * DBL_EPSILON * sqrt(pb), DBL_MIN);
+    __syncwarp(om);
+    const double* DA = sc + SC_DA;
+    const double* DB = sc + SC_DB;
     if (k == 2 && DA[0] * DB[5] == DA[5] * DB[0]) {
-        // equal generalized eigenvalues: in order already
+        // equal generalized eigenvalues: in order already (identity factors)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            Qs[i] = Zs[i] = ((i & 3) == (i >> 2)) ? 1.0 : 0.0;
-            NA[i] = DA[i];
-            NB[i] = DB[i];
+        for (int t = 0; t < 2; ++t) {
+            const int e = 2 * l + t;
+            const double id = ((e & 3) == (e >> 2)) ? 1.0 : 0.0;
+            sc[SC_Q + e] = id;
+            sc[SC_Z + e] = id;
+            sc[SC_NA + e] = DA[e];
+            sc[SC_NB + e] = DB[e];
         }
+        __syncwarp(om);
         return true;
     }
-    double R[4], L[4];
-    const double g = gen_sylvester(p, q, DA, DB, R, L);
-    qr_orth(p, q, L, g, Qs);
-    qr_orth(p, q, R, g, Zs);
-    double W[16];
-    mm_tn(Qs, DA, W);
-    mm_nn(W, Zs, NA);
-    mm_tn(Qs, DB, W);
-    mm_nn(W, Zs, NB);
-    unsigned long long la = 0, lb = 0;
+
+    // --- Kronecker row l: unknowns [vec R; vec L], equations [first; second]
+    double K[8], b = 0.0;
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < 8; ++c) K[c] = 0.0;
+    if (l < N) {
+        const int e = l / pq, rem = l - e * pq, i = rem % p, cc = rem / p;
+        const double* D = e ? DB : DA;
+        b = -D[(p + cc) * 4 + i];
 #pragma unroll
-        for (int r = 1; r < 4; ++r)
-            if (c < q && r >= q && r < k) {
-                la = max(la, mag(NA[c * 4 + r]));
-                lb = max(lb, mag(NB[c * 4 + r]));
-                NA[c * 4 + r] = 0.0;
-                NB[c * 4 + r] = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            double v = 0.0;
+            if (c < pq) {
+                if (c / p == cc) v += D[(c % p) * 4 + i];          // X11[i][l'] R[l'][cc]
+            } else if (c < N) {
+                const int u = c - pq;
+                if (u % p == i) v -= D[(p + cc) * 4 + p + u / p];  // -L[i][m] X22[m][cc]
             }
-    if (la > mag(tha) || lb > mag(thb)) return false;
-    if (strong) {
-        // D - Qs N Zs^T with the lower-left block zeroed
-        for (int e = 0; e < 2; ++e) {
-            const double* N0 = e ? NB : NA;
-            const double* D = e ? DB : DA;
-            double V[16];
-            mm_nn(Qs, N0, V);
-            unsigned long long err = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) s = fma(V[t * 4 + r], Zs[t * 4 + c], s);
-                    err = max(err, mag(s - D[c * 4 + r]));
-                }
-            if (err > mag(e ? thb : tha)) return false;
+            K[c] = v;
         }
     }
-    // T stays upper triangular: rotate the columns of each new 2x2 block
+    unsigned long long km = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) km = max(km, mag(K[c]));
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const unsigned long long v = __shfl_xor_sync(om, km, o);
+        km = max(km, v);
+    }
+    const double smin = fmax(DBL_EPSILON * __longlong_as_double((long long)km), DBL_MIN);
+    int perm = l;
+    for (int s = 0; s < N; ++s) {
+        // arg-max over rows >= s, columns [s, N): (magnitude, row * 8 + col),
+        // the first in row-major order on ties
+        unsigned long long bm = 0;
+        int bi = 64;
+        if (l >= s && l < N) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const unsigned long long v = mag(K[c]);
+                if (c >= s && c < N && (bi == 64 || v > bm)) { bm = v; bi = l * 8 + c; }
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned long long v = __shfl_xor_sync(om, bm, o);
+            const int vi = __shfl_xor_sync(om, bi, o);
+            if (vi != 64 && (bi == 64 || v > bm || (v == bm && vi < bi))) { bm = v; bi = vi; }
+        }
+        const int pr = bi >> 3, pc = bi & 7;
+        // rows s <-> pr
+        const int prt = (l == s) ? pr : (l == pr ? s : l);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) K[c] = __shfl_sync(om, K[c], ob + prt);
+        b = __shfl_sync(om, b, ob + prt);
+        // columns s <-> pc
+        {
+            const double vs = pick8(K, s), vp = pick8(K, pc);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) K[c] = (c == s) ? vp : ((c == pc) ? vs : K[c]);
+            const int pct = (l == s) ? pc : (l == pc ? s : l);
+            perm = __shfl_sync(om, perm, ob + pct);
+        }
+        if (l == s && mag(pick8(K, s)) < mag(smin)) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) K[c] = (c == s) ? smin : K[c];
+        }
+        // eliminate below the pivot
+        double prow[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) prow[c] = __shfl_sync(om, K[c], ob + s);
+        const double pbv = __shfl_sync(om, b, ob + s);
+        const double piv = pick8(prow, s);
+        if (l > s && l < N) {
+            const double f = pick8(K, s) / piv;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) K[c] = (c > s) ? fma(-f, prow[c], K[c]) : (c == s ? 0.0 : K[c]);
+            b = fma(-f, pbv, b);
+        }
+    }
+    // back substitution, column by column: acc holds row l's remaining sum
+    double acc = b, y = 0.0, g = 1.0;
+    const double big = DBL_MAX / 4.0;
+    for (int s = N - 1; s >= 0; --s) {
+        double f = 1.0;
+        if (l == s) {
+            const double pv = fabs(pick8(K, s));
+            if (pv < 1.0 && fabs(acc) > big * pv) f = (big * pv) / fabs(acc);
+        }
+        f = __shfl_sync(om, f, ob + s);
+        if (f != 1.0) {
+            acc *= f;
+            y *= f;
+            g *= f;
+        }
+        if (l == s) y = acc / pick8(K, s);
+        const double ys = __shfl_sync(om, y, ob + s);
+        if (l < s) acc = fma(-pick8(K, s), ys, acc);
+    }
+    // unknown perm[c] = y of lane c: gather R (lanes 0-3 need L, 4-7 need R)
+    double X[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool zhalf = l >= 4;
+    for (int c = 0; c < N; ++c) {
+        const double v = __shfl_sync(om, y, ob + c);
+        const int u = __shfl_sync(om, perm, ob + c);
+        const int want = zhalf ? (u < pq ? u : -1) : u - pq;   // R for Zs, L for Qs
+#pragma unroll
+        for (int t = 0; t < 4; ++t) X[t] = (want == t) ? v : X[t];
+    }
+    // --- QR factor: column (l & 3) of Qs (lanes 0-3, from [L; g I]) or of
+    // Zs (lanes 4-7, from [R; g I]); H1 for column 0, H2 on rows 1..3
+    {
+        double M0[4], M1[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            M0[i] = i < p ? X[i] : (i == p ? g : 0.0);
+            M1[i] = (q == 2) ? (i < p ? X[i + p] : (i == p + 1 ? g : 0.0)) : 0.0;
+        }
+        double v1[4], v2[4], t1, t2 = 0.0;
+        house4(M0, v1, &t1);
+        v2[0] = 1.0; v2[1] = v2[2] = v2[3] = 0.0;
+        if (q == 2) {
+            double d = 0.0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d = fma(v1[i], M1[i], d);
+            d *= t1;
+            double x2[4];
+#pragma unroll
+            for (int i = 1; i < 4; ++i) x2[i - 1] = fma(-d, v1[i], M1[i]);
+            x2[3] = 0.0;
+            house4(x2, v2, &t2);
+        }
+        // column c of H1 diag(1, H2): w = diag(1, H2) e_c, then H1 w
+        const int c = l & 3;
+        double w[4];
+        w[0] = (c == 0) ? 1.0 : 0.0;
+#pragma unroll
+        for (int i = 1; i < 4; ++i)
+            w[i] = (c == 0) ? 0.0 : (((i == c) ? 1.0 : 0.0) - t2 * v2[i - 1] * v2[c - 1]);
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d = fma(v1[i], w[i], d);
+        d *= t1;
+        double* out = sc + (zhalf ? SC_Z : SC_Q) + c * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] = fma(-d, v1[i], w[i]);
+    }
+    __syncwarp(om);
+    const double* Qs = sc + SC_Q;
+    const double* Zs = sc + SC_Z;
+    // --- W = Qs^T D (own entries), then N = W Zs
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int r = er + t;
+        double wa = 0.0, wb = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            wa = fma(Qs[r * 4 + a], DA[ec * 4 + a], wa);
+            wb = fma(Qs[r * 4 + a], DB[ec * 4 + a], wb);
+        }
+        sc[SC_WA + ec * 4 + r] = wa;
+        sc[SC_WB + ec * 4 + r] = wb;
+    }
+    __syncwarp(om);
+    bool low = false;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int r = er + t;
+        double na = 0.0, nb = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            na = fma(sc[SC_WA + a * 4 + r], Zs[ec * 4 + a], na);
+            nb = fma(sc[SC_WB + a * 4 + r], Zs[ec * 4 + a], nb);
+        }
+        // weak test on the block that must vanish: rows [q, k) x columns [0, q)
+        if (ec < q && r >= q && r < k) {
+            low |= mag(na) > mag(tha) || mag(nb) > mag(thb);
+            na = 0.0;
+            nb = 0.0;
+        }
+        sc[SC_NA + ec * 4 + r] = na;
+        sc[SC_NB + ec * 4 + r] = nb;
+    }
+    if (__any_sync(om, low)) return false;
+    __syncwarp(om);
+    if (strong) {
+        // V = Qs N (into W), then D - V Zs^T must stay below the thresholds
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int r = er + t;
+            double va = 0.0, vb = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                va = fma(Qs[a * 4 + r], sc[SC_NA + ec * 4 + a], va);
+                vb = fma(Qs[a * 4 + r], sc[SC_NB + ec * 4 + a], vb);
+            }
+            sc[SC_WA + ec * 4 + r] = va;
+            sc[SC_WB + ec * 4 + r] = vb;
+        }
+        __syncwarp(om);
+        bool bad = false;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int r = er + t;
+            double ea = 0.0, eb = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                ea = fma(sc[SC_WA + a * 4 + r], Zs[a * 4 + ec], ea);
+                eb = fma(sc[SC_WB + a * 4 + r], Zs[a * 4 + ec], eb);
+            }
+            bad |= mag(ea - DA[ec * 4 + r]) > mag(tha) || mag(eb - DB[ec * 4 + r]) > mag(thb);
+        }
+        if (__any_sync(om, bad)) return false;
+    }
+    // --- T stays upper triangular: rotate the two columns of each new 2x2
+    // block (lanes 0-3: rows of NA, lanes 4-7: rows of NB, then all of Zs)
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
         const int sz = blk ? p : q, c0 = blk ? q : 0;
         if (sz != 2) continue;
-        const double b10 = NB[c0 * 4 + c0 + 1], b11 = NB[(c0 + 1) * 4 + c0 + 1];
+        const double b10 = sc[SC_NB + c0 * 4 + c0 + 1], b11 = sc[SC_NB + (c0 + 1) * 4 + c0 + 1];
         if (b10 == 0.0) continue;
         const double h = hypot(b10, b11);
         const double cs = b11 / h, sn = -b10 / h;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            double x = NA[c0 * 4 + r], y = NA[(c0 + 1) * 4 + r];
-            NA[c0 * 4 + r] = fma(cs, x, sn * y);
-            NA[(c0 + 1) * 4 + r] = fma(cs, y, -sn * x);
-            x = NB[c0 * 4 + r]; y = NB[(c0 + 1) * 4 + r];
-            NB[c0 * 4 + r] = fma(cs, x, sn * y);
-            NB[(c0 + 1) * 4 + r] = fma(cs, y, -sn * x);
-            x = Zs[c0 * 4 + r]; y = Zs[(c0 + 1) * 4 + r];
-            Zs[c0 * 4 + r] = fma(cs, x, sn * y);
-            Zs[(c0 + 1) * 4 + r] = fma(cs, y, -sn * x);
+        __syncwarp(om);
+        {
+            double* M = sc + (zhalf ? SC_NB : SC_NA);
+            const int r = l & 3;
+            const double x = M[c0 * 4 + r], yv = M[(c0 + 1) * 4 + r];
+            M[c0 * 4 + r] = fma(cs, x, sn * yv);
+            M[(c0 + 1) * 4 + r] = fma(cs, yv, -sn * x);
         }
-        NB[c0 * 4 + c0 + 1] = 0.0;
+        if (l < 4) {
+            double* M = sc + SC_Z;
+            const double x = M[c0 * 4 + l], yv = M[(c0 + 1) * 4 + l];
+            M[c0 * 4 + l] = fma(cs, x, sn * yv);
+            M[(c0 + 1) * 4 + l] = fma(cs, yv, -sn * x);
+        }
+        __syncwarp(om);
+        if (l == 0) sc[SC_NB + c0 * 4 + c0 + 1] = 0.0;
+        __syncwarp(om);
     }
     return true;
 }
@@ -326,8 +409,8 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
     double* UZ = UQ + GW * GW;                            // GW * GW
     double* Sp = UZ + GW * GW;                            // packed window of S
     double* Tp = Sp + gpoff(GW);                          // packed window of T
-    double* QZ = Tp + gpoff(GW);                          // per slot: Qs (16), Zs (16)
-    int* swj = reinterpret_cast<int*>(QZ + GMAXSW * 32);  // per slot: first row
+    double* SCR = Tp + gpoff(GW);                         // per slot: gen_swap_octet scratch
+    int* swj = reinterpret_cast<int*>(SCR + GMAXSW * GSLOT);  // per slot: first row
     int* swk = swj + GMAXSW;                              // k, 0 = rejected
     int* swp = swk + GMAXSW;                              // p, or the stuck block's row
     uint8_t* bst = reinterpret_cast<uint8_t*>(swp + GMAXSW);
@@ -387,31 +470,30 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
         __syncthreads();
         const int ns = nsw;
         if (ns == 0) break;
-        // one thread per swap
-        if (tid < ns) {
-            const int slot = tid, ja = swj[slot], k = swk[slot], p = swp[slot], q = k - p;
-            double DA[16], DB[16], NA[16], NB[16];
+        // one octet (8 lanes) per swap
+        {
+            const int lane = tid & 31;
+            const int oct = (tid >> 5) * 4 + (lane >> 3);
+            const int l = lane & 7, ob = lane & ~7;
+            const unsigned om = 0xffu << ob;
+            if (oct < ns) {
+                const int slot = oct, ja = swj[slot], k = swk[slot], p = swp[slot], q = k - p;
+                double* sc = SCR + slot * GSLOT;
+                if (gen_swap_octet(p, q, Sp, Tp, ja, strong != 0, l, ob, om, sc)) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const bool in = c < k && r < k && r <= c + 1;
-                    DA[c * 4 + r] = in ? Sp[gpoff(ja + c) + ja + r] : 0.0;
-                    DB[c * 4 + r] = in ? Tp[gpoff(ja + c) + ja + r] : 0.0;
-                }
-            double* Qs = &QZ[slot * 32];
-            double* Zs = Qs + 16;
-            if (gen_swap(p, q, DA, DB, strong != 0, Qs, Zs, NA, NB)) {
-                for (int c = 0; c < k; ++c)
-                    for (int r = 0; r <= min(c + 1, k - 1); ++r) {
-                        Sp[gpoff(ja + c) + ja + r] = NA[c * 4 + r];
-                        Tp[gpoff(ja + c) + ja + r] = NB[c * 4 + r];
+                    for (int t = 0; t < 2; ++t) {
+                        const int e = 2 * l + t, r = e & 3, c = e >> 2;
+                        if (c < k && r < k && r <= c + 1) {
+                            Sp[gpoff(ja + c) + ja + r] = sc[SC_NA + e];
+                            Tp[gpoff(ja + c) + ja + r] = sc[SC_NB + e];
+                        }
                     }
-                atomicAdd(&nacc, 1);
-            } else {
-                swk[slot] = 0;
-                swp[slot] = ja + p;   // the stuck (selected) block
-                atomicAdd(&nrej, 1);
+                    if (l == 0) atomicAdd(&nacc, 1);
+                } else if (l == 0) {
+                    swk[slot] = 0;
+                    swp[slot] = ja + p;   // the stuck (selected) block
+                    atomicAdd(&nrej, 1);
+                }
             }
         }
         __syncthreads();
@@ -420,7 +502,7 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             const int slot = it / w, c = it - slot * w;
             const int j = swj[slot], k = swk[slot];
             if (k == 0 || c < j + k) continue;
-            const double* Qs = &QZ[slot * 32];
+            const double* Qs = SCR + slot * GSLOT + SC_Q;
             double xs[4], xt[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -447,8 +529,8 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             const int slot = it / (2 * w), t = it - slot * 2 * w;
             const int j = swj[slot], k = swk[slot];
             if (k == 0) continue;
-            const double* Qs = &QZ[slot * 32];
-            const double* Zs = Qs + 16;
+            const double* Qs = SCR + slot * GSLOT + SC_Q;
+            const double* Zs = SCR + slot * GSLOT + SC_Z;
             if (t < w) {
                 const int r = t;
                 if (r >= j) continue;
