@@ -181,6 +181,7 @@ __device__ __forceinline__ bool gen_swap_octet(int p, int q, const double* __res
     }
     const double smin = fmax(DBL_EPSILON * __longlong_as_double((long long)km), DBL_MIN);
     int perm = l;
+    double rpiv = 1.0;
     for (int s = 0; s < N; ++s) {
         // arg-max over rows >= s, columns [s, N): (magnitude, row * 8 + col),
         // the first in row-major order on ties
@@ -222,9 +223,12 @@ __device__ __forceinline__ bool gen_swap_octet(int p, int q, const double* __res
 #pragma unroll
         for (int c = 0; c < 8; ++c) prow[c] = __shfl_sync(om, K[c], ob + s);
         const double pbv = __shfl_sync(om, b, ob + s);
-        const double piv = pick8(prow, s);
+        // one reciprocal per pivot, kept by the pivot's lane for the back
+        // substitution (no division there)
+        const double rinv = 1.0 / pick8(prow, s);
+        if (l == s) rpiv = rinv;
         if (l > s && l < N) {
-            const double f = pick8(K, s) / piv;
+            const double f = pick8(K, s) * rinv;
 #pragma unroll
             for (int c = 0; c < 8; ++c) K[c] = (c > s) ? fma(-f, prow[c], K[c]) : (c == s ? 0.0 : K[c]);
             b = fma(-f, pbv, b);
@@ -245,7 +249,7 @@ __device__ __forceinline__ bool gen_swap_octet(int p, int q, const double* __res
             y *= f;
             g *= f;
         }
-        if (l == s) y = acc / pick8(K, s);
+        if (l == s) y = acc * rpiv;
         const double ys = __shfl_sync(om, y, ob + s);
         if (l < s) acc = fma(-pick8(K, s), ys, acc);
     }
@@ -365,16 +369,33 @@ __device__ __forceinline__ bool gen_swap_octet(int p, int q, const double* __res
         if (__any_sync(om, bad)) return false;
     }
     // --- T stays upper triangular: rotate the two columns of each new 2x2
-    // block (lanes 0-3: rows of NA, lanes 4-7: rows of NB, then all of Zs)
+    // block (lanes 0-3: rows of NA, lanes 4-7: rows of NB, then all of Zs).
+    // The two blocks own disjoint columns, so both rotations are computed
+    // first (independent chains) and applied one after the other.
+    double rc[2], rs[2];
+    bool act[2];
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
         const int sz = blk ? p : q, c0 = blk ? q : 0;
-        if (sz != 2) continue;
-        const double b10 = sc[SC_NB + c0 * 4 + c0 + 1], b11 = sc[SC_NB + (c0 + 1) * 4 + c0 + 1];
-        if (b10 == 0.0) continue;
-        const double h = hypot(b10, b11);
-        const double cs = b11 / h, sn = -b10 / h;
-        __syncwarp(om);
+        act[blk] = false;
+        rc[blk] = 1.0;
+        rs[blk] = 0.0;
+        if (sz == 2) {
+            const double b10 = sc[SC_NB + c0 * 4 + c0 + 1], b11 = sc[SC_NB + (c0 + 1) * 4 + c0 + 1];
+            if (b10 != 0.0) {
+                const double rh = 1.0 / hypot(b10, b11);
+                act[blk] = true;
+                rc[blk] = b11 * rh;
+                rs[blk] = -b10 * rh;
+            }
+        }
+    }
+    __syncwarp(om);
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        if (!act[blk]) continue;
+        const int c0 = blk ? q : 0;
+        const double cs = rc[blk], sn = rs[blk];
         {
             double* M = sc + (zhalf ? SC_NB : SC_NA);
             const int r = l & 3;
@@ -417,6 +438,10 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
     uint8_t* sel = bst + GW;
     __shared__ int nsw, nrej, nacc;
     __shared__ int wall_top, wall_bot;
+    __shared__ int gcnt[3], glist[3][GMAXSW];   // slots per block-size sum k = 2, 3, 4
+    __shared__ int gpl[3][GMAXSW + 1], gpr[3][GMAXSW + 1];  // item prefix sums per group
+    __shared__ short urlo[GW], urhi[GW];        // nonzero rows of each column of UQ, UZ
+    __shared__ short slo[GMAXSW], shi[GMAXSW];  // per slot: rows of UQ, UZ it updates
     unsigned long long wflops = 0;
     const int tid = threadIdx.x, nth = blockDim.x;
 
@@ -432,7 +457,11 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
         UQ[i] = v;
         UZ[i] = v;
     }
-    for (int i = tid; i < w; i += nth) sel[i] = __ldcg(&gsel[s0 + i]);
+    for (int i = tid; i < w; i += nth) {
+        sel[i] = __ldcg(&gsel[s0 + i]);
+        urlo[i] = (short)i;
+        urhi[i] = (short)i;
+    }
     if (tid == 0) {
         nrej = 0;
         nacc = 0;
@@ -454,6 +483,7 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
         }
         for (int i = tid; i < w; i += nth) bst[i] = (i == 0) || (Sp[gpoff(i - 1) + i] == 0.0);
         if (tid == 0) nsw = 0;
+        if (tid < 3) gcnt[tid] = 0;
         __syncthreads();
         // find this step's swaps: a selected block below an unselected one
         for (int t = tid; t < w; t += nth) {
@@ -466,18 +496,26 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             swj[slot] = ja;
             swk[slot] = p + q;
             swp[slot] = p;
+            glist[p + q - 2][atomicAdd(&gcnt[p + q - 2], 1)] = slot;
         }
         __syncthreads();
         const int ns = nsw;
         if (ns == 0) break;
-        // one octet (8 lanes) per swap
+        // One octet (8 lanes) per swap, the four octets of a warp on swaps of
+        // the same sizes (k = 4 first, then 3, then 2), so that they follow
+        // one instruction stream with the same trip counts.  At most 32
+        // swaps need at most 11 of the 16 warps.
         {
-            const int lane = tid & 31;
-            const int oct = (tid >> 5) * 4 + (lane >> 3);
+            const int lane = tid & 31, warp = tid >> 5;
+            const int nw4 = (gcnt[2] + 3) >> 2, nw3 = (gcnt[1] + 3) >> 2;
+            const int g = warp < nw4 ? 2 : (warp < nw4 + nw3 ? 1 : 0);
+            const int wbase = g == 2 ? 0 : (g == 1 ? nw4 : nw4 + nw3);
+            const int idx = (warp - wbase) * 4 + (lane >> 3);
             const int l = lane & 7, ob = lane & ~7;
             const unsigned om = 0xffu << ob;
-            if (oct < ns) {
-                const int slot = oct, ja = swj[slot], k = swk[slot], p = swp[slot], q = k - p;
+            if (idx < gcnt[g]) {
+                const int slot = glist[g][idx], ja = swj[slot], k = swk[slot], p = swp[slot],
+                          q = k - p;
                 double* sc = SCR + slot * GSLOT;
                 if (gen_swap_octet(p, q, Sp, Tp, ja, strong != 0, l, ob, om, sc)) {
 #pragma unroll
@@ -497,80 +535,127 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             }
         }
         __syncthreads();
-        // left: rows [j, j+k) of S and T, columns [j+k, w), by Qs^T
-        for (int it = tid; it < ns * w; it += nth) {
-            const int slot = it / w, c = it - slot * w;
-            const int j = swj[slot], k = swk[slot];
-            if (k == 0 || c < j + k) continue;
-            const double* Qs = SCR + slot * GSLOT + SC_Q;
-            double xs[4], xt[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                xs[r] = r < k ? Sp[gpoff(c) + j + r] : 0.0;
-                xt[r] = r < k ? Tp[gpoff(c) + j + r] : 0.0;
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (r >= k) break;
-                double as = 0.0, at = 0.0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    as = fma(Qs[r * 4 + i], xs[i], as);
-                    at = fma(Qs[r * 4 + i], xt[i], at);
+        // Work lists of the updates, per block-size sum k (so that a warp
+        // applies one k): prefix sums of the left items (columns [j+k, w) of
+        // rows [j, j+k) of S and T) and of the right items (rows [0, j) of
+        // columns [j, j+k) of S and T, then the rows [lo, hi] of UQ and UZ
+        // holding the nonzeros of those columns: UQ and UZ start as I and a
+        // swap mixes only its own columns, the same ones in both).  Warp g
+        // scans group g; rejected swaps have no items.
+        {
+            const int lane = tid & 31, warp = tid >> 5;
+            if (warp < 3) {
+                const int g = warp, k = g + 2, cnt = gcnt[g];
+                int il = 0, ir = 0;
+                if (lane < cnt) {
+                    const int slot = glist[g][lane], j = swj[slot];
+                    if (swk[slot] != 0) {
+                        int lo = urlo[j], hi = urhi[j];
+                        for (int c = 1; c < k; ++c) {
+                            lo = min(lo, (int)urlo[j + c]);
+                            hi = max(hi, (int)urhi[j + c]);
+                        }
+                        slo[slot] = (short)lo;
+                        shi[slot] = (short)hi;
+                        il = w - j - k;
+                        ir = j + (hi - lo + 1);
+                    }
                 }
-                Sp[gpoff(c) + j + r] = as;
-                Tp[gpoff(c) + j + r] = at;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int a2 = __shfl_up_sync(0xffffffffu, il, o);
+                    const int b2 = __shfl_up_sync(0xffffffffu, ir, o);
+                    if (lane >= o) { il += a2; ir += b2; }
+                }
+                if (lane < cnt) { gpl[g][lane + 1] = il; gpr[g][lane + 1] = ir; }
+                if (lane == 0) { gpl[g][0] = 0; gpr[g][0] = 0; }
             }
         }
         __syncthreads();
-        // right: columns [j, j+k) of S and T rows [0, j) by Zs; of UQ by Qs
-        // and UZ by Zs, rows [0, w)
-        for (int it = tid; it < ns * 2 * w; it += nth) {
-            const int slot = it / (2 * w), t = it - slot * 2 * w;
-            const int j = swj[slot], k = swk[slot];
-            if (k == 0) continue;
-            const double* Qs = SCR + slot * GSLOT + SC_Q;
-            const double* Zs = SCR + slot * GSLOT + SC_Z;
-            if (t < w) {
-                const int r = t;
-                if (r >= j) continue;
+        // left: rows [j, j+k) of S and T, columns [j+k, w), by Qs^T
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const int k = g + 2, cnt = gcnt[g], total = cnt ? gpl[g][cnt] : 0;
+            for (int it = tid; it < total; it += nth) {
+                int lo = 0, hi = cnt - 1;   // last i with gpl[g][i] <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (gpl[g][mid] <= it) lo = mid; else hi = mid - 1;
+                }
+                const int slot = glist[g][lo], j = swj[slot];
+                const int c = j + k + (it - gpl[g][lo]);
+                const double* Qs = SCR + slot * GSLOT + SC_Q;
                 double xs[4], xt[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    xs[i] = i < k ? Sp[gpoff(j + i) + r] : 0.0;
-                    xt[i] = i < k ? Tp[gpoff(j + i) + r] : 0.0;
+                for (int r = 0; r < k; ++r) {
+                    xs[r] = Sp[gpoff(c) + j + r];
+                    xt[r] = Tp[gpoff(c) + j + r];
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (c >= k) break;
+                for (int r = 0; r < k; ++r) {
                     double as = 0.0, at = 0.0;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        as = fma(xs[i], Zs[c * 4 + i], as);
-                        at = fma(xt[i], Zs[c * 4 + i], at);
+                    for (int i = 0; i < k; ++i) {
+                        as = fma(Qs[r * 4 + i], xs[i], as);
+                        at = fma(Qs[r * 4 + i], xt[i], at);
                     }
-                    Sp[gpoff(j + c) + r] = as;
-                    Tp[gpoff(j + c) + r] = at;
+                    Sp[gpoff(c) + j + r] = as;
+                    Tp[gpoff(c) + j + r] = at;
                 }
-            } else {
-                const int r = t - w;
-                double xq[4], xz[4];
+            }
+        }
+        __syncthreads();
+        // right: columns [j, j+k) of S and T (rows [0, j)) by Zs, of UQ by Qs
+        // and UZ by Zs (rows [lo, hi])
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    xq[i] = i < k ? UQ[(j + i) * w + r] : 0.0;
-                    xz[i] = i < k ? UZ[(j + i) * w + r] : 0.0;
+        for (int g = 0; g < 3; ++g) {
+            const int k = g + 2, cnt = gcnt[g], total = cnt ? gpr[g][cnt] : 0;
+            for (int it = tid; it < total; it += nth) {
+                int lo = 0, hi = cnt - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (gpr[g][mid] <= it) lo = mid; else hi = mid - 1;
                 }
+                const int slot = glist[g][lo], j = swj[slot];
+                const int rr = it - gpr[g][lo];
+                const double* Qs = SCR + slot * GSLOT + SC_Q;
+                const double* Zs = SCR + slot * GSLOT + SC_Z;
+                double x1[4], x2[4];
+                if (rr < j) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (c >= k) break;
-                    double aq = 0.0, az = 0.0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        aq = fma(xq[i], Qs[c * 4 + i], aq);
-                        az = fma(xz[i], Zs[c * 4 + i], az);
+                    for (int i = 0; i < k; ++i) {
+                        x1[i] = Sp[gpoff(j + i) + rr];
+                        x2[i] = Tp[gpoff(j + i) + rr];
                     }
-                    UQ[(j + c) * w + r] = aq;
-                    UZ[(j + c) * w + r] = az;
+#pragma unroll
+                    for (int c = 0; c < k; ++c) {
+                        double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+                        for (int i = 0; i < k; ++i) {
+                            a1 = fma(x1[i], Zs[c * 4 + i], a1);
+                            a2 = fma(x2[i], Zs[c * 4 + i], a2);
+                        }
+                        Sp[gpoff(j + c) + rr] = a1;
+                        Tp[gpoff(j + c) + rr] = a2;
+                    }
+                } else {
+                    const int r = rr - j + slo[slot];
+#pragma unroll
+                    for (int i = 0; i < k; ++i) {
+                        x1[i] = UQ[(j + i) * w + r];
+                        x2[i] = UZ[(j + i) * w + r];
+                    }
+#pragma unroll
+                    for (int c = 0; c < k; ++c) {
+                        double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+                        for (int i = 0; i < k; ++i) {
+                            a1 = fma(x1[i], Qs[c * 4 + i], a1);
+                            a2 = fma(x2[i], Zs[c * 4 + i], a2);
+                        }
+                        UQ[(j + c) * w + r] = a1;
+                        UZ[(j + c) * w + r] = a2;
+                    }
                 }
             }
         }
@@ -582,9 +667,14 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
                 sel[swp[sw]] = SEL_STUCK;
                 continue;
             }
-            // left (S, T) + right (S, T) + UQ + UZ: k x k applied to
-            // 2 (w - j - k) + 2 j + 2 w vectors
-            wflops += 2ull * k * k * (unsigned long long)(2 * (w - j - k) + 2 * j + 2 * w);
+            // left (S, T) + right (S, T) + UQ, UZ rows [lo, hi]: k x k
+            // applied to 2 (w - j - k) + 2 j + 2 (hi - lo + 1) vectors
+            wflops += 2ull * k * k *
+                      (unsigned long long)(2 * (w - j - k) + 2 * j + 2 * (shi[sw] - slo[sw] + 1));
+            for (int c = 0; c < k; ++c) {
+                urlo[j + c] = slo[sw];
+                urhi[j + c] = shi[sw];
+            }
             const int p = swp[sw], q = k - p;
             for (int i = 0; i < q; ++i) sel[j + i] = SEL_YES;
             for (int i = q; i < k; ++i) sel[j + i] = SEL_NO;
