@@ -65,7 +65,8 @@ METRIC = "selected eigenvalues reordered per second"
 # a workload has no entry while no capture of the current build exists.
 NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
                ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
-               ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9}
+               ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
+               ("g4000", "persistent"): 10.841124e9 + 12.765499e9}
 
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
