@@ -8,8 +8,10 @@ The arithmetic lives in `reorder_oracle.c` (plain C, binary64,
 -ffp-contract=off): the scalar-update reordering of Section 3.2 / Fig. 1a,
 producing the reordered Schur form of Eq. 7; and in `eigvec_oracle.c`: the
 eigenvectors of a real Schur form (Eq. 5) by back substitution with
-overflow protection; and in `gen_oracle.c`: the reordering of a generalized
-real Schur form (S, T) with Q and Z (Eq. 7, second form).  This module only compiles them with gcc, marshals
+overflow protection; in `gen_oracle.c`: the reordering of a generalized
+real Schur form (S, T) with Q and Z (Eq. 7, second form); and in
+`sweep_oracle.c`: one bulge-chasing sweep of the Schur reduction (Section
+3.2).  This module only compiles them with gcc, marshals
 numpy arrays through ctypes, and back-transforms the eigenvectors with one
 matrix product (Eq. 6).
 """
@@ -25,6 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "reorder_oracle.c")
 _SRC_EV = os.path.join(_HERE, "eigvec_oracle.c")
 _SRC_GEN = os.path.join(_HERE, "gen_oracle.c")
+_SRC_SWEEP = os.path.join(_HERE, "sweep_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -35,7 +38,7 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 
 def build(force: bool = False, src: str = _SRC, out: str = _SO, extra=()) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off)."""
-    srcs = [src] + ([_SRC_EV, _SRC_GEN] if src == _SRC else [])
+    srcs = [src] + ([_SRC_EV, _SRC_GEN, _SRC_SWEEP] if src == _SRC else [])
     if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(x)
                                                  for x in srcs):
         return out
@@ -87,6 +90,10 @@ def load(path: str | None = None):
                                         _dp, ctypes.c_int, _dp, ctypes.c_int, _ip, _dp, _dp,
                                         _ip, ctypes.c_int, _llp, _llp]
         lib.orc_gen_reorder.restype = ctypes.c_int
+    if hasattr(lib, "orc_qr_sweep"):
+        lib.orc_qr_sweep.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                     ctypes.c_int, _dp, _dp]
+        lib.orc_qr_sweep.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -313,3 +320,24 @@ def gen_reorder(S, T, Q, Z, select, *, strong=True, lib=None):
                                          ctypes.byref(ns), ctypes.byref(nr))
     return dict(S=S, T=T, Q=Q, Z=Z, eigs=wr + 1j * wi, m=m.value, status=st,
                 nswaps=ns.value, nrej=nr.value)
+
+
+# ---------------------------------------------------------------------------
+# Bulge-chasing sweep on an upper Hessenberg matrix
+# ---------------------------------------------------------------------------
+def qr_sweep(H, Q, shifts, lib=None):
+    """One pipelined multishift sweep on H (upper Hessenberg) with the given
+    complex shifts (pairs: real or conjugate).  Returns (status, H_new,
+    Q_new)."""
+    H = _f64(H)
+    n = H.shape[0]
+    Qp = None
+    if Q is not None:
+        Q = _f64(Q)
+        Qp = _ptr(Q)
+    sh = np.asarray(shifts, dtype=complex).reshape(-1)
+    sr = np.ascontiguousarray(sh.real, dtype=np.float64)
+    si = np.ascontiguousarray(sh.imag, dtype=np.float64)
+    st = (lib or load()).orc_qr_sweep(n, _ptr(H), max(n, 1), Qp, max(n, 1), int(sh.size),
+                                      _ptr(sr), _ptr(si))
+    return st, H, Q

@@ -39,6 +39,13 @@ Generalized real Schur form (S, T) (the pair case of Eq. 7):
 * Q and Z: products of seeded Householder reflectors (as Q above), drawn
   one after the other from the same generator.
 
+Bulge-chasing sweep (Schur reduction):
+
+* H upper Hessenberg: entries on and above the subdiagonal ~ N(0,1);
+* Q: product of seeded Householder reflectors (as above);
+* shifts: s pairs, alternately a complex-conjugate pair a +- i b
+  (a ~ N(0,1), b ~ U(0.1, 1)) and two real shifts ~ N(0,1).
+
 All matrices are float64 in column-major (Fortran) order.
 """
 from __future__ import annotations
@@ -47,7 +54,8 @@ import numpy as np
 
 __all__ = ["block_sizes", "schur_form", "householder_q", "selection",
            "reorder_problem", "batch_problems", "request_stream", "serve_base",
-           "serve_request", "gen_schur_pair", "gen_problem", "gen_config"]
+           "serve_request", "gen_schur_pair", "gen_problem", "gen_config",
+           "hessenberg_problem", "sweep_config"]
 
 
 def block_sizes(n: int, rng: np.random.Generator, frac_1x1: float = 0.6) -> np.ndarray:
@@ -289,4 +297,32 @@ def gen_config(name: str, seed: int = 0):
         return gen_problem(400, seed, select_frac=0.30, qz="householder", reflectors=16)
     if name == "g4000":
         return gen_problem(4000, seed, select_frac=0.35, qz="householder")
+    raise ValueError(name)
+
+
+def hessenberg_problem(n: int, seed: int = 0, *, nshifts: int = 8, reflectors: int = 64,
+                       q: str = "householder"):
+    """One sweep instance: (H, Q, shifts); shifts complex, nshifts even."""
+    rng = np.random.default_rng(seed)
+    H = np.asfortranarray(np.triu(rng.standard_normal((n, n)), k=-1))
+    if q == "identity":
+        Q = np.asfortranarray(np.eye(n))
+    else:
+        Q = householder_q(n, rng, reflectors)
+    sh = []
+    for b in range(nshifts // 2):
+        if b % 2 == 0:
+            a, im = rng.standard_normal(), rng.uniform(0.1, 1.0)
+            sh += [complex(a, im), complex(a, -im)]
+        else:
+            sh += [complex(rng.standard_normal(), 0.0), complex(rng.standard_normal(), 0.0)]
+    return H, Q, np.array(sh, dtype=complex)
+
+
+def sweep_config(name: str, seed: int = 0):
+    """Named sweep workloads: 'h4000' (n = 4000, 64 shifts), 'h400'."""
+    if name == "h4000":
+        return hessenberg_problem(4000, seed, nshifts=64, reflectors=64)
+    if name == "h400":
+        return hessenberg_problem(400, seed, nshifts=16, reflectors=16)
     raise ValueError(name)
