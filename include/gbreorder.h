@@ -196,6 +196,36 @@ int gbr_reorder_gen(int n, double *S, int ldS, double *T, int ldT, double *Q, in
                     double *Z, int ldZ, const int *select, double *eig_re, double *eig_im,
                     int *m_out, const gbr_opts *opts, gbr_stats *stats, void *cuda_stream);
 
+/*
+ * One bulge-chasing sweep of the Schur reduction on an upper Hessenberg H
+ * resident in device memory (Section 3.2): one pipelined QR iteration, a
+ * bulge per pair of shifts introduced at the top and chased to the bottom by
+ * overlapping 3x3 Householder reflectors, H <- Q3^T H Q3, Q <- Q Q3.  At chain
+ * step tau bulge j of a chain sits at k_j = tau - 3 j - 1; the introduction
+ * uses the first column of (H - sigma1 I)(H - sigma2 I); a chase step maps
+ * H[k+1..k+3, k] onto beta e_0 and leaves exact zeros below beta.
+ *
+ *  1 n            order (n >= 0; n < 3 or no shifts: nothing to do)
+ *  2 H, 3 ldH     device, n x n column-major, upper Hessenberg (entries two
+ *                 or more below the diagonal must be zero), overwritten
+ *  4 Q, 5 ldQ     device or NULL; overwritten by Q Q3
+ *  6 nshifts      even; 7 shift_re, 8 shift_im: host, the shifts; each pair
+ *                 (2i, 2i+1) is two real shifts or a complex-conjugate pair
+ *  9 opts         NULL for the defaults; window = window size (capped at
+ *                 96), chain = shifts per chain of bulges (capped at w / 3);
+ *                 precision GBR_PREC_DMMA only; validate checks the form
+ * 10 stats        host or NULL (windows, chains, update and window flops,
+ *                 kernel times with opts.timing)
+ * 11 cuda_stream  cudaStream_t or NULL
+ *
+ * Returns 0, or -1 bad n, -2 NULL H or H not upper Hessenberg, -3 bad ldH,
+ * -5 bad ldQ, -6 bad shifts (odd count, NULL, a pair neither real nor
+ * conjugate), -10 bad options, GBR_ERR_UNSUPPORTED (split precision).
+ */
+int gbr_qr_sweep(int n, double *H, int ldH, double *Q, int ldQ, int nshifts,
+                 const double *shift_re, const double *shift_im, const gbr_opts *opts,
+                 gbr_stats *stats, void *cuda_stream);
+
 /* gbr_reorder_gen with S, T, Q, Z in HOST memory (copied to the device and
  * back inside the call; device buffers from the library's pool). */
 int gbr_reorder_gen_host(int n, double *S, int ldS, double *T, int ldT, double *Q, int ldQ,

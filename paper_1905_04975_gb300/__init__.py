@@ -84,6 +84,10 @@ _REORDER_GEN_ARGS = [ctypes.c_int] + [ctypes.c_void_p, ctypes.c_int] * 4 + [
 SYMBOLS = {
     "gbr_default_opts": (None, [ctypes.POINTER(GbrOpts)]),
     "gbr_reorder_gen": (ctypes.c_int, _REORDER_GEN_ARGS),
+    "gbr_qr_sweep": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                    ctypes.POINTER(GbrOpts), ctypes.POINTER(GbrStats),
+                                    ctypes.c_void_p]),
     "gbr_reorder_gen_host": (ctypes.c_int, _REORDER_GEN_ARGS),
     "gbr_reorder": (ctypes.c_int, _REORDER_ARGS),
     "gbr_reorder_host": (ctypes.c_int, _REORDER_ARGS),
@@ -447,6 +451,41 @@ def reorder_gen_host(S, T, Q, Z, select, *, opts: GbrOpts | None = None, stream=
                                   wi.ctypes.data_as(_dp), ctypes.byref(m), ctypes.byref(o),
                                   ctypes.byref(stats), _stream_handle(stream))
     return _finish(rc, n, m, wr, wi, stats, allow_partial)
+
+
+@dataclass
+class SweepResult:
+    status: int
+    stats: GbrStats
+
+
+def qr_sweep(H, Q, shifts, *, opts: GbrOpts | None = None, stream=None, **kw) -> SweepResult:
+    """One bulge-chasing sweep on the upper Hessenberg H (column-major float64
+    CUDA tensor) with the given complex shifts (pairs: two real shifts or a
+    conjugate pair); H and Q (or None) are updated in place.  Keyword
+    options: window (<= 96), chain (shifts per chain), sched, validate,
+    timing."""
+    lib = load()
+    n = int(H.shape[0])
+    ldH = _colmajor_ld(H)
+    qptr, ldQ = None, max(n, 1)
+    if Q is not None:
+        ldQ = _colmajor_ld(Q)
+        qptr = ctypes.c_void_p(Q.data_ptr())
+    sh = np.asarray(shifts, dtype=complex).reshape(-1)
+    sr = np.ascontiguousarray(sh.real, dtype=np.float64)
+    si = np.ascontiguousarray(sh.imag, dtype=np.float64)
+    if opts is None:
+        kw.setdefault("window", 96)
+        kw.setdefault("chain", 32)
+    o = opts if opts is not None else make_opts(**kw)
+    stats = GbrStats()
+    rc = lib.gbr_qr_sweep(n, ctypes.c_void_p(H.data_ptr()), ldH, qptr, ldQ, int(sh.size),
+                          sr.ctypes.data_as(_dp), si.ctypes.data_as(_dp), ctypes.byref(o),
+                          ctypes.byref(stats), _stream_handle(stream))
+    if rc < 0:
+        raise GbrError(rc, status_string(rc))
+    return SweepResult(status=rc, stats=stats)
 
 
 def plan(sub, select, window=128, chain=64, with_q=True):

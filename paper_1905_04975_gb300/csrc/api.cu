@@ -21,7 +21,8 @@ static std::vector<long long> g_trace;  // last traced persistent launch, 8 word
 // ---------------------------------------------------------------------------
 enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_PANEL = 4,
                 POOL_EIGVEC = 5 };
-static_assert(POOL_GEN_SCRATCH == 6 && POOL_GEN_HOST == 7 && POOL_GEN_SCHED == 8 && POOL_NSLOTS == 9,
+static_assert(POOL_GEN_SCRATCH == 6 && POOL_GEN_HOST == 7 && POOL_GEN_SCHED == 8 &&
+                  POOL_SWEEP == 9 && POOL_SWEEP_SCHED == 10 && POOL_NSLOTS == 11,
               "pool slots of the generalized entry points");
 struct DevPool {
     void* ptr[POOL_NSLOTS] = {};

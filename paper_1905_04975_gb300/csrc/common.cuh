@@ -53,6 +53,7 @@ struct Inst {
     double* T;           // generalized form (S, T): T, else null
     double* Z;           // generalized form: right factor Z, or null
     int ldT, ldZ;
+    const double* sp;    // bulge-chasing sweep (S holds H): (s, p) per bulge, else null
 };
 
 // One diagonal window in program order.
@@ -61,6 +62,7 @@ struct Window {
     int chain;           // chain index (within its instance)
     int inst;            // instance index (scheduler launches)
     long long u_off;     // offset (in doubles) of this window's U in the U pool
+    int t0, t1, b0, nb;  // bulge-chasing sweep: chain steps [t0, t1) of bulges [b0, b0 + nb)
 };
 
 // Persistent scheduler (sched.cu): task kinds and launch parameters.
@@ -77,7 +79,8 @@ struct SchedTask {
 
 struct SchedParams {
     int strong, ntasks;
-    int pair;                 // nonzero: generalized instances (S, T) with Q and Z
+    int mode;                 // 0: reordering, 1: generalized (S, T) with Q and Z,
+                              // 2: bulge-chasing sweep (window tasks chase bulges)
     const Inst* inst;         // instance table
     const SchedTask* tasks;   // queue order
     const Window* wins;

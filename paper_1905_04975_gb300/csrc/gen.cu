@@ -224,7 +224,7 @@ int run_persistent_gen(int n, const std::vector<Window>& wins, double* S, int ld
         },
         &L, info, st);
     if (rc) return rc;
-    L.P.pair = 1;
+    L.P.mode = 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (o.timing) {
         GBR_CK(cudaEventCreate(&e0), "event");

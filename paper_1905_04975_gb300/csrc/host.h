@@ -30,7 +30,8 @@ int num_sms();
 
 // Device scratch pool (api.cu): one grow-only allocation per device and slot;
 // callers hold api_mutex() while they use it.
-constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_NSLOTS = 9;
+constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_SWEEP = 9,
+              POOL_SWEEP_SCHED = 10, POOL_NSLOTS = 11;
 int pool_get(int slot, size_t bytes, void** out);
 std::mutex& api_mutex();
 
@@ -51,6 +52,13 @@ void plan_pass(PlanState& st, int w, int m, std::vector<Window>& win, int& nchai
 int selection_positions(int n, const uint8_t* sub, const int* select, uint8_t* sel);
 // Update flops of a window list: 2 w^2 (panel rows of L, R and Q).
 double update_flops(int n, const std::vector<Window>& win, bool withQ);
+
+// Bulge-chasing sweep (sweep.cu): one window of a chain of bulges [b0, b0 + nb)
+// over rows / columns [s, e), running chain steps [t0, t1).
+struct SweepWin {
+    int s, e, t0, t1, b0, nb;
+};
+void plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out);
 
 // ---------------------------------------------------------------------------
 // Task graph and queue order (Section 3.2, Fig. 2)

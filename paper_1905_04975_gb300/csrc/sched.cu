@@ -18,6 +18,7 @@
 #include "scan_body.cuh"
 #include "gen_body.cuh"
 #include "ozaki.cuh"
+#include "sweep_body.cuh"
 #include "update_body.cuh"
 #include "window_body.cuh"
 
@@ -28,8 +29,9 @@ namespace {
 constexpr int SCHED_THREADS = win::WIN_THREADS;
 constexpr size_t kMax2(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kSchedSmem = kMax2(kMax2(win::kWindowSmem, upd::kUpdateSmem), oz::kSmem);
-// the generalized (pair) instance of the kernel
+// the generalized (pair) and the sweep instances of the kernel
 constexpr size_t kSchedSmemPair = kMax2(gen::kGenWindowSmem, upd::kUpdateSmem);
+constexpr size_t kSchedSmemSweep = kMax2(swp::kSweepSmem, upd::kUpdateSmem);
 
 __device__ __forceinline__ int ld_volatile(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
@@ -51,10 +53,11 @@ __device__ __forceinline__ unsigned smid() {
 // names the U held in shared memory by the previous task of this CTA (an
 // update tile of the same window reuses it); key names this task's window.
 // Split-precision tiles run on the tensor cores with the CTA's tensor memory
-// (tmem); if one of their bounded waits runs out, *err is set.  PAIR: the
-// instance is a generalized form (S, T) (its own kernel instance, so that the
-// standard path's code and register allocation are untouched).
-template <bool PAIR>
+// (tmem); if one of their bounded waits runs out, *err is set.  MODE 1: the
+// instance is a generalized form (S, T); MODE 2: a bulge-chasing sweep on
+// the Hessenberg matrix in I.S (each its own kernel instance, so that the
+// reordering's code and register allocation are untouched).
+template <int MODE>
 __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, const Inst& I,
                                          double* Ug, unsigned char* uslices,
                                          int strong, unsigned long long key,
@@ -63,15 +66,18 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
     const int tid = threadIdx.x;
     const int w = wd.e - wd.s;
     if (tk.kind == TASK_W) {
-        if constexpr (PAIR)
+        if constexpr (MODE == 1)
             gen::window_gen_body(I.n, I.S, I.ldS, I.T, I.ldT, wd.s, w, I.sel, Ug, Ug + w * w, strong,
                                  I.ctr, smem_raw);
+        else if constexpr (MODE == 2)
+            swp::sweep_body(I.n, I.S, I.ldS, wd.s, w, wd.t0, wd.t1, wd.nb, I.sp + 2 * wd.b0, Ug,
+                            I.ctr, smem_raw);
         else
             win::window_body(I.n, I.S, I.ldS, wd.s, w, I.sel, Ug, strong, I.ctr, smem_raw, uslices);
         if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds a U
         return;
     }
-    if constexpr (PAIR) {
+    if constexpr (MODE == 1) {
         // generalized form: left tiles of S and T by UQ, right tiles of S and
         // T by UZ, Q by UQ, Z by UZ (UQ then UZ at the window's U offset)
         const bool byZ = (tk.kind == TASK_R || tk.kind == TASK_Z);
@@ -138,7 +144,7 @@ __device__ __forceinline__ void tmem_release(bool need, uint32_t tmem) {
     if ((threadIdx.x >> 5) == 0) oz::tmem_dealloc(tmem, oz::TMEM_COLS);
 }
 
-template <bool PAIR>
+template <int MODE>
 __global__ void __launch_bounds__(SCHED_THREADS, 1)
 sched_kernel(SchedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -179,7 +185,7 @@ sched_kernel(SchedParams P) {
         const SchedTask tk = P.tasks[t];
         const Window wd = P.wins[tk.win];
         const Inst I = P.inst[wd.inst];
-        run_task<PAIR>(tk, wd, I, P.upool + wd.u_off,
+        run_task<MODE>(tk, wd, I, P.upool + wd.u_off,
                  P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
                  P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err);
         // release: every thread's writes are ordered before the counters drop
@@ -289,7 +295,7 @@ server_kernel(SrvParams P) {
                 wd.inst = 0;
                 wd.u_off = __ldcg(&wp->u_off);
             }
-            run_task<false>(tk, wd, R.inst, R.upool + wd.u_off,
+            run_task<0>(tk, wd, R.inst, R.upool + wd.u_off,
                      R.uslices ? R.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
                      P.strong, ((unsigned long long)(unsigned)R.id << 32) | (unsigned)tk.win, &u_key,
                      smem_raw, tmem, P.err);
@@ -323,11 +329,14 @@ cudaError_t sched_configure() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && configured[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(sched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sched_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSchedSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sched_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSchedSmemPair);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sched_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSchedSmemSweep);
     if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = true;
     return e;
 }
@@ -350,10 +359,12 @@ cudaError_t launch_server(const SrvParams& P, int grid, cudaStream_t st) {
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st) {
     cudaError_t e = sched_configure();
     if (e != cudaSuccess) return e;
-    if (P.pair)
-        sched_kernel<true><<<grid, SCHED_THREADS, kSchedSmemPair, st>>>(P);
+    if (P.mode == 1)
+        sched_kernel<1><<<grid, SCHED_THREADS, kSchedSmemPair, st>>>(P);
+    else if (P.mode == 2)
+        sched_kernel<2><<<grid, SCHED_THREADS, kSchedSmemSweep, st>>>(P);
     else
-        sched_kernel<false><<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
+        sched_kernel<0><<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
     return cudaGetLastError();
 }
 

@@ -141,6 +141,33 @@ def test_reorder_gen_argument_checks(lib):
     assert m.value == 0
 
 
+def test_qr_sweep_argument_checks(lib):
+    """gbr_qr_sweep checks its arguments before any GPU work."""
+    d = ctypes.c_void_p(0x1000)  # never dereferenced
+    dp = ctypes.POINTER(ctypes.c_double)
+    re = np.array([0.5, 0.5, 1.0, 2.0])
+    im = np.array([0.3, -0.3, 0.0, 0.0])
+    bad_im = np.array([0.3, 0.3, 0.0, 0.0])
+    R, I, B = (a.ctypes.data_as(dp) for a in (re, im, bad_im))
+    o = g.default_opts()
+
+    def call(n, H, ldH, Q, ldQ, ns, r, i, opts=o):
+        return lib.gbr_qr_sweep(n, H, ldH, Q, ldQ, ns, r, i,
+                                ctypes.byref(opts) if opts is not None else None, None, None)
+
+    assert call(-1, d, 4, None, 4, 4, R, I) == -1
+    assert call(4, None, 4, None, 4, 4, R, I) == -2
+    assert call(4, d, 3, None, 4, 4, R, I) == -3
+    assert call(4, d, 4, d, 3, 4, R, I) == -5
+    assert call(4, d, 4, None, 4, 3, R, I) == -6
+    assert call(4, d, 4, None, 4, 4, R, B) == -6
+    assert call(4, d, 4, None, 4, 4, None, I) == -6
+    assert call(4, d, 4, None, 4, 4, R, I, g.make_opts(window=2)) == -10
+    assert call(4, d, 4, None, 4, 4, R, I, g.make_opts(precision="ozaki")) == g.ERR_UNSUPPORTED
+    assert call(2, d, 2, None, 2, 4, R, I) == 0     # n < 3: nothing to do
+    assert call(0, None, 1, None, 1, 0, None, None, None) == 0
+
+
 def batch_create(lib, count, n, S, ldS, Q, ldQ, sel, opts=None, want_out=True):
     ip = ctypes.POINTER(ctypes.c_int)
     arr = lambda a: a.ctypes.data_as(ip) if a is not None else None
