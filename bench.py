@@ -57,7 +57,10 @@ WORKLOADS = {
                   q="8 Householder reflectors", mem_cap=60e9),
     "g4000": dict(name="g4000", kind="gen", n=4000, select=0.35,
                   q="Q and Z: 64 Householder reflectors each", window=64, chain=32),
+    "h4000": dict(name="h4000", kind="sweep", n=4000, shifts=64,
+                  q="64 Householder reflectors", window=64, chain=16),
 }
+SWEEP_METRIC = "shifts chased per second (one bulge-chasing sweep)"
 METRIC = "selected eigenvalues reordered per second"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
@@ -66,7 +69,8 @@ METRIC = "selected eigenvalues reordered per second"
 NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
                ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
                ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
-               ("g4000", "persistent"): 10.841124e9 + 12.765499e9}
+               ("g4000", "persistent"): 10.841124e9 + 12.765499e9,
+               ("h4000", "persistent"): 0.220397e9 + 0.188294e9}
 
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
@@ -243,6 +247,27 @@ def run_reference(args, wl):
                 "cpu_baseline": {"value": value, "unit": "eigenvectors/s", "cores": cb["cores"],
                                  "kind": "oracle", "sample": samples[-1]},
                 "e2e": {"value": value, "unit": "eigenvectors/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    elif wl.get("kind") == "sweep":
+        H, Q, sh = si.sweep_config(wl["name"])
+        times, samples = [], []
+        for i in range(args.warmup + args.steps):
+            cb = sweep_cpu(H, Q, sh)
+            if i >= args.warmup:
+                times.append(len(sh) / cb["value"])
+                samples.append(cb["sample"])
+        value = len(sh) * len(times) / sum(times)
+        line = {"impl": "reference", "metric": SWEEP_METRIC, "value": value, "unit": "shifts/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "n": wl["n"], "shifts": wl["shifts"],
+                           "q": wl["q"], "window": wl["window"], "chain": wl["chain"]},
+                "cpu_baseline": {"value": value, "unit": "shifts/s", "cores": 1, "kind": "oracle",
+                                 "sample": samples[-1]},
+                "e2e": {"value": value, "unit": "shifts/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -755,6 +780,136 @@ def run_gen(args, wl):
     return 0
 
 
+def sweep_cpu(H, Q, sh):
+    """The sweep oracle on the whole workload (a few seconds on one core)."""
+    import oracle
+    t0 = time.perf_counter()
+    st, _, _ = oracle.qr_sweep(H, Q, sh)
+    dt = time.perf_counter() - t0
+    assert st == 0
+    return {"value": len(sh) / dt, "unit": "shifts/s", "cores": 1, "kind": "oracle",
+            "sample": f"the whole n={H.shape[0]} sweep with {len(sh)} shifts, {dt:.1f} s on 1 core"}
+
+
+def run_sweep(args, wl):
+    """One bulge-chasing sweep (Section 3.2) on the n = 4000 Hessenberg
+    matrix with 64 shifts: shifts chased per second."""
+    import torch
+    import paper_1905_04975_gb300 as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+    H_np, Q_np, sh = si.sweep_config(wl["name"])
+    n = H_np.shape[0]
+    H0, Q0 = g.to_device(H_np), g.to_device(Q_np)
+    H, Q = g.to_device(H_np), g.to_device(Q_np)
+    stream = torch.cuda.Stream()
+    opts = g.make_opts(window=wl["window"], chain=wl["chain"], timing=True, sched=args.sched)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")  # > L2
+
+    def step():
+        with torch.cuda.stream(stream):
+            H.copy_(H0)
+            Q.copy_(Q0)
+            flush.fill_(1.0)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = g.qr_sweep(H, Q, sh, opts=opts, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            r, t = step()
+            ms.append(t)
+            stats.append(r.stats)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    nsh = len(sh)
+    value, total_ms = whole_job_rate(nsh * args.steps, sum(ms), dist, "cuda")
+    st0 = stats[0]
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)
+    flops_iss = st0.upd_flops_issued if st0.upd_flops_issued > 0 else st0.upd_flops
+    if args.sched == "persistent":
+        ms_k = sum(s.ms_sched for s in stats) / len(stats)
+        kern = "sched_kernel<sweep> (persistent: bulge-chasing window tasks + DMMA tiles)"
+        work_fl = flops_iss + st0.win_flops
+    else:
+        ms_k = sum(s.ms_update for s in stats) / len(stats)
+        kern = "update_kernel (DMMA FP64 Y <- Y U)"
+        work_fl = flops_iss
+    achieved = work_fl / (ms_k / 1e3) / 1e12
+    roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "traffic": NCU_TRAFFIC.get((wl["name"], args.sched)),
+            "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
+                            "1.25/2250 (FP64 DMMA probe: 1.047 TF/s)"),
+            "flops_per_launch": work_fl, "update_flops_dense": st0.upd_flops,
+            "update_flops_issued": flops_iss, "window_flops": st0.win_flops,
+            "avg_launch_ms": ms_k,
+            "critical_path_model_ms": sum(s.sched_cp_ms for s in stats) / len(stats),
+            "share_of_step": ms_k / (total_ms / args.steps)}
+    e2e = None
+    if args.e2e_steps > 0:
+        hH = torch.from_numpy(np.asfortranarray(H_np).T.copy()).pin_memory()
+        hQ = torch.from_numpy(np.asfortranarray(Q_np).T.copy()).pin_memory()
+        oH = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        oQ = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        et = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                H.t().copy_(hH, non_blocking=True)
+                Q.t().copy_(hQ, non_blocking=True)
+            g.qr_sweep(H, Q, sh, opts=opts, stream=stream)
+            with torch.cuda.stream(stream):
+                oH.copy_(H.t(), non_blocking=True)
+                oQ.copy_(Q.t(), non_blocking=True)
+            stream.synchronize()
+            if i > 0:
+                et.append(time.perf_counter() - t0)
+        e2e = {"value": nsh * len(et) / sum(et) * world, "unit": "shifts/s",
+               "h2d_bytes_per_step": 2 * n * n * 8 + 16 * nsh,
+               "d2h_bytes_per_step": 2 * n * n * 8}
+    cpu = sweep_cpu(H_np, Q_np, sh) if (rank == 0 and not args.no_cpu_baseline) else None
+    if rank == 0:
+        line = {"metric": SWEEP_METRIC, "value": value, "unit": "shifts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "n": n, "shifts": nsh, "q": wl["q"],
+                           "window": wl["window"], "chain": wl["chain"], "sched": args.sched,
+                           "l2": "H, Q restored and a 256 MB buffer written before each step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": int(sum(s.launches for s in stats)),
+                "detail": {"windows": int(st0.windows), "chains": int(st0.chains),
+                           "tasks": int(st0.tasks), "ms_graph": st0.ms_graph,
+                           "ms_order": st0.ms_order}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_eigvec(args, wl):
     """Eigenvectors (Eq. 5) of every eigenvalue of the n = 4000 Schur form,
     back-transformed by its Q (Eq. 6): eigenvectors per second."""
@@ -894,6 +1049,8 @@ def main():
         return run_eigvec(args, wl)
     if wl.get("kind") == "gen":
         return run_gen(args, wl)
+    if wl.get("kind") == "sweep":
+        return run_sweep(args, wl)
 
     import torch
     import paper_1905_04975_gb300 as g
