@@ -463,8 +463,8 @@ def qr_sweep(H, Q, shifts, *, opts: GbrOpts | None = None, stream=None, **kw) ->
     """One bulge-chasing sweep on the upper Hessenberg H (column-major float64
     CUDA tensor) with the given complex shifts (pairs: two real shifts or a
     conjugate pair); H and Q (or None) are updated in place.  Keyword
-    options: window (<= 96), chain (shifts per chain), sched, validate,
-    timing."""
+    options: window (<= 96, default 64), chain (shifts per chain, default
+    16), sched, validate, timing."""
     lib = load()
     n = int(H.shape[0])
     ldH = _colmajor_ld(H)
@@ -476,8 +476,8 @@ def qr_sweep(H, Q, shifts, *, opts: GbrOpts | None = None, stream=None, **kw) ->
     sr = np.ascontiguousarray(sh.real, dtype=np.float64)
     si = np.ascontiguousarray(sh.imag, dtype=np.float64)
     if opts is None:
-        kw.setdefault("window", 96)
-        kw.setdefault("chain", 32)
+        kw.setdefault("window", 64)
+        kw.setdefault("chain", 16)
     o = opts if opts is not None else make_opts(**kw)
     stats = GbrStats()
     rc = lib.gbr_qr_sweep(n, ctypes.c_void_p(H.data_ptr()), ldH, qptr, ldQ, int(sh.size),
