@@ -183,8 +183,9 @@ int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *s
  * 13 m_out      host or NULL: number of selected eigenvalues
  * 14 opts       options or NULL for the defaults.  window > 64 is reduced
  *               to 64 and chain then to at most 32 (both factors of a window
- *               live in shared memory); precision GBR_PREC_DMMA only
- *               (GBR_PREC_OZAKI: GBR_ERR_UNSUPPORTED); both schedules
+ *               live in shared memory); both schedules; precision
+ *               GBR_PREC_DMMA, or GBR_PREC_OZAKI on the persistent schedule
+ *               (split-precision updates from the digit slices of UQ and UZ)
  * 15 stats      host or NULL (upd_flops counts S, T, Q and Z panels)
  * 16 cuda_stream  cudaStream_t or NULL
  *

@@ -215,6 +215,7 @@ int run_persistent_gen(int n, const std::vector<Window>& wins, double* S, int ld
     CostModel cm;
     cm.lr_mats = 2.0;
     cm.win_us_128 = kGenWinUs128;
+    if (o.precision == GBR_PREC_OZAKI) cm.tile_rate = 100000.0;
     SchedLaunch L;
     int rc = sched_prepare(
         plans, o, cm, num_sms(),
@@ -409,8 +410,12 @@ int gen_args(int n, const void* S, int ldS, const void* T, int ldT, const void* 
     if ((Q && ldQ < ld1) || (Z && ldZ < ld1)) return -5;
     if (n > 0 && !select) return -6;
     if (o.window < 4 || o.window > WMAX || o.chain < 1 || o.chain > o.window - 2) return -10;
-    if (o.precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
     if (o.sched != GBR_SCHED_PERSISTENT && o.sched != GBR_SCHED_SEQUENTIAL) return -10;
+    if (o.precision != GBR_PREC_DMMA && o.precision != GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    // split precision runs on the persistent scheduler only
+    if (o.precision == GBR_PREC_OZAKI &&
+        (o.sched != GBR_SCHED_PERSISTENT || (o.slices != 0 && o.slices != OZ_SLICES)))
+        return GBR_ERR_UNSUPPORTED;
     if (o.wait_limit_ms < 0) return -10;
     if (o.on_reject != GBR_ON_REJECT_CONTINUE) return GBR_ERR_UNSUPPORTED;
     return 0;

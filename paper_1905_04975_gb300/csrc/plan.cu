@@ -570,7 +570,10 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     const size_t b_succ = al(sizeof(int) * std::max<size_t>(1, succ.size()));
     const size_t b_ctl = 256;
     const size_t b_tr = (o.timing >= 2) ? al(sizeof(unsigned long long) * 4 * std::max(1, nt)) : 0;
-    const size_t b_us = ozaki ? al(OZ_USLICE_BYTES * wins.size()) : 0;
+    // digit slices per window: one U, or UQ and UZ for a generalized instance
+    bool pair = false;
+    for (size_t i = 0; i < ni; ++i) pair |= (plans[i].d.T != nullptr);
+    const size_t b_us = ozaki ? al(OZ_USLICE_BYTES * wins.size() * (pair ? 2 : 1)) : 0;
     const size_t b_u = al(sizeof(double) * std::max<long long>(1, u_total));
     const size_t total = b_inst + b_tasks + b_wins + 2 * b_deps + b_soff + b_succ + b_ctl + b_tr +
                          b_us + b_u;

@@ -30,7 +30,7 @@ constexpr int SCHED_THREADS = win::WIN_THREADS;
 constexpr size_t kMax2(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kSchedSmem = kMax2(kMax2(win::kWindowSmem, upd::kUpdateSmem), oz::kSmem);
 // the generalized (pair) and the sweep instances of the kernel
-constexpr size_t kSchedSmemPair = kMax2(gen::kGenWindowSmem, upd::kUpdateSmem);
+constexpr size_t kSchedSmemPair = kMax2(kMax2(gen::kGenWindowSmem, upd::kUpdateSmem), oz::kSmem);
 constexpr size_t kSchedSmemSweep = kMax2(swp::kSweepSmem, upd::kUpdateSmem);
 
 __device__ __forceinline__ int ld_volatile(const int* p) {
@@ -66,10 +66,18 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
     const int tid = threadIdx.x;
     const int w = wd.e - wd.s;
     if (tk.kind == TASK_W) {
-        if constexpr (MODE == 1)
+        if constexpr (MODE == 1) {
             gen::window_gen_body(I.n, I.S, I.ldS, I.T, I.ldT, wd.s, w, I.sel, Ug, Ug + w * w, strong,
                                  I.ctr, smem_raw);
-        else if constexpr (MODE == 2)
+            if (uslices) {
+                // split precision: digit slices of UQ, then of UZ (from the
+                // factors the task just wrote; the barrier orders the reads)
+                __syncthreads();
+                win::write_u_slices(Ug, w, uslices);
+                __syncthreads();
+                win::write_u_slices(Ug + w * w, w, uslices + OZ_USLICE_BYTES);
+            }
+        } else if constexpr (MODE == 2)
             swp::sweep_body(I.n, I.S, I.ldS, wd.s, w, wd.t0, wd.t1, wd.nb, I.sp + 2 * wd.b0, Ug,
                             I.ctr, smem_raw);
         else
@@ -95,13 +103,22 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
             const int ldX = mi ? I.ldT : I.ldS;
             upd::panel_geom(panel, I.n, wd.s, wd.e, X, ldX, tk.kind == TASK_Z ? I.Z : I.Q,
                             tk.kind == TASK_Z ? I.ldZ : I.ldQ, &base, &rs, &ks, &R);
+            if (uslices) {
+                // split precision on the tensor cores (the slices of UQ or UZ)
+                if (!oz::update_tile_tc(base, rs, ks, tk.y0, tk.rows, w,
+                                        uslices + (byZ ? OZ_USLICE_BYTES : 0), smem_raw, tmem) &&
+                    tid == 0)
+                    atomicExch(err, 1);
+                __syncthreads();
+                continue;
+            }
             for (int r = 0; r < tk.rows; r += upd::BM) {
                 upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w, U, load_u,
                                  smem_raw, &I.ctr->upd_issued);
                 load_u = false;
             }
         }
-        if (tid == 0) *u_key = k2;
+        if (tid == 0) *u_key = uslices ? ~0ull : k2;
         return;
     }
     double* base;
@@ -186,7 +203,8 @@ sched_kernel(SchedParams P) {
         const Window wd = P.wins[tk.win];
         const Inst I = P.inst[wd.inst];
         run_task<MODE>(tk, wd, I, P.upool + wd.u_off,
-                 P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
+                 P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES * (MODE == 1 ? 2 : 1)
+                           : nullptr,
                  P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err);
         // release: every thread's writes are ordered before the counters drop
         __threadfence();

@@ -114,8 +114,8 @@ def test_eigenvectors_argument_checks(lib):
 
 def test_reorder_gen_argument_checks(lib):
     """gbr_reorder_gen checks its arguments before any GPU work; options
-    the pair path does not build (split precision) are refused; n = 0 is a
-    no-op."""
+    the pair path does not build (split precision off the persistent
+    schedule, other slice counts) are refused; n = 0 is a no-op."""
     d = ctypes.c_void_p(0x1000)  # never dereferenced
     sel = np.zeros(4, dtype=np.int32)
     ip = sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
@@ -137,6 +137,8 @@ def test_reorder_gen_argument_checks(lib):
                                                                   sched="sequential")) == -10
     assert call(4, d, 4, d, 4, None, 4, None, 4, ip, g.make_opts(precision="ozaki",
                                                                   sched="sequential")) == g.ERR_UNSUPPORTED
+    assert call(4, d, 4, d, 4, None, 4, None, 4, ip, g.make_opts(precision="ozaki",
+                                                                  slices=5)) == g.ERR_UNSUPPORTED
     assert call(0, None, 1, None, 1, None, 1, None, 1, None, None) == 0
     assert m.value == 0
 

@@ -191,3 +191,29 @@ def test_persistent_matches_sequential(gbr, n, w, m):
     for a, b, ref in ((Sp, Ss, S), (Tp, Ts, T), (Qp, Qs, Q), (Zp, Zs, Z)):
         assert np.linalg.norm(a - b) <= 50 * n * EPS * np.linalg.norm(ref)
     check(S, T, Q, Z, sel, rp, Sp, Tp, Qp, Zp)
+
+
+@pytest.mark.parametrize("name,n,w,m", [("n200", 200, 64, 32), ("ragged515", 515, 32, 12),
+                                        ("g400", 400, 64, 32)])
+def test_split_precision_updates(gbr, name, n, w, m):
+    """Off-diagonal updates of S, T, Q, Z in emulated FP64 (7 digit slices of
+    UQ and UZ, exact bf16 tensor-core products): the same parity bar as the
+    DMMA path, and close to the DMMA result."""
+    if name == "g400":
+        S, T, Q, Z, sel = si.gen_config("g400")
+    else:
+        S, T, Q, Z, sel = si.gen_problem(n, n + 11, select_frac=0.4, reflectors=16)
+    ref = oracle.gen_reorder(S, T, Q, Z, sel)
+    ro, So, To, Qo, Zo = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m, precision="ozaki")
+    assert ro.status == 0
+    check(S, T, Q, Z, sel, ro, So, To, Qo, Zo, ref)
+    rd, Sd, Td, Qd, Zd = run_gpu(gbr, S, T, Q, Z, sel, window=w, chain=m, precision="dmma")
+    for a, b, x in ((So, Sd, S), (To, Td, T), (Qo, Qd, Q), (Zo, Zd, Z)):
+        assert np.linalg.norm(a - b) <= 50 * n * EPS * np.linalg.norm(x)
+
+
+def test_split_precision_g4000(gbr):
+    S, T, Q, Z, sel = si.gen_config("g4000")
+    r, Sg, Tg, Qg, Zg = run_gpu(gbr, S, T, Q, Z, sel, precision="ozaki")
+    assert r.status == 0
+    check(S, T, Q, Z, sel, r, Sg, Tg, Qg, Zg)
