@@ -100,3 +100,23 @@ def test_not_hessenberg_is_refused(gbr):
     with pytest.raises(gbr.GbrError) as ei:
         run_gpu(gbr, H, Q, sh, sched="sequential")
     assert ei.value.status == -2
+
+
+def test_reducible_hessenberg(gbr):
+    """A zero subdiagonal entry stops the bulges that reach it (their
+    reflectors become the identity there); GPU and oracle agree."""
+    n = 120
+    H, Q, sh = si.hessenberg_problem(n, 21, nshifts=8, reflectors=4)
+    H[60, 59] = 0.0
+    r, Hg, Qg = run_gpu(gbr, H, Q, sh, window=32, chain=4)
+    check(H, Q, sh, r, Hg, Qg)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6])
+def test_smallest_sizes_many_shifts(gbr, n):
+    """More bulges than the matrix can hold at once: the chains still run to
+    the end on both schedules."""
+    H, Q, sh = si.hessenberg_problem(n, 40 + n, nshifts=8, reflectors=2)
+    for sched in ("persistent", "sequential"):
+        r, Hg, Qg = run_gpu(gbr, H, Q, sh, window=8, chain=2, sched=sched)
+        check(H, Q, sh, r, Hg, Qg)
