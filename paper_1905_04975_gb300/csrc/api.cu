@@ -33,6 +33,21 @@ static DevPool g_pool[64];
 
 std::mutex& api_mutex() { return g_mu; }
 
+int store_trace(const SchedLaunch& L) {
+    const int nt = L.P.ntasks;
+    std::vector<unsigned long long> raw((size_t)4 * nt);
+    GBR_CK(cudaMemcpy(raw.data(), L.P.trace, sizeof(unsigned long long) * 4 * nt,
+                      cudaMemcpyDeviceToHost), "D2H trace");
+    g_trace.assign((size_t)8 * nt, 0);
+    for (int q = 0; q < nt; ++q) {
+        const SchedTask& k = L.tq[q];
+        long long* r = &g_trace[(size_t)8 * q];
+        r[0] = k.kind; r[1] = k.win; r[2] = k.y0; r[3] = k.rows;
+        for (int j = 0; j < 4; ++j) r[4 + j] = (long long)raw[4 * q + j];
+    }
+    return 0;
+}
+
 int pool_get(int slot, size_t bytes, void** out) {
     int dev = 0;
     GBR_CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -108,16 +123,8 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
     *ntasks_out += nt;
     g_last_sched = inf;
     if (L.trace_bytes) {
-        std::vector<unsigned long long> raw((size_t)4 * nt);
-        GBR_CK(cudaMemcpy(raw.data(), L.P.trace, sizeof(unsigned long long) * 4 * nt,
-                          cudaMemcpyDeviceToHost), "D2H trace");
-        g_trace.assign((size_t)8 * nt, 0);
-        for (int q = 0; q < nt; ++q) {
-            const SchedTask& k = L.tq[q];
-            long long* r = &g_trace[(size_t)8 * q];
-            r[0] = k.kind; r[1] = k.win; r[2] = k.y0; r[3] = k.rows;
-            for (int j = 0; j < 4; ++j) r[4 + j] = (long long)raw[4 * q + j];
-        }
+        int rct = store_trace(L);
+        if (rct) return rct;
     }
     if (h_err) {
         set_last_error("persistent scheduler: a task waited longer than wait_limit_ms");

@@ -248,6 +248,10 @@ int run_persistent_gen(int n, const std::vector<Window>& wins, double* S, int ld
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
+    if (L.trace_bytes) {
+        const int rct = store_trace(L);
+        if (rct) return rct;
+    }
     *ntasks_out += L.P.ntasks;
     if (h_err) {
         set_last_error("persistent scheduler (pair): a task waited longer than wait_limit_ms");

@@ -416,6 +416,136 @@ __device__ __forceinline__ bool gen_swap_octet(int p, int q, const double* __res
     return true;
 }
 
+// Warps [base[g], base[g+1]) serve group g (k = g + 2): counts in proportion
+// to tot[g] k^2, at least one warp for a group with items, nwarps in all.
+// Every thread computes the same split.
+__device__ __forceinline__ void split_warps(const int tot[3], int nwarps, int base[4]) {
+    int wt[3], c[3], sum = 0;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        wt[g] = tot[g] * (g + 2) * (g + 2);
+        sum += wt[g];
+    }
+    int used = 0;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        c[g] = tot[g] == 0 ? 0 : max(1, (int)((long long)wt[g] * nwarps / (sum > 0 ? sum : 1)));
+        used += c[g];
+    }
+    // fix the total: take from the group with the most warps, give to the
+    // group with the most work per warp
+    while (used > nwarps) {
+        int gi = 0;
+        for (int g = 1; g < 3; ++g) if (c[g] > c[gi]) gi = g;
+        --c[gi];
+        --used;
+    }
+    while (used < nwarps && sum > 0) {
+        int gi = -1;
+        for (int g = 0; g < 3; ++g)
+            if (c[g] > 0 && (gi < 0 || (long long)wt[g] * c[gi] > (long long)wt[gi] * c[g])) gi = g;
+        if (gi < 0) break;
+        ++c[gi];
+        ++used;
+    }
+    base[0] = 0;
+    base[1] = c[0];
+    base[2] = c[0] + c[1];
+    base[3] = c[0] + c[1] + c[2];
+}
+
+// Left items of group k: item it of the group's flat list (prefix sums pre
+// over its cnt slots) is column j + k + (it - pre[i]) of swap list[i].
+template <int K>
+__device__ __forceinline__ void apply_left(int first, int stride, int total, int cnt, const int* pre,
+                                           const int* list, const int* swj, const double* SCR,
+                                           double* Sp, double* Tp) {
+    for (int it = first; it < total; it += stride) {
+        int lo = 0, hi = cnt - 1;   // last i with pre[i] <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const int slot = list[lo], j = swj[slot];
+        const int c = j + K + (it - pre[lo]);
+        const double* Qs = SCR + slot * GSLOT + SC_Q;
+        double xs[K], xt[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            xs[r] = Sp[gpoff(c) + j + r];
+            xt[r] = Tp[gpoff(c) + j + r];
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            double as = 0.0, at = 0.0;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                as = fma(Qs[r * 4 + i], xs[i], as);
+                at = fma(Qs[r * 4 + i], xt[i], at);
+            }
+            Sp[gpoff(c) + j + r] = as;
+            Tp[gpoff(c) + j + r] = at;
+        }
+    }
+}
+
+// Right items of group k: rows [0, j) of S and T, then rows [lo, hi] of UQ
+// and UZ, for the columns [j, j+k) of swap list[i].
+template <int K>
+__device__ __forceinline__ void apply_right(int first, int stride, int total, int cnt, const int* pre,
+                                            const int* list, const int* swj, const short* slo,
+                                            const double* SCR, double* Sp, double* Tp, double* UQ,
+                                            double* UZ, int w) {
+    for (int it = first; it < total; it += stride) {
+        int lo = 0, hi = cnt - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const int slot = list[lo], j = swj[slot];
+        const int rr = it - pre[lo];
+        const double* Qs = SCR + slot * GSLOT + SC_Q;
+        const double* Zs = SCR + slot * GSLOT + SC_Z;
+        double x1[K], x2[K];
+        if (rr < j) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                x1[i] = Sp[gpoff(j + i) + rr];
+                x2[i] = Tp[gpoff(j + i) + rr];
+            }
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    a1 = fma(x1[i], Zs[c * 4 + i], a1);
+                    a2 = fma(x2[i], Zs[c * 4 + i], a2);
+                }
+                Sp[gpoff(j + c) + rr] = a1;
+                Tp[gpoff(j + c) + rr] = a2;
+            }
+        } else {
+            const int r = rr - j + slo[slot];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                x1[i] = UQ[(j + i) * w + r];
+                x2[i] = UZ[(j + i) * w + r];
+            }
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    a1 = fma(x1[i], Qs[c * 4 + i], a1);
+                    a2 = fma(x2[i], Zs[c * 4 + i], a2);
+                }
+                UQ[(j + c) * w + r] = a1;
+                UZ[(j + c) * w + r] = a2;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Window task of the pair: window [s0, s0 + w) of (S, T), w <= GW; writes
 // the accumulated factors UQ, UZ (w x w, column-major, ld w) to UQg, UZg.
@@ -572,91 +702,39 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             }
         }
         __syncthreads();
-        // left: rows [j, j+k) of S and T, columns [j+k, w), by Qs^T
+        // The warps are split among the three k groups in proportion to
+        // their FP64 work (items x k^2), so that every warp applies one k
+        // and the sub-partitions carry equal shares; then the left products
+        // (rows [j, j+k) of S and T, columns [j+k, w), by Qs^T) and, after a
+        // barrier, the right ones (columns [j, j+k) of S and T for rows
+        // [0, j) by Zs, of UQ by Qs and UZ by Zs for rows [lo, hi]).
+        {
+            const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+            int tl[3], tr[3], bl[4], br[4];
 #pragma unroll
-        for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = gcnt[g], total = cnt ? gpl[g][cnt] : 0;
-            for (int it = tid; it < total; it += nth) {
-                int lo = 0, hi = cnt - 1;   // last i with gpl[g][i] <= it
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (gpl[g][mid] <= it) lo = mid; else hi = mid - 1;
-                }
-                const int slot = glist[g][lo], j = swj[slot];
-                const int c = j + k + (it - gpl[g][lo]);
-                const double* Qs = SCR + slot * GSLOT + SC_Q;
-                double xs[4], xt[4];
-#pragma unroll
-                for (int r = 0; r < k; ++r) {
-                    xs[r] = Sp[gpoff(c) + j + r];
-                    xt[r] = Tp[gpoff(c) + j + r];
-                }
-#pragma unroll
-                for (int r = 0; r < k; ++r) {
-                    double as = 0.0, at = 0.0;
-#pragma unroll
-                    for (int i = 0; i < k; ++i) {
-                        as = fma(Qs[r * 4 + i], xs[i], as);
-                        at = fma(Qs[r * 4 + i], xt[i], at);
-                    }
-                    Sp[gpoff(c) + j + r] = as;
-                    Tp[gpoff(c) + j + r] = at;
-                }
+            for (int g = 0; g < 3; ++g) {
+                tl[g] = gcnt[g] ? gpl[g][gcnt[g]] : 0;
+                tr[g] = gcnt[g] ? gpr[g][gcnt[g]] : 0;
             }
-        }
-        __syncthreads();
-        // right: columns [j, j+k) of S and T (rows [0, j)) by Zs, of UQ by Qs
-        // and UZ by Zs (rows [lo, hi])
-#pragma unroll
-        for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = gcnt[g], total = cnt ? gpr[g][cnt] : 0;
-            for (int it = tid; it < total; it += nth) {
-                int lo = 0, hi = cnt - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (gpr[g][mid] <= it) lo = mid; else hi = mid - 1;
-                }
-                const int slot = glist[g][lo], j = swj[slot];
-                const int rr = it - gpr[g][lo];
-                const double* Qs = SCR + slot * GSLOT + SC_Q;
-                const double* Zs = SCR + slot * GSLOT + SC_Z;
-                double x1[4], x2[4];
-                if (rr < j) {
-#pragma unroll
-                    for (int i = 0; i < k; ++i) {
-                        x1[i] = Sp[gpoff(j + i) + rr];
-                        x2[i] = Tp[gpoff(j + i) + rr];
-                    }
-#pragma unroll
-                    for (int c = 0; c < k; ++c) {
-                        double a1 = 0.0, a2 = 0.0;
-#pragma unroll
-                        for (int i = 0; i < k; ++i) {
-                            a1 = fma(x1[i], Zs[c * 4 + i], a1);
-                            a2 = fma(x2[i], Zs[c * 4 + i], a2);
-                        }
-                        Sp[gpoff(j + c) + rr] = a1;
-                        Tp[gpoff(j + c) + rr] = a2;
-                    }
-                } else {
-                    const int r = rr - j + slo[slot];
-#pragma unroll
-                    for (int i = 0; i < k; ++i) {
-                        x1[i] = UQ[(j + i) * w + r];
-                        x2[i] = UZ[(j + i) * w + r];
-                    }
-#pragma unroll
-                    for (int c = 0; c < k; ++c) {
-                        double a1 = 0.0, a2 = 0.0;
-#pragma unroll
-                        for (int i = 0; i < k; ++i) {
-                            a1 = fma(x1[i], Qs[c * 4 + i], a1);
-                            a2 = fma(x2[i], Zs[c * 4 + i], a2);
-                        }
-                        UQ[(j + c) * w + r] = a1;
-                        UZ[(j + c) * w + r] = a2;
-                    }
-                }
+            split_warps(tl, nwarps, bl);
+            split_warps(tr, nwarps, br);
+            const int gL = warp < bl[1] ? 0 : (warp < bl[2] ? 1 : 2);
+            if (warp < bl[3]) {
+                const int first = (warp - bl[gL]) * 32 + lane, stride = (bl[gL + 1] - bl[gL]) * 32;
+                if (gL == 0) apply_left<2>(first, stride, tl[0], gcnt[0], gpl[0], glist[0], swj, SCR, Sp, Tp);
+                else if (gL == 1) apply_left<3>(first, stride, tl[1], gcnt[1], gpl[1], glist[1], swj, SCR, Sp, Tp);
+                else apply_left<4>(first, stride, tl[2], gcnt[2], gpl[2], glist[2], swj, SCR, Sp, Tp);
+            }
+            __syncthreads();
+            const int gR = warp < br[1] ? 0 : (warp < br[2] ? 1 : 2);
+            if (warp < br[3]) {
+                const int first = (warp - br[gR]) * 32 + lane, stride = (br[gR + 1] - br[gR]) * 32;
+                if (gR == 0)
+                    apply_right<2>(first, stride, tr[0], gcnt[0], gpr[0], glist[0], swj, slo, SCR, Sp, Tp, UQ, UZ, w);
+                else if (gR == 1)
+                    apply_right<3>(first, stride, tr[1], gcnt[1], gpr[1], glist[1], swj, slo, SCR, Sp, Tp, UQ, UZ, w);
+                else
+                    apply_right<4>(first, stride, tr[2], gcnt[2], gpr[2], glist[2], swj, slo, SCR, Sp, Tp, UQ, UZ, w);
             }
         }
         __syncthreads();

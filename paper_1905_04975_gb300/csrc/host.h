@@ -132,5 +132,8 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
 // the kernel.  Only stream operations: capturable into a CUDA graph.
 int sched_enqueue(const SchedLaunch& L, cudaStream_t st,
                   const std::function<int(cudaStream_t)>& pre = nullptr);
+// Keeps the per-task timeline of a finished traced launch (opts.timing = 2)
+// for gbr_last_trace.
+int store_trace(const SchedLaunch& L);
 
 }  // namespace gbr

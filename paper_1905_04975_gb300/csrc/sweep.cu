@@ -152,6 +152,10 @@ int run_persistent_sweep(int n, const std::vector<SweepWin>& sw, double* H, int 
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
+    if (L.trace_bytes) {
+        const int rct = store_trace(L);
+        if (rct) return rct;
+    }
     *ntasks_out += L.P.ntasks;
     if (h_err) {
         set_last_error("persistent scheduler (sweep): a task waited longer than wait_limit_ms");
