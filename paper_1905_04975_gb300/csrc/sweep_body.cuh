@@ -77,7 +77,7 @@ __device__ __forceinline__ void sweep_body(int n, double* __restrict__ H, int ld
     double* R = Us + SW * SW;                           // per bulge: v1, v2, tau, beta
     int* rk = reinterpret_cast<int*>(R + MAXB * 4);     // per bulge: local k (or -1: intro)
     int* rl = rk + MAXB;                                // per bulge: length (0: inactive)
-    __shared__ int lo_b, hi_b;                          // active bulges of the step
+    __shared__ int lo_b;                                // active bulges of the step
     __shared__ int pre_l[MAXB + 1], pre_r[MAXB + 1];
     __shared__ short urlo[SW], urhi[SW];                // nonzero rows of each column of U
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -93,83 +93,98 @@ __device__ __forceinline__ void sweep_body(int n, double* __restrict__ H, int ld
         urhi[i] = (short)i;
     }
     __syncthreads();
+    // Per chase step three barriers: warp 0 (which owns every bulge: at most
+    // 32) first records the previous step's U row ranges, finds the active
+    // bulges, computes their reflectors and the prefix sums of the work
+    // items; then all threads apply the left products, then the right ones.
+    // Lane i of warp 0 keeps bulge i's columns and U rows across the step.
+    const int lane = tid & 31, warp = tid >> 5;
+    int my_c1 = 0, my_len = 0, my_lo = 0, my_cnt = 0;   // warp 0: last step's bulge
     for (int tau = t0; tau < t1; ++tau) {
-        __syncthreads();
-        // active bulges: -1 <= k_j <= n - 3, k_j = tau - 3 j - 1 (global)
-        if (tid == 0) {
-            int lo = 0, hi = nb - 1;
-            while (lo <= hi && tau - 3 * lo - 1 > n - 3) ++lo;
-            while (hi >= lo && tau - 3 * hi - 1 < -1) --hi;
-            lo_b = lo;
-            hi_b = hi;
-        }
-        __syncthreads();
-        const int jlo = lo_b, jhi = hi_b;
-        if (jlo > jhi) continue;
-        // reflectors, one thread per bulge
-        if (tid <= jhi - jlo) {
-            const int j = jlo + tid;
-            const int kg = tau - 3 * j - 1;
-            double x0, x1, x2;
-            int len = 3, kl;
-            if (kg < 0) {
-                // introduction (the window starts at row 0)
-                const double h00 = Hs[0], h10 = Hs[1], h01 = Hs[w], h11 = Hs[w + 1];
-                const double h21 = Hs[w + 2];
-                const double ss = sp[2 * j], pp = sp[2 * j + 1];
-                x0 = fma(h00, h00, fma(h01, h10, fma(-ss, h00, pp)));
-                x1 = h10 * (h00 + h11 - ss);
-                x2 = h10 * h21;
-                kl = -1;
-            } else {
-                kl = kg - s0;
-                len = (kg + 3 <= n - 1) ? 3 : 2;
-                x0 = Hs[kl * w + kl + 1];
-                x1 = Hs[kl * w + kl + 2];
-                x2 = (len == 3) ? Hs[kl * w + kl + 3] : 0.0;
+        if (warp == 0) {
+            if (my_len) {
+                for (int c = 0; c < my_len; ++c) {
+                    urlo[my_c1 + c] = (short)my_lo;
+                    urhi[my_c1 + c] = (short)(my_lo + my_cnt - 1);
+                }
+                my_len = 0;
             }
-            double v1, v2, tu, be;
-            refl3(len, x0, x1, x2, &v1, &v2, &tu, &be);
-            R[tid * 4 + 0] = v1;
-            R[tid * 4 + 1] = v2;
-            R[tid * 4 + 2] = tu;
-            R[tid * 4 + 3] = be;
-            rk[tid] = kl;
-            rl[tid] = len;
-        }
-        __syncthreads();
-        const int na = jhi - jlo + 1;
-        // item counts: left = columns [max(k, 0), w); right = rows [0, min(k + 5, w))
-        // of H plus the rows [lo, hi] of U holding the nonzeros of the
-        // reflector's columns
-        if (tid < 32) {
+            __syncwarp();
+            // active bulges: -1 <= k_j <= n - 3, k_j = tau - 3 j - 1 (global)
+            int jlo = 0, jhi = nb - 1;
+            while (jlo <= jhi && tau - 3 * jlo - 1 > n - 3) ++jlo;
+            while (jhi >= jlo && tau - 3 * jhi - 1 < -1) --jhi;
+            const int na = jhi - jlo + 1;
             int il = 0, ir = 0;
-            if (tid < na) {
-                const int kl = rk[tid], len = rl[tid], c1 = kl + 1;
-                il = w - (kl < 0 ? 0 : kl);
+            if (lane < na) {
+                const int j = jlo + lane;
+                const int kg = tau - 3 * j - 1;
+                double x0, x1, x2;
+                int len = 3, kl;
+                if (kg < 0) {
+                    // introduction (the window starts at row 0)
+                    const double h00 = Hs[0], h10 = Hs[1], h01 = Hs[w], h11 = Hs[w + 1];
+                    const double h21 = Hs[w + 2];
+                    const double ss = sp[2 * j], pp = sp[2 * j + 1];
+                    x0 = fma(h00, h00, fma(h01, h10, fma(-ss, h00, pp)));
+                    x1 = h10 * (h00 + h11 - ss);
+                    x2 = h10 * h21;
+                    kl = -1;
+                } else {
+                    kl = kg - s0;
+                    len = (kg + 3 <= n - 1) ? 3 : 2;
+                    x0 = Hs[kl * w + kl + 1];
+                    x1 = Hs[kl * w + kl + 2];
+                    x2 = (len == 3) ? Hs[kl * w + kl + 3] : 0.0;
+                }
+                double v1, v2, tu, be;
+                refl3(len, x0, x1, x2, &v1, &v2, &tu, &be);
+                R[lane * 4 + 0] = v1;
+                R[lane * 4 + 1] = v2;
+                R[lane * 4 + 2] = tu;
+                R[lane * 4 + 3] = be;
+                rk[lane] = kl;
+                // item counts: left = columns [max(k, 0), w); right = rows
+                // [0, min(k + 5, w)) of H plus the rows [lo, hi] of U holding
+                // the nonzeros of the reflector's columns
+                const int c1 = kl + 1;
                 int lo = urlo[c1], hi = urhi[c1];
                 for (int c = 1; c < len; ++c) {
                     lo = min(lo, (int)urlo[c1 + c]);
                     hi = max(hi, (int)urhi[c1 + c]);
                 }
+                il = w - (kl < 0 ? 0 : kl);
                 ir = min(kl + 5, w) + (hi - lo + 1);
                 // length, first U row and U row count packed into one word
-                rl[tid] = len | (lo << 8) | ((hi - lo + 1) << 20);
+                rl[lane] = len | (lo << 8) | ((hi - lo + 1) << 20);
+                my_c1 = c1;
+                my_len = len;
+                my_lo = lo;
+                my_cnt = hi - lo + 1;
+                // 4 len flops per updated vector (dot + axpy): the left
+                // columns but the input one, the right rows of H and of U
+                const int nl = w - (kl < 0 ? 0 : kl) - (kl < 0 ? 0 : 1);
+                wflops += 4ull * len * (unsigned long long)(nl + min(kl + 5, w) + my_cnt);
             }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int a = __shfl_up_sync(0xffffffffu, il, o);
-                const int b = __shfl_up_sync(0xffffffffu, ir, o);
-                if (tid >= o) { il += a; ir += b; }
+                const int a2 = __shfl_up_sync(0xffffffffu, il, o);
+                const int b2 = __shfl_up_sync(0xffffffffu, ir, o);
+                if (lane >= o) { il += a2; ir += b2; }
             }
-            if (tid < na) { pre_l[tid + 1] = il; pre_r[tid + 1] = ir; }
-            if (tid == 0) { pre_l[0] = 0; pre_r[0] = 0; }
+            if (lane < na) { pre_l[lane + 1] = il; pre_r[lane + 1] = ir; }
+            if (lane == 0) {
+                pre_l[0] = 0;
+                pre_r[0] = 0;
+                lo_b = na;
+            }
         }
         __syncthreads();
+        const int na = lo_b;
         // left: rows k+1 .. k+len of the window, columns [max(k,0), w); the
         // input column gets beta and exact zeros
         {
-            const int total = pre_l[na];
+            const int total = na > 0 ? pre_l[na] : 0;
             for (int it = tid; it < total; it += nth) {
                 int lo = 0, hi = na - 1;
                 while (lo < hi) {
@@ -197,7 +212,7 @@ __device__ __forceinline__ void sweep_body(int n, double* __restrict__ H, int ld
         // right: columns k+1 .. k+len of rows [0, min(k+5, w)) of the window
         // and of rows [lo, hi] of U
         {
-            const int total = pre_r[na];
+            const int total = na > 0 ? pre_r[na] : 0;
             for (int it = tid; it < total; it += nth) {
                 int lo = 0, hi = na - 1;
                 while (lo < hi) {
@@ -223,20 +238,6 @@ __device__ __forceinline__ void sweep_body(int n, double* __restrict__ H, int ld
                 p0[w] = fma(-d, v1, y1);
                 if (len == 3) p0[2 * w] = fma(-d, v2, y2);
             }
-        }
-        __syncthreads();
-        // U row ranges of the mixed columns; flops of the step
-        if (tid < na) {
-            const int kl = rk[tid], pk = rl[tid], len = pk & 0xff, c1 = kl + 1;
-            const int lo = (pk >> 8) & 0xfff, cnt = (pk >> 20) & 0xfff;
-            for (int c = 0; c < len; ++c) {
-                urlo[c1 + c] = (short)lo;
-                urhi[c1 + c] = (short)(lo + cnt - 1);
-            }
-            // 4 len flops per updated vector (dot + axpy): the left columns
-            // but the input one, the right rows of H and of U
-            const int nl = w - (kl < 0 ? 0 : kl) - (kl < 0 ? 0 : 1);
-            wflops += 4ull * len * (unsigned long long)(nl + min(kl + 5, w) + cnt);
         }
         __syncthreads();
     }

@@ -243,8 +243,13 @@ def serve_request(base, n: int, frac: float, seed: int, reflectors: int = 8):
     return S, Q, sel
 
 
-def gen_schur_pair(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6):
-    """Random generalized real Schur form (S, T). Returns (S, T, sizes)."""
+def gen_schur_pair(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6,
+                   clusters: bool = False, spread: float = 1e-6, kappa: float = 1.0):
+    """Random generalized real Schur form (S, T). Returns (S, T, sizes).
+
+    clusters / spread / kappa as for schur_form: eigenvalues drawn from 12
+    real and 8 complex centres, the standardized 2x2 parts M made non-normal
+    by kappa (the combination that produces rejected swaps)."""
     sizes = block_sizes(n, rng, frac_1x1)
     S = np.zeros((n, n), dtype=np.float64, order="F")
     T = np.zeros((n, n), dtype=np.float64, order="F")
@@ -255,10 +260,24 @@ def gen_schur_pair(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6):
     T[np.diag_indices(n)] = rng.uniform(0.5, 2.0, n)
     nb1 = int(np.sum(sizes == 1))
     nb2 = int(np.sum(sizes == 2))
-    lam = rng.standard_normal(nb1)
-    a = rng.standard_normal(nb2)
-    b = rng.uniform(0.1, 2.0, nb2) * rng.choice([-1.0, 1.0], nb2)
-    c = -np.sign(b) * rng.uniform(0.1, 2.0, nb2)
+    if clusters:
+        rc = rng.standard_normal(12)
+        ca = rng.standard_normal(8)
+        cb = rng.uniform(0.1, 2.0, 8) * rng.choice([-1.0, 1.0], 8)
+        cc = -np.sign(cb) * rng.uniform(0.1, 2.0, 8)
+        lam = rc[rng.integers(0, 12, nb1)] + spread * rng.standard_normal(nb1)
+        pick = rng.integers(0, 8, nb2)
+        a = ca[pick] + spread * rng.standard_normal(nb2)
+        b = cb[pick] * (1.0 + spread * rng.standard_normal(nb2))
+        c = cc[pick] * (1.0 + spread * rng.standard_normal(nb2))
+    else:
+        lam = rng.standard_normal(nb1)
+        a = rng.standard_normal(nb2)
+        b = rng.uniform(0.1, 2.0, nb2) * rng.choice([-1.0, 1.0], nb2)
+        c = -np.sign(b) * rng.uniform(0.1, 2.0, nb2)
+    if kappa != 1.0:
+        b = b * kappa
+        c = c / kappa
     i1 = i2 = 0
     pos = 0
     for sz in sizes:
@@ -275,10 +294,11 @@ def gen_schur_pair(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6):
 
 
 def gen_problem(n: int, seed: int = 0, *, select_frac: float = 0.3, qz: str = "householder",
-                reflectors: int = 64):
+                reflectors: int = 64, clusters: bool = False, spread: float = 1e-6,
+                kappa: float = 1.0):
     """One generalized reordering instance: (S, T, Q, Z, select)."""
     rng = np.random.default_rng(seed)
-    S, T, sizes = gen_schur_pair(n, rng)
+    S, T, sizes = gen_schur_pair(n, rng, clusters=clusters, spread=spread, kappa=kappa)
     if qz == "identity":
         Q = np.asfortranarray(np.eye(n))
         Z = np.asfortranarray(np.eye(n))
