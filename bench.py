@@ -69,8 +69,8 @@ METRIC = "selected eigenvalues reordered per second"
 NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
                ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
                ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
-               ("g4000", "persistent"): 10.841124e9 + 12.765499e9,
-               ("h4000", "persistent"): 0.220397e9 + 0.188294e9}
+               ("g4000", "persistent"): 11.265847e9 + 13.376260e9,
+               ("h4000", "persistent"): 0.220709e9 + 0.187885e9}
 
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
