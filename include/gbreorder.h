@@ -506,6 +506,25 @@ int gbr_server_get_stats(gbr_server *srv, gbr_server_stats *out);
 void gbr_server_destroy(gbr_server *srv);
 
 /*
+ * Window plan of a bulge-chasing sweep (gbr_qr_sweep), on the host only (no
+ * GPU work): chains of bulges, each chain's windows top to bottom, in
+ * program order.  A window (s, e, t0, t1, b0, nb) runs chain steps
+ * [t0, t1) of the bulges [b0, b0 + nb) over rows / columns [s, e): at step
+ * tau bulge j of the chain sits at k_j = tau - 3 j - 1, and every active
+ * bulge (-1 <= k_j <= n - 3) has its input column at or below s (or is
+ * introduced, s = 0) and its rows k_j + 1 .. k_j + 4 above e (or e = n).
+ *
+ *  n, nshifts     order and (even) shift count
+ *  window, chain  as for gbr_qr_sweep (window capped at 96, chain = shifts
+ *                 per chain, at most window / 3)
+ *  out            host, 6 * max_windows ints or NULL
+ *  max_windows    capacity of out
+ * Returns the number of windows (only the first max_windows are written),
+ * or -1 (n < 0 or odd / negative nshifts), -10 (bad window or chain).
+ */
+int gbr_plan_sweep(int n, int nshifts, int window, int chain, int *out, int max_windows);
+
+/*
  * Window plan of a reordering, on the host only (no GPU work): the diagonal
  * windows that gbr_reorder launches, in program order, assuming no swap is
  * rejected (Section 3.2, Fig. 2: one chain of windows per group of at most

@@ -84,6 +84,8 @@ _REORDER_GEN_ARGS = [ctypes.c_int] + [ctypes.c_void_p, ctypes.c_int] * 4 + [
 SYMBOLS = {
     "gbr_default_opts": (None, [ctypes.POINTER(GbrOpts)]),
     "gbr_reorder_gen": (ctypes.c_int, _REORDER_GEN_ARGS),
+    "gbr_plan_sweep": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
+                                      ctypes.c_int]),
     "gbr_qr_sweep": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_int, _dp, _dp,
                                     ctypes.POINTER(GbrOpts), ctypes.POINTER(GbrStats),
@@ -486,6 +488,19 @@ def qr_sweep(H, Q, shifts, *, opts: GbrOpts | None = None, stream=None, **kw) ->
     if rc < 0:
         raise GbrError(rc, status_string(rc))
     return SweepResult(status=rc, stats=stats)
+
+
+def plan_sweep(n, nshifts, window=64, chain=16):
+    """Host-only window plan of a bulge-chasing sweep: int array (k x 6) of
+    (s, e, t0, t1, b0, nb) per window, in program order."""
+    lib = load()
+    cnt = lib.gbr_plan_sweep(int(n), int(nshifts), int(window), int(chain), None, 0)
+    if cnt < 0:
+        raise GbrError(cnt, "invalid sweep plan arguments")
+    out = np.zeros(6 * max(cnt, 1), dtype=np.int32)
+    cnt = lib.gbr_plan_sweep(int(n), int(nshifts), int(window), int(chain), out.ctypes.data_as(_ip),
+                             cnt)
+    return out[:6 * cnt].reshape(cnt, 6)
 
 
 def plan(sub, select, window=128, chain=64, with_q=True):

@@ -271,6 +271,26 @@ using namespace gbr;
 
 extern "C" {
 
+int gbr_plan_sweep(int n, int nshifts, int window, int chain, int* out, int max_windows) {
+    if (n < 0 || nshifts < 0 || (nshifts & 1)) return -1;
+    if (window < 4 || window > WMAX || chain < 1) return -10;
+    gbr_opts o;
+    gbr_default_opts(&o);
+    o.window = window;
+    o.chain = chain;
+    int w, nbc;
+    sweep_shape(o, &w, &nbc);
+    std::vector<SweepWin> wins;
+    plan_sweep(n, nshifts / 2, w, nbc, wins);
+    if (out)
+        for (int i = 0; i < (int)wins.size() && i < max_windows; ++i) {
+            const SweepWin& x = wins[i];
+            int* r = out + 6 * i;
+            r[0] = x.s; r[1] = x.e; r[2] = x.t0; r[3] = x.t1; r[4] = x.b0; r[5] = x.nb;
+        }
+    return (int)wins.size();
+}
+
 int gbr_qr_sweep(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, const double* shift_re,
                  const double* shift_im, const gbr_opts* opts, gbr_stats* stats,
                  void* cuda_stream) {
