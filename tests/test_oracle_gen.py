@@ -221,3 +221,22 @@ def test_rejected_swap_changes_nothing():
     assert r["status"] == 1 and r["nrej"] == 1 and r["nswaps"] == 0
     assert np.array_equal(r["S"], S) and np.array_equal(r["T"], T)
     assert np.array_equal(r["Q"], Q) and np.array_equal(r["Z"], Q)
+
+
+def test_eigenvalues_of_a_real_pair_block():
+    """A 2x2 block whose pencil has two real eigenvalues (which rounding in a
+    swap could produce) gives both roots, the larger first, as LAPACK's
+    generalized eigenvalues of that block; a 1x1 block with t = 0 gives an
+    infinite eigenvalue."""
+    Tb = np.array([[1.5, 0.3], [0.0, 0.8]])
+    M = np.array([[1.0, 2.0], [0.5, -0.7]])          # real eigenvalues
+    S = np.zeros((3, 3))
+    T = np.zeros((3, 3))
+    S[:2, :2] = Tb @ M
+    T[:2, :2] = Tb
+    S[2, 2], T[2, 2] = 1.0, 0.0
+    S[0, 2], T[0, 2] = 0.4, 0.2
+    ev = oracle.gen_eigenvalues(S, T)
+    ref = np.sort(np.linalg.eigvals(M).real)[::-1]
+    assert np.allclose(ev[:2].real, ref, rtol=1e-14, atol=0) and np.all(ev[:2].imag == 0)
+    assert np.isinf(ev[2].real)

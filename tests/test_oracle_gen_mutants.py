@@ -36,6 +36,8 @@ MUTANTS = [
      "*b = s11 * t22 + s22 * t11 + s21 * t12;"),
     ("second reflector skipped", "house0(k - 1, x, v2, &tau2);", "tau2 = 0.0;"),
     ("weak test dropped", "if (lowa > tha || lowb > thb) return 1;", ";"),
+    ("real pair roots swapped", "wr[j] = m + r; wi[j] = 0.0;\n                wr[j + 1] = m - r;",
+     "wr[j] = m - r; wi[j] = 0.0;\n                wr[j + 1] = m + r;"),
 ]
 
 BATTERY = r"""
@@ -54,6 +56,7 @@ checks = [
     lambda: [P.test_generalized_sylvester_residual(p, q) for p, q in [(1, 1), (1, 2), (2, 1), (2, 2)]],
     lambda: P.test_equal_eigenvalues_and_selection_rules(),
     lambda: P.test_rejected_swap_changes_nothing(),
+    lambda: P.test_eigenvalues_of_a_real_pair_block(),
 ]
 failed = 0
 for c in checks:
