@@ -63,3 +63,40 @@ def test_serve_requests_are_standard_subblocks():
         # the sub-block is the base form's principal block at some offset
         k0 = next(i for i in range(1025 - m) if np.array_equal(base[0][i:i + m, i:i + m], S))
         assert k0 == 0 or base[0][k0, k0 - 1] == 0.0
+
+
+def test_generalized_pair_laws():
+    """(S, T): T upper triangular with diagonal in [0.5, 2]; a 1x1 block of
+    S is lambda t_jj; a 2x2 block is T_b M with M standardized, so the
+    pencil block has M's complex pair; Q and Z orthogonal."""
+    from tests.helpers import gen_block_eigs, is_gen_schur
+    S, T, Q, Z, sel = si.gen_problem(300, 5, select_frac=0.35, reflectors=8)
+    assert is_gen_schur(S, T)
+    d = np.diag(T)
+    assert np.all((d >= 0.5) & (d <= 2.0))
+    ev = gen_block_eigs(S, T)
+    for j, sz in blocks(S):
+        if sz == 2:
+            M = np.linalg.solve(T[j:j + 2, j:j + 2], S[j:j + 2, j:j + 2])
+            assert abs(M[0, 0] - M[1, 1]) <= 1e-12 * max(1.0, abs(M[0, 0]))
+            assert M[0, 1] * M[1, 0] < 0
+            assert abs(ev[j].imag) > 0 and np.isclose(ev[j], np.conj(ev[j + 1]))
+            assert sel[j] == sel[j + 1]
+    for X in (Q, Z):
+        assert np.linalg.norm(X.T @ X - np.eye(300)) <= 1e-12
+    assert round(0.35 * 300) <= sel.sum() <= round(0.35 * 300) + 1
+
+
+def test_hessenberg_sweep_inputs():
+    """H upper Hessenberg with N(0,1) entries; shifts in pairs, alternately
+    a conjugate pair with imaginary part in [0.1, 1] and two real shifts."""
+    H, Q, sh = si.hessenberg_problem(200, 2, nshifts=8, reflectors=8)
+    assert np.all(np.tril(H, -2) == 0.0) and np.all(np.diag(H, -1) != 0.0)
+    assert len(sh) == 8
+    for b in range(4):
+        a1, a2 = sh[2 * b], sh[2 * b + 1]
+        if b % 2 == 0:
+            assert a1 == np.conj(a2) and 0.1 <= a1.imag <= 1.0
+        else:
+            assert a1.imag == 0.0 and a2.imag == 0.0
+    assert np.linalg.norm(Q.T @ Q - np.eye(200)) <= 1e-12
