@@ -201,6 +201,13 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
     std::vector<HostTask>& T = G.t;
     std::vector<std::pair<int, int>> edges;
     T.clear();
+    {
+        // capacity: per window its task and at most the near tiles, the far
+        // tiles of the left / right panels and the Q and Z tiles
+        const size_t per = 2 + 4 * (size_t)UPD_NEAR / UPD_BM + 4 * ((size_t)n / FAR + 1);
+        T.reserve(wins.size() * per);
+        edges.reserve(wins.size() * per);
+    }
     for (int i = 0; i < (int)wins.size(); ++i) {
         const int s = wins[i].s, e = wins[i].e, w = e - s;
         const int iw = (int)T.size();
@@ -349,21 +356,29 @@ void build_graph(int n, const std::vector<Window>& wins, bool withQ, const CostM
         for (int k = 0; k < NT; ++k) th.emplace_back(worker, k);
         for (auto& x : th) x.join();
     }
-    for (auto& v : tedges) edges.insert(edges.end(), v.begin(), v.end());
     // No edge is listed twice: a pair is emitted only in its first common cell
     // row, where the thread stamps each predecessor once per task, and a
-    // window task overlaps none of its own tiles.
+    // window task overlaps none of its own tiles.  CSR straight from the
+    // window-to-tile edges and the threads' lists, in that order.
     const int nt = (int)T.size();
     G.ndeps.assign(nt, 0);
     G.soff.assign(nt + 1, 0);
-    G.succ.resize(edges.size());
-    for (auto& ed : edges) {
-        G.ndeps[ed.second]++;
-        G.soff[ed.first + 1]++;
-    }
+    size_t ne = edges.size();
+    for (const auto& v : tedges) ne += v.size();
+    G.succ.resize(ne);
+    auto count = [&](const std::vector<std::pair<int, int>>& v) {
+        for (const auto& ed : v) {
+            G.ndeps[ed.second]++;
+            G.soff[ed.first + 1]++;
+        }
+    };
+    count(edges);
+    for (const auto& v : tedges) count(v);
     for (int i = 0; i < nt; ++i) G.soff[i + 1] += G.soff[i];
     std::vector<int> fill(G.soff.begin(), G.soff.end() - 1);
-    for (auto& ed : edges) G.succ[fill[ed.first]++] = ed.second;
+    for (const auto& ed : edges) G.succ[fill[ed.first]++] = ed.second;
+    for (const auto& v : tedges)
+        for (const auto& ed : v) G.succ[fill[ed.first]++] = ed.second;
 }
 
 // Program order for the persistent schedule.  Two windows whose row ranges do
