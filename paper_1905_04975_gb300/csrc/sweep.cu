@@ -44,33 +44,6 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-// Windows of one sweep, in program order: chain by chain (chain c holds
-// bulges [c nbc, c nbc + nb_c)), each chain's windows top to bottom.  A
-// window [s, e) runs the chain steps [t0, t1) during which every active
-// bulge j (k_j = tau - 3 j - 1) has its input column at or below s and its
-// rows k_j + 1 .. k_j + 4 above e (or e = n): t1 = e - 3 unless e = n; the
-// next window starts at the top bulge's position.  The first window of a
-// chain starts at row 0 and holds all of the chain's introductions
-// (3 (nb_c - 1) < w - 3).
-void plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out) {
-    out.clear();
-    if (n < 3 || nbulges <= 0) return;
-    for (int c = 0, b0 = 0; b0 < nbulges; ++c, b0 += nbc) {
-        const int nbk = std::min(nbc, nbulges - b0);
-        const int t_end = (n - 3) + 3 * (nbk - 1) + 2;  // exclusive
-        int t0 = 0, s = 0;
-        for (;;) {
-            const int e = std::min(n, s + w);
-            const int t1 = (e == n) ? t_end : std::min(t_end, e - 3);
-            out.push_back(SweepWin{s, e, t0, t1, b0, nbk});
-            if (t1 >= t_end) break;
-            const int ktop = t1 - 3 * (nbk - 1) - 1;
-            s = std::max(0, ktop);
-            t0 = t1;
-        }
-    }
-}
-
 cudaError_t launch_validate_hess(int n, const double* H, int ldH, DevCounters* ctr, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int threads = 256, grid = std::min(1024, (n * 32 + threads - 1) / threads);
