@@ -70,7 +70,8 @@ NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
                ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
                ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
                ("g4000", "persistent"): 11.265847e9 + 13.376260e9,
-               ("h4000", "persistent"): 0.220709e9 + 0.187885e9}
+               ("h4000", "persistent"): 0.220709e9 + 0.187885e9,
+               ("g4000", "ozaki"): 15.672467e9 + 25.754819e9}
 
 
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
@@ -727,7 +728,7 @@ def run_gen(args, wl):
         roof = {"kernel": "sched_kernel<pair> (persistent: pair window tasks + bf16 slice-product "
                           "tiles of S, T, Q, Z)",
                 "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": achieved / bf16_peak, "traffic": None,
+                "frac": achieved / bf16_peak, "traffic": NCU_TRAFFIC.get((wl["name"], "ozaki")),
                 "peak_source": f"{src} bf16 {bf16_peak} TF/s",
                 "flops_per_launch": work, "bf16_slice_flops": 28.0 * st0.upd_flops,
                 "fp64_window_flops": st0.win_flops, "avg_launch_ms": ms_k,
