@@ -212,7 +212,8 @@ int gbr_reorder_gen(int n, double *S, int ldS, double *T, int ldT, double *Q, in
  *  4 Q, 5 ldQ     device or NULL; overwritten by Q Q3
  *  6 nshifts      even; 7 shift_re, 8 shift_im: host, the shifts; each pair
  *                 (2i, 2i+1) is two real shifts or a complex-conjugate pair
- *  9 opts         NULL for the defaults; window = window size (capped at
+ *  9 opts         NULL for window 64 and 16 shifts per chain (otherwise the
+ *                 gbr_default_opts values); window = window size (capped at
  *                 96), chain = shifts per chain of bulges (capped at w / 3);
  *                 precision GBR_PREC_DMMA only; validate checks the form
  * 10 stats        host or NULL (windows, chains, update and window flops,

@@ -269,7 +269,14 @@ int gbr_qr_sweep(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, con
                  void* cuda_stream) {
     auto t0 = std::chrono::steady_clock::now();
     gbr_opts o;
-    if (opts) o = *opts; else gbr_default_opts(&o);
+    if (opts) {
+        o = *opts;
+    } else {
+        // the measured best shape of a sweep (window 64, 16 shifts per chain)
+        gbr_default_opts(&o);
+        o.window = 64;
+        o.chain = 16;
+    }
     const int ld1 = n > 1 ? n : 1;
     if (n < 0) return -1;
     if (n > 0 && !H) return -2;
