@@ -20,9 +20,10 @@
 //
 // The window task mirrors the standard-form one (window_body.cuh): every
 // selected block whose upper neighbour is unselected swaps with it in the
-// same step (one thread computes one swap), then the left transformations
-// (rows of S and T) and the right ones (columns of S and T, the columns of
-// the accumulators UQ and UZ) are applied by all threads.
+// same step (8 lanes compute one swap, the octets of a warp on swaps of one
+// size), then the left transformations (rows of S and T) and the right ones
+// (columns of S and T, the columns of the accumulators UQ and UZ) are
+// applied by all warps, split among the swap sizes by their work.
 #pragma once
 
 #include "common.cuh"
