@@ -213,8 +213,9 @@ int gbr_reorder_gen(int n, double *S, int ldS, double *T, int ldT, double *Q, in
  *  6 nshifts      even; 7 shift_re, 8 shift_im: host, the shifts; each pair
  *                 (2i, 2i+1) is two real shifts or a complex-conjugate pair
  *  9 opts         NULL for window 64 and 16 shifts per chain (otherwise the
- *                 gbr_default_opts values); window = window size (capped at
- *                 96), chain = shifts per chain of bulges (capped at w / 3);
+ *                 gbr_default_opts values); window = window size (8 .. 128,
+ *                 capped at 96), chain = shifts per chain of bulges (capped
+ *                 at w / 3);
  *                 precision GBR_PREC_DMMA only; validate checks the form
  * 10 stats        host or NULL (windows, chains, update and window flops,
  *                 kernel times with opts.timing)
@@ -516,8 +517,8 @@ void gbr_server_destroy(gbr_server *srv);
  * introduced, s = 0) and its rows k_j + 1 .. k_j + 4 above e (or e = n).
  *
  *  n, nshifts     order and (even) shift count
- *  window, chain  as for gbr_qr_sweep (window capped at 96, chain = shifts
- *                 per chain, at most window / 3)
+ *  window, chain  as for gbr_qr_sweep (window 8 .. 128, capped at 96,
+ *                 chain = shifts per chain, at most window / 3)
  *  out            host, 6 * max_windows ints or NULL
  *  max_windows    capacity of out
  * Returns the number of windows (only the first max_windows are written),

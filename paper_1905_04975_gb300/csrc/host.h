@@ -58,7 +58,7 @@ double update_flops(int n, const std::vector<Window>& win, bool withQ);
 struct SweepWin {
     int s, e, t0, t1, b0, nb;
 };
-void plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out);
+int plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out);
 
 // ---------------------------------------------------------------------------
 // Task graph and queue order (Section 3.2, Fig. 2)

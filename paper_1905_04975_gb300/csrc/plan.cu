@@ -173,10 +173,11 @@ double update_flops(int n, const std::vector<Window>& win, bool withQ) {
 // rows k_j + 1 .. k_j + 4 above e (or e = n): t1 = e - 3 unless e = n; the
 // next window starts at the top bulge's position.  The first window of a
 // chain starts at row 0 and holds all of the chain's introductions
-// (3 (nb_c - 1) < w - 3).
-void plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out) {
+// (3 (nb_c - 1) < w - 3).  Returns -1 (and no windows) if a window is too
+// short to move its chain (w <= 3 nb_c + 1).
+int plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out) {
     out.clear();
-    if (n < 3 || nbulges <= 0) return;
+    if (n < 3 || nbulges <= 0) return 0;
     for (int c = 0, b0 = 0; b0 < nbulges; ++c, b0 += nbc) {
         const int nbk = std::min(nbc, nbulges - b0);
         const int t_end = (n - 3) + 3 * (nbk - 1) + 2;  // exclusive
@@ -184,6 +185,11 @@ void plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out) 
         for (;;) {
             const int e = std::min(n, s + w);
             const int t1 = (e == n) ? t_end : std::min(t_end, e - 3);
+            // a window too short for the chain makes no progress
+            if (t1 <= t0) {
+                out.clear();
+                return -1;
+            }
             out.push_back(SweepWin{s, e, t0, t1, b0, nbk});
             if (t1 >= t_end) break;
             const int ktop = t1 - 3 * (nbk - 1) - 1;
@@ -191,6 +197,7 @@ void plan_sweep(int n, int nbulges, int w, int nbc, std::vector<SweepWin>& out) 
             t0 = t1;
         }
     }
+    return 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -169,7 +169,7 @@ int sweep_device(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, con
     int w, nbc;
     sweep_shape(o, &w, &nbc);
     std::vector<SweepWin> wins;
-    plan_sweep(n, nb, w, nbc, wins);
+    if (plan_sweep(n, nb, w, nbc, wins)) return -10;
     double flops = 0.0;
     std::vector<cudaEvent_t> ev;
     struct Cleanup {
@@ -246,7 +246,7 @@ extern "C" {
 
 int gbr_plan_sweep(int n, int nshifts, int window, int chain, int* out, int max_windows) {
     if (n < 0 || nshifts < 0 || (nshifts & 1)) return -1;
-    if (window < 4 || window > WMAX || chain < 1) return -10;
+    if (window < 8 || window > WMAX || chain < 1) return -10;
     gbr_opts o;
     gbr_default_opts(&o);
     o.window = window;
@@ -254,7 +254,7 @@ int gbr_plan_sweep(int n, int nshifts, int window, int chain, int* out, int max_
     int w, nbc;
     sweep_shape(o, &w, &nbc);
     std::vector<SweepWin> wins;
-    plan_sweep(n, nshifts / 2, w, nbc, wins);
+    if (window < 8 || plan_sweep(n, nshifts / 2, w, nbc, wins)) return -10;
     if (out)
         for (int i = 0; i < (int)wins.size() && i < max_windows; ++i) {
             const SweepWin& x = wins[i];
@@ -287,7 +287,8 @@ int gbr_qr_sweep(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, con
         const double a1 = shift_re[j], b1 = shift_im[j], a2 = shift_re[j + 1], b2 = shift_im[j + 1];
         if (!((b1 == 0.0 && b2 == 0.0) || (a1 == a2 && b1 == -b2))) return -6;
     }
-    if (o.window < 4 || o.window > WMAX || o.chain < 1) return -10;
+    // a sweep window holds at least one bulge with room to move (w >= 8)
+    if (o.window < 8 || o.window > WMAX || o.chain < 1) return -10;
     if (o.precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
     if (o.sched != GBR_SCHED_PERSISTENT && o.sched != GBR_SCHED_SEQUENTIAL) return -10;
     if (stats) memset(stats, 0, sizeof *stats);

@@ -165,6 +165,7 @@ def test_qr_sweep_argument_checks(lib):
     assert call(4, d, 4, None, 4, 4, R, B) == -6
     assert call(4, d, 4, None, 4, 4, None, I) == -6
     assert call(4, d, 4, None, 4, 4, R, I, g.make_opts(window=2)) == -10
+    assert call(4, d, 4, None, 4, 4, R, I, g.make_opts(window=4)) == -10  # no room to move
     assert call(4, d, 4, None, 4, 4, R, I, g.make_opts(precision="ozaki")) == g.ERR_UNSUPPORTED
     assert call(2, d, 2, None, 2, 4, R, I) == 0     # n < 3: nothing to do
     assert call(0, None, 1, None, 1, 0, None, None, None) == 0

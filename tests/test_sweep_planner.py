@@ -141,3 +141,15 @@ def test_windowed_replay_matches_oracle(n, ns, window, chain):
     assert np.all(np.tril(Hr, -2) == 0.0)
     assert np.max(np.abs(Hr - Ho)) <= 1e-10 * np.linalg.norm(H)
     assert np.max(np.abs(Qr - Qo)) <= 1e-8
+
+
+def test_plan_random_shapes():
+    """Seeded random shapes (n, shifts, window >= 8, chain): the invariants
+    hold and every chain makes progress; a window below 8 is refused."""
+    rng = np.random.default_rng(7)
+    for _ in range(400):
+        n = int(rng.choice([3, 4, 5, 6, 7, 8, 10, 13, 20, 33, 64, 65, 96, 97, 128, 200, 257]))
+        check_plan(n, 2 * int(rng.integers(1, 41)), int(rng.integers(8, 129)),
+                   int(rng.integers(1, 81)))
+    for w in (4, 5, 7):
+        assert g.load().gbr_plan_sweep(100, 8, w, 4, None, 0) == -10
