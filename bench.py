@@ -1,13 +1,17 @@
 #!/usr/bin/env python
 """Benchmark: selected eigenvalues reordered per second on one GB300.
 
-Workload (default): a real Schur form of order n = 4000 from the seeded
+Workload (default): a real Schur form of order n = 16000 from the seeded
 generator (60% of positions in 1x1 blocks, 40% in standardized 2x2 blocks,
-N(0,1) strict upper part), Q = product of 64 seeded Householder reflectors,
-35% of the eigenvalues selected, window 128, chain 64, FP64 DMMA updates.
+N(0,1) strict upper part) with its eigenvalues in 20 tight clusters (spread
+1e-6), Q = product of 64 seeded Householder reflectors, 50% of the
+eigenvalues selected, window 128, chain 64.  The line's own fields are the
+FP64 updates on the FMA pipe; `split_precision` holds the same workload with
+split-precision updates on the tensor cores (both with the accuracy of one
+result), `fp64_tensor_core` a shorter run with FP64 DMMA updates.
 
 A step is one full reordering (every planner, window, update and eigenvalue
-kernel of the call).  S and Q (256 MB, larger than L2) are restored from a
+kernel of the call).  S and Q (4.1 GB, larger than L2) are restored from a
 pristine device copy before each step, outside the timed region; that
 rewrite also evicts them from L2.  Each step is timed with CUDA events on the
 library's stream; `value` = selected eigenvalues of all steps (and ranks) /
@@ -48,7 +52,7 @@ WORKLOADS = {
                   chain=64),
     "n400": dict(name="n400", n=400, select=0.30, q="identity", window=128, chain=64),
     "n16000c": dict(name="n16000c", n=16000, select=0.50, q="64 Householder reflectors",
-                    window=128, chain=64),
+                    window=128, chain=64, clusters="20 clusters, spread 1e-6"),
     "batch4096": dict(name="batch4096", kind="batch", count=4096, nmin=32, nmax=512,
                       select="U(0.2, 0.6) per instance", q="min(n, 64) Householder reflectors"),
     "eigvec4000": dict(name="eigvec4000", kind="eigvec", n=4000, select=0.35,
@@ -61,6 +65,12 @@ WORKLOADS = {
                   q="64 Householder reflectors", window=64, chain=16),
 }
 SWEEP_METRIC = "shifts chased per second (one bulge-chasing sweep)"
+
+# FP64 on the FMA pipe: 2 fused multiply-adds per clock per SM (the nominal
+# 1.25 TFLOP/s FP64 rate of the part), 152 SMs, 2070 MHz maximum SM clock.
+FP64_FMA_PEAK = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_FMA_PEAK_SOURCE = ("FP64 FMA: 2 per clock per SM x 152 SMs x 2070 MHz x 2 flops "
+                        "(nominal FP64 1.25 TFLOP/s); measured DFMA probe 1.195 TFLOP/s")
 METRIC = "selected eigenvalues reordered per second"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
@@ -69,8 +79,8 @@ METRIC = "selected eigenvalues reordered per second"
 NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
                ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
                ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
-               ("g4000", "persistent"): 11.265847e9 + 13.376260e9,
-               ("h4000", "persistent"): 0.220709e9 + 0.187885e9,
+               ("g4000", "persistent-dmma"): 11.265847e9 + 13.376260e9,
+               ("h4000", "persistent-dmma"): 0.220709e9 + 0.187885e9,
                ("g4000", "ozaki"): 15.672467e9 + 25.754819e9}
 
 
@@ -87,6 +97,17 @@ def whole_job_rate(units, local_ms, dist=None, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         job_ms = float(t.item())
     return units * world / (job_ms / 1e3), job_ms
+
+
+def fp64_roof_basis(prec, pk, src):
+    """(tile name, bound, peak TFLOP/s, peak source) of the FP64 update tiles
+    of a precision: FMA-pipe tiles against the FP64 FMA rate, DMMA tiles
+    against the FP64 tensor rate (measured bf16 peak x nominal ratio)."""
+    if prec == "fma":
+        return "FP64 FMA tiles", "alu", FP64_FMA_PEAK, FP64_FMA_PEAK_SOURCE
+    return ("DMMA tiles", "tensor", pk["bf16_tflops"] * (1.25 / 2250.0),
+            f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 1.25/2250 "
+            "(FP64 DMMA probe: 1.047 TF/s)")
 
 
 def peaks():
@@ -157,15 +178,9 @@ def make_inputs(wl, seed=0):
     return si.config("n4000" if wl["name"] == "eigvec4000" else wl["name"], seed)
 
 
-def cpu_oracle_sample(S, Q, sel, budget_s=15.0, run=None, what="workload"):
-    """Time the oracle on the first k selected blocks (top to bottom) of the
-    workload, k grown until ~budget_s of work, and extrapolate to the whole
-    workload by the number of adjacent block swaps it needs.  run(sub_sel)
-    runs the oracle and returns its result dict (default: the standard-form
-    reordering of (S, Q))."""
-    import oracle
-    if run is None:
-        run = lambda sub_sel: oracle.reorder(S, Q, sub_sel)
+def block_list(S, sel):
+    """Diagonal blocks of S: starts, sizes and per-block selection (a 2x2
+    block is selected if either position is)."""
     n = S.shape[0]
     sub = np.append(np.diag(S, -1) != 0, False)
     starts, sizes = [], []
@@ -176,140 +191,289 @@ def cpu_oracle_sample(S, Q, sel, budget_s=15.0, run=None, what="workload"):
         sizes.append(sz)
         p += sz
     selb = [bool(sel[s] or (sz == 2 and sel[s + 1])) for s, sz in zip(starts, sizes)]
+    return starts, sizes, selb
 
-    def swaps_needed(k_blocks):
-        cnt, unsel_above, taken = 0, 0, 0
-        for b, flag in enumerate(selb):
-            if flag:
-                if taken >= k_blocks:
-                    break
-                cnt += unsel_above
-                taken += 1
-            else:
-                unsel_above += 1
-        return cnt
 
+def first_selected(n, starts, sizes, selb, k):
+    """Selection of the first k selected blocks (top to bottom)."""
+    sub_sel = np.zeros(n, np.int32)
+    taken = 0
+    for s, sz, flag in zip(starts, sizes, selb):
+        if flag and taken < k:
+            sub_sel[s:s + sz] = 1
+            taken += 1
+    return sub_sel
+
+
+def swaps_needed(selb, k_blocks):
+    """Adjacent block swaps of the stable partition of the first k selected
+    blocks (each passes every unselected block above it)."""
+    cnt, unsel_above, taken = 0, 0, 0
+    for flag in selb:
+        if flag:
+            if taken >= k_blocks:
+                break
+            cnt += unsel_above
+            taken += 1
+        else:
+            unsel_above += 1
+    return cnt
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def calibrate_sample(S, sel, run, budget_s):
+    """Grows k (the first k selected blocks) until run(sub_sel) takes about
+    budget_s / 3.  Returns (k, result, seconds)."""
+    n = S.shape[0]
+    starts, sizes, selb = block_list(S, sel)
     nsel_blocks = sum(selb)
-    full_swaps = swaps_needed(nsel_blocks)
-    k = max(1, nsel_blocks // 8)
+    k = max(1, nsel_blocks // 64)
     while True:
-        sub_sel = np.zeros(n, np.int32)
-        taken = 0
-        for s, sz, flag in zip(starts, sizes, selb):
-            if flag and taken < k:
-                sub_sel[s:s + sz] = 1
-                taken += 1
+        sub_sel = first_selected(n, starts, sizes, selb, k)
         t0 = time.perf_counter()
         r = run(sub_sel)
         dt = time.perf_counter() - t0
         if dt >= budget_s / 3 or k >= nsel_blocks:
-            break
+            return k, r, dt
         k = min(nsel_blocks, int(k * 1.6) + 1)
-    est_full = dt * full_swaps / max(r["nswaps"], 1)
+
+
+def sample_record(S, sel, k, dt, nswaps, cores, what, who):
+    """A timed sample of the first k selected blocks in the metric's unit:
+    the eigenvalue-equivalent work it did (the workload's selected
+    eigenvalues x its share of the workload's adjacent block swaps) over
+    the time it took."""
+    n = S.shape[0]
+    starts, sizes, selb = block_list(S, sel)
+    nsel_blocks = sum(selb)
+    full_swaps = swaps_needed(selb, nsel_blocks)
     nsel = int(np.sum([sz for sz, f in zip(sizes, selb) if f]))
-    return {"value": nsel / est_full, "unit": "eigs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"first {k} of {nsel_blocks} selected blocks of the n={n} {what} "
-                       f"({r['nswaps']} of {full_swaps} block swaps) timed {dt:.1f} s on 1 core, "
-                       f"scaled by swap count to the full workload (est. {est_full:.0f} s)")}
+    share = nswaps / max(full_swaps, 1)
+    est_full = dt / max(share, 1e-300)
+    return {"value": nsel * share / dt, "unit": "eigs/s", "cores": cores, "kind": "oracle",
+            "secs": dt, "est_full_s": est_full, "k": k,
+            "sample": (f"{who}: first {k} of {nsel_blocks} selected blocks of the n={n} {what} "
+                       f"({nswaps} of {full_swaps} block swaps) in {dt:.2f} s on {cores} "
+                       f"core(s); value = the eigenvalue-equivalent share of the workload done "
+                       f"(swaps) per second (whole workload est. {est_full:.0f} s)")}
+
+
+def cpu_oracle_sample(S, Q, sel, budget_s=15.0, run=None, what="workload", k=None, lib=None,
+                      cores=1, who="oracle, 1 thread"):
+    """The oracle on the first k selected blocks (top to bottom) of the
+    workload; k grown until ~budget_s / 3 of work unless given.  run(sub_sel)
+    runs the oracle and returns its result dict (default: the standard-form
+    reordering of (S, Q) with the oracle library `lib`)."""
+    import oracle
+    if run is None:
+        run = lambda sub_sel: oracle.reorder(S, Q, sub_sel, lib=lib)
+    if k is None:
+        k, r, dt = calibrate_sample(S, sel, run, budget_s)
+    else:
+        n = S.shape[0]
+        starts, sizes, selb = block_list(S, sel)
+        sub_sel = first_selected(n, starts, sizes, selb, k)
+        t0 = time.perf_counter()
+        r = run(sub_sel)
+        dt = time.perf_counter() - t0
+    return sample_record(S, sel, k, dt, r["nswaps"], cores, what, who)
+
+
+def dtrsen_sample(S, Q, sel, k, cores):
+    """LAPACK dtrsen (scipy, called, not read) on the same first k selected
+    blocks, Q accumulated, no condition numbers; BLAS threads = cores."""
+    from scipy.linalg import lapack
+    n = S.shape[0]
+    starts, sizes, selb = block_list(S, sel)
+    sub_sel = first_selected(n, starts, sizes, selb, k)
+    St, Qt = np.asfortranarray(S.copy()), np.asfortranarray(Q.copy())
+    t0 = time.perf_counter()
+    out = lapack.dtrsen(sub_sel, St, Qt, job="N", wantq=1, overwrite_t=1, overwrite_q=1,
+                        lwork=max(1, n), liwork=1)
+    dt = time.perf_counter() - t0
+    info = out[-1]
+    rec = sample_record(S, sel, k, dt, swaps_needed(selb, k), cores, "workload",
+                        "scipy LAPACK dtrsen (OpenBLAS)")
+    rec["kind"] = "library"
+    rec["info"] = int(info)
+    return rec
+
+
+def cpu_leg(wl, budget_s=15.0):
+    """The CPU baselines of a reordering workload, in a process of their own
+    (no torch): the oracle single-threaded, the same oracle built with
+    OpenMP on all host cores, and scipy's dtrsen, on the same bounded
+    sample (the first k selected blocks).  Prints one JSON object."""
+    import oracle
+    if wl.get("kind") == "batch":
+        print(json.dumps(batch_cpu_sample(batch_inputs(wl), budget_s=budget_s)), flush=True)
+        return 0
+    S, Q, sel = make_inputs(wl)
+    cores = host_cores()
+    one = cpu_oracle_sample(S, Q, sel, budget_s=budget_s, lib=oracle.load())
+    k = one["k"]
+    omp = cpu_oracle_sample(S, Q, sel, k=k, lib=oracle.load_omp(), cores=cores,
+                            who=f"oracle, OpenMP {cores} threads")
+    lap = dtrsen_sample(S, Q, sel, k, cores)
+    best = omp if omp["value"] >= one["value"] else one
+    out = dict(best)
+    out.update({"cpu_model": cpu_model(), "host_cores": cores,
+                "single_thread": one, "openmp": omp, "scipy_dtrsen": lap})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_cpu_leg(wl):
+    """Runs cpu_leg in a fresh interpreter (OpenMP and BLAS threads on all
+    host cores, nothing else running); returns its JSON object or an error
+    record."""
+    cores = host_cores()
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores))
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload",
+                        wl["name"]], capture_output=True, text=True, env=env)
+    if p.returncode != 0:
+        return {"error": p.stderr[-500:]}
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def reference_reorder_steps(args, S, Q, sel, what, run_one, budget_s, cores, who):
+    """Reference-arm steps: each one the oracle on the same bounded sample
+    (k calibrated once, untimed), timed as it runs.  Returns (value,
+    ms_per_step, last record)."""
+    k, _, _ = calibrate_sample(S, sel, run_one, budget_s)
+    recs = []
+    for i in range(args.warmup + args.steps):
+        rec = cpu_oracle_sample(S, Q, sel, k=k, run=run_one, what=what, cores=cores, who=who)
+        if i >= args.warmup:
+            recs.append(rec)
+    secs = sum(r["secs"] for r in recs)
+    units = sum(r["value"] * r["secs"] for r in recs)
+    return units / secs, 1e3 * secs / len(recs), recs[-1]
+
+
+def reference_instances(args, probs, budget_s):
+    """Reference-arm steps for independent instances (batch, serving): each
+    step the oracle on the same first instances (count calibrated once),
+    one instance per worker process on all host cores."""
+    cores = host_cores()
+    with InstancePool(cores) as pool:
+        count = pool.calibrate(probs, budget_s)
+        recs = []
+        for i in range(args.warmup + args.steps):
+            rec = pool.sample(probs, count)
+            if i >= args.warmup:
+                recs.append(rec)
+    secs = sum(r["secs"] for r in recs)
+    value = sum(r["value"] * r["secs"] for r in recs) / secs
+    return value, 1e3 * secs / len(recs), recs[-1]
 
 
 def run_reference(args, wl):
+    """The reference arm: the CPU oracle (the reference is a paper, with no
+    program of its own), its OpenMP build on all host cores, on a bounded
+    sample of the workload per step.  ms_per_step is the time of the
+    sample actually run; the whole workload's estimated time is reported
+    under its own key."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import oracle
+    cores = host_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    lib = oracle.load_omp()
+    extra = {}
     if wl.get("kind") == "serve":
-        base = si.serve_base(wl["nmax"])
-        reqs = si.request_stream(args.requests, seed=1000, nmin=wl["nmin"], nmax=wl["nmax"],
+        reqs = si.request_stream(args.requests, seed=2000, nmin=wl["nmin"], nmax=wl["nmax"],
                                  pmin=0.1, pmax=0.6)
         # the oracle's cost grows as n^3: its sample takes the requests of
         # order <= 1024 of the stream, in order
-        probs = [si.serve_request(base, n, p, sd) for _, n, p, sd in reqs if n <= 1024][:200]
-        nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
-        sample = lambda: batch_cpu_sample(probs, budget_s=6.0)
+        probs = [si.serve_problem(n, p, sd) for _, n, p, sd in reqs if n <= 1024][:200]
         cfg = {"workload": "serve", "n": "requests of order <= 1024 of the stream",
                "select": wl["select"], "q": wl["q"]}
+        value, ms, rec = reference_instances(args, probs, budget_s=4.0)
+        unit, metric = "eigs/s", METRIC
     elif wl.get("kind") == "eigvec":
         S, Q, _ = make_inputs(wl)
         n = S.shape[0]
-        times, samples = [], []
+        recs = []
         for i in range(args.warmup + args.steps):
             cb = eigvec_cpu_sample(S, Q)
             if i >= args.warmup:
-                times.append(n / cb["value"])
-                samples.append(cb["sample"])
-        value = n * len(times) / sum(times)
-        line = {"impl": "reference", "metric": "eigenvectors computed per second", "value": value,
-                "unit": "eigenvectors/s", "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl["name"], "n": n, "eigenvectors": f"all ({n})",
-                           "q": wl["q"]},
-                "cpu_baseline": {"value": value, "unit": "eigenvectors/s", "cores": cb["cores"],
-                                 "kind": "oracle", "sample": samples[-1]},
-                "e2e": {"value": value, "unit": "eigenvectors/s", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return 0
+                recs.append(cb)
+        secs = sum(r["secs"] for r in recs)
+        value = sum(r["value"] * r["secs"] for r in recs) / secs
+        ms, rec = 1e3 * secs / len(recs), recs[-1]
+        unit, metric = "eigenvectors/s", "eigenvectors computed per second"
+        cfg = {"workload": wl["name"], "n": n, "eigenvectors": f"all ({n})", "q": wl["q"]}
     elif wl.get("kind") == "sweep":
         H, Q, sh = si.sweep_config(wl["name"])
-        times, samples = [], []
+        recs = []
         for i in range(args.warmup + args.steps):
             cb = sweep_cpu(H, Q, sh)
             if i >= args.warmup:
-                times.append(len(sh) / cb["value"])
-                samples.append(cb["sample"])
-        value = len(sh) * len(times) / sum(times)
-        line = {"impl": "reference", "metric": SWEEP_METRIC, "value": value, "unit": "shifts/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl["name"], "n": wl["n"], "shifts": wl["shifts"],
-                           "q": wl["q"], "window": wl["window"], "chain": wl["chain"]},
-                "cpu_baseline": {"value": value, "unit": "shifts/s", "cores": 1, "kind": "oracle",
-                                 "sample": samples[-1]},
-                "e2e": {"value": value, "unit": "shifts/s", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return 0
+                recs.append(cb)
+        secs = sum(r["secs"] for r in recs)
+        value = sum(r["value"] * r["secs"] for r in recs) / secs
+        ms, rec = 1e3 * secs / len(recs), recs[-1]
+        unit, metric = "shifts/s", SWEEP_METRIC
+        cfg = {"workload": wl["name"], "n": wl["n"], "shifts": wl["shifts"], "q": wl["q"],
+               "window": wl["window"], "chain": wl["chain"]}
     elif wl.get("kind") == "gen":
-        import oracle
         S, T, Q, Z, sel = si.gen_config(wl["name"])
-        nsel = int(expected_selected(S, sel))
-        sample = lambda: cpu_oracle_sample(
-            S, Q, sel, budget_s=8.0, what="pair workload",
-            run=lambda ss: oracle.gen_reorder(S, T, Q, Z, ss))
+        run_one = lambda ss: oracle.gen_reorder(S, T, Q, Z, ss)
+        value, ms, rec = reference_reorder_steps(args, S, Q, sel, "pair workload", run_one, 4.0,
+                                                 1, "generalized oracle, 1 thread")
+        unit, metric = "eigs/s", METRIC
         cfg = {"workload": wl["name"], "n": wl["n"], "select": wl["select"], "q": wl["q"],
                "window": wl["window"], "chain": wl["chain"]}
     elif wl.get("kind") == "batch":
         probs = batch_inputs(wl)
-        nsel = int(sum(expected_selected(S, sel) for S, _, sel in probs))
-        sample = lambda: batch_cpu_sample(probs, budget_s=6.0)
         cfg = {"workload": wl["name"], "instances": wl["count"],
                "n": f"U{{{wl['nmin']}..{wl['nmax']}}}", "select": wl["select"], "q": wl["q"]}
+        value, ms, rec = reference_instances(args, probs, budget_s=4.0)
+        unit, metric = "eigs/s", METRIC
     else:
         S, Q, sel = make_inputs(wl)
-        nsel = int(expected_selected(S, sel))
-        sample = lambda: cpu_oracle_sample(S, Q, sel, budget_s=8.0)
+        run_one = lambda ss: oracle.reorder(S, Q, ss, lib=lib)
+        value, ms, rec = reference_reorder_steps(args, S, Q, sel, "workload", run_one, 4.0,
+                                                 cores, f"oracle, OpenMP {cores} threads")
+        unit, metric = "eigs/s", METRIC
         cfg = {"workload": wl["name"], "n": wl["n"], "select": wl["select"],
                "q": wl["q"], "window": wl["window"], "chain": wl["chain"]}
-    times = []
-    samples = []
-    for i in range(args.warmup + args.steps):
-        cb = sample()
-        if i >= args.warmup:
-            times.append(nsel / cb["value"])
-            samples.append(cb["sample"])
-    value = nsel * len(times) / sum(times)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigs/s",
+        extra["estimated_full_workload_ms"] = 1e3 * rec["est_full_s"]
+    cb = {k2: v for k2, v in rec.items() if k2 not in ("secs", "est_full_s", "k")}
+    cb["value"] = value
+    cb["cpu_model"] = cpu_model()
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": cfg,
-            "cpu_baseline": {"value": value, "unit": "eigs/s", "cores": 1, "kind": "oracle",
-                             "sample": samples[-1]},
-            "e2e": {"value": value, "unit": "eigs/s", "h2d_bytes_per_step": 0,
+            "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -328,14 +492,14 @@ def expected_selected(S, sel):
     return cnt
 
 
-def error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream):
+def error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream, with_oracle=True):
     """Accuracy of one reordering of the workload (after the timed steps):
     residual ||A - Q S Q^T||_F / ||A||_F and ||Q^T Q - I||_F estimated with 32
     Gaussian probe vectors on the GPU, eigenvalue order against the stable
     partition of the input eigenvalues, and for n <= 4000 the difference to
     the FP64 oracle's result (eigenvalues, leading invariant subspace)."""
     import oracle
-    from tests.helpers import block_eigs, expected_order, sin_angle
+    from tests.helpers import block_eigs, expected_order, is_standard, sin_angle
     with torch.cuda.stream(stream):
         S.copy_(S0)
         Q.copy_(Q0)
@@ -355,7 +519,9 @@ def error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream):
     want, m = expected_order(S_np, sel)
     out = {"status": r.status, "residual_est": res, "orth_est": orth, "bound_50n_eps": 50 * n * 2.0 ** -52,
            "eig_order_max_rel_dev": float(np.max(np.abs(got - want) / np.maximum(np.abs(want), 1.0)))}
-    if n <= 4000:
+    out["rejected"] = int(r.stats.rejected)
+    out["standard_form"] = bool(is_standard(Sg))
+    if n <= 4000 and with_oracle:
         t0 = time.perf_counter()
         ref = oracle.reorder(S_np, Q_np, sel)
         out["oracle_s"] = time.perf_counter() - t0
@@ -376,22 +542,81 @@ def batch_inputs(wl, seed=0):
     return out
 
 
-def batch_cpu_sample(probs, budget_s=12.0):
-    """The oracle on the first instances of the batch until ~budget_s,
-    scaled to the whole batch by selected eigenvalues."""
+def _oracle_instance(prob):
+    """One instance through the oracle (a worker process of InstancePool)."""
     import oracle
-    t0 = time.perf_counter()
-    done = 0
-    eigs = 0
-    while done < len(probs) and time.perf_counter() - t0 < budget_s:
-        S, Q, sel = probs[done]
-        oracle.reorder(S, Q, sel)
-        eigs += expected_selected(S, sel)
-        done += 1
-    dt = time.perf_counter() - t0
-    return {"value": eigs / dt, "unit": "eigs/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {len(probs)} instances ({eigs} selected eigenvalues) "
-                      f"in {dt:.1f} s on 1 core"}
+    S, Q, sel = prob
+    oracle.reorder(S, Q, sel)
+    return int(expected_selected(S, sel))
+
+
+def _pool_ready(_):
+    import oracle
+    oracle.load()
+    return os.getpid()
+
+
+class InstancePool:
+    """The oracle over independent instances: in turn on one core
+    (workers=1), or one instance per worker on `workers` processes started
+    with spawn (and warmed up) before any timing."""
+
+    def __init__(self, workers):
+        self.workers = workers
+        self.ex = None
+
+    def __enter__(self):
+        if self.workers > 1:
+            import multiprocessing as mp
+            from concurrent.futures import ProcessPoolExecutor
+            self.ex = ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"))
+            list(self.ex.map(_pool_ready, range(4 * self.workers)))
+        return self
+
+    def __exit__(self, *a):
+        if self.ex:
+            self.ex.shutdown()
+
+    def sample(self, probs, count):
+        t0 = time.perf_counter()
+        if self.ex is None:
+            eigs = sum(_oracle_instance(p) for p in probs[:count])
+        else:
+            eigs = sum(self.ex.map(_oracle_instance, probs[:count], chunksize=1))
+        dt = time.perf_counter() - t0
+        who = "1 core" if self.ex is None else f"{self.workers} worker processes"
+        return {"value": eigs / dt, "unit": "eigs/s", "cores": self.workers, "kind": "oracle",
+                "secs": dt, "count": count,
+                "sample": f"first {count} of {len(probs)} instances ({eigs} selected "
+                          f"eigenvalues) in {dt:.2f} s on {who}"}
+
+    def calibrate(self, probs, budget_s):
+        """Instance count whose sample takes about budget_s."""
+        count = min(len(probs), 2 * self.workers)
+        while True:
+            rec = self.sample(probs, count)
+            if rec["secs"] >= budget_s / 2 or count >= len(probs):
+                return count
+            count = min(len(probs), int(count * budget_s / max(rec["secs"], 1e-3) * 0.8) + 1)
+
+
+def batch_cpu_sample(probs, budget_s=12.0):
+    """The oracle on the first instances of the batch: on one core until
+    ~budget_s, then the same instances on all host cores (one instance per
+    worker process).  The faster is the headline value; both are kept."""
+    with InstancePool(1) as p1:
+        count = p1.calibrate(probs, budget_s)
+        one = p1.sample(probs, count)
+    cores = host_cores()
+    out = one
+    if cores > 1:
+        with InstancePool(cores) as pc:
+            many = pc.sample(probs, count)
+        out = dict(many if many["value"] > one["value"] else one)
+        out["single_thread"] = one
+        out["all_cores"] = many
+    out["cpu_model"] = cpu_model()
+    return out
 
 
 def run_batch(args, wl):
@@ -476,10 +701,10 @@ def run_batch(args, wl):
     upd_iss = st0.upd_flops_issued if st0.upd_flops_issued > 0 else st0.upd_flops
     work = upd_iss + st0.win_flops
     achieved = work / (ms_sched / 1e3) / 1e12
-    roof = {"kernel": "sched_kernel (persistent, all instances: window tasks + update tiles)",
-            "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": None,
-            "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 1.25/2250"),
+    tname, bound, fpk, fsrc = fp64_roof_basis(args.precision, pk, src)
+    roof = {"kernel": f"sched_kernel (persistent, all instances: window tasks + {tname})",
+            "bound": bound, "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
+            "frac": achieved / fpk, "traffic": None, "peak_source": fsrc,
             "flops_per_launch": work, "launches_per_step": 1, "avg_launch_ms": ms_sched,
             "share_of_step": ms_sched / (total_ms / args.steps),
             "critical_path_model_ms": st0.sched_cp_ms}
@@ -538,11 +763,57 @@ def run_batch(args, wl):
     return 0
 
 
+def _serve_make_pinned(n, p, sd):
+    """One serving request in pinned host memory: the generator's row-major
+    form of the request, copied transposed (torch's blocked CPU transpose)
+    into pinned buffers whose memory is the column-major matrix."""
+    import torch
+    S, Q, sel = si.serve_problem(n, p, sd, order="C")
+    nn = S.shape[0]
+    tS = torch.empty((nn, nn), dtype=torch.float64).pin_memory()
+    tQ = torch.empty((nn, nn), dtype=torch.float64).pin_memory()
+    tS.copy_(torch.from_numpy(S).t())
+    tQ.copy_(torch.from_numpy(Q).t())
+    return tS, tQ, sel, int(expected_selected(S, sel))
+
+
+class RequestFeed:
+    """Serving requests generated ahead of their arrival by a pool of host
+    threads (the generator's bulk work, random fills, matrix products and
+    copies, runs without the interpreter lock), at most `ahead` in flight,
+    in stream order."""
+
+    def __init__(self, specs, workers, ahead=24, make=None):
+        from concurrent.futures import ThreadPoolExecutor
+        self.make = make or (lambda n, p, sd: si.serve_problem(n, p, sd))
+        self.specs = specs
+        self.ex = ThreadPoolExecutor(workers)
+        self.futs = []
+        self.next = 0
+        self.ahead = ahead
+        self._fill()
+
+    def _fill(self):
+        while self.next < len(self.specs) and len(self.futs) < self.ahead:
+            n, p, sd = self.specs[self.next]
+            self.futs.append(self.ex.submit(self.make, n, p, sd))
+            self.next += 1
+
+    def get(self):
+        f = self.futs.pop(0)
+        self._fill()
+        return f.result()
+
+    def close(self):
+        self.ex.shutdown(cancel_futures=True)
+
+
 def run_serve(args, wl):
     """Serving: a Poisson stream of requests (n log-uniform, see the
     workload) through the continuous-batching server.  A saturation burst
     first measures the throughput; the stream then arrives at each --load
-    fraction of it.  Requests are cut from one base form (schur_inputs)."""
+    fraction of it.  Every request is an independent form from the seeded
+    generator, made by host threads ahead of its arrival."""
     import torch
     import paper_1905_04975_gb300 as g
 
@@ -550,65 +821,65 @@ def run_serve(args, wl):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     g.load()
-    base = si.serve_base(wl["nmax"], seed=rank)
-    reqs = si.request_stream(args.requests, seed=1000 + rank, nmin=wl["nmin"], nmax=wl["nmax"],
-                             pmin=0.1, pmax=0.6, rate=1.0)
+    workers = max(1, min(8, host_cores() // 2))
 
-    def make(i):
-        _, n, p, sd = reqs[i % len(reqs)]
-        S, Q, sel = si.serve_request(base, n, p, sd)
-        nn = S.shape[0]
-        # pinned host buffers (the caching host allocator reuses them)
-        tS = torch.empty((nn, nn), dtype=torch.float64).pin_memory()
-        tQ = torch.empty((nn, nn), dtype=torch.float64).pin_memory()
-        hS, hQ = tS.numpy().T, tQ.numpy().T      # Fortran-ordered views
-        hS[:] = S
-        hQ[:] = Q
-        return (tS, tQ, hS, hQ, sel, int(expected_selected(S, sel)))
+    def specs(count, seed):
+        return [(n, p, sd) for _, n, p, sd in
+                si.request_stream(count, seed=seed, nmin=wl["nmin"], nmax=wl["nmax"],
+                                  pmin=0.1, pmax=0.6, rate=1.0)]
 
-    def run(rate, count, offset):
+    def run(rate, count, seed):
         """Submits `count` requests (Poisson arrivals at `rate` per second,
         or all at once when rate is None) and waits for all of them."""
+        feed = RequestFeed(specs(count, seed), workers, make=_serve_make_pinned)
         srv = g.Server(mem_cap_bytes=wl["mem_cap"], precision=args.precision)
+        late = 0.0
         try:
-            gaps = np.random.default_rng(7 + offset).exponential(1.0 / rate, count) if rate else None
+            gaps = np.random.default_rng(seed + 7).exponential(1.0 / rate, count) if rate else None
             pending = {}
-            t0 = time.perf_counter()
-            t_next = t0
             eigs = 0
-            for i in range(count):
-                item = make(offset + i)
-                if gaps is not None:
-                    t_next += gaps[i]
-                    dt = t_next - time.perf_counter()
-                    if dt > 0:
-                        time.sleep(dt)
-                t = srv.submit(item[2], item[3], item[4], eigs=False)
-                pending[t] = item
-                eigs += item[5]
-                for tk in [tk for tk in pending if srv.poll(tk) is not None]:
-                    del pending[tk]
-            for tk in list(pending):
-                r = srv.wait(tk, -1)
-                assert r.status >= 0, r.status
-            wall = time.perf_counter() - t0
+            with ClockSampler(local) as clk:
+                t0 = time.perf_counter()
+                t_next = t0
+                for i in range(count):
+                    tS, tQ, sel, nsel_i = feed.get()
+                    item = (tS, tQ, tS.numpy().T, tQ.numpy().T)   # Fortran-ordered views
+                    if gaps is not None:
+                        t_next += gaps[i]
+                        dt = t_next - time.perf_counter()
+                        if dt > 0:
+                            time.sleep(dt)
+                        else:
+                            late = max(late, -dt)
+                    t = srv.submit(item[2], item[3], sel, eigs=False)
+                    pending[t] = item
+                    eigs += nsel_i
+                    for tk in [tk for tk in pending if srv.poll(tk) is not None]:
+                        del pending[tk]
+                for tk in list(pending):
+                    r = srv.wait(tk, -1)
+                    assert r.status >= 0, r.status
+                wall = time.perf_counter() - t0
             st = srv.stats()
         finally:
             srv.close()
-        return st, wall, eigs
+            feed.close()
+        return st, wall, eigs, clk.summary(), late
 
     burst = max(20, args.requests // 10)
-    st_b, wall_b, eigs_b = run(None, burst, 0)
+    st_b, wall_b, eigs_b, clk_b, _ = run(None, burst, 1000 + rank)
     sat = st_b["req_per_s"]
     loads = []
-    for load in args.loads:
-        st, wall, eigs = run(load * sat, args.requests, burst)
-        loads.append({"load": load, "rate_req_s": load * sat, "requests": args.requests,
+    for li, load in enumerate(args.loads):
+        st, wall, eigs, clk, late = run(load * sat, args.requests, 2000 + 100 * li + rank)
+        loads.append({"load": load, "rate_req_s": load * sat,
+                      "achieved_arrival_req_s": args.requests / wall if wall else None,
+                      "max_arrival_lag_s": late, "requests": args.requests,
                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                       "mean_ms": st["mean_ms"], "req_per_s": st["req_per_s"],
                       "eigs_per_s": st["eigs_per_s"], "mean_inflight": st["mean_inflight"],
                       "peak_mem_gb": st["peak_mem_bytes"] / 1e9, "failed": st["failed"],
-                      "wall_s": wall})
+                      "wall_s": wall, "clocks": clk})
     if rank == 0:
         head = loads[-1] if loads else None
         line = {"metric": "serve p50/p99 latency and throughput",
@@ -619,11 +890,16 @@ def run_serve(args, wl):
                 "config": {"workload": "serve", "n": "log-uniform [64, 8192]",
                            "select": wl["select"], "q": wl["q"], "precision": args.precision,
                            "mem_cap_gb": wl["mem_cap"] / 1e9,
+                           "requests_per_load": args.requests,
+                           "forms": "independent, from the seeded generator, made by "
+                                    f"{workers} host threads ahead of arrival",
                            "arrivals": "Poisson at load x saturated req/s"},
+                "clocks": head["clocks"] if head else clk_b,
                 "serve": {"saturated": {"requests": burst, "req_per_s": sat,
                                         "eigs_per_s": st_b["eigs_per_s"],
                                         "p50_ms": st_b["p50_ms"], "p99_ms": st_b["p99_ms"],
-                                        "wall_s": wall_b},
+                                        "mean_inflight": st_b["mean_inflight"],
+                                        "wall_s": wall_b, "clocks": clk_b},
                           "loads": loads}}
         print(json.dumps(line), flush=True)
     return 0
@@ -656,6 +932,7 @@ def eigvec_cpu_sample(S, Q, step=16):
     est = (t1 - t0) * full / work + (t2 - t1) * n / X.shape[1]
     cores = len(os.sched_getaffinity(0))
     return {"value": n / est, "unit": "eigenvectors/s", "cores": cores, "kind": "oracle",
+            "secs": t2 - t0,
             "sample": (f"{X.shape[1]} of {n} eigenvectors (every {step}th eigenvalue): back "
                        f"substitution {t1 - t0:.2f} s on 1 core, back-transformation "
                        f"{t2 - t1:.2f} s (numpy/BLAS, up to {cores} threads); scaled by work "
@@ -738,19 +1015,21 @@ def run_gen(args, wl):
         kern = None
     elif args.sched == "persistent":
         ms_k = sum(s.ms_sched for s in stats) / len(stats)
-        kern = "sched_kernel<pair> (persistent: pair window tasks + DMMA tiles of S, T, Q, Z)"
+        kern = (f"sched_kernel<pair> (persistent: pair window tasks + "
+                f"{fp64_roof_basis(args.precision, pk, src)[0]} of S, T, Q, Z)")
         work_fl = flops_iss + st0.win_flops
     else:
         ms_k = sum(s.ms_update for s in stats) / len(stats)
-        kern = "update_gen_kernel (DMMA FP64 Y <- Y U on S, T, Q, Z)"
+        kern = (f"update_gen_kernel ({fp64_roof_basis(args.precision, pk, src)[0]}: "
+                "Y <- Y U on S, T, Q, Z)")
         work_fl = flops_iss
     if kern is not None:
         achieved = work_fl / (ms_k / 1e3) / 1e12
-        roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": NCU_TRAFFIC.get((wl["name"], args.sched)),
-                "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
-                                "1.25/2250 (FP64 DMMA probe: 1.047 TF/s)"),
+        _, bound, fpk, fsrc = fp64_roof_basis(args.precision, pk, src)
+        roof = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": fpk,
+                "unit": "TFLOP/s", "frac": achieved / fpk,
+                "traffic": NCU_TRAFFIC.get((wl["name"], args.sched + "-" + args.precision)),
+                "peak_source": fsrc,
                 "flops_per_launch": work_fl, "update_flops_dense": st0.upd_flops,
                 "update_flops_issued": flops_iss, "window_flops": st0.win_flops,
                 "avg_launch_ms": ms_k,
@@ -807,7 +1086,7 @@ def sweep_cpu(H, Q, sh):
     st, _, _ = oracle.qr_sweep(H, Q, sh)
     dt = time.perf_counter() - t0
     assert st == 0
-    return {"value": len(sh) / dt, "unit": "shifts/s", "cores": 1, "kind": "oracle",
+    return {"value": len(sh) / dt, "unit": "shifts/s", "cores": 1, "kind": "oracle", "secs": dt,
             "sample": f"the whole n={H.shape[0]} sweep with {len(sh)} shifts, {dt:.1f} s on 1 core"}
 
 
@@ -869,18 +1148,19 @@ def run_sweep(args, wl):
     flops_iss = st0.upd_flops_issued if st0.upd_flops_issued > 0 else st0.upd_flops
     if args.sched == "persistent":
         ms_k = sum(s.ms_sched for s in stats) / len(stats)
-        kern = "sched_kernel<sweep> (persistent: bulge-chasing window tasks + DMMA tiles)"
+        kern = (f"sched_kernel<sweep> (persistent: bulge-chasing window tasks + "
+                f"{fp64_roof_basis(args.precision, pk, src)[0]})")
         work_fl = flops_iss + st0.win_flops
     else:
         ms_k = sum(s.ms_update for s in stats) / len(stats)
-        kern = "update_kernel (DMMA FP64 Y <- Y U)"
+        kern = f"update_kernel ({fp64_roof_basis(args.precision, pk, src)[0]}: Y <- Y U)"
         work_fl = flops_iss
     achieved = work_fl / (ms_k / 1e3) / 1e12
-    roof = {"kernel": kern, "bound": "tensor", "achieved": achieved, "peak": fp64_peak,
-            "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-            "traffic": NCU_TRAFFIC.get((wl["name"], args.sched)),
-            "peak_source": (f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 "
-                            "1.25/2250 (FP64 DMMA probe: 1.047 TF/s)"),
+    _, bound, fpk, fsrc = fp64_roof_basis(args.precision, pk, src)
+    roof = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": fpk,
+            "unit": "TFLOP/s", "frac": achieved / fpk,
+            "traffic": NCU_TRAFFIC.get((wl["name"], args.sched + "-" + args.precision)),
+            "peak_source": fsrc,
             "flops_per_launch": work_fl, "update_flops_dense": st0.upd_flops,
             "update_flops_issued": flops_iss, "window_flops": st0.win_flops,
             "avg_launch_ms": ms_k,
@@ -1041,58 +1321,15 @@ def run_eigvec(args, wl):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
-    ap.add_argument("--workload", default="n4000", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--sched", default="persistent", choices=["persistent", "sequential"])
-    ap.add_argument("--precision", default="dmma", choices=["dmma", "ozaki"])
-    ap.add_argument("--requests", type=int, default=400, help="serve: requests per load")
-    ap.add_argument("--error", action="store_true",
-                    help="report the accuracy of one reordering (and vs the oracle, n <= 4000)")
-    ap.add_argument("--loads", type=lambda v: [float(x) for x in v.split(",")],
-                    default=[0.5, 0.9], help="serve: arrival rates as fractions of saturation")
-    args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
-    if args.impl == "reference":
-        return run_reference(args, wl)
-    if wl.get("kind") == "batch":
-        return run_batch(args, wl)
-    if wl.get("kind") == "serve":
-        return run_serve(args, wl)
-    if wl.get("kind") == "eigvec":
-        return run_eigvec(args, wl)
-    if wl.get("kind") == "gen":
-        return run_gen(args, wl)
-    if wl.get("kind") == "sweep":
-        return run_sweep(args, wl)
-
-    import torch
-    import paper_1905_04975_gb300 as g
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    g.load()
-
-    S_np, Q_np, sel = make_inputs(wl)
+def measure_reorder(args, g, torch, dist, wl, prec, S_np, Q_np, sel, S, Q, S0, Q0, stream,
+                    nsel, local, with_error):
+    """Warm-up, timed steps (CUDA events on the library's stream, clocks
+    sampled), the dominant kernel's roofline, the end-to-end rate through
+    gbr_reorder_host and the accuracy of one more reordering, for one
+    precision of the off-diagonal updates."""
     n = S_np.shape[0]
-    nsel = expected_selected(S_np, sel)
-    S0, Q0 = g.to_device(S_np), g.to_device(Q_np)
-    S, Q = g.to_device(S_np), g.to_device(Q_np)
-    stream = torch.cuda.Stream()
-    opts = g.make_opts(window=wl["window"], chain=wl["chain"], precision=args.precision,
-                       timing=True, sched=args.sched)
+    opts = g.make_opts(window=wl["window"], chain=wl["chain"], precision=prec, timing=True,
+                       sched=args.sched)
 
     def step():
         with torch.cuda.stream(stream):
@@ -1125,40 +1362,55 @@ def main():
     value, total_ms = whole_job_rate(nsel * args.steps, sum(ms), dist, "cuda")
 
     # dominant kernel and its roofline.  With the persistent scheduler one
-    # kernel runs every window task and update tile; all of its arithmetic is
-    # FP64 (DMMA for the updates, FP64 FMA inside the windows), so its roofline
-    # is the FP64 peak and its algorithmic work is the planner's exact update
-    # flop count plus the in-window flops the kernel counts.
+    # kernel runs every window task and update tile.
     st0 = stats[0]
     nwin = st0.windows
     flops_upd = st0.upd_flops
     flops_win = st0.win_flops
+    flops_iss = st0.upd_flops_issued if st0.upd_flops_issued > 0 else flops_upd
     ms_sched = sum(s.ms_sched for s in stats) / len(stats)
     pk, src = peaks()
     fp64_peak = pk["bf16_tflops"] * (1.25 / 2250.0)   # bf16 measured x nominal FP64/bf16
     cp_ms = sum(s.sched_cp_ms for s in stats) / len(stats)
-    if ms_sched > 0 and args.precision == "ozaki":
-        # Split-precision updates: 28 bf16 slice products per FP64 product,
-        # issued on the tensor pipe; the window tasks stay FP64.  The kernel's
-        # work in bf16-peak-equivalent flops (window flops scaled by the
-        # bf16/FP64 peak ratio), so frac = (minimum time at both peaks) / time.
+    if ms_sched > 0 and prec == "ozaki":
+        # Split-precision updates: 28 bf16 slice products per FP64 product on
+        # the tensor pipe (the tiles run K = w densely); the window tasks stay
+        # FP64.  frac counts the slice products only; frac_min_time adds the
+        # time the FP64 window flops need at the FP64 peak.
         bf16_peak = pk["bf16_tflops"]
-        work = 28.0 * flops_upd + flops_win * (bf16_peak / fp64_peak)
-        achieved = work / (ms_sched / 1e3) / 1e12
+        slice_flops = 28.0 * flops_upd
+        achieved = slice_flops / (ms_sched / 1e3) / 1e12
+        min_s = slice_flops / (bf16_peak * 1e12) + flops_win / (fp64_peak * 1e12)
         roof = {"kernel": "sched_kernel (persistent: FP64 window tasks + bf16 slice-product "
                           "update tiles)",
                 "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": achieved / bf16_peak,
                 "traffic": NCU_TRAFFIC.get((wl["name"], "ozaki")),
                 "peak_source": f"{src} bf16 {bf16_peak} TF/s",
-                "flops_per_launch": work, "bf16_slice_flops": 28.0 * flops_upd,
+                "flops_per_launch": slice_flops, "bf16_slice_flops": slice_flops,
                 "fp64_window_flops": flops_win, "launches_per_step": 1,
+                "frac_min_time": min_s / (ms_sched / 1e3),
                 "avg_launch_ms": ms_sched, "critical_path_model_ms": cp_ms,
-                "share_of_step": ms_sched / (total_ms / args.steps),
-                "note": "latency-bound: the window tasks on the critical path set the time"}
+                "share_of_step": ms_sched / (total_ms / args.steps)}
+    elif ms_sched > 0 and prec == "fma":
+        # FP64 on the FMA pipe: flops the tiles issued (all-zero rows of U
+        # skipped) plus the in-window FP64 flops of accepted swaps, against
+        # the FP64 FMA rate from the unit counts and the clock
+        achieved = (flops_iss + flops_win) / (ms_sched / 1e3) / 1e12
+        alu_peak = FP64_FMA_PEAK
+        roof = {"kernel": "sched_kernel (persistent: window tasks + FP64 FMA update tiles)",
+                "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": NCU_TRAFFIC.get((wl["name"], "fma")),
+                "peak_source": FP64_FMA_PEAK_SOURCE,
+                "frac_of_fp64_tensor_peak": achieved / fp64_peak,
+                "flops_per_launch": flops_iss + flops_win, "launches_per_step": 1,
+                "update_flops_dense": flops_upd, "update_flops_issued": flops_iss,
+                "critical_path_model_ms": cp_ms,
+                "avg_launch_ms": ms_sched,
+                "share_of_step": ms_sched / (total_ms / args.steps)}
     elif ms_sched > 0:
-        # flops the DMMA tiles issued: the all-zero rows of U are skipped
-        flops_iss = st0.upd_flops_issued if st0.upd_flops_issued > 0 else flops_upd
+        # flops the DMMA tiles issued (the all-zero rows of U are skipped)
+        # plus the in-window FP64 flops of accepted swaps
         achieved = (flops_iss + flops_win) / (ms_sched / 1e3) / 1e12
         roof = {"kernel": "sched_kernel (persistent: window tasks + DMMA update tiles)",
                 "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -1173,10 +1425,11 @@ def main():
     else:
         ms_upd = sum(s.ms_update for s in stats) / len(stats)
         ms_win = sum(s.ms_window for s in stats) / len(stats)
-        achieved = flops_upd / (ms_upd / 1e3) / 1e12 if ms_upd > 0 else None
-        roof = {"kernel": "update_kernel (DMMA FP64 Y <- Y U)", "bound": "tensor",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+        achieved = flops_iss / (ms_upd / 1e3) / 1e12 if ms_upd > 0 else None
+        tname, bound, fpk, _ = fp64_roof_basis(prec, pk, src)
+        roof = {"kernel": f"update_kernel ({tname}: Y <- Y U)", "bound": bound,
+                "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
+                "frac": achieved / fpk if achieved else None, "traffic": None,
                 "launches_per_step": nwin, "avg_launch_ms": ms_upd / max(nwin, 1),
                 "share_of_step": ms_upd / (total_ms / args.steps), "window_ms": ms_win}
 
@@ -1194,39 +1447,157 @@ def main():
             t0 = time.perf_counter()
             r = g.reorder_host(Sh, Qh, sel, opts=opts, stream=stream)
             dt = time.perf_counter() - t0
+            assert r.status == 0, r.status
             if i > 0:
                 et.append(dt)
+        world = dist.get_world_size() if dist else 1
         e2e = {"value": nsel * len(et) / sum(et) * world, "unit": "eigs/s",
+               "steps": len(et), "ms_per_step": 1e3 * sum(et) / len(et),
                "h2d_bytes_per_step": 2 * n * n * 8 + 4 * n,
                "d2h_bytes_per_step": 2 * n * n * 8 + 2 * 8 * n}
+        del Sp, Qp
+    err = None
+    if with_error:
+        err = error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream,
+                           with_oracle=args.error)
+    return {"value": value, "ms": total_ms / args.steps, "roofline": roof, "e2e": e2e,
+            "clocks": clk.summary(), "error": err,
+            "gpu_launches": int(sum(s.launches for s in stats)),
+            "stats": st0, "fp64_tflops_of_step": (flops_iss + flops_win)
+            / (total_ms / args.steps / 1e3) / 1e12}
 
+
+def run_reorder(args, wl):
+    """One reordering per step on the device-resident workload; for the
+    clustered n = 16000 workload both precisions of the off-diagonal updates
+    (FP64 DMMA in the line's own fields, split precision in its
+    `split_precision` record) with the accuracy of each result."""
+    import torch
+    import paper_1905_04975_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load()
+
+    S_np, Q_np, sel = make_inputs(wl)
+    n = S_np.shape[0]
+    nsel = expected_selected(S_np, sel)
+    S0, Q0 = g.to_device(S_np), g.to_device(Q_np)
+    S, Q = g.to_device(S_np), g.to_device(Q_np)
+    stream = torch.cuda.Stream()
+    precs = ["fma", "ozaki", "dmma"] if args.precision == "both" else [args.precision]
+    with_error = args.error or (wl["name"] == "n16000c" and not args.no_error)
+    res = {}
+    for i, p in enumerate(precs):
+        a = args
+        if i == 2:
+            # the FP64 tensor-core (DMMA) form: a shorter run beside the line
+            a = argparse.Namespace(**vars(args))
+            a.steps, a.warmup = min(args.steps, args.dmma_steps), min(args.warmup, 1)
+            a.e2e_steps = 0
+        res[p] = measure_reorder(a, g, torch, dist, wl, p, S_np, Q_np, sel, S, Q, S0, Q0, stream,
+                                 nsel, local, with_error and i < 2)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(S_np, Q_np, sel)
-    err = error_report(g, torch, S_np, Q_np, sel, S, Q, S0, Q0, opts, stream) if args.error else None
-
+        cpu = run_cpu_leg(wl)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "eigs/s", "n_gpus": world,
+        m = res[precs[0]]
+        st0 = m["stats"]
+        line = {"metric": METRIC, "value": m["value"], "unit": "eigs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "ms_per_step": m["ms"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl["name"], "n": n, "select": wl["select"],
                            "selected_eigs": nsel, "q": wl["q"], "window": wl["window"],
-                           "chain": wl["chain"], "precision": args.precision, "sched": args.sched,
-                           "l2": "S,Q (256 MB > L2) restored from a device copy before each step",
+                           "chain": wl["chain"], "precision": precs[0],
+                           "clusters": wl.get("clusters"), "sched": args.sched,
+                           "l2": (f"S,Q ({2 * n * n * 8 / 1e9:.2f} GB > L2) restored from a "
+                                  "device copy before each step"),
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
-                "clocks": clk.summary(), "error": err,
-                "gpu_launches": int(sum(s.launches for s in stats)),
-                "detail": {"windows": int(nwin), "chains": int(st0.chains),
+                "roofline": m["roofline"], "e2e": m["e2e"], "cpu_baseline": cpu,
+                "clocks": m["clocks"], "error": m["error"],
+                "gpu_launches": m["gpu_launches"],
+                "detail": {"windows": int(st0.windows), "chains": int(st0.chains),
                            "tasks": int(st0.tasks), "swaps": int(st0.swaps),
-                           "upd_flops": flops_upd, "win_flops": flops_win,
-                           "fp64_tflops_of_step": (flops_upd + flops_win)
-                           / (total_ms / args.steps / 1e3) / 1e12}}
+                           "rejected": int(st0.rejected),
+                           "upd_flops": st0.upd_flops, "upd_flops_issued": st0.upd_flops_issued,
+                           "win_flops": st0.win_flops,
+                           "fp64_tflops_of_step": m["fp64_tflops_of_step"],
+                           "host_graph_ms": st0.ms_graph, "host_order_ms": st0.ms_order}}
+        if len(precs) > 1:
+            o = res[precs[1]]
+            line["split_precision"] = {
+                "precision": precs[1], "value": o["value"], "unit": "eigs/s",
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": o["ms"],
+                "roofline": o["roofline"], "e2e": o["e2e"], "clocks": o["clocks"],
+                "error": o["error"], "gpu_launches": o["gpu_launches"],
+                "rejected": int(o["stats"].rejected)}
+            line["gpu_launches"] = m["gpu_launches"] + o["gpu_launches"]
+        if len(precs) > 2:
+            d = res[precs[2]]
+            line["fp64_tensor_core"] = {
+                "precision": precs[2], "value": d["value"], "unit": "eigs/s",
+                "steps": min(args.steps, args.dmma_steps), "warmup": min(args.warmup, 1),
+                "ms_per_step": d["ms"], "roofline": d["roofline"], "clocks": d["clocks"],
+                "gpu_launches": d["gpu_launches"]}
+            line["gpu_launches"] += d["gpu_launches"]
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
+    ap.add_argument("--workload", default="n16000c", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--sched", default="persistent", choices=["persistent", "sequential"])
+    ap.add_argument("--precision", default=None, choices=["fma", "dmma", "ozaki", "both"],
+                    help="off-diagonal updates: FP64 on the FMA pipe, FP64 on the tensor "
+                         "cores (DMMA) or split precision (default: both = all three for "
+                         "n16000c, else fma)")
+    ap.add_argument("--dmma-steps", type=int, default=3,
+                    help="both: timed steps of the DMMA form beside the line")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests per load")
+    ap.add_argument("--error", action="store_true",
+                    help="report the accuracy of one reordering (and vs the oracle, n <= 4000)")
+    ap.add_argument("--no-error", action="store_true",
+                    help="n16000c: skip the accuracy report")
+    ap.add_argument("--loads", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[0.7, 0.95], help="serve: arrival rates as fractions of saturation")
+    ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.cpu_leg:
+        return cpu_leg(wl)
+    if args.precision is None:
+        args.precision = "both" if wl["name"] == "n16000c" else "fma"
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    if wl.get("kind") is not None and args.precision == "both":
+        args.precision = "fma"
+    if wl.get("kind") == "batch":
+        return run_batch(args, wl)
+    if wl.get("kind") == "serve":
+        return run_serve(args, wl)
+    if wl.get("kind") == "eigvec":
+        return run_eigvec(args, wl)
+    if wl.get("kind") == "gen":
+        return run_gen(args, wl)
+    if wl.get("kind") == "sweep":
+        return run_sweep(args, wl)
+    return run_reorder(args, wl)
 
 
 if __name__ == "__main__":

@@ -64,8 +64,21 @@ extern "C" {
                               7 signed 8-bit digit slices per operand, 28 exact
                               bf16 tensor-core slice products, integer combination,
                               one rounding to double; the windows stay in FP64 */
+#define GBR_PREC_FMA    2  /* off-diagonal updates in FP64 on the FP64 FMA pipe (DFMA
+                              register tiles, no tensor cores); same arithmetic
+                              type as GBR_PREC_DMMA, another instruction mix */
 
 #define GBR_ON_REJECT_CONTINUE 0 /* a rejected block stays; later blocks stop below it */
+#define GBR_ON_REJECT_ABORT    1 /* the first rejected swap stops the reordering: the
+                                    window task that rejected it finishes its current
+                                    step and restores the standard form of its 2x2
+                                    blocks; window tasks that start later do nothing;
+                                    tasks already running complete.  S and Q remain an
+                                    exact orthogonal similarity, partially reordered
+                                    (as LAPACK's dtrsen with info = 1); which blocks
+                                    moved before the stop depends on the schedule.
+                                    gbr_reorder, gbr_reorder_host and
+                                    gbr_reorder_noalloc only */
 
 /* Options; gbr_default_opts() fills the defaults shown. */
 typedef struct gbr_opts {
@@ -74,11 +87,17 @@ typedef struct gbr_opts {
                           the autotuner (gbr_autotune)                        */
     int chain;         /* selected eigenvalues per chain m, 1..w-2 (default 64);
                           GBR_AUTO with window = GBR_AUTO                     */
-    int precision;     /* GBR_PREC_DMMA (default) or GBR_PREC_OZAKI (persistent
-                          schedule only)                                       */
-    int slices;        /* split-precision slices: 0 or 7 (the only count built) */
+    int precision;     /* GBR_PREC_FMA (default: the faster FP64 path on this
+                          GPU), GBR_PREC_DMMA or GBR_PREC_OZAKI (persistent
+                          schedule only)                                      */
+    int slices;        /* split-precision digit slices per operand: 0 (default)
+                          or 7, the only count built: 7 balanced 8-bit digits
+                          hold the 55-bit fixed-point form of every entry, so
+                          the slices lose nothing of a binary64 significand
+                          (fewer would drop its low bits, more add nothing);
+                          any other value: GBR_ERR_UNSUPPORTED             */
     int strong_test;   /* 1: weak + strong stability test       (default 1)   */
-    int on_reject;     /* GBR_ON_REJECT_CONTINUE                (default)     */
+    int on_reject;     /* GBR_ON_REJECT_CONTINUE (default) or GBR_ON_REJECT_ABORT */
     int validate;      /* 1: check the standard-form input      (default 1)   */
     int timing;        /* 1: time the kernels with CUDA events into gbr_stats;
                           2: also record a per-task timeline of the persistent
@@ -184,8 +203,9 @@ int gbr_reorder_host(int n, double *S, int ldS, double *Q, int ldQ, const int *s
  * 14 opts       options or NULL for the defaults.  window > 64 is reduced
  *               to 64 and chain then to at most 32 (both factors of a window
  *               live in shared memory); both schedules; precision
- *               GBR_PREC_DMMA, or GBR_PREC_OZAKI on the persistent schedule
- *               (split-precision updates from the digit slices of UQ and UZ)
+ *               GBR_PREC_FMA or GBR_PREC_DMMA, or GBR_PREC_OZAKI on the
+ *               persistent schedule (split-precision updates from the digit
+ *               slices of UQ and UZ)
  * 15 stats      host or NULL (upd_flops counts S, T, Q and Z panels)
  * 16 cuda_stream  cudaStream_t or NULL
  *
@@ -216,7 +236,8 @@ int gbr_reorder_gen(int n, double *S, int ldS, double *T, int ldT, double *Q, in
  *                 gbr_default_opts values); window = window size (8 .. 128,
  *                 capped at 96), chain = shifts per chain of bulges (capped
  *                 at w / 3);
- *                 precision GBR_PREC_DMMA only; validate checks the form
+ *                 precision GBR_PREC_FMA or GBR_PREC_DMMA (FP64 updates);
+ *                 validate checks the form
  * 10 stats        host or NULL (windows, chains, update and window flops,
  *                 kernel times with opts.timing)
  * 11 cuda_stream  cudaStream_t or NULL
@@ -238,25 +259,31 @@ int gbr_reorder_gen_host(int n, double *S, int ldS, double *T, int ldT, double *
 
 /*
  * Same operation as gbr_reorder, for callers that must not allocate device
- * memory (for example code that runs while a stream is being captured into
- * a CUDA graph, or a program that owns all device memory through its own
- * arena).  The paper has no counterpart: this is an interface convenience.
+ * memory: programs whose device memory is all handed out by their own arena
+ * or allocator, and processes where a cudaMalloc (which may synchronize the
+ * device) must not happen in the middle of their work.  The paper has no
+ * counterpart: this is an interface convenience.
  *
  * Arguments and return values are those of gbr_reorder, plus
- * GBR_ERR_NOALLOC_LIMIT when n > GBR_NOALLOC_MAX_N.  The call never calls
- * cudaMalloc, cudaFree or any other allocating routine, and creates no CUDA
- * events (opts->timing is ignored).  Its scratch is a fixed array of
- * GBR_NOALLOC_SCRATCH_BYTES in device global memory, part of the library
- * image: every GPU that loads the library holds it until the process exits.
+ * GBR_ERR_NOALLOC_LIMIT when n > GBR_NOALLOC_MAX_N (checked before anything
+ * else is touched).  The call never calls cudaMalloc, cudaFree or any other
+ * allocating routine, and creates no CUDA events (opts->timing is ignored).
+ * It runs the window/update launch pairs with FP64 DMMA updates
+ * (opts->sched and opts->precision other than DMMA are not used:
+ * GBR_ERR_UNSUPPORTED for split precision).  Like gbr_reorder it
+ * synchronizes cuda_stream during the call (the planner reads the block
+ * structure and the rejection counters back to the host between passes) and
+ * returns after the stream work has completed.
  *
- * Set-up: the first call on each device looks up the device address of that
- * array (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * previous call's contents (each call re-initialises what must start at
- * zero), so calls that overlap on the GPU -- from several host threads or
- * several streams at once -- race; calls from one process are serialized by
- * the library, but the caller must not run two such calls concurrently from
- * separate processes on one device.
+ * Its scratch is a fixed array of GBR_NOALLOC_SCRATCH_BYTES in device global
+ * memory, part of the library image: every GPU that loads the library holds
+ * it until the process exits, and each process (each CUDA context) has its
+ * own copy.  Every call looks up the array's device address in the current
+ * context (cudaGetSymbolAddress, with the device current).  All calls of one
+ * process share the array, which keeps the previous call's contents (each
+ * call re-initialises what must start at zero); the library serializes the
+ * calls of one process (a lock held until the call's stream work has
+ * completed), so they never overlap on the GPU.
  */
 #define GBR_NOALLOC_MAX_N 16384
 #define GBR_NOALLOC_SCRATCH_BYTES (256 + 2 * 16384 + 2 * 16384 * 8 + 128 * 128 * 8)
@@ -286,6 +313,8 @@ int gbr_reorder_noalloc(int n, double *S, int ldS, double *Q, int ldQ, const int
  *  6 U          device: w x w, column-major, leading dimension ldU; read only
  *  7 ldU        >= w
  *  8 precision  GBR_PREC_DMMA: FP64 tensor-core products (DMMA);
+ *               GBR_PREC_FMA: FP64 fused multiply-adds, one chain per output
+ *               over k in increasing order from +0 (register tiles);
  *               GBR_PREC_OZAKI: emulated FP64 on the bf16 tensor cores (7
  *               balanced 8-bit digit slices of every entry, relative to
  *               the largest exponent of its row of Y or column of U; the 28
@@ -565,6 +594,11 @@ const char *gbr_status_string(int status);
 
 /* Text of the last CUDA error seen by the calling thread ("" if none). */
 const char *gbr_last_error(void);
+
+/* Bytes of device memory the library's scratch pool holds on the current
+ * device (all slots; 0 before the first allocating call and after
+ * gbr_release), or -1 if no device is current.  Diagnostic only. */
+long long gbr_pool_bytes(void);
 
 /* Release the library's device scratch pool on the current device. */
 void gbr_release(void);

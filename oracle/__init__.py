@@ -29,7 +29,11 @@ _SRC_EV = os.path.join(_HERE, "eigvec_oracle.c")
 _SRC_GEN = os.path.join(_HERE, "gen_oracle.c")
 _SRC_SWEEP = os.path.join(_HERE, "sweep_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
+# the same sources built with -fopenmp: the long row/column/Q loops of the
+# reordering split over the host cores (the CPU baseline's multi-core leg)
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -97,6 +101,21 @@ def load(path: str | None = None):
     if path is None:
         _lib = lib
     return lib
+
+
+def build_omp(force: bool = False) -> str:
+    """The oracle built with -fopenmp (same sources, same arithmetic)."""
+    return build(force, out=_SO_OMP, extra=("-fopenmp",))
+
+
+def load_omp():
+    """The OpenMP build of the oracle (ctypes CDLL with the same functions);
+    pass it as `lib=` to the functions below.  Threads: OMP_NUM_THREADS, else
+    all cores the process may run on."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = load(build_omp())
+    return _lib_omp
 
 
 def _f64(a):

@@ -96,11 +96,22 @@ void orc_eigenvalues(int n, const double *S, int ldS, double *wr, double *wi)
 /* Elementary orthogonal transformations applied to the whole matrix.     */
 /* ---------------------------------------------------------------------- */
 
+/* The four loops below are the long ones (a whole row or column range of S,
+ * or all rows of Q).  Built with -fopenmp (the CPU baseline's multi-core
+ * timing only), each is split over the host cores when it is long; every
+ * element is still computed by the same operations, so the result is
+ * bitwise the same as the single-threaded build, where the pragmas are
+ * ignored. */
+#ifndef ORC_OMP_MIN
+#define ORC_OMP_MIN 2048
+#endif
+
 /* Rotation G = [[c, -s], [s, c]] on index pair (i, i+1):
  *   rows    i, i+1 of A, columns [c0, c1):   [x; y] <- G^T [x; y]
  *   columns i, i+1 of A, rows    [r0, r1):   [x, y] <- [x, y] G      */
 static void rot_rows(double *A, int ld, int i, int c0, int c1, double c, double s)
 {
+#pragma omp parallel for schedule(static) if (c1 - c0 >= ORC_OMP_MIN)
     for (int k = c0; k < c1; ++k) {
         double x = EL(A, ld, i, k), y = EL(A, ld, i + 1, k);
         EL(A, ld, i, k) = c * x + s * y;
@@ -110,6 +121,7 @@ static void rot_rows(double *A, int ld, int i, int c0, int c1, double c, double 
 
 static void rot_cols(double *A, int ld, int i, int r0, int r1, double c, double s)
 {
+#pragma omp parallel for schedule(static) if (r1 - r0 >= ORC_OMP_MIN)
     for (int k = r0; k < r1; ++k) {
         double x = EL(A, ld, k, i), y = EL(A, ld, k, i + 1);
         EL(A, ld, k, i) = c * x + s * y;
@@ -122,6 +134,7 @@ static void rot_cols(double *A, int ld, int i, int r0, int r1, double c, double 
 static void house_rows(double *A, int ld, int i, int len, const double *v, double tau,
                        int c0, int c1)
 {
+#pragma omp parallel for schedule(static) if (c1 - c0 >= ORC_OMP_MIN)
     for (int k = c0; k < c1; ++k) {
         double w = 0.0;
         for (int t = 0; t < len; ++t) w += v[t] * EL(A, ld, i + t, k);
@@ -133,6 +146,7 @@ static void house_rows(double *A, int ld, int i, int len, const double *v, doubl
 static void house_cols(double *A, int ld, int i, int len, const double *v, double tau,
                        int r0, int r1)
 {
+#pragma omp parallel for schedule(static) if (r1 - r0 >= ORC_OMP_MIN)
     for (int k = r0; k < r1; ++k) {
         double w = 0.0;
         for (int t = 0; t < len; ++t) w += EL(A, ld, k, i + t) * v[t];

@@ -23,6 +23,10 @@ SO_PATH = os.path.join(_HERE, "libgbreorder.so")
 
 PREC_DMMA = 0
 PREC_OZAKI = 1
+PREC_FMA = 2
+_PREC = {"dmma": PREC_DMMA, "ozaki": PREC_OZAKI, "fma": PREC_FMA}
+ON_REJECT_CONTINUE = 0
+ON_REJECT_ABORT = 1
 SCHED_PERSISTENT = 0
 SCHED_SEQUENTIAL = 1
 INJECT_STALL = 1
@@ -97,6 +101,7 @@ SYMBOLS = {
     "gbr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbr_last_error": (ctypes.c_char_p, []),
     "gbr_release": (None, []),
+    "gbr_pool_bytes": (ctypes.c_longlong, []),
     "gbr_version": (ctypes.c_int, []),
     "gbr_last_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "gbr_eigenvectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -175,14 +180,18 @@ def default_opts() -> GbrOpts:
 
 
 def make_opts(window=None, chain=None, precision=None, slices=None, strong=None,
-              validate=None, timing=None, sched=None, inject=None, wait_limit_ms=None) -> GbrOpts:
+              validate=None, timing=None, sched=None, inject=None, wait_limit_ms=None,
+              on_reject=None) -> GbrOpts:
     o = default_opts()
+    if on_reject is not None:
+        o.on_reject = {"continue": ON_REJECT_CONTINUE, "abort": ON_REJECT_ABORT}.get(on_reject,
+                                                                                     on_reject)
     if window is not None:
         o.window = int(window)
     if chain is not None:
         o.chain = int(chain)
     if precision is not None:
-        o.precision = {"dmma": PREC_DMMA, "ozaki": PREC_OZAKI}.get(precision, precision)
+        o.precision = _PREC.get(precision, precision)
     if slices is not None:
         o.slices = int(slices)
     if strong is not None:
@@ -287,7 +296,7 @@ def update_panel(Y, U, precision="dmma", *, stream=None) -> None:
     if tuple(U.shape) != (w, w):
         raise ValueError("U must be w x w")
     ldU = _colmajor_ld(U)
-    prec = {"dmma": PREC_DMMA, "ozaki": PREC_OZAKI}.get(precision, precision)
+    prec = _PREC.get(precision, precision)
     rc = lib.gbr_update_panel(rows, w, ctypes.c_void_p(Y.data_ptr()), int(Y.stride(0)),
                               int(Y.stride(1)), ctypes.c_void_p(U.data_ptr()), ldU, int(prec),
                               _stream_handle(stream))

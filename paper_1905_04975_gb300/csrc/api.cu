@@ -77,7 +77,9 @@ static CostModel cost_model(const gbr_opts& o) {
     CostModel c;
     // one SM on an update tile: DMMA ~7.0 GFLOP/s; split precision ~33 GFLOP/s
     // FP64-equivalent (both measured on a panel of 256-row tiles)
-    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0 : 6900.0;
+    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0
+                : (o.precision == GBR_PREC_FMA)  ? 7600.0
+                                                 : 6900.0;
     return c;
 }
 
@@ -139,11 +141,14 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
 static int check_opts(const gbr_opts* o) {
     if (o->window < 4 || o->window > WMAX) return -10;
     if (o->chain < 1 || o->chain > o->window - 2) return -10;
-    if (o->precision != GBR_PREC_DMMA && o->precision != GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    if (o->precision != GBR_PREC_DMMA && o->precision != GBR_PREC_OZAKI &&
+        o->precision != GBR_PREC_FMA)
+        return GBR_ERR_UNSUPPORTED;
     if (o->precision == GBR_PREC_OZAKI &&
         (o->sched != GBR_SCHED_PERSISTENT || (o->slices != 0 && o->slices != OZ_SLICES)))
         return GBR_ERR_UNSUPPORTED;
-    if (o->on_reject != GBR_ON_REJECT_CONTINUE) return GBR_ERR_UNSUPPORTED;
+    if (o->on_reject != GBR_ON_REJECT_CONTINUE && o->on_reject != GBR_ON_REJECT_ABORT)
+        return GBR_ERR_UNSUPPORTED;
     if (o->sched != GBR_SCHED_PERSISTENT && o->sched != GBR_SCHED_SEQUENTIAL) return -10;
     if (o->wait_limit_ms < 0) return -10;
     return 0;
@@ -246,9 +251,13 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
           flops += update_flops(n, win, Q != nullptr);
           for (const Window& wdw : win) {
             if (o.timing) GBR_CK(mark(evw), "event");
-            GBR_CK(launch_window(n, wdw, S, ldS, d_sel, d_u, o.strong_test, d_ctr, st), "window kernel");
+            GBR_CK(launch_window(n, wdw, S, ldS, d_sel, d_u, o.strong_test, d_ctr, st,
+                                 o.on_reject == GBR_ON_REJECT_ABORT),
+                   "window kernel");
             if (o.timing) { GBR_CK(mark(evw), "event"); GBR_CK(mark(evu), "event"); }
-            GBR_CK(launch_update(n, wdw, S, ldS, Q, ldQ, d_u, d_ctr, st), "update kernel");
+            GBR_CK(launch_update(n, wdw, S, ldS, Q, ldQ, d_u, d_ctr, st,
+                                 o.precision == GBR_PREC_FMA),
+                   "update kernel");
             if (o.timing) GBR_CK(mark(evu), "event");
             launches += 2;
           }
@@ -257,6 +266,7 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         GBR_CK(cudaMemcpyAsync(&h_ctr, d_ctr, sizeof h_ctr, cudaMemcpyDeviceToHost, st), "D2H counters");
         GBR_CK(cudaStreamSynchronize(st), "sync");
         if (h_ctr.rejected == seen_rej) break;  // the simulated plan was exact
+        if (o.on_reject == GBR_ON_REJECT_ABORT) break;  // stopped at the first rejection
         seen_rej = h_ctr.rejected;
         // re-plan from the device state: stuck blocks are barriers now
         GBR_CK(launch_subdiag(n, S, ldS, d_sub, st), "subdiag kernel");
@@ -326,7 +336,7 @@ void gbr_default_opts(gbr_opts* o) {
     memset(o, 0, sizeof *o);
     o->window = 128;
     o->chain = 64;
-    o->precision = GBR_PREC_DMMA;
+    o->precision = GBR_PREC_FMA;
     o->slices = 0;
     o->strong_test = 1;
     o->on_reject = GBR_ON_REJECT_CONTINUE;
@@ -454,33 +464,29 @@ int gbr_plan(int n, const unsigned char* sub, const int* select, int window, int
 // Reordering without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// reorder: code running while a stream is being captured into a CUDA graph,
-// programs whose memory is all handed out by their own arena, or processes
-// where a cudaMalloc would synchronize the device at a bad moment.  For them
-// this entry point takes its scratch (counters, block flags, selection
+// reorder: programs whose device memory is all handed out by their own
+// arena or allocator, and processes where a cudaMalloc (which may
+// synchronize the device) must not happen in the middle of their work.  For
+// them this entry point takes its scratch (counters, block flags, selection
 // flags, eigenvalue staging and one window accumulator) from a fixed array
 // in device global memory that is part of the library image instead of the
 // library's pool.  Every GPU that loads the library holds this array
-// (GBR_NOALLOC_SCRATCH_BYTES) until the process exits.
+// (GBR_NOALLOC_SCRATCH_BYTES) until the process exits; each process (each
+// CUDA context) has its own copy.
 // ---------------------------------------------------------------------------
 static constexpr size_t kNoallocBytes = scratch_layout(GBR_NOALLOC_MAX_N).total;
 static_assert(kNoallocBytes == GBR_NOALLOC_SCRATCH_BYTES, "header and layout disagree");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-// Device address of g_noalloc_scratch for each device, looked up once with
-// that device current (in host code the symbol is only a host-side stand-in).
-static void* g_noalloc_ptr[64];
-
+// Device address of g_noalloc_scratch in the current context.  In host code
+// the symbol is only a host-side stand-in, so the address is looked up with
+// the device current, on every call: a cached address would outlive a
+// cudaDeviceReset or belong to another context.  The lookup allocates
+// nothing once the library's module is loaded.
 static int noalloc_scratch(char** out) {
-    int dev = 0;
-    GBR_CK(cudaGetDevice(&dev), "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return GBR_ERR_CUDA;
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        GBR_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = (char*)g_noalloc_ptr[dev];
+    void* p = nullptr;
+    GBR_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
+    *out = (char*)p;
     return 0;
 }
 
@@ -497,7 +503,7 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
     if (rc) return rc;
     o.timing = 0;  // event timing would create events; this path creates nothing
     o.sched = GBR_SCHED_SEQUENTIAL;  // the persistent schedule needs scratch sized per plan
-    if (o.precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
+    if (o.precision == GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
     if (stats) memset(stats, 0, sizeof *stats);
     if (n == 0) {
         if (m_out) *m_out = 0;
@@ -523,7 +529,8 @@ int gbr_update_panel(int rows, int w, double* Y, long long rs, long long ks, con
     if (rs < 1 || ks < 1 || (rs != 1 && ks != 1)) return -4;
     if (!U) return -6;
     if (ldU < w) return -7;
-    if (precision != GBR_PREC_DMMA && precision != GBR_PREC_OZAKI) return -8;
+    if (precision != GBR_PREC_DMMA && precision != GBR_PREC_OZAKI && precision != GBR_PREC_FMA)
+        return -8;
     if (rows == 0) return 0;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     std::lock_guard<std::mutex> lock(g_mu);
@@ -539,8 +546,9 @@ int gbr_update_panel(int rows, int w, double* Y, long long rs, long long ks, con
     GBR_CK(cudaMemcpy2DAsync(dU, (size_t)w * sizeof(double), U, (size_t)ldU * sizeof(double),
                              (size_t)w * sizeof(double), (size_t)w, cudaMemcpyDeviceToDevice, st),
            "D2D U");
-    if (precision == GBR_PREC_DMMA) {
-        GBR_CK(launch_panel_dmma(rows, w, Y, rs, ks, dU, st), "panel kernel");
+    if (precision != GBR_PREC_OZAKI) {
+        GBR_CK(launch_panel_dmma(rows, w, Y, rs, ks, dU, st, precision == GBR_PREC_FMA),
+               "panel kernel");
         GBR_CK(cudaStreamSynchronize(st), "sync");
         return 0;
     }
@@ -716,6 +724,15 @@ const char* gbr_status_string(int s) {
 }
 
 const char* gbr_last_error(void) { return last_error_cstr(); }
+
+long long gbr_pool_bytes(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    long long b = 0;
+    for (int s = 0; s < POOL_NSLOTS; ++s) b += (long long)g_pool[dev].bytes[s];
+    return b;
+}
 
 void gbr_release(void) {
     std::lock_guard<std::mutex> lock(g_mu);

@@ -90,7 +90,9 @@ static TuneChoice tune_lookup(int n, bool* tuned) {
 
 static CostModel batch_cost_model(const gbr_opts& o) {
     CostModel c;
-    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0 : 6900.0;
+    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0
+                : (o.precision == GBR_PREC_FMA)  ? 7600.0
+                                                 : 6900.0;
     return c;
 }
 
@@ -98,7 +100,9 @@ static int check_batch_opts(const gbr_opts& o) {
     const bool auto_w = (o.window == GBR_AUTO);
     if (!auto_w && (o.window < 4 || o.window > WMAX)) return -8;
     if (o.chain != GBR_AUTO && (o.chain < 1 || (!auto_w && o.chain > o.window - 2))) return -8;
-    if (o.precision != GBR_PREC_DMMA && o.precision != GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    if (o.precision != GBR_PREC_DMMA && o.precision != GBR_PREC_OZAKI &&
+        o.precision != GBR_PREC_FMA)
+        return GBR_ERR_UNSUPPORTED;
     if (o.precision == GBR_PREC_OZAKI && o.slices != 0 && o.slices != OZ_SLICES)
         return GBR_ERR_UNSUPPORTED;
     if (o.sched != GBR_SCHED_PERSISTENT) return GBR_ERR_UNSUPPORTED;

@@ -41,6 +41,8 @@ struct DevCounters {
     int step_overflow;   // windows that hit the step cap (a logic error if nonzero)
     unsigned long long win_flops;  // FP64 flops of in-window updates of accepted swaps
     unsigned long long upd_issued; // flops issued by the DMMA update tiles (zero rows of U skipped)
+    int aborted;         // on_reject = ABORT: set by the window task that rejected a swap
+    int pad;
 };
 
 // One reordering problem on the device: a scheduler launch may carry many.
@@ -89,10 +91,13 @@ struct SchedParams {
     const int* succ;
     double* upool;            // U of every window, at Window::u_off (w x w, column-major;
                               // a generalized instance's window has UQ then UZ there)
-    unsigned char* uslices;   // null (DMMA updates) or OZ_USLICE_BYTES per window
+    unsigned char* uslices;   // null (FP64 updates) or OZ_USLICE_BYTES per window
+    int fp64_fma;             // FP64 updates: 1 = DFMA register tiles, 0 = DMMA tiles
+    int* abort_word;          // on_reject = ABORT: set at the first rejected swap, else null
+    int* wskip;               // ABORT: per window, 1 if its task did nothing (tiles skip)
     int* head;                // next queue position
     int* err;                 // nonzero: a wait ran out (1) or the plan does not fit S (2)
-    long long wait_limit;     // spins (~128 ns each) before a wait gives up
+    long long wait_limit_ns;  // a dependency wait gives up after this long (%globaltimer)
     unsigned long long* trace;  // null, or 4 words per queue position:
                                 // smid | wait start | exec start | end (ns)
 };
@@ -131,8 +136,9 @@ struct SrvParams {
     int* done;                  // completion words (host memory, mapped)
     int strong;
     int ozaki;                  // nonzero: split-precision updates (tensor memory held)
-    long long wait_limit;       // spins (~128 ns) of a dependency wait
-    long long park_limit;       // spins (~1 us) of a wait for the ring to fill
+    int fp64_fma;               // FP64 updates: 1 = DFMA register tiles, 0 = DMMA tiles
+    long long wait_limit_ns;    // a dependency wait gives up after this long (%globaltimer)
+    long long park_limit_ns;    // a wait for the ring to fill gives up after this long
 };
 
 // Launchers (each .cu file owns its kernels).
@@ -140,9 +146,9 @@ cudaError_t launch_validate(int n, const double* S, int ldS, DevCounters* ctr, c
 cudaError_t launch_subdiag(int n, const double* S, int ldS, uint8_t* sub, cudaStream_t st);
 cudaError_t launch_eigs(int n, const double* S, int ldS, double* wr, double* wi, cudaStream_t st);
 cudaError_t launch_window(int n, const Window& w, double* S, int ldS, uint8_t* sel, double* U,
-                          int strong, DevCounters* ctr, cudaStream_t st);
+                          int strong, DevCounters* ctr, cudaStream_t st, bool abort = false);
 cudaError_t launch_update(int n, const Window& w, double* S, int ldS, double* Q, int ldQ,
-                          const double* U, DevCounters* ctr, cudaStream_t st);
+                          const double* U, DevCounters* ctr, cudaStream_t st, bool fma = false);
 size_t window_smem_bytes(int w);
 size_t update_smem_bytes(int w);
 cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st);
@@ -163,7 +169,7 @@ int sched_threads();
 // precision launch writes U's digit slices to us (OZ_USLICE_BYTES) first and
 // sets *err if a tile's bounded wait runs out.
 cudaError_t launch_panel_dmma(int rows, int w, double* Y, long long rs, long long ks,
-                              const double* Ug, cudaStream_t st);
+                              const double* Ug, cudaStream_t st, bool fma = false);
 cudaError_t launch_panel_ozaki(int rows, int w, double* Y, long long rs, long long ks,
                                const double* Ug, unsigned char* us, int* err, int grid,
                                cudaStream_t st);

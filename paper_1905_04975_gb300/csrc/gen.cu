@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(upd::UPD_THREADS, 1)
 update_gen_kernel(int n, int s, int e, double* __restrict__ S, int ldS, double* __restrict__ T,
                   int ldT, double* __restrict__ Q, int ldQ, double* __restrict__ Z, int ldZ,
                   const double* __restrict__ UQg, const double* __restrict__ UZg, GenPanels pc,
-                  DevCounters* ctr) {
+                  DevCounters* ctr, int fma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = blockIdx.x, k = 0;
     while (k < 5 && b >= pc.cnt[k]) b -= pc.cnt[k++];
@@ -116,8 +116,12 @@ update_gen_kernel(int n, int s, int e, double* __restrict__ S, int ldS, double* 
                     &base, &rs, &ks, &R);
     const double* U = (k == 0 || k == 1 || k == 4) ? UQg : UZg;
     const int r0 = b * upd::BM;
-    upd::update_tile(base, rs, ks, r0, min(upd::BM, R - r0), e - s, U, true, smem_raw,
-                     ctr ? &ctr->upd_issued : nullptr);
+    if (fma)
+        upd::update_tile_fma(base, rs, ks, r0, min(upd::BM, R - r0), e - s, U, true, smem_raw,
+                             ctr ? &ctr->upd_issued : nullptr);
+    else
+        upd::update_tile(base, rs, ks, r0, min(upd::BM, R - r0), e - s, U, true, smem_raw,
+                         ctr ? &ctr->upd_issued : nullptr);
 }
 
 bool g_win_cfg[64], g_upd_cfg[64];
@@ -162,7 +166,7 @@ cudaError_t launch_window_gen(int n, const Window& wd, double* S, int ldS, doubl
 
 cudaError_t launch_update_gen(int n, const Window& wd, double* S, int ldS, double* T, int ldT,
                               double* Q, int ldQ, double* Z, int ldZ, const double* UQ,
-                              const double* UZ, DevCounters* ctr, cudaStream_t st) {
+                              const double* UZ, DevCounters* ctr, cudaStream_t st, bool fma) {
     cudaError_t e = configure((const void*)update_gen_kernel, upd::kUpdateSmem, g_upd_cfg);
     if (e != cudaSuccess) return e;
     const int BM = upd::BM;
@@ -175,7 +179,7 @@ cudaError_t launch_update_gen(int n, const Window& wd, double* S, int ldS, doubl
     for (int k = 0; k < 6; ++k) grid += pc.cnt[k];
     if (grid == 0) return cudaSuccess;
     update_gen_kernel<<<grid, upd::UPD_THREADS, upd::kUpdateSmem, st>>>(
-        n, wd.s, wd.e, S, ldS, T, ldT, Q, ldQ, Z, ldZ, UQ, UZ, pc, ctr);
+        n, wd.s, wd.e, S, ldS, T, ldT, Q, ldQ, Z, ldZ, UQ, UZ, pc, ctr, fma ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -216,6 +220,7 @@ int run_persistent_gen(int n, const std::vector<Window>& wins, double* S, int ld
     cm.lr_mats = 2.0;
     cm.win_us_128 = kGenWinUs128;
     if (o.precision == GBR_PREC_OZAKI) cm.tile_rate = 100000.0;
+    if (o.precision == GBR_PREC_FMA) cm.tile_rate = 7600.0;
     SchedLaunch L;
     int rc = sched_prepare(
         plans, o, cm, num_sms(),
@@ -340,7 +345,8 @@ int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q,
             GBR_CK(launch_window_gen(n, wd, S, ldS, T, ldT, d_sel, d_uq, d_uz, o.strong_test, d_ctr, st),
                    "window kernel (pair)");
             if (o.timing) { GBR_CK(mark(evw), "event"); GBR_CK(mark(evu), "event"); }
-            GBR_CK(launch_update_gen(n, wd, S, ldS, T, ldT, Q, ldQ, Z, ldZ, d_uq, d_uz, d_ctr, st),
+            GBR_CK(launch_update_gen(n, wd, S, ldS, T, ldT, Q, ldQ, Z, ldZ, d_uq, d_uz, d_ctr, st,
+                                     o.precision == GBR_PREC_FMA),
                    "update kernel (pair)");
             if (o.timing) GBR_CK(mark(evu), "event");
             launches += 2;
@@ -415,7 +421,9 @@ int gen_args(int n, const void* S, int ldS, const void* T, int ldT, const void* 
     if (n > 0 && !select) return -6;
     if (o.window < 4 || o.window > WMAX || o.chain < 1 || o.chain > o.window - 2) return -10;
     if (o.sched != GBR_SCHED_PERSISTENT && o.sched != GBR_SCHED_SEQUENTIAL) return -10;
-    if (o.precision != GBR_PREC_DMMA && o.precision != GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    if (o.precision != GBR_PREC_DMMA && o.precision != GBR_PREC_OZAKI &&
+        o.precision != GBR_PREC_FMA)
+        return GBR_ERR_UNSUPPORTED;
     // split precision runs on the persistent scheduler only
     if (o.precision == GBR_PREC_OZAKI &&
         (o.sched != GBR_SCHED_PERSISTENT || (o.slices != 0 && o.slices != OZ_SLICES)))

@@ -19,6 +19,16 @@ panel_dmma_kernel(double* __restrict__ Y, long long rs, long long ks, int rows, 
     upd::update_tile(Y, rs, ks, r0, min(upd::BM, rows - r0), w, Ug, true, smem_raw, nullptr);
 }
 
+// One BM-row tile per CTA (FP64 FMA register tiles), the scheduler's CTA size.
+constexpr int PANEL_FMA_THREADS = 512;
+__global__ void __launch_bounds__(PANEL_FMA_THREADS, 1)
+panel_fma_kernel(double* __restrict__ Y, long long rs, long long ks, int rows, int w,
+                 const double* __restrict__ Ug) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int r0 = blockIdx.x * upd::BM;
+    upd::update_tile_fma(Y, rs, ks, r0, min(upd::BM, rows - r0), w, Ug, true, smem_raw, nullptr);
+}
+
 // U's digit slices and column exponents (the window task's writer).
 __global__ void __launch_bounds__(512, 1) uslices_kernel(const double* __restrict__ Ug, int w,
                                                          unsigned char* __restrict__ us) {
@@ -60,7 +70,15 @@ cudaError_t set_smem_once(K kernel, size_t bytes, bool* done) {
 }  // namespace
 
 cudaError_t launch_panel_dmma(int rows, int w, double* Y, long long rs, long long ks,
-                              const double* Ug, cudaStream_t st) {
+                              const double* Ug, cudaStream_t st, bool fma) {
+    if (fma) {
+        static bool done_f[64] = {};
+        cudaError_t e = set_smem_once(panel_fma_kernel, upd::kUpdateSmem, done_f);
+        if (e != cudaSuccess || rows == 0) return e;
+        panel_fma_kernel<<<(rows + upd::BM - 1) / upd::BM, PANEL_FMA_THREADS, upd::kUpdateSmem,
+                           st>>>(Y, rs, ks, rows, w, Ug);
+        return cudaGetLastError();
+    }
     static bool done[64] = {};
     cudaError_t e = set_smem_once(panel_dmma_kernel, upd::kUpdateSmem, done);
     if (e != cudaSuccess || rows == 0) return e;

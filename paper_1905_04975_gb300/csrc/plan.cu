@@ -624,8 +624,12 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     for (size_t i = 0; i < ni; ++i) pair |= (plans[i].d.T != nullptr);
     const size_t b_us = ozaki ? al(OZ_USLICE_BYTES * wins.size() * (pair ? 2 : 1)) : 0;
     const size_t b_u = al(sizeof(double) * std::max<long long>(1, u_total));
+    // ABORT on rejection: one word per window (its task did nothing); every
+    // window task writes its own before its tiles read it
+    const bool abort = (o.on_reject == GBR_ON_REJECT_ABORT);
+    const size_t b_ws = abort ? al(sizeof(int) * std::max<size_t>(1, wins.size())) : 0;
     const size_t total = b_inst + b_tasks + b_wins + 2 * b_deps + b_soff + b_succ + b_ctl + b_tr +
-                         b_us + b_u;
+                         b_us + b_ws + b_u;
     char* p = (char*)alloc(total);
     if (!p) return GBR_ERR_NOMEM;
     Inst* d_inst = (Inst*)p; p += b_inst;
@@ -638,6 +642,7 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     int* d_ctl = (int*)p; p += b_ctl;
     unsigned long long* d_tr = b_tr ? (unsigned long long*)p : nullptr; p += b_tr;
     unsigned char* d_us = b_us ? (unsigned char*)p : nullptr; p += b_us;
+    int* d_ws = b_ws ? (int*)p : nullptr; p += b_ws;
     double* d_u = (double*)p;
     GBR_CK(cudaMemcpyAsync(d_inst, itab.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice, st), "H2D instances");
     if (nt) {
@@ -663,10 +668,13 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     P.succ = d_succ;
     P.upool = d_u;
     P.uslices = d_us;
+    P.fp64_fma = (o.precision == GBR_PREC_FMA) ? 1 : 0;
     P.head = d_ctl;
     P.err = d_ctl + 1;
+    P.abort_word = abort ? d_ctl + 2 : nullptr;   // reset with the control words per launch
+    P.wskip = d_ws;
     const long long lim_ms = o.wait_limit_ms > 0 ? o.wait_limit_ms : 60000;
-    P.wait_limit = lim_ms * 1000000 / 128;
+    P.wait_limit_ns = lim_ms * 1000000;
     P.trace = d_tr;
     L->grid = grid;
     L->deps_init = d_deps0;

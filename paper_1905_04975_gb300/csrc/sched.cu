@@ -43,10 +43,29 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Deadline of a bounded wait that starts now: limit_ns of %globaltimer time.
+// The spin cap is a backstop only (every poll is an L2 round trip of well
+// over 16 ns), so that a stopped timer could not make a wait endless.
+struct WaitBound {
+    unsigned long long deadline;
+    long long spins, max_spins;
+    __device__ __forceinline__ explicit WaitBound(long long limit_ns);
+    // true once the wait has run out
+    __device__ __forceinline__ bool expired();
+};
+
 __device__ __forceinline__ unsigned smid() {
     unsigned r;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
     return r;
+}
+
+__device__ __forceinline__ WaitBound::WaitBound(long long limit_ns)
+    : deadline(global_ns() + (unsigned long long)limit_ns), spins(0),
+      max_spins(limit_ns / 16 + 1) {}
+
+__device__ __forceinline__ bool WaitBound::expired() {
+    return ++spins > max_spins || global_ns() > deadline;
 }
 
 // Runs one window task or update task of window wd of instance I.  u_key
@@ -62,9 +81,13 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
                                          double* Ug, unsigned char* uslices,
                                          int strong, unsigned long long key,
                                          unsigned long long* u_key, unsigned char* smem_raw,
-                                         uint32_t tmem, int* err) {
+                                         uint32_t tmem, int* err, bool fma,
+                                         int* abort_word = nullptr, int* wskip = nullptr) {
     const int tid = threadIdx.x;
     const int w = wd.e - wd.s;
+    // ABORT: the update tasks of a window whose task did nothing do nothing
+    // (its U was never formed); the window task ran before them (a predecessor)
+    if (wskip && tk.kind != TASK_W && __ldcg(wskip) != 0) return;
     if (tk.kind == TASK_W) {
         if constexpr (MODE == 1) {
             gen::window_gen_body(I.n, I.S, I.ldS, I.T, I.ldT, wd.s, w, I.sel, Ug, Ug + w * w, strong,
@@ -81,7 +104,8 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
             swp::sweep_body(I.n, I.S, I.ldS, wd.s, w, wd.t0, wd.t1, wd.nb, I.sp + 2 * wd.b0, Ug,
                             I.ctr, smem_raw);
         else
-            win::window_body(I.n, I.S, I.ldS, wd.s, w, I.sel, Ug, strong, I.ctr, smem_raw, uslices);
+            win::window_body(I.n, I.S, I.ldS, wd.s, w, I.sel, Ug, strong, I.ctr, smem_raw, uslices,
+                             abort_word, wskip);
         if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds a U
         return;
     }
@@ -113,8 +137,12 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
                 continue;
             }
             for (int r = 0; r < tk.rows; r += upd::BM) {
-                upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w, U, load_u,
-                                 smem_raw, &I.ctr->upd_issued);
+                if (fma)
+                    upd::update_tile_fma(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w, U,
+                                         load_u, smem_raw, &I.ctr->upd_issued);
+                else
+                    upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w, U,
+                                     load_u, smem_raw, &I.ctr->upd_issued);
                 load_u = false;
             }
         }
@@ -134,8 +162,12 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
         if (tid == 0) *u_key = ~0ull;  // shared memory no longer holds U
     } else {
         for (int r = 0; r < tk.rows; r += upd::BM) {
-            upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s, Ug,
-                             load_u, smem_raw, &I.ctr->upd_issued);
+            if (fma)
+                upd::update_tile_fma(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r),
+                                     wd.e - wd.s, Ug, load_u, smem_raw, &I.ctr->upd_issued);
+            else
+                upd::update_tile(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), wd.e - wd.s,
+                                 Ug, load_u, smem_raw, &I.ctr->upd_issued);
             load_u = false;
         }
         if (tid == 0) *u_key = key;
@@ -179,11 +211,11 @@ sched_kernel(SchedParams P) {
                 P.trace[4 * t + 0] = smid();
                 P.trace[4 * t + 1] = global_ns();
             }
-            if (t < P.ntasks) {
-                long long spins = 0;
+            if (t < P.ntasks && ld_volatile(&P.deps_left[t]) > 0) {
+                WaitBound wb(P.wait_limit_ns);
                 while (ld_volatile(&P.deps_left[t]) > 0) {
                     if (ld_volatile(P.err) != 0) { t = -1; break; }
-                    if (++spins > P.wait_limit) {
+                    if (wb.expired()) {
                         atomicExch(P.err, 1);
                         t = -1;
                         break;
@@ -205,7 +237,8 @@ sched_kernel(SchedParams P) {
         run_task<MODE>(tk, wd, I, P.upool + wd.u_off,
                  P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES * (MODE == 1 ? 2 : 1)
                            : nullptr,
-                 P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err);
+                 P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err,
+                 P.fp64_fma != 0, P.abort_word, P.wskip ? P.wskip + tk.win : nullptr);
         // release: every thread's writes are ordered before the counters drop
         __threadfence();
         __syncthreads();
@@ -247,16 +280,18 @@ server_kernel(SrvParams P) {
     for (;;) {
         if (tid == 0) {
             long long t = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(P.head), 1ull);
-            long long spins = 0;
             // hold the position until it is published
-            while (t >= ld_volatile64(P.tail)) {
+            if (t >= ld_volatile64(P.tail)) {
+              WaitBound park(P.park_limit_ns);
+              while (t >= ld_volatile64(P.tail)) {
                 if (ld_volatile(P.stop) != 0 || ld_volatile(P.err) != 0) { t = -1; break; }
-                if (++spins > P.park_limit) {
+                if (park.expired()) {
                     atomicExch(P.err, 3);
                     t = -1;
                     break;
                 }
                 __nanosleep(1024);
+              }
             }
             RingEntry e{-1, -1};
             if (t >= 0) {
@@ -265,10 +300,10 @@ server_kernel(SrvParams P) {
                 e.local = __ldcg(&rp->local);
                 const int* deps = reinterpret_cast<const int*>(__ldcg(
                     reinterpret_cast<const unsigned long long*>(&P.reqs[e.req].deps)));
-                spins = 0;
+                WaitBound wb(P.wait_limit_ns);
                 while (ld_volatile(&deps[e.local]) > 0) {
                     if (ld_volatile(P.err) != 0) { t = -1; break; }
-                    if (++spins > P.wait_limit) {
+                    if (wb.expired()) {
                         atomicExch(P.err, 1);
                         t = -1;
                         break;
@@ -316,7 +351,7 @@ server_kernel(SrvParams P) {
             run_task<0>(tk, wd, R.inst, R.upool + wd.u_off,
                      R.uslices ? R.uslices + (size_t)tk.win * OZ_USLICE_BYTES : nullptr,
                      P.strong, ((unsigned long long)(unsigned)R.id << 32) | (unsigned)tk.win, &u_key,
-                     smem_raw, tmem, P.err);
+                     smem_raw, tmem, P.err, P.fp64_fma != 0);
         }
         __threadfence();
         __syncthreads();

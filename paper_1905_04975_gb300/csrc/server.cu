@@ -151,7 +151,9 @@ bool host_standard(int n, const double* S, int ldS) {
 
 CostModel server_cost(const gbr_opts& o) {
     CostModel c;
-    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0 : 6900.0;
+    c.tile_rate = (o.precision == GBR_PREC_OZAKI) ? 100000.0
+                : (o.precision == GBR_PREC_FMA)  ? 7600.0
+                                                 : 6900.0;
     return c;
 }
 
@@ -537,7 +539,9 @@ int gbr_server_create(const gbr_server_cfg* cfg, gbr_server** out) {
         return -1;
     if (c.opts.sched != GBR_SCHED_PERSISTENT || c.opts.on_reject != GBR_ON_REJECT_CONTINUE)
         return GBR_ERR_UNSUPPORTED;
-    if (c.opts.precision != GBR_PREC_DMMA && c.opts.precision != GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    if (c.opts.precision != GBR_PREC_DMMA && c.opts.precision != GBR_PREC_OZAKI &&
+        c.opts.precision != GBR_PREC_FMA)
+        return GBR_ERR_UNSUPPORTED;
     if (c.opts.precision == GBR_PREC_OZAKI && c.opts.slices != 0 && c.opts.slices != OZ_SLICES)
         return GBR_ERR_UNSUPPORTED;
     if (c.opts.window != GBR_AUTO && (c.opts.window < 4 || c.opts.window > WMAX)) return -1;
@@ -597,11 +601,12 @@ int gbr_server_create(const gbr_server_cfg* cfg, gbr_server** out) {
     P.err = s->d_err;
     P.reqs = s->d_reqs;
     P.ozaki = s->ozaki ? 1 : 0;
+    P.fp64_fma = (c.opts.precision == GBR_PREC_FMA) ? 1 : 0;
     P.done = s->d_done;
     P.strong = c.opts.strong_test;
     const long long lim_ms = c.opts.wait_limit_ms > 0 ? c.opts.wait_limit_ms : 60000;
-    P.wait_limit = lim_ms * 1000000 / 128;
-    P.park_limit = (c.idle_limit_ms > 0 ? c.idle_limit_ms : 3600000LL) * 1000;
+    P.wait_limit_ns = lim_ms * 1000000;
+    P.park_limit_ns = (c.idle_limit_ms > 0 ? c.idle_limit_ms : 3600000LL) * 1000000;
     GBR_CK(launch_server(P, s->grid, s->ks), "server kernel");
     s->kernel_running = true;
     s->th = std::thread(server_loop, s);

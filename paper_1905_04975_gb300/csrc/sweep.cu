@@ -202,7 +202,8 @@ int sweep_device(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, con
         GBR_CK(launch_sweep_window(n, sw, H, ldH, d_sp, d_u, d_ctr, st), "sweep window kernel");
         if (o.timing) GBR_CK(mark(), "event");
         Window wd{sw.s, sw.e, 0, 0, 0};
-        GBR_CK(launch_update(n, wd, H, ldH, Q, ldQ, d_u, d_ctr, st), "update kernel (sweep)");
+        GBR_CK(launch_update(n, wd, H, ldH, Q, ldQ, d_u, d_ctr, st, o.precision == GBR_PREC_FMA),
+               "update kernel (sweep)");
         if (o.timing) GBR_CK(mark(), "event");
         launches += 2;
     }
@@ -289,7 +290,7 @@ int gbr_qr_sweep(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, con
     }
     // a sweep window holds at least one bulge with room to move (w >= 8)
     if (o.window < 8 || o.window > WMAX || o.chain < 1) return -10;
-    if (o.precision != GBR_PREC_DMMA) return GBR_ERR_UNSUPPORTED;
+    if (o.precision != GBR_PREC_DMMA && o.precision != GBR_PREC_FMA) return GBR_ERR_UNSUPPORTED;
     if (o.sched != GBR_SCHED_PERSISTENT && o.sched != GBR_SCHED_SEQUENTIAL) return -10;
     if (stats) memset(stats, 0, sizeof *stats);
     if (n < 3 || nshifts == 0) return 0;

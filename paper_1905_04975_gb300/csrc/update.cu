@@ -8,7 +8,7 @@ namespace {
 
 __global__ void __launch_bounds__(upd::UPD_THREADS, 1)
 update_kernel(int n, int s, int e, double* __restrict__ S, int ldS, double* __restrict__ Q,
-              int ldQ, const double* __restrict__ Ug, int tL, int tR, DevCounters* ctr) {
+              int ldQ, const double* __restrict__ Ug, int tL, int tR, DevCounters* ctr, int fma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = blockIdx.x;
     int panel = upd::PANEL_L;
@@ -19,8 +19,12 @@ update_kernel(int n, int s, int e, double* __restrict__ S, int ldS, double* __re
     int R;
     upd::panel_geom(panel, n, s, e, S, ldS, Q, ldQ, &base, &rs, &ks, &R);
     const int r0 = b * upd::BM;
-    upd::update_tile(base, rs, ks, r0, min(upd::BM, R - r0), e - s, Ug, true, smem_raw,
-                     ctr ? &ctr->upd_issued : nullptr);
+    if (fma)
+        upd::update_tile_fma(base, rs, ks, r0, min(upd::BM, R - r0), e - s, Ug, true, smem_raw,
+                             ctr ? &ctr->upd_issued : nullptr);
+    else
+        upd::update_tile(base, rs, ks, r0, min(upd::BM, R - r0), e - s, Ug, true, smem_raw,
+                         ctr ? &ctr->upd_issued : nullptr);
 }
 
 }  // namespace
@@ -28,7 +32,7 @@ update_kernel(int n, int s, int e, double* __restrict__ S, int ldS, double* __re
 size_t update_smem_bytes(int /*w*/) { return upd::kUpdateSmem; }
 
 cudaError_t launch_update(int n, const Window& wd, double* S, int ldS, double* Q, int ldQ,
-                          const double* U, DevCounters* ctr, cudaStream_t st) {
+                          const double* U, DevCounters* ctr, cudaStream_t st, bool fma) {
     static bool configured[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -46,7 +50,8 @@ cudaError_t launch_update(int n, const Window& wd, double* S, int ldS, double* Q
     int tQ = Q ? (n + BM - 1) / BM : 0;
     int grid = tL + tR + tQ;
     if (grid == 0) return cudaSuccess;
-    update_kernel<<<grid, upd::UPD_THREADS, smem, st>>>(n, wd.s, wd.e, S, ldS, Q, ldQ, U, tL, tR, ctr);
+    update_kernel<<<grid, upd::UPD_THREADS, smem, st>>>(n, wd.s, wd.e, S, ldS, Q, ldQ, U, tL, tR, ctr,
+                                                        fma ? 1 : 0);
     return cudaGetLastError();
 }
 

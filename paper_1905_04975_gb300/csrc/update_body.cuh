@@ -29,7 +29,10 @@ constexpr int BM = UPD_BM;        // panel rows per tile
 constexpr int UPD_THREADS = 256;  // 8 warps, each owning 16 output columns
 constexpr int LDY = WMAX + 4;     // padded row pitch of the Y tile in shared memory
 constexpr int LDU = WMAX + 8;     // padded row pitch of U (row k holds U[k, :])
-constexpr size_t kUpdateSmem = sizeof(double) * ((size_t)WMAX * LDU + (size_t)BM * LDY);
+constexpr size_t kUpdateSmem = sizeof(double) * ((size_t)WMAX * LDU +
+                                                  (size_t)(BM * LDY > WMAX * (BM + 2)
+                                                               ? BM * LDY
+                                                               : WMAX * (BM + 2)));
 
 enum Panel { PANEL_L = 0, PANEL_R = 1, PANEL_Q = 2 };
 
@@ -181,6 +184,122 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
                     int k = c0 + ct * 8 + tig * 2 + v;
                     if (k < w) __stcg(&base[(long long)(r0 + r) * rs + (long long)k * ks], acc[rt][ct][v]);
                 }
+        }
+    }
+    __syncthreads();
+}
+
+// The same product Y <- Y U on the FP64 FMA pipe (DFMA) instead of the FP64
+// tensor path.  On this GPU both share one FP64 pipe, and plain FMAs reach
+// a higher rate than m8n8k4 DMMA (measured: 1.195 against 1.047 TFLOP/s for
+// the whole GPU), so this tile trades the MMA fragments for a register tile.
+//
+// Shared memory: U as in update_tile (row k holds U[k, :]), the Y tile
+// k-major (Yk[k * LDK + r]), so that a lane reads its two rows as one
+// 16-byte load and its eight columns of U as four broadcast 16-byte loads.
+// The output columns are cut into groups of 8; warp v computes groups v,
+// v + nwarps, ...: lane l owns rows 2l, 2l + 1 of the 64-row tile and the 8
+// columns of the group (16 FP64 accumulators).  Each group runs over the
+// rows [klo, khi) of U where its 8 columns have nonzeros (the staircase of
+// a product of adjacent swaps).  Every output is one FMA chain over k in
+// increasing order, starting from 0.
+constexpr int LDK = BM + 2;   // padded pitch of the k-major Y tile (16-byte rows)
+constexpr int FMA_GROUPS = WMAX / 8;
+
+__device__ __forceinline__ void update_tile_fma(double* base, long long rs, long long ks, int r0,
+                                                int rows, int w, const double* __restrict__ Ug,
+                                                bool load_u, unsigned char* smem_raw,
+                                                unsigned long long* issued = nullptr) {
+    static_assert(BM == 64, "one lane owns two rows of the 64-row tile");
+    double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU
+    double* Yk = Us + WMAX * LDU;                        // WMAX x LDK (k-major)
+    __shared__ int g_lo[FMA_GROUPS], g_hi[FMA_GROUPS];
+    const int wp = (w + 7) & ~7;  // padded to the group width
+    const int ng = wp >> 3;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+    if (load_u) {
+        for (int i = tid; i < wp * wp; i += nth) {
+            int k = i / wp, c = i % wp;
+            Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+        }
+        __syncthreads();
+        // rows of U where each group of 8 columns has nonzeros
+        for (int g = warp; g < ng; g += nw) {
+            int lo = wp, hi = 0;
+            for (int k = lane; k < wp; k += 32) {
+                bool nz = false;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) nz |= Us[k * LDU + 8 * g + c] != 0.0;
+                if (nz) {
+                    lo = min(lo, k);
+                    hi = max(hi, k + 1);
+                }
+            }
+            for (int o = 16; o; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) {
+                g_lo[g] = lo < hi ? lo : 0;
+                g_hi[g] = lo < hi ? hi : 0;
+            }
+        }
+    }
+    if (rs == 1) {
+        for (int i = tid; i < BM * wp; i += nth) {
+            int r = i % BM, k = i / BM;
+            Yk[k * LDK + r] = (r < rows && k < w) ? __ldcg(&base[(r0 + r) + (long long)k * ks]) : 0.0;
+        }
+    } else {
+        for (int i = tid; i < BM * wp; i += nth) {
+            int k = i % wp, r = i / wp;
+            Yk[k * LDK + r] = (r < rows && k < w) ? __ldcg(&base[(long long)(r0 + r) * rs + k]) : 0.0;
+        }
+    }
+    __syncthreads();
+    if (issued && tid == 0) {
+        unsigned long long f = 0;
+        for (int g = 0; g < ng; ++g)
+            f += 2ull * rows * (unsigned long long)min(8, w - 8 * g) * (g_hi[g] - g_lo[g]);
+        atomicAdd(issued, f);
+    }
+    const int ra = 2 * lane;
+    for (int g = warp; g < ng; g += nw) {
+        const int lo = g_lo[g], hi = g_hi[g];
+        double acc[2][8];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+        const double* up = Us + 8 * g;
+#pragma unroll 2
+        for (int k = lo; k < hi; ++k) {
+            const double2 y = *reinterpret_cast<const double2*>(&Yk[k * LDK + ra]);
+            const double2* u2 = reinterpret_cast<const double2*>(up + k * LDU);
+            double u[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double2 t = u2[j];
+                u[2 * j] = t.x;
+                u[2 * j + 1] = t.y;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                acc[0][j] = fma(y.x, u[j], acc[0][j]);
+                acc[1][j] = fma(y.y, u[j], acc[1][j]);
+            }
+        }
+        // write back (in place: the tile's rows were all read before)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = ra + i;
+            if (r >= rows) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 8 * g + j;
+                if (k < w) __stcg(&base[(long long)(r0 + r) * rs + (long long)k * ks], acc[i][j]);
+            }
         }
     }
     __syncthreads();

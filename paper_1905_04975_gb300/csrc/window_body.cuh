@@ -312,11 +312,16 @@ constexpr size_t kWindowSmem = sizeof(double) * ((size_t)WMAX * WMAX +
                                                  (size_t)MAXSW * 16) +
                                sizeof(int) * 3 * MAXSW + 2 * WMAX;
 
+// abort_word (ABORT on rejection, else null): a window task that starts
+// after it was set does nothing (U = I, *skip_out = 1); a window task that
+// rejects a swap sets it, finishes the step it is in, restores the standard
+// form of its 2x2 blocks and stops.  skip_out (nullable) receives 0 or 1.
 __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int ldS, int s0, int w,
                                             uint8_t* __restrict__ gsel, double* __restrict__ Ug,
                                             int strong, DevCounters* __restrict__ ctr,
                                             unsigned char* smem_raw,
-                                            unsigned char* __restrict__ uslices = nullptr) {
+                                            unsigned char* __restrict__ uslices = nullptr,
+                                            int* abort_word = nullptr, int* skip_out = nullptr) {
     double* U = reinterpret_cast<double*>(smem_raw);           // w*w
     double* Sp = U + WMAX * WMAX;                               // packed window
     double* Zs = Sp + poff(WMAX);                               // MAXSW * 16
@@ -340,6 +345,20 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
+
+    if (abort_word) {
+        __shared__ int skip;
+        __syncthreads();
+        if (tid == 0) skip = *reinterpret_cast<volatile int*>(abort_word) != 0;
+        __syncthreads();
+        if (skip) {
+            // the reordering stopped before this window started: U = I
+            for (int i = tid; i < w * w; i += nth) Ug[i] = ((i % w) == (i / w)) ? 1.0 : 0.0;
+            if (tid == 0 && skip_out) *skip_out = 1;
+            return;
+        }
+    }
+    if (tid == 0 && skip_out) *skip_out = 0;
 
     // load: packed window of S, selection, U = I
     for (int c = 0; c < w; ++c) {
@@ -370,6 +389,12 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     bool final_pass = false;
     for (int iter = 0;; ++iter) {
         __syncthreads();
+        if (abort_word && !final_pass && nrej > 0) {
+            // ABORT: the first rejection stops the reordering; this window
+            // only restores the standard form of its 2x2 blocks
+            final_pass = true;
+            if (tid == 0) atomicExch(abort_word, 1);
+        }
         if (iter > 4 * WMAX * WMAX) {
             if (tid == 0) atomicAdd(&ctr->step_overflow, 1);
             break;

@@ -21,11 +21,11 @@ are this project's synthetic stand-in):
 * selection: blocks in seeded random order are selected until the selected
   eigenvalue count reaches round(p n); a 2x2 block (a conjugate pair) is
   always selected whole;
-* serving requests: a principal diagonal block S[k:k+n, k:k+n] of one large
-  seeded base form, cut at block boundaries (so it is again a standard
-  form), at a seeded offset k; Q of 8 seeded reflectors; the selection is
-  drawn as above from the sub-block's own blocks.  Twenty thousand
-  independent forms of order up to 8192 would not fit in host memory.
+* serving requests: an independent form of order n per request from this
+  generator (serve_problem, Q of 8 seeded reflectors), made when the
+  request is about to arrive; or (serve_request, for the CPU sample of the
+  reference arm) a principal diagonal block S[k:k+n, k:k+n] of one seeded
+  base form cut at block boundaries, at a seeded offset k.
 
 Generalized real Schur form (S, T) (the pair case of Eq. 7):
 
@@ -54,7 +54,7 @@ import numpy as np
 
 __all__ = ["block_sizes", "schur_form", "householder_q", "selection",
            "reorder_problem", "batch_problems", "request_stream", "serve_base",
-           "serve_request", "gen_schur_pair", "gen_problem", "gen_config",
+           "serve_request", "serve_problem", "gen_schur_pair", "gen_problem", "gen_config",
            "hessenberg_problem", "sweep_config"]
 
 
@@ -73,20 +73,25 @@ def block_sizes(n: int, rng: np.random.Generator, frac_1x1: float = 0.6) -> np.n
 
 
 def schur_form(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6,
-               clusters: bool = False, spread: float = 1e-6, kappa: float = 1.0):
-    """Random standard real Schur form. Returns (S, sizes).
+               clusters: bool = False, spread: float = 1e-6, kappa: float = 1.0,
+               order: str = "F"):
+    """Random standard real Schur form. Returns (S, sizes); S in the given
+    memory order (the values do not depend on it).
 
     kappa > 1 makes the 2x2 blocks non-normal (|b| scaled by kappa, |c| by
     1/kappa, eigenvalues' imaginary parts unchanged); with clustered,
     nearly equal eigenvalues this is what makes block swaps ill-conditioned
     enough to be rejected."""
     sizes = block_sizes(n, rng, frac_1x1)
-    S = np.zeros((n, n), dtype=np.float64, order="F")
+    S = np.zeros((n, n), dtype=np.float64, order=order)
     if n == 0:
         return S, sizes
     # strict upper triangle ~ N(0,1)
     upper = rng.standard_normal((n, n))
-    S[:] = np.triu(upper, k=1)
+    if order == "C":
+        S = np.triu(upper, k=1)
+    else:
+        S[:] = np.triu(upper, k=1)
     del upper
     nb1 = int(np.sum(sizes == 1))
     nb2 = int(np.sum(sizes == 2))
@@ -125,14 +130,16 @@ def schur_form(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6,
     return S, sizes
 
 
-def householder_q(n: int, rng: np.random.Generator, k: int = 64) -> np.ndarray:
+def householder_q(n: int, rng: np.random.Generator, k: int = 64,
+                  order: str = "F") -> np.ndarray:
     """Q = H_1 H_2 ... H_k, H_i = I - 2 v_i v_i^T / (v_i^T v_i), v_i ~ N(0,1)^n.
 
     Formed in compact WY form, Q = I - V T V^T with T upper triangular, so
-    that large n costs one matrix product.
+    that large n costs one matrix product.  Memory order as given (the
+    values do not depend on it).
     """
     k = min(k, n)
-    Q = np.zeros((n, n), dtype=np.float64, order="F")
+    Q = np.zeros((n, n), dtype=np.float64, order=order)
     if n == 0:
         return Q
     V = rng.standard_normal((n, k))
@@ -142,7 +149,10 @@ def householder_q(n: int, rng: np.random.Generator, k: int = 64) -> np.ndarray:
         T[i, i] = tau[i]
         if i:
             T[:i, i] = -tau[i] * (T[:i, :i] @ (V[:, :i].T @ V[:, i]))
-    Q[:] = -(V @ T) @ V.T
+    if order == "C":
+        Q = -(V @ T) @ V.T
+    else:
+        Q[:] = -(V @ T) @ V.T
     Q[np.diag_indices(n)] += 1.0
     return Q
 
@@ -166,14 +176,16 @@ def selection(sizes: np.ndarray, frac: float, rng: np.random.Generator) -> np.nd
 
 def reorder_problem(n: int, seed: int = 0, *, select_frac: float = 0.3,
                     q: str = "identity", reflectors: int = 64,
-                    clusters: bool = False, spread: float = 1e-6, kappa: float = 1.0):
-    """One reordering instance: (S, Q, select), S and Q column-major float64."""
+                    clusters: bool = False, spread: float = 1e-6, kappa: float = 1.0,
+                    order: str = "F"):
+    """One reordering instance: (S, Q, select), S and Q float64, column-major
+    (order "F", the default) or row-major (order "C": the same values)."""
     rng = np.random.default_rng(seed)
-    S, sizes = schur_form(n, rng, clusters=clusters, spread=spread, kappa=kappa)
+    S, sizes = schur_form(n, rng, clusters=clusters, spread=spread, kappa=kappa, order=order)
     if q == "identity":
-        Q = np.asfortranarray(np.eye(n))
+        Q = np.asfortranarray(np.eye(n)) if order == "F" else np.eye(n)
     elif q == "householder":
-        Q = householder_q(n, rng, reflectors)
+        Q = householder_q(n, rng, reflectors, order=order)
     else:
         raise ValueError(f"unknown Q kind {q!r}")
     sel = selection(sizes, select_frac, rng)
@@ -241,6 +253,13 @@ def serve_request(base, n: int, frac: float, seed: int, reflectors: int = 8):
     Q = householder_q(e - k, rng, reflectors)
     sel = selection(sizes[b0:b1], frac, rng)
     return S, Q, sel
+
+
+def serve_problem(n: int, frac: float, seed: int, reflectors: int = 8, order: str = "F"):
+    """One serving request: an independent form of order n from the seeded
+    generator (as reorder_problem), Q of `reflectors` reflectors."""
+    return reorder_problem(int(n), seed, select_frac=frac, q="householder",
+                           reflectors=reflectors, order=order)
 
 
 def gen_schur_pair(n: int, rng: np.random.Generator, *, frac_1x1: float = 0.6,

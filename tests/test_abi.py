@@ -37,7 +37,7 @@ def test_header_symbols_exported(lib):
 
 def test_defaults_and_strings(lib):
     o = g.default_opts()
-    assert (o.window, o.chain, o.precision, o.strong_test, o.validate, o.timing) == (128, 64, 0, 1, 1, 0)
+    assert (o.window, o.chain, o.precision, o.strong_test, o.validate, o.timing) == (128, 64, 2, 1, 1, 0)
     assert lib.gbr_version() >= 100
     for code in (0, 3, -1, -2, -3, -5, -6, -10, g.ERR_CUDA, g.ERR_NOMEM, g.ERR_TIMEOUT,
                  g.ERR_UNSUPPORTED):

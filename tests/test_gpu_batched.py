@@ -55,7 +55,7 @@ def test_batched_matches_oracle(gbr, w, m):
         check(S, Q, sel, ri, Sg, Qg, ref)
 
 
-@pytest.mark.parametrize("precision", ["dmma", "ozaki"])
+@pytest.mark.parametrize("precision", ["dmma", "ozaki", "fma"])
 def test_batched_equals_single_calls(gbr, precision):
     """Bitwise: every output element is computed by the same operations in
     the same order whatever the batch (tasks only regroup rows)."""

@@ -1,8 +1,11 @@
 """One off-diagonal update Y <- Y U on one panel (Section 3.2, the level-3
 step of a window) through gbr_update_panel, in both precisions.
 
-FP64 DMMA: against the exact product (long double accumulation) within the
-forward error bound of a w-term dot product.
+FP64 DMMA and FP64 FMA tiles: against the exact product (long double
+accumulation) within the forward error bound of a w-term dot product; the
+FMA tile also bitwise against its stated operation order (one fused
+multiply-add chain per output over k in increasing order, from +0),
+emulated with exact rationals and one correct rounding per step.
 
 Split precision (tcgen05): bitwise against an independent emulation of the
 stated digit scheme, written here from its definition with numpy integer
@@ -13,6 +16,7 @@ and against the exact product within the stated bound
 (2^-50 |y|max |u|max per term).
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -133,6 +137,45 @@ def test_dmma_panel_against_exact(gbr, rows, w, layout):
     ref = exact(Y, U)
     bound = 2 * w * EPS * (np.abs(Y) @ np.abs(U))
     assert np.all(np.abs(got - ref) <= bound + 1e-300)
+
+
+@pytest.mark.parametrize("rows,w,layout", CASES)
+def test_fma_panel_against_exact(gbr, rows, w, layout):
+    Y, U = make_case(rows, w, seed=rows * 1000 + w + 2)
+    t = to_panel(Y, layout)
+    gbr.update_panel(t, to_u(U), "fma")
+    got = t.cpu().numpy()
+    ref = exact(Y, U)
+    bound = 2 * w * EPS * (np.abs(Y) @ np.abs(U))
+    assert np.all(np.abs(got - ref) <= bound + 1e-300)
+
+
+def fma_chain(Y, U):
+    """Each output as acc = fma(y_k, u_k, acc) over k = 0..w-1 from +0, every
+    step rounded once (Python's int/int division rounds correctly)."""
+    rows, w = Y.shape
+    out = np.zeros((rows, w))
+    for r in range(rows):
+        for n in range(w):
+            acc = 0.0
+            for k in range(w):
+                if U[k, n] == 0.0 or Y[r, k] == 0.0:
+                    continue      # fma(y, 0, acc) = acc exactly (finite y, acc)
+                exact_v = Fraction(Y[r, k]) * Fraction(U[k, n]) + Fraction(acc)
+                acc = exact_v.numerator / exact_v.denominator if exact_v != 0 else 0.0
+            out[r, n] = acc
+    return out
+
+
+@pytest.mark.parametrize("rows,w,layout", [(70, 24, "col"), (33, 19, "row")])
+def test_fma_panel_bitwise_chain(gbr, rows, w, layout):
+    Y, U = make_case(rows, w, seed=rows + w)
+    t = to_panel(Y, layout)
+    gbr.update_panel(t, to_u(U), "fma")
+    got = t.cpu().numpy()
+    want = fma_chain(Y, U)
+    mism = np.argwhere(got.view(np.uint64) != want.view(np.uint64))
+    assert mism.size == 0, f"{len(mism)} outputs differ, first {mism[:3].tolist()}"
 
 
 @pytest.mark.parametrize("rows,w,layout", CASES)

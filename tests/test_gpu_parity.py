@@ -189,6 +189,50 @@ def test_rejections_clustered_nonnormal(gbr):
     assert match_eigs(got_g[:k], got_o[:k], 0) <= 1e-6
 
 
+@pytest.mark.parametrize("seed", [11, 13])
+def test_rejections_clustered_nonnormal_n1200(gbr, seed):
+    """The rejection path at n = 1200 (two more seeds of the kappa = 1e6
+    clustered law, both precisions of the updates): the oracle rejects
+    swaps here; the GPU, which retries a failed swap in double-double
+    arithmetic, may reject fewer.  Both results are valid similarities; the
+    eigenvalue order agrees with the stable partition before the first
+    stuck block in either, and the rejection counts are reported."""
+    n = 1200
+    S, Q, sel = si.reorder_problem(n, seed, select_frac=0.5, clusters=True, spread=1e-6,
+                                   kappa=1e6)
+    ref = oracle.reorder(S, Q, sel)
+    assert ref["status"] > 0
+    A = Q @ S @ Q.T
+    want, m = expected_order(S, sel)
+    got_o = ref["wr"] + 1j * ref["wi"]
+
+    def multiset_dev(S1):
+        a, b = block_eigs(S), block_eigs(S1)
+        cost = np.abs(a[:, None] - b[None, :])
+        i, j = linear_sum_assignment(cost)
+        return cost[i, j].max()
+
+    # some of these eigenvalues are nearly defective (the oracle itself
+    # moves one by 3.6e-2 on seed 11): the GPU must be as accurate as the
+    # oracle on the same input
+    dev_o = multiset_dev(ref["S"])
+    for prec in ("dmma", "ozaki"):
+        r, Sg, Qg = run_gpu(gbr, S, Q, sel, precision=prec)
+        print(f"seed {seed} {prec}: rejections oracle {ref['nrej']}, gpu {r.status}")
+        assert r.status >= 0 and r.m == m
+        assert is_standard(Sg)
+        assert residual(A, Sg, Qg) <= 50 * n * EPS
+        assert orth_err(Qg) <= 50 * n * EPS
+        assert multiset_dev(Sg) <= max(1e-3, 10 * dev_o)
+        got_g = block_eigs(Sg)
+        k = 0
+        while k < m and abs(got_o[k] - want[k]) <= 1e-6 * max(1, abs(want[k])) and \
+                abs(got_g[k] - want[k]) <= 1e-6 * max(1, abs(want[k])):
+            k += 1
+        assert k > 0
+        assert match_eigs(got_g[:k], got_o[:k], 0) <= 1e-6
+
+
 def test_invalid_input_rejected(gbr):
     S, Q, sel = si.config("n400")
     bad = S.copy(order="F")
@@ -283,8 +327,71 @@ def test_split_precision_updates(gbr, name, w, m):
     assert np.linalg.norm(Qo - Qd) <= 50 * n * EPS * np.sqrt(n)
 
 
+@pytest.mark.parametrize("name,w,m", [("n400", 128, 64), ("ragged", 64, 30), ("tiny", 16, 6)])
+def test_fma_updates(gbr, name, w, m):
+    """Off-diagonal updates in FP64 on the FMA pipe (DFMA register tiles):
+    the same parity bar as the DMMA path and close to the DMMA result."""
+    if name == "n400":
+        S, Q, sel = si.config("n400")
+    elif name == "tiny":
+        S, Q, sel = si.reorder_problem(37, 4, select_frac=0.5, q="householder", reflectors=8)
+    else:
+        S, Q, sel = si.reorder_problem(515, 6, select_frac=0.6, q="householder")
+    ref = oracle.reorder(S, Q, sel)
+    rf, Sf, Qf = run_gpu(gbr, S, Q, sel, window=w, chain=m, precision="fma")
+    assert rf.status == 0
+    check(S, Q, sel, rf, Sf, Qf, ref)
+    rd, Sd, Qd = run_gpu(gbr, S, Q, sel, window=w, chain=m, precision="dmma")
+    n = S.shape[0]
+    assert rf.stats.swaps == rd.stats.swaps
+    assert np.linalg.norm(Sf - Sd) <= 50 * n * EPS * np.linalg.norm(S)
+    assert np.linalg.norm(Qf - Qd) <= 50 * n * EPS * np.sqrt(n)
+
+
+def test_fma_n4000(gbr):
+    (S, Q, sel), ref = n4000_oracle()
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=128, chain=64, precision="fma")
+    assert r.status == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
+
+
 def test_split_precision_n4000(gbr):
     (S, Q, sel), ref = n4000_oracle()
     r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=128, chain=64, precision="ozaki")
     assert r.status == 0
     check(S, Q, sel, r, Sg, Qg, ref)
+
+
+@pytest.mark.parametrize("sched", ["sequential", "persistent"])
+def test_abort_on_first_rejection(gbr, sched):
+    """on_reject = ABORT on the clustered kappa = 1e6 input (the rejection
+    path): the oracle stops at its first rejected swap (dtrsen's info = 1);
+    the GPU stops at its first rejection too (the rejecting window finishes
+    its step, later window tasks do nothing).  The GPU's windows move their
+    blocks as a wavefront, so its first rejection can come at another swap
+    than the oracle's block-by-block order meets first: what is compared is
+    that both stop with a positive status, that both results are valid
+    similarities in standard form with the input's eigenvalues, that the
+    GPU does fewer swaps than with CONTINUE on the same input (it stopped),
+    and that the sequential schedule gives the same result twice."""
+    n = 300
+    S, Q, sel = si.reorder_problem(n, 3, select_frac=0.5, clusters=True, spread=1e-6, kappa=1e6)
+    ref = oracle.reorder(S, Q, sel, abort=True)
+    assert ref["status"] >= 1
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, sched=sched, on_reject="abort")
+    rc, _, _ = run_gpu(gbr, S, Q, sel, sched=sched)
+    print(f"ABORT: oracle {ref['nrej']} rejected / {ref['nswaps']} swaps; gpu {r.status} "
+          f"rejected / {r.stats.swaps} swaps; CONTINUE gpu {rc.status} / {rc.stats.swaps}")
+    assert r.status >= 1 and rc.status >= 1
+    assert r.stats.swaps < rc.stats.swaps
+    assert is_standard(Sg)
+    A = Q @ S @ Q.T
+    assert residual(A, Sg, Qg) <= 50 * n * EPS
+    assert orth_err(Qg) <= 50 * n * EPS
+    a, b = block_eigs(S), block_eigs(Sg)
+    cost = np.abs(a[:, None] - b[None, :])
+    i, j = linear_sum_assignment(cost)
+    assert cost[i, j].max() <= 1e-3   # attainable accuracy of these eigenvalues
+    if sched == "sequential":
+        r2, Sg2, Qg2 = run_gpu(gbr, S, Q, sel, sched=sched, on_reject="abort")
+        assert r2.status == r.status and np.array_equal(Sg2, Sg) and np.array_equal(Qg2, Qg)

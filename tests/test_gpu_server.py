@@ -38,7 +38,7 @@ def alone(g, S, Q, sel, **kw):
     return r, g.to_host(Sd), g.to_host(Qd)
 
 
-@pytest.mark.parametrize("precision", ["dmma", "ozaki"])
+@pytest.mark.parametrize("precision", ["dmma", "ozaki", "fma"])
 def test_mix_equals_alone(gbr, precision):
     probs = stream_of(30, 1, 16, 900)
     with gbr.Server(window=128, chain=64, precision=precision) as srv:

@@ -1,14 +1,21 @@
 """gbr_reorder_noalloc: the reordering entry point for callers that cannot
-allocate device memory (e.g. while a stream is being captured, or when an
-application owns all device memory).  Its scratch is a fixed device array in
-the library image.  Its results must match gbr_reorder's, call after call:
-the shared scratch keeps the previous call's contents, so a second call must
-start from a clean state.
+allocate device memory (programs whose device memory is all handed out by
+their own arena, or that must not have a cudaMalloc synchronize the device
+in the middle of their work).  Its scratch is a fixed device array in the
+library image.  Its results must match gbr_reorder's, call after call: the
+shared scratch keeps the previous call's contents, so a second call must
+start from a clean state.  And it must really allocate nothing: in a fresh
+process whose first library call is this one, the library's pool stays
+empty and the device's free memory does not change across a call.
 
 This file is collected last so that, in a run that stops at the first
 failure, every other test has already run.
 """
 import ctypes
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -72,3 +79,49 @@ def test_noalloc_rejects_oversized(g):
                                  None, None, None, None, None, None)
     assert rc == g.ERR_NOALLOC_LIMIT
     assert b"GBR_NOALLOC_MAX_N" in lib.gbr_status_string(rc)
+
+
+_FRESH = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+import paper_1905_04975_gb300 as g
+import schur_inputs as si
+lib = g.load()
+torch.cuda.set_device(0)
+S, Q, sel = si.reorder_problem(500, 5, select_frac=0.4, q="householder")
+Sd, Qd = g.to_device(S), g.to_device(Q)          # the caller's buffers
+S0, Q0 = Sd.clone(), Qd.clone()
+torch.cuda.synchronize()
+out = []
+for call in range(3):
+    Sd.copy_(S0)
+    Qd.copy_(Q0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    r = g.reorder_noalloc(Sd, Qd, sel)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    out.append([int(r.status), int(lib.gbr_pool_bytes()), int(free0), int(free1),
+                float(r.eigs[0].real)])
+print(json.dumps(out))
+"""
+
+
+def test_noalloc_allocates_nothing_in_a_fresh_process(g):
+    """A process whose first library call is gbr_reorder_noalloc: the pool
+    stays empty, and after the first call (which may load the library's
+    module, array included, into the context) the device's free memory is
+    the same before and after each call."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True,
+                       timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    calls = json.loads(p.stdout.strip().splitlines()[-1])
+    assert len(calls) == 3
+    for status, pool, free0, free1, eig0 in calls:
+        assert status == 0
+        assert pool == 0
+    for status, pool, free0, free1, eig0 in calls[1:]:
+        assert free1 == free0
+    assert calls[0][4] == calls[1][4] == calls[2][4]
