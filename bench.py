@@ -77,6 +77,7 @@ METRIC = "selected eigenvalues reordered per second"
 # capture of the current kernels (the sched_kernel captures under profiles/);
 # a workload has no entry while no capture of the current build exists.
 NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
+               ("n4000", "fma"): 1.267562e9 + 2.714466e9,
                ("n4000", "ozaki"): 3.083860e9 + 5.508523e9,
                ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
                ("g4000", "persistent-dmma"): 11.265847e9 + 13.376260e9,
