@@ -228,6 +228,10 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, unsigned (&v)[2]) {
                  : "r"(taddr)
                  : "memory");
 }
+// Prefetch of one line of global memory into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -418,6 +422,22 @@ static __device__ __noinline__ bool update_tile_tc(double* base, long long rs, l
             } else if (halves == 1) {
                 loaded = true;
                 if (tid == 0) mbar_arrive(&bar[2]);  // U stays: an empty phase for the next wait
+            }
+            // the next block's rows into L2 while this block's last epilogue runs
+            if (h == halves - 1 && pass + 1 < passes) {
+                const int q0 = p0 + (int)TC_M, qn = min((int)TC_M, rows - q0);
+                if (rs == 1) {
+                    for (int i = tid; i < w * 8; i += TILE_THREADS) {
+                        const int k = i >> 3, seg = i & 7;
+                        if (seg * 16 < qn)
+                            prefetch_l2(&base[(long long)(y0 + q0 + seg * 16) + (long long)k * ks]);
+                    }
+                } else {
+                    for (int i = tid; i < qn * 8; i += TILE_THREADS) {
+                        const int r = i >> 3, seg = i & 7;
+                        if (seg * 16 < w) prefetch_l2(&base[(long long)(y0 + q0 + r) * rs + seg * 16]);
+                    }
+                }
             }
             // 4. epilogue: each thread one row (TMEM lane), 2 columns at a time
             const int hc = (halves == 2) ? h : 0;
