@@ -306,11 +306,31 @@ __device__ __forceinline__ void write_u_slices(const double* U, int w, unsigned 
     }
 }
 
-// Dynamic shared memory needed by window_body.
+// Dynamic shared memory needed by window_body: U, the packed window, the
+// transforms and swap lists of two steps, block-start and selection flags.
 constexpr size_t kWindowSmem = sizeof(double) * ((size_t)WMAX * WMAX +
                                                  (size_t)((WMAX * (WMAX + 3)) / 2) +
-                                                 (size_t)MAXSW * 16) +
-                               sizeof(int) * 3 * MAXSW + 2 * WMAX;
+                                                 (size_t)2 * MAXSW * 16) +
+                               sizeof(int) * 2 * 3 * MAXSW + 2 * WMAX;
+
+// Row r of U, columns [j, j + K) <- (those columns) Z (the right
+// transformation of one swap, applied to U).
+template <int K>
+__device__ __forceinline__ void right_u_row(double* __restrict__ U, int w, int j, int r,
+                                            const double* __restrict__ Z) {
+    double x[K], y[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) x[i] = U[(j + i) * w + r];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc = fma(x[i], Z[c * 4 + i], acc);
+        y[c] = acc;
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) U[(j + c) * w + r] = y[c];
+}
 
 // abort_word (ABORT on rejection, else null): a window task that starts
 // after it was set does nothing (U = I, *skip_out = 1); a window task that
@@ -322,25 +342,31 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                                             unsigned char* smem_raw,
                                             unsigned char* __restrict__ uslices = nullptr,
                                             int* abort_word = nullptr, int* skip_out = nullptr) {
+    // The state of a step (its swaps, their transforms and the prefix sums
+    // of their work) is kept for two steps, by the step's parity: the part
+    // of a step's right transformations that acts on U (rows of U, which no
+    // swap reads) is applied during the next step's transform phase, by the
+    // warps that have no transform of their own to compute.
     double* U = reinterpret_cast<double*>(smem_raw);           // w*w
     double* Sp = U + WMAX * WMAX;                               // packed window
-    double* Zs = Sp + poff(WMAX);                               // MAXSW * 16
-    int* swj = reinterpret_cast<int*>(Zs + MAXSW * 16);         // per slot: start j
-    int* swk = swj + MAXSW;                                     // per slot: k (0 = rejected)
-    int* swp = swk + MAXSW;                                     // per slot: p (or stuck block)
-    uint8_t* bst = reinterpret_cast<uint8_t*>(swp + MAXSW);
+    double* Zbuf = Sp + poff(WMAX);                             // [2][MAXSW * 16]
+    int* swbuf = reinterpret_cast<int*>(Zbuf + 2 * MAXSW * 16); // [2][3][MAXSW]: j, k, p
+    uint8_t* bst = reinterpret_cast<uint8_t*>(swbuf + 2 * 3 * MAXSW);
     uint8_t* sel = bst + WMAX;
     __shared__ int nsw, nrej, nacc;
     unsigned long long wflops = 0;   // per thread (phase D), summed at the end
-    __shared__ int tcnt[3];
-    __shared__ int tlist[3][MAXSW];     // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
+    __shared__ int tcnt2[2][3];
+    __shared__ int tlist2[2][3][MAXSW];   // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
     __shared__ int kpre_l[3][MAXSW + 1];  // prefix sums of left-apply columns per k group
-    __shared__ int kpre_r[3][MAXSW + 1];  // prefix sums of right-apply rows (S rows + U rows)
+    __shared__ int kpre_s[3][MAXSW + 1];  // prefix sums of right-apply rows of S
+    __shared__ int kpre_u2[2][3][MAXSW + 1];  // prefix sums of right-apply rows of U
     // Rows [urlo[c], urhi[c]] hold every nonzero of column c of U: U starts as
     // I and a swap on columns [j, j+k) mixes only those columns, so the rows
     // outside the union of their ranges stay exactly zero and are skipped.
     __shared__ short urlo[WMAX], urhi[WMAX];
-    __shared__ short slo[MAXSW], shi[MAXSW];  // per slot: U rows its right transform touches
+    __shared__ short slo2[2][MAXSW], shi2[2][MAXSW];  // per slot: U rows its right transform touches
+    __shared__ int pu_par;    // parity of the step whose U rows are pending, or -1
+    __shared__ int pu_next;   // next pending U row item to claim
 
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
@@ -376,6 +402,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     if (tid == 0) {
         nrej = 0;
         nacc = 0;
+        pu_par = -1;
         wall_top = s0 > 0 && __ldcg(&S[cm(s0, s0 - 1, ldS)]) != 0.0;
         wall_bot = s0 + w < n && __ldcg(&S[cm(s0 + w, s0 + w - 1, ldS)]) != 0.0;
     }
@@ -383,11 +410,56 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     if (tid == 0 && wall_top) sel[0] = SEL_WALL;
     if (tid == 0 && wall_bot) sel[w - 1] = SEL_WALL;
 
+    // The U rows of the right transformations of the step of parity pp,
+    // claimed by whole warps in chunks of 32 (pu_next): each item is one row
+    // of U for one swap, the swaps' items grouped by k and counted by the
+    // prefix sums kpre_u2[pp].
+    auto pending_u = [&](int pp) {
+        const int* pj = swbuf + pp * 3 * MAXSW;
+        const int* pk = pj + MAXSW;
+        const int T0 = kpre_u2[pp][0][tcnt2[pp][0]], T1 = kpre_u2[pp][1][tcnt2[pp][1]];
+        const int total = T0 + T1 + kpre_u2[pp][2][tcnt2[pp][2]];
+        for (;;) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&pu_next, 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= total) break;
+            const int it = base + lane;
+            if (it >= total) continue;
+            const int g = it < T0 ? 0 : (it < T0 + T1 ? 1 : 2);
+            const int itg = it - (g == 0 ? 0 : (g == 1 ? T0 : T0 + T1));
+            const int* pre = kpre_u2[pp][g];
+            int lo = 0, hi = tcnt2[pp][g] - 1;   // last i with pre[i] <= itg
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (pre[mid] <= itg) lo = mid; else hi = mid - 1;
+            }
+            const int slot = tlist2[pp][g][lo];
+            if (pk[slot] == 0) continue;  // rejected
+            const int j = pj[slot];
+            const int r = slo2[pp][slot] + (itg - pre[lo]);
+            const double* Z = Zbuf + pp * MAXSW * 16 + slot * 16;
+            if (g == 0) right_u_row<2>(U, w, j, r, Z);
+            else if (g == 1) right_u_row<3>(U, w, j, r, Z);
+            else right_u_row<4>(U, w, j, r, Z);
+        }
+    };
+
     // Every accepted swap moves a selected block up and every rejected one
     // retires a block, so the loop ends within w * w steps; the cap only
     // guards against a logic error (reported through the counters).
     bool final_pass = false;
     for (int iter = 0;; ++iter) {
+        const int par = iter & 1;
+        double* Zs = Zbuf + par * MAXSW * 16;
+        int* swj = swbuf + par * 3 * MAXSW;
+        int* swk = swj + MAXSW;
+        int* swp = swk + MAXSW;
+        int (*tlist)[MAXSW] = tlist2[par];
+        int* tcnt = tcnt2[par];
+        short* slo = slo2[par];
+        short* shi = shi2[par];
+        int (*kpre_u)[MAXSW + 1] = kpre_u2[par];
         __syncthreads();
         if (abort_word && !final_pass && nrej > 0) {
             // ABORT: the first rejection stops the reordering; this window
@@ -437,6 +509,12 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
         __syncthreads();
         const int ns = nsw;
         if (ns == 0) {
+            // the previous step's U rows now, before its state is reused
+            if (pu_par >= 0) {
+                pending_u(pu_par);
+                __syncthreads();
+                if (tid == 0) pu_par = -1;
+            }
             if (final_pass) break;
             final_pass = true;
             continue;
@@ -552,10 +630,10 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
             // applied.  k comes from the group (A2 zeroes swk of a rejection).
             if (ty == T_11 && rank >= 1) {
                 const int g = rank - 1, k = g + 2, cnt = tcnt[g];
-                int runl = 0, runr = 0;
+                int runl = 0, runr = 0, runu = 0;
                 for (int base = 0; base < cnt; base += 32) {
                     int i = base + lane;
-                    int nl = 0, nr = 0;
+                    int nl = 0, nr = 0, nu = 0;
                     if (i < cnt) {
                         const int slot = tlist[g][i], j = swj[slot];
                         int lo = urlo[j], hi = urhi[j];
@@ -566,23 +644,36 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                         slo[slot] = (short)lo;
                         shi[slot] = (short)hi;
                         nl = w - j - k;
-                        nr = j + (hi - lo + 1);
+                        nr = j;
+                        nu = hi - lo + 1;
                     }
-                    int il = nl, ir = nr;
+                    int il = nl, ir = nr, iu = nu;
                     for (int o = 1; o < 32; o <<= 1) {
                         int a = __shfl_up_sync(0xffffffffu, il, o);
                         int b2 = __shfl_up_sync(0xffffffffu, ir, o);
-                        if (lane >= o) { il += a; ir += b2; }
+                        int c2 = __shfl_up_sync(0xffffffffu, iu, o);
+                        if (lane >= o) { il += a; ir += b2; iu += c2; }
                     }
-                    if (i < cnt) { kpre_l[g][i + 1] = runl + il; kpre_r[g][i + 1] = runr + ir; }
+                    if (i < cnt) {
+                        kpre_l[g][i + 1] = runl + il;
+                        kpre_s[g][i + 1] = runr + ir;
+                        kpre_u[g][i + 1] = runu + iu;
+                    }
                     runl += __shfl_sync(0xffffffffu, il, 31);
                     runr += __shfl_sync(0xffffffffu, ir, 31);
+                    runu += __shfl_sync(0xffffffffu, iu, 31);
                 }
                 if (lane == 0) {
                     kpre_l[g][0] = 0;
-                    kpre_r[g][0] = 0;
+                    kpre_s[g][0] = 0;
+                    kpre_u[g][0] = 0;
                 }
             }
+            // the previous step's U rows, by each warp once its own
+            // transforms are done; while 2|2 swaps are computed (on
+            // sub-partitions 0 and 1) only the warps of sub-partitions 2 and
+            // 3 take them, so that those latency chains keep their FP64 pipes
+            if (pu_par >= 0 && ((warp & 3) >= 2 || tcnt[T_22] == 0)) pending_u(pu_par);
         }
         __syncthreads();
         // --- phase B: left transformations, rows [j, j+k) x columns [j+k, w),
@@ -617,26 +708,24 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
         }
         __syncthreads();
         // --- phase C: right transformations, columns [j, j+k) of S rows [0, j)
-        // and of U rows [0, w)
+        // (their rows of U follow during the next step's transforms)
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = tcnt[g], total = kpre_r[g][cnt];
+            const int k = g + 2, cnt = tcnt[g], total = kpre_s[g][cnt];
             for (int it = tid; it < total; it += nth) {
                 int lo = 0, hi = cnt - 1;
                 while (lo < hi) {
                     int mid = (lo + hi + 1) >> 1;
-                    if (kpre_r[g][mid] <= it) lo = mid; else hi = mid - 1;
+                    if (kpre_s[g][mid] <= it) lo = mid; else hi = mid - 1;
                 }
                 const int slot = tlist[g][lo];
                 if (swk[slot] == 0) continue;  // rejected
                 const int j = swj[slot];
-                const int rr = it - kpre_r[g][lo];
+                const int r = it - kpre_s[g][lo];
                 const double* Z = &Zs[slot * 16];
                 double x[4], y[4];
-                const bool inS = rr < j;
-                const int r = inS ? rr : rr - j + slo[slot];
 #pragma unroll
-                for (int i = 0; i < k; ++i) x[i] = inS ? Sp[poff(j + i) + r] : U[(j + i) * w + r];
+                for (int i = 0; i < k; ++i) x[i] = Sp[poff(j + i) + r];
 #pragma unroll
                 for (int c = 0; c < k; ++c) {
                     double acc = 0.0;
@@ -644,16 +733,16 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
                     for (int i = 0; i < k; ++i) acc = fma(x[i], Z[c * 4 + i], acc);
                     y[c] = acc;
                 }
-                if (inS) {
 #pragma unroll
-                    for (int c = 0; c < k; ++c) Sp[poff(j + c) + r] = y[c];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < k; ++c) U[(j + c) * w + r] = y[c];
-                }
+                for (int c = 0; c < k; ++c) Sp[poff(j + c) + r] = y[c];
             }
         }
         __syncthreads();
+        // this step's U rows are pending now
+        if (tid == 0) {
+            pu_par = par;
+            pu_next = 0;
+        }
         // --- phase D: move the selection flags with the blocks; widen the U
         // row ranges of the columns each accepted transform mixed
         for (int sw = tid; sw < ns; sw += nth) {
@@ -679,6 +768,9 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
         for (int t = tid; t + 1 < w; t += nth)
             if (sel[t] == SEL_STUCK && Sp[poff(t) + t + 1] != 0.0) sel[t + 1] = SEL_STUCK;
     }
+    // the last step's U rows
+    __syncthreads();
+    if (pu_par >= 0) pending_u(pu_par);
     __shared__ unsigned long long wfl_sum;
     if (tid == 0) wfl_sum = 0;
     __syncthreads();
