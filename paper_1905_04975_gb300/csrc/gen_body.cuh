@@ -45,8 +45,8 @@ __host__ __device__ constexpr int gpoff(int c) { return (c * (c + 3)) / 2; }
 // slot (gen_swap_octet: its Qs and Zs stay there for the updates).
 constexpr int GSLOT = 128;
 constexpr size_t kGenWindowSmem =
-    sizeof(double) * (2 * (size_t)GW * GW + 2 * (size_t)gpoff(GW) + (size_t)GMAXSW * GSLOT) +
-    sizeof(int) * 3 * GMAXSW + 2 * GW;
+    sizeof(double) * (2 * (size_t)GW * GW + 2 * (size_t)gpoff(GW) + 2 * (size_t)GMAXSW * GSLOT) +
+    sizeof(int) * 2 * 3 * GMAXSW + 2 * GW;
 
 // |x| order through the bit pattern: for non-negative doubles the integer
 // order of the bits is the numeric order (integer compares, no FP64 issue).
@@ -490,13 +490,12 @@ __device__ __forceinline__ void apply_left(int first, int stride, int total, int
     }
 }
 
-// Right items of group k: rows [0, j) of S and T, then rows [lo, hi] of UQ
-// and UZ, for the columns [j, j+k) of swap list[i].
+// Right items of group k: rows [0, j) of S and T for the columns [j, j+k)
+// of swap list[i].
 template <int K>
 __device__ __forceinline__ void apply_right(int first, int stride, int total, int cnt, const int* pre,
-                                            const int* list, const int* swj, const short* slo,
-                                            const double* SCR, double* Sp, double* Tp, double* UQ,
-                                            double* UZ, int w) {
+                                            const int* list, const int* swj, const double* SCR,
+                                            double* Sp, double* Tp) {
     for (int it = first; it < total; it += stride) {
         int lo = 0, hi = cnt - 1;
         while (lo < hi) {
@@ -505,45 +504,49 @@ __device__ __forceinline__ void apply_right(int first, int stride, int total, in
         }
         const int slot = list[lo], j = swj[slot];
         const int rr = it - pre[lo];
-        const double* Qs = SCR + slot * GSLOT + SC_Q;
         const double* Zs = SCR + slot * GSLOT + SC_Z;
         double x1[K], x2[K];
-        if (rr < j) {
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                x1[i] = Sp[gpoff(j + i) + rr];
-                x2[i] = Tp[gpoff(j + i) + rr];
-            }
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                double a1 = 0.0, a2 = 0.0;
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    a1 = fma(x1[i], Zs[c * 4 + i], a1);
-                    a2 = fma(x2[i], Zs[c * 4 + i], a2);
-                }
-                Sp[gpoff(j + c) + rr] = a1;
-                Tp[gpoff(j + c) + rr] = a2;
-            }
-        } else {
-            const int r = rr - j + slo[slot];
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                x1[i] = UQ[(j + i) * w + r];
-                x2[i] = UZ[(j + i) * w + r];
-            }
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                double a1 = 0.0, a2 = 0.0;
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    a1 = fma(x1[i], Qs[c * 4 + i], a1);
-                    a2 = fma(x2[i], Zs[c * 4 + i], a2);
-                }
-                UQ[(j + c) * w + r] = a1;
-                UZ[(j + c) * w + r] = a2;
-            }
+        for (int i = 0; i < K; ++i) {
+            x1[i] = Sp[gpoff(j + i) + rr];
+            x2[i] = Tp[gpoff(j + i) + rr];
         }
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                a1 = fma(x1[i], Zs[c * 4 + i], a1);
+                a2 = fma(x2[i], Zs[c * 4 + i], a2);
+            }
+            Sp[gpoff(j + c) + rr] = a1;
+            Tp[gpoff(j + c) + rr] = a2;
+        }
+    }
+}
+
+// Row r of UQ and UZ, columns [j, j + K) <- (those columns) Qs and Zs (the
+// right transformations of one swap, applied to the accumulators).
+template <int K>
+__device__ __forceinline__ void right_uqz_row(double* __restrict__ UQ, double* __restrict__ UZ,
+                                              int w, int j, int r, const double* __restrict__ Qs,
+                                              const double* __restrict__ Zs) {
+    double x1[K], x2[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        x1[i] = UQ[(j + i) * w + r];
+        x2[i] = UZ[(j + i) * w + r];
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        double a1 = 0.0, a2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            a1 = fma(x1[i], Qs[c * 4 + i], a1);
+            a2 = fma(x2[i], Zs[c * 4 + i], a2);
+        }
+        UQ[(j + c) * w + r] = a1;
+        UZ[(j + c) * w + r] = a2;
     }
 }
 
@@ -561,20 +564,58 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
     double* UZ = UQ + GW * GW;                            // GW * GW
     double* Sp = UZ + GW * GW;                            // packed window of S
     double* Tp = Sp + gpoff(GW);                          // packed window of T
-    double* SCR = Tp + gpoff(GW);                         // per slot: gen_swap_octet scratch
-    int* swj = reinterpret_cast<int*>(SCR + GMAXSW * GSLOT);  // per slot: first row
-    int* swk = swj + GMAXSW;                              // k, 0 = rejected
-    int* swp = swk + GMAXSW;                              // p, or the stuck block's row
-    uint8_t* bst = reinterpret_cast<uint8_t*>(swp + GMAXSW);
+    // The state of a step (swaps, their scratch with Qs and Zs, item prefix
+    // sums) is kept for two steps, by the step's parity: the rows of UQ and
+    // UZ of a step's right transformations (read by no later swap) are
+    // applied during the next step's swap transforms, by warps whose
+    // sub-partition carries no k = 3 or 4 pair swap.
+    double* SCRbuf = Tp + gpoff(GW);                      // [2][GMAXSW * GSLOT]
+    int* swbuf = reinterpret_cast<int*>(SCRbuf + 2 * GMAXSW * GSLOT);  // [2][3][GMAXSW]
+    uint8_t* bst = reinterpret_cast<uint8_t*>(swbuf + 2 * 3 * GMAXSW);
     uint8_t* sel = bst + GW;
     __shared__ int nsw, nrej, nacc;
     __shared__ int wall_top, wall_bot;
-    __shared__ int gcnt[3], glist[3][GMAXSW];   // slots per block-size sum k = 2, 3, 4
-    __shared__ int gpl[3][GMAXSW + 1], gpr[3][GMAXSW + 1];  // item prefix sums per group
+    __shared__ int gcnt2[2][3], glist2[2][3][GMAXSW];   // slots per block-size sum k = 2, 3, 4
+    __shared__ int gpl[3][GMAXSW + 1], gps[3][GMAXSW + 1];  // left / right S, T item prefix sums
+    __shared__ int gpu2[2][3][GMAXSW + 1];      // right UQ, UZ item prefix sums
     __shared__ short urlo[GW], urhi[GW];        // nonzero rows of each column of UQ, UZ
-    __shared__ short slo[GMAXSW], shi[GMAXSW];  // per slot: rows of UQ, UZ it updates
+    __shared__ short slo2[2][GMAXSW], shi2[2][GMAXSW];  // per slot: rows of UQ, UZ it updates
+    __shared__ int pu_par, pu_next;             // step whose UQ, UZ rows are pending (-1: none)
     unsigned long long wflops = 0;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane_ = tid & 31;
+    // the UQ, UZ rows of the step of parity pp, claimed by whole warps in
+    // chunks of 32 (pu_next)
+    auto pending_uqz = [&](int pp) {
+        const int* pj = swbuf + pp * 3 * GMAXSW;
+        const int* pk = pj + GMAXSW;
+        const int T0 = gpu2[pp][0][gcnt2[pp][0]], T1 = gpu2[pp][1][gcnt2[pp][1]];
+        const int total = T0 + T1 + gpu2[pp][2][gcnt2[pp][2]];
+        for (;;) {
+            int base = 0;
+            if (lane_ == 0) base = atomicAdd(&pu_next, 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= total) break;
+            const int it = base + lane_;
+            if (it >= total) continue;
+            const int g = it < T0 ? 0 : (it < T0 + T1 ? 1 : 2);
+            const int itg = it - (g == 0 ? 0 : (g == 1 ? T0 : T0 + T1));
+            const int* pre = gpu2[pp][g];
+            int lo = 0, hi = gcnt2[pp][g] - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (pre[mid] <= itg) lo = mid; else hi = mid - 1;
+            }
+            const int slot = glist2[pp][g][lo];
+            if (pk[slot] == 0) continue;  // rejected
+            const int j = pj[slot];
+            const int r = slo2[pp][slot] + (itg - pre[lo]);
+            const double* sc = SCRbuf + (size_t)pp * GMAXSW * GSLOT + slot * GSLOT;
+            if (g == 0) right_uqz_row<2>(UQ, UZ, w, j, r, sc + SC_Q, sc + SC_Z);
+            else if (g == 1) right_uqz_row<3>(UQ, UZ, w, j, r, sc + SC_Q, sc + SC_Z);
+            else right_uqz_row<4>(UQ, UZ, w, j, r, sc + SC_Q, sc + SC_Z);
+        }
+    };
 
     for (int c = 0; c < w; ++c) {
         const int rows = min(c + 2, w);
@@ -596,6 +637,7 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
     if (tid == 0) {
         nrej = 0;
         nacc = 0;
+        pu_par = -1;
         wall_top = s0 > 0 && __ldcg(&S[cm(s0, s0 - 1, ldS)]) != 0.0;
         wall_bot = s0 + w < n && __ldcg(&S[cm(s0 + w, s0 + w - 1, ldS)]) != 0.0;
     }
@@ -607,6 +649,16 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
     // retires a block, so the loop ends within w * w steps; the cap only
     // guards against a logic error (reported through the counters)
     for (int iter = 0;; ++iter) {
+        const int par = iter & 1;
+        double* SCR = SCRbuf + (size_t)par * GMAXSW * GSLOT;
+        int* swj = swbuf + par * 3 * GMAXSW;
+        int* swk = swj + GMAXSW;
+        int* swp = swk + GMAXSW;
+        int* gcnt = gcnt2[par];
+        int (*glist)[GMAXSW] = glist2[par];
+        int (*gpu)[GMAXSW + 1] = gpu2[par];
+        short* slo = slo2[par];
+        short* shi = shi2[par];
         __syncthreads();
         if (iter > 4 * GW * GW) {
             if (tid == 0) atomicAdd(&ctr->step_overflow, 1);
@@ -631,7 +683,7 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
         }
         __syncthreads();
         const int ns = nsw;
-        if (ns == 0) break;
+        if (ns == 0) break;  // the pending rows are applied after the loop
         // One octet (8 lanes) per swap, the four octets of a warp on swaps of
         // the same sizes (k = 4 first, then 3, then 2), so that they follow
         // one instruction stream with the same trip counts.  At most 32
@@ -664,8 +716,13 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
                     atomicAdd(&nrej, 1);
                 }
             }
+            // the previous step's UQ, UZ rows, by the warps of the
+            // sub-partitions that carry no k = 3 or 4 swap chain
+            if (pu_par >= 0 && (warp & 3) >= min(nw4 + nw3, 4)) pending_uqz(pu_par);
         }
         __syncthreads();
+        // what is left of them (UQ, UZ only: no conflict with the steps below)
+        if (pu_par >= 0) pending_uqz(pu_par);
         // Work lists of the updates, per block-size sum k (so that a warp
         // applies one k): prefix sums of the left items (columns [j+k, w) of
         // rows [j, j+k) of S and T) and of the right items (rows [0, j) of
@@ -677,7 +734,7 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             const int lane = tid & 31, warp = tid >> 5;
             if (warp < 3) {
                 const int g = warp, k = g + 2, cnt = gcnt[g];
-                int il = 0, ir = 0;
+                int il = 0, ir = 0, iu = 0;
                 if (lane < cnt) {
                     const int slot = glist[g][lane], j = swj[slot];
                     if (swk[slot] != 0) {
@@ -689,17 +746,19 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
                         slo[slot] = (short)lo;
                         shi[slot] = (short)hi;
                         il = w - j - k;
-                        ir = j + (hi - lo + 1);
+                        ir = j;
+                        iu = hi - lo + 1;
                     }
                 }
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int a2 = __shfl_up_sync(0xffffffffu, il, o);
                     const int b2 = __shfl_up_sync(0xffffffffu, ir, o);
-                    if (lane >= o) { il += a2; ir += b2; }
+                    const int c2 = __shfl_up_sync(0xffffffffu, iu, o);
+                    if (lane >= o) { il += a2; ir += b2; iu += c2; }
                 }
-                if (lane < cnt) { gpl[g][lane + 1] = il; gpr[g][lane + 1] = ir; }
-                if (lane == 0) { gpl[g][0] = 0; gpr[g][0] = 0; }
+                if (lane < cnt) { gpl[g][lane + 1] = il; gps[g][lane + 1] = ir; gpu[g][lane + 1] = iu; }
+                if (lane == 0) { gpl[g][0] = 0; gps[g][0] = 0; gpu[g][0] = 0; }
             }
         }
         __syncthreads();
@@ -715,7 +774,7 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
 #pragma unroll
             for (int g = 0; g < 3; ++g) {
                 tl[g] = gcnt[g] ? gpl[g][gcnt[g]] : 0;
-                tr[g] = gcnt[g] ? gpr[g][gcnt[g]] : 0;
+                tr[g] = gcnt[g] ? gps[g][gcnt[g]] : 0;
             }
             split_warps(tl, nwarps, bl);
             split_warps(tr, nwarps, br);
@@ -731,14 +790,19 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
             if (warp < br[3]) {
                 const int first = (warp - br[gR]) * 32 + lane, stride = (br[gR + 1] - br[gR]) * 32;
                 if (gR == 0)
-                    apply_right<2>(first, stride, tr[0], gcnt[0], gpr[0], glist[0], swj, slo, SCR, Sp, Tp, UQ, UZ, w);
+                    apply_right<2>(first, stride, tr[0], gcnt[0], gps[0], glist[0], swj, SCR, Sp, Tp);
                 else if (gR == 1)
-                    apply_right<3>(first, stride, tr[1], gcnt[1], gpr[1], glist[1], swj, slo, SCR, Sp, Tp, UQ, UZ, w);
+                    apply_right<3>(first, stride, tr[1], gcnt[1], gps[1], glist[1], swj, SCR, Sp, Tp);
                 else
-                    apply_right<4>(first, stride, tr[2], gcnt[2], gpr[2], glist[2], swj, slo, SCR, Sp, Tp, UQ, UZ, w);
+                    apply_right<4>(first, stride, tr[2], gcnt[2], gps[2], glist[2], swj, SCR, Sp, Tp);
             }
         }
         __syncthreads();
+        // this step's UQ, UZ rows are pending now
+        if (tid == 0) {
+            pu_par = par;
+            pu_next = 0;
+        }
         // move the selection flags with the blocks
         for (int sw = tid; sw < ns; sw += nth) {
             const int j = swj[sw], k = swk[sw];
@@ -762,6 +826,9 @@ __device__ __forceinline__ void window_gen_body(int n, double* __restrict__ S, i
         for (int t = tid; t + 1 < w; t += nth)
             if (sel[t] == SEL_STUCK && Sp[gpoff(t) + t + 1] != 0.0) sel[t + 1] = SEL_STUCK;
     }
+    // the last step's UQ, UZ rows
+    __syncthreads();
+    if (pu_par >= 0) pending_uqz(pu_par);
     __syncthreads();
     for (int c = 0; c < w; ++c) {
         const int rows = min(c + 2, w);
