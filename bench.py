@@ -1441,19 +1441,27 @@ def measure_reorder(args, g, torch, dist, wl, prec, S_np, Q_np, sel, S, Q, S0, Q
         Qp = torch.empty((n, n), dtype=torch.float64).pin_memory()
         Sh = Sp.numpy().T  # Fortran-ordered view of the pinned buffer
         Qh = Qp.numpy().T
-        et = []
-        for i in range(args.e2e_steps + 1):
-            Sh[:] = S_np
-            Qh[:] = Q_np
-            t0 = time.perf_counter()
-            r = g.reorder_host(Sh, Qh, sel, opts=opts, stream=stream)
-            dt = time.perf_counter() - t0
-            assert r.status == 0, r.status
-            if i > 0:
-                et.append(dt)
+        et, ek, ec, el = [], [], [], []
+        with ClockSampler(local) as eclk:
+            for i in range(args.e2e_steps + 1):
+                Sh[:] = S_np
+                Qh[:] = Q_np
+                t0 = time.perf_counter()
+                r = g.reorder_host(Sh, Qh, sel, opts=opts, stream=stream)
+                dt = time.perf_counter() - t0
+                assert r.status == 0, r.status
+                if i > 0:
+                    et.append(dt)
+                    ek.append(r.stats.ms_sched if r.stats.ms_sched > 0
+                              else r.stats.ms_window + r.stats.ms_update)
+                    ec.append(r.stats.ms_h2d + r.stats.ms_d2h)
+                    el.append(r.stats.ms_total)
         world = dist.get_world_size() if dist else 1
         e2e = {"value": nsel * len(et) / sum(et) * world, "unit": "eigs/s",
                "steps": len(et), "ms_per_step": 1e3 * sum(et) / len(et),
+               "step_ms": [round(1e3 * x, 2) for x in et],
+               "kernel_ms": [round(x, 2) for x in ek], "copy_ms": [round(x, 2) for x in ec],
+               "library_ms": [round(x, 2) for x in el], "clocks": eclk.summary(),
                "h2d_bytes_per_step": 2 * n * n * 8 + 4 * n,
                "d2h_bytes_per_step": 2 * n * n * 8 + 2 * 8 * n}
         del Sp, Qp

@@ -136,9 +136,12 @@ typedef struct gbr_stats {
     double sched_sim_ms;  /* makespan of the scheduler's list-scheduling model   */
     double ms_graph;      /* host time building the task graph                   */
     double ms_order;      /* host time computing the queue order                 */
-    double upd_flops_issued; /* flops the DMMA update tiles issued: upd_flops less
-                             the products with the all-zero rows of U each warp
-                             skips (0 for split precision)                        */
+    double upd_flops_issued; /* flops the FP64 update tiles (FMA or DMMA) issued:
+                             upd_flops less the products with the all-zero rows
+                             of U each warp skips (0 for split precision)         */
+    double ms_h2d;        /* host-buffer entry points with opts.timing: time of the
+                             host-to-device copies of the call (CUDA events)     */
+    double ms_d2h;        /* the same for the device-to-host copies              */
 } gbr_stats;
 
 /* Fill *opts with the defaults. */

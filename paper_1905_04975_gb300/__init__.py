@@ -58,7 +58,8 @@ class GbrStats(ctypes.Structure):
                 ("win_flops", ctypes.c_double), ("tasks", ctypes.c_longlong),
                 ("sched_cp_ms", ctypes.c_double), ("sched_sim_ms", ctypes.c_double),
                 ("ms_graph", ctypes.c_double), ("ms_order", ctypes.c_double),
-                ("upd_flops_issued", ctypes.c_double)]
+                ("upd_flops_issued", ctypes.c_double), ("ms_h2d", ctypes.c_double),
+                ("ms_d2h", ctypes.c_double)]
 
 
 class GbrServerCfg(ctypes.Structure):

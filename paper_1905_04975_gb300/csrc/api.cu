@@ -405,19 +405,25 @@ int gbr_reorder_host(int n, double* S, int ldS, double* Q, int ldQ, const int* s
         rc = pool_get(POOL_HOST_Q, mat, &dQ);
         if (rc) return rc;
     }
+    CopyTimer ct(o.timing != 0 && stats != nullptr);
+    ct.mark(0, st);
     GBR_CK(cudaMemcpy2DAsync(dS, n * sizeof(double), S, (size_t)ldS * sizeof(double),
                              n * sizeof(double), n, cudaMemcpyHostToDevice, st), "H2D S");
     if (Q)
         GBR_CK(cudaMemcpy2DAsync(dQ, n * sizeof(double), Q, (size_t)ldQ * sizeof(double),
                                  n * sizeof(double), n, cudaMemcpyHostToDevice, st), "H2D Q");
+    ct.mark(1, st);
     rc = reorder_device(n, (double*)dS, n, (double*)dQ, n, select, eig_re, eig_im, m_out, o, stats, st);
     if (rc < 0) return rc;
+    ct.mark(2, st);
     GBR_CK(cudaMemcpy2DAsync(S, (size_t)ldS * sizeof(double), dS, n * sizeof(double),
                              n * sizeof(double), n, cudaMemcpyDeviceToHost, st), "D2H S");
     if (Q)
         GBR_CK(cudaMemcpy2DAsync(Q, (size_t)ldQ * sizeof(double), dQ, n * sizeof(double),
                                  n * sizeof(double), n, cudaMemcpyDeviceToHost, st), "D2H Q");
+    ct.mark(3, st);
     GBR_CK(cudaStreamSynchronize(st), "sync");
+    ct.report(stats);
     if (stats)
         stats->ms_total =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -487,6 +487,8 @@ int gbr_reorder_gen_host(int n, double* S, int ldS, double* T, int ldT, double* 
     const int lds[4] = {ldS, ldT, ldQ, ldZ};
     double* dv[4] = {nullptr, nullptr, nullptr, nullptr};
     int used = 0;
+    CopyTimer ct(o.timing != 0 && stats != nullptr);
+    ct.mark(0, st);
     for (int i = 0; i < 4; ++i) {
         if (!hs[i]) continue;
         dv[i] = d + (size_t)used * n * n;
@@ -494,15 +496,19 @@ int gbr_reorder_gen_host(int n, double* S, int ldS, double* T, int ldT, double* 
         GBR_CK(cudaMemcpy2DAsync(dv[i], n * sizeof(double), hs[i], (size_t)lds[i] * sizeof(double),
                                  n * sizeof(double), n, cudaMemcpyHostToDevice, st), "H2D pair");
     }
+    ct.mark(1, st);
     rc = reorder_gen_device(n, dv[0], n, dv[1], n, dv[2], n, dv[3], n, select, eig_re, eig_im, m_out,
                             o, stats, st);
     if (rc < 0) return rc;
+    ct.mark(2, st);
     for (int i = 0; i < 4; ++i) {
         if (!hs[i]) continue;
         GBR_CK(cudaMemcpy2DAsync(hs[i], (size_t)lds[i] * sizeof(double), dv[i], n * sizeof(double),
                                  n * sizeof(double), n, cudaMemcpyDeviceToHost, st), "D2H pair");
     }
+    ct.mark(3, st);
     GBR_CK(cudaStreamSynchronize(st), "sync");
+    ct.report(stats);
     if (stats)
         stats->ms_total =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

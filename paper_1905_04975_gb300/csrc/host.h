@@ -35,6 +35,33 @@ constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_
 int pool_get(int slot, size_t bytes, void** out);
 std::mutex& api_mutex();
 
+// CUDA events around the copies of the host-buffer entry points when
+// opts.timing is set: [0, 1] bracket the host-to-device copies, [2, 3] the
+// device-to-host copies.  report() runs after the stream has synchronized.
+struct CopyTimer {
+    cudaEvent_t ev[4] = {};
+    bool on = false;
+    explicit CopyTimer(bool timing) : on(timing) {
+        for (int i = 0; on && i < 4; ++i)
+            if (cudaEventCreate(&ev[i]) != cudaSuccess) on = false;
+    }
+    ~CopyTimer() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    CopyTimer(const CopyTimer&) = delete;
+    CopyTimer& operator=(const CopyTimer&) = delete;
+    void mark(int i, cudaStream_t st) {
+        if (on && cudaEventRecord(ev[i], st) != cudaSuccess) on = false;
+    }
+    void report(gbr_stats* s) const {
+        if (!on || !s) return;
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess) s->ms_h2d = a;
+        if (cudaEventElapsedTime(&b, ev[2], ev[3]) == cudaSuccess) s->ms_d2h = b;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Planner (Section 3.2: windows and chains)
 // ---------------------------------------------------------------------------

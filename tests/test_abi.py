@@ -237,3 +237,36 @@ def test_server_argument_checks(lib):
     assert lib.gbr_server_wait(None, 0, None, None, 0) == -1
     assert lib.gbr_server_get_stats(None, None) == -1
     lib.gbr_server_destroy(None)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every public struct has the same size and field offsets in the C
+    header (compiled with gcc) as in the Python binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"gbr_opts": g.GbrOpts, "gbr_stats": g.GbrStats, "gbr_ev_stats": g.GbrEvStats,
+               "gbr_server_cfg": g.GbrServerCfg, "gbr_server_stats": g.GbrServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gbreorder.h"',
+             'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = {}
+    for ln in out.splitlines():
+        cname, key, val = ln.split()
+        seen[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert seen[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert seen[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
