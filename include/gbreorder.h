@@ -82,7 +82,14 @@ extern "C" {
 
 /* Options; gbr_default_opts() fills the defaults shown. */
 typedef struct gbr_opts {
-    int window;        /* diagonal window size w, 4..128        (default 128);
+    int window;        /* diagonal window size w, 4..256        (default 128);
+                          above 128 (the window of S and its U no longer fit
+                          in one SM's shared memory: the window task keeps
+                          them in L1/L2-resident global memory) only with the
+                          persistent schedule and FP64 updates (FMA or DMMA),
+                          else GBR_ERR_UNSUPPORTED; gbr_reorder,
+                          gbr_reorder_host and gbr_plan only (the other
+                          entry points take 4..128).
                           GBR_AUTO in batched calls: chosen per instance by
                           the autotuner (gbr_autotune)                        */
     int chain;         /* selected eigenvalues per chain m, 1..w-2 (default 64);
@@ -271,9 +278,9 @@ int gbr_reorder_gen_host(int n, double *S, int ldS, double *T, int ldT, double *
  * GBR_ERR_NOALLOC_LIMIT when n > GBR_NOALLOC_MAX_N (checked before anything
  * else is touched).  The call never calls cudaMalloc, cudaFree or any other
  * allocating routine, and creates no CUDA events (opts->timing is ignored).
- * It runs the window/update launch pairs with FP64 DMMA updates
- * (opts->sched and opts->precision other than DMMA are not used:
- * GBR_ERR_UNSUPPORTED for split precision).  Like gbr_reorder it
+ * It runs the window/update launch pairs (opts->sched is not used) with
+ * FP64 updates, FMA or DMMA tiles as opts->precision says
+ * (GBR_ERR_UNSUPPORTED for split precision and for windows above 128).  Like gbr_reorder it
  * synchronizes cuda_stream during the call (the planner reads the block
  * structure and the rejection counters back to the host between passes) and
  * returns after the stream work has completed.

@@ -139,7 +139,7 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
 // Reorder on device-resident S, Q.
 // ---------------------------------------------------------------------------
 static int check_opts(const gbr_opts* o) {
-    if (o->window < 4 || o->window > WMAX) return -10;
+    if (o->window < 4 || o->window > WMAX_WIDE) return -10;
     if (o->chain < 1 || o->chain > o->window - 2) return -10;
     if (o->precision != GBR_PREC_DMMA && o->precision != GBR_PREC_OZAKI &&
         o->precision != GBR_PREC_FMA)
@@ -151,6 +151,9 @@ static int check_opts(const gbr_opts* o) {
         return GBR_ERR_UNSUPPORTED;
     if (o->sched != GBR_SCHED_PERSISTENT && o->sched != GBR_SCHED_SEQUENTIAL) return -10;
     if (o->wait_limit_ms < 0) return -10;
+    // windows wider than WMAX: the persistent schedule with FP64 updates
+    if (o->window > WMAX && (o->sched != GBR_SCHED_PERSISTENT || o->precision == GBR_PREC_OZAKI))
+        return GBR_ERR_UNSUPPORTED;
     return 0;
 }
 
@@ -434,7 +437,7 @@ int gbr_plan(int n, const unsigned char* sub, const int* select, int window, int
              int with_q, int* windows, int max_windows, int* chains, double* upd_flops) {
     if (n < 0) return -1;
     if (n > 0 && (!sub || !select)) return -2;
-    if (window < 4 || window > WMAX) return -4;
+    if (window < 4 || window > WMAX_WIDE) return -4;
     if (chain < 1 || chain > window - 2) return -5;
     std::vector<uint8_t> sb(n), sl(n);
     for (int p = 0; p < n;) {
@@ -509,7 +512,7 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
     if (rc) return rc;
     o.timing = 0;  // event timing would create events; this path creates nothing
     o.sched = GBR_SCHED_SEQUENTIAL;  // the persistent schedule needs scratch sized per plan
-    if (o.precision == GBR_PREC_OZAKI) return GBR_ERR_UNSUPPORTED;
+    if (o.precision == GBR_PREC_OZAKI || o.window > WMAX) return GBR_ERR_UNSUPPORTED;
     if (stats) memset(stats, 0, sizeof *stats);
     if (n == 0) {
         if (m_out) *m_out = 0;
@@ -716,7 +719,7 @@ const char* gbr_status_string(int s) {
         case -3: return "invalid argument 3: ldS < max(1, n)";
         case -5: return "invalid argument 5: ldQ < max(1, n)";
         case -6: return "invalid argument 6: select is NULL";
-        case -10: return "invalid argument 10: window must be 4..128 and chain 1..window-2";
+        case -10: return "invalid argument 10: window must be 4..256 and chain 1..window-2";
         case GBR_ERR_CUDA: return "CUDA error (see gbr_last_error)";
         case GBR_ERR_NOMEM: return "out of device memory";
         case GBR_ERR_TIMEOUT: return "a bounded device-side wait timed out";

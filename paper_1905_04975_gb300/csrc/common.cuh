@@ -7,9 +7,15 @@
 
 namespace gbr {
 
-// Largest diagonal window handled by the window kernel (shared-memory bound:
-// packed upper-Hessenberg S window + dense accumulator U).
+// Largest diagonal window whose packed upper-Hessenberg S window and dense
+// accumulator U both fit in one CTA's shared memory.
 constexpr int WMAX = 128;
+
+// Wide windows, WMAX < w <= WMAX_WIDE: the window task keeps its packed S
+// window in a per-CTA global scratch area (WIDE_SP_STRIDE doubles per CTA)
+// and forms U in place in the U pool; both stay in the SM's L1 and in L2.
+constexpr int WMAX_WIDE = 256;
+constexpr size_t WIDE_SP_STRIDE = ((size_t)(WMAX_WIDE * (WMAX_WIDE + 3)) / 2 + 31) & ~(size_t)31;
 
 // Split-precision (Ozaki) updates: OZ_SLICES signed 8-bit digit slices per
 // FP64 operand; one window's U slices take OZ_USLICE_BYTES (bf16 digits
@@ -82,7 +88,8 @@ struct SchedTask {
 struct SchedParams {
     int strong, ntasks;
     int mode;                 // 0: reordering, 1: generalized (S, T) with Q and Z,
-                              // 2: bulge-chasing sweep (window tasks chase bulges)
+                              // 2: bulge-chasing sweep (window tasks chase bulges),
+                              // 3: reordering with windows wider than WMAX
     const Inst* inst;         // instance table
     const SchedTask* tasks;   // queue order
     const Window* wins;
@@ -100,6 +107,7 @@ struct SchedParams {
     long long wait_limit_ns;  // a dependency wait gives up after this long (%globaltimer)
     unsigned long long* trace;  // null, or 4 words per queue position:
                                 // smid | wait start | exec start | end (ns)
+    double* wscr;             // mode 3: WIDE_SP_STRIDE doubles per CTA (packed S window)
 };
 
 // Server kernel (sched.cu): a ring of (request slot, local task) entries and

@@ -67,7 +67,7 @@ void init_state(PlanState& st, int n, const uint8_t* sub, const uint8_t* sel) {
 // the nearest selected or stuck block; stuck blocks do not move.
 void sim_window(PlanState& st, int s, int e) {
     struct B { uint8_t sz, sel; };
-    B out[WMAX], pend[WMAX];
+    B out[WMAX_WIDE], pend[WMAX_WIDE];
     int no = 0, np = 0;
     for (int p = s; p < e;) {
         B b{st.bsz[p], st.sel[p]};
@@ -623,13 +623,23 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     bool pair = false;
     for (size_t i = 0; i < ni; ++i) pair |= (plans[i].d.T != nullptr);
     const size_t b_us = ozaki ? al(OZ_USLICE_BYTES * wins.size() * (pair ? 2 : 1)) : 0;
+    // windows wider than WMAX: the wide kernel instance, with a packed-window
+    // scratch area per CTA (reordering of standard forms, FP64 tiles only)
+    int wmax_win = 0;
+    for (const Window& w : wins) wmax_win = std::max(wmax_win, w.e - w.s);
+    const bool wide = wmax_win > WMAX;
+    if (wide && (ozaki || pair || wmax_win > WMAX_WIDE)) {
+        set_last_error("scheduler: windows wider than 128 need FP64 updates of a standard form");
+        return GBR_ERR_UNSUPPORTED;
+    }
+    const size_t b_wscr = wide ? al(sizeof(double) * WIDE_SP_STRIDE * (size_t)grid) : 0;
     const size_t b_u = al(sizeof(double) * std::max<long long>(1, u_total));
     // ABORT on rejection: one word per window (its task did nothing); every
     // window task writes its own before its tiles read it
     const bool abort = (o.on_reject == GBR_ON_REJECT_ABORT);
     const size_t b_ws = abort ? al(sizeof(int) * std::max<size_t>(1, wins.size())) : 0;
     const size_t total = b_inst + b_tasks + b_wins + 2 * b_deps + b_soff + b_succ + b_ctl + b_tr +
-                         b_us + b_ws + b_u;
+                         b_us + b_ws + b_wscr + b_u;
     char* p = (char*)alloc(total);
     if (!p) return GBR_ERR_NOMEM;
     Inst* d_inst = (Inst*)p; p += b_inst;
@@ -643,6 +653,7 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     unsigned long long* d_tr = b_tr ? (unsigned long long*)p : nullptr; p += b_tr;
     unsigned char* d_us = b_us ? (unsigned char*)p : nullptr; p += b_us;
     int* d_ws = b_ws ? (int*)p : nullptr; p += b_ws;
+    double* d_wscr = b_wscr ? (double*)p : nullptr; p += b_wscr;
     double* d_u = (double*)p;
     GBR_CK(cudaMemcpyAsync(d_inst, itab.data(), sizeof(Inst) * ni, cudaMemcpyHostToDevice, st), "H2D instances");
     if (nt) {
@@ -676,6 +687,8 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     const long long lim_ms = o.wait_limit_ms > 0 ? o.wait_limit_ms : 60000;
     P.wait_limit_ns = lim_ms * 1000000;
     P.trace = d_tr;
+    P.mode = wide ? 3 : 0;
+    P.wscr = d_wscr;
     L->grid = grid;
     L->deps_init = d_deps0;
     L->ctl = d_ctl;

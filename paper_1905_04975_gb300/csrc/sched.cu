@@ -32,6 +32,7 @@ constexpr size_t kSchedSmem = kMax2(kMax2(win::kWindowSmem, upd::kUpdateSmem), o
 // the generalized (pair) and the sweep instances of the kernel
 constexpr size_t kSchedSmemPair = kMax2(kMax2(gen::kGenWindowSmem, upd::kUpdateSmem), oz::kSmem);
 constexpr size_t kSchedSmemSweep = kMax2(swp::kSweepSmem, upd::kUpdateSmem);
+constexpr size_t kSchedSmemWide = kMax2(win::kWindowSmemWide, upd::kUpdateSmemWide);
 
 __device__ __forceinline__ int ld_volatile(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
@@ -75,14 +76,17 @@ __device__ __forceinline__ bool WaitBound::expired() {
 // (tmem); if one of their bounded waits runs out, *err is set.  MODE 1: the
 // instance is a generalized form (S, T); MODE 2: a bulge-chasing sweep on
 // the Hessenberg matrix in I.S (each its own kernel instance, so that the
-// reordering's code and register allocation are untouched).
+// reordering's code and register allocation are untouched); MODE 3: a
+// reordering with windows wider than WMAX (window tasks keep the packed S
+// window in gsp, this CTA's global scratch; tiles read U from global memory).
 template <int MODE>
 __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, const Inst& I,
                                          double* Ug, unsigned char* uslices,
                                          int strong, unsigned long long key,
                                          unsigned long long* u_key, unsigned char* smem_raw,
                                          uint32_t tmem, int* err, bool fma,
-                                         int* abort_word = nullptr, int* wskip = nullptr) {
+                                         int* abort_word = nullptr, int* wskip = nullptr,
+                                         double* gsp = nullptr) {
     const int tid = threadIdx.x;
     const int w = wd.e - wd.s;
     // ABORT: the update tasks of a window whose task did nothing do nothing
@@ -103,6 +107,9 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
         } else if constexpr (MODE == 2)
             swp::sweep_body(I.n, I.S, I.ldS, wd.s, w, wd.t0, wd.t1, wd.nb, I.sp + 2 * wd.b0, Ug,
                             I.ctr, smem_raw);
+        else if constexpr (MODE == 3)
+            win::window_body_t<WMAX_WIDE>(I.n, I.S, I.ldS, wd.s, w, I.sel, Ug, strong, I.ctr,
+                                          smem_raw, nullptr, abort_word, wskip, gsp);
         else
             win::window_body(I.n, I.S, I.ldS, wd.s, w, I.sel, Ug, strong, I.ctr, smem_raw, uslices,
                              abort_word, wskip);
@@ -155,6 +162,20 @@ __device__ __forceinline__ void run_task(const SchedTask& tk, const Window& wd, 
     upd::panel_geom(tk.kind - TASK_L, I.n, wd.s, wd.e, I.S, I.ldS, I.Q, I.ldQ, &base, &rs, &ks, &R);
     bool load_u = (*u_key != key);
     __syncthreads();
+    if constexpr (MODE == 3) {
+        // wide window: FP64 tiles only, U read from global memory
+        for (int r = 0; r < tk.rows; r += upd::BM) {
+            if (fma)
+                upd::update_tile_fma<true>(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w,
+                                           Ug, load_u, smem_raw, &I.ctr->upd_issued);
+            else
+                upd::update_tile<true>(base, rs, ks, tk.y0 + r, min(upd::BM, tk.rows - r), w, Ug,
+                                       load_u, smem_raw, &I.ctr->upd_issued);
+            load_u = false;
+        }
+        if (tid == 0) *u_key = key;
+        return;
+    }
     if (uslices) {
         if (!oz::update_tile_tc(base, rs, ks, tk.y0, tk.rows, wd.e - wd.s, uslices, smem_raw, tmem) &&
             tid == 0)
@@ -238,7 +259,8 @@ sched_kernel(SchedParams P) {
                  P.uslices ? P.uslices + (size_t)tk.win * OZ_USLICE_BYTES * (MODE == 1 ? 2 : 1)
                            : nullptr,
                  P.strong, (unsigned long long)tk.win, &u_key, smem_raw, tmem, P.err,
-                 P.fp64_fma != 0, P.abort_word, P.wskip ? P.wskip + tk.win : nullptr);
+                 P.fp64_fma != 0, P.abort_word, P.wskip ? P.wskip + tk.win : nullptr,
+                 P.wscr ? P.wscr + (size_t)blockIdx.x * WIDE_SP_STRIDE : nullptr);
         // release: every thread's writes are ordered before the counters drop
         __threadfence();
         __syncthreads();
@@ -390,6 +412,9 @@ cudaError_t sched_configure() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sched_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSchedSmemSweep);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sched_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSchedSmemWide);
     if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = true;
     return e;
 }
@@ -416,6 +441,8 @@ cudaError_t launch_sched(const SchedParams& P, int grid, cudaStream_t st) {
         sched_kernel<1><<<grid, SCHED_THREADS, kSchedSmemPair, st>>>(P);
     else if (P.mode == 2)
         sched_kernel<2><<<grid, SCHED_THREADS, kSchedSmemSweep, st>>>(P);
+    else if (P.mode == 3)
+        sched_kernel<3><<<grid, SCHED_THREADS, kSchedSmemWide, st>>>(P);
     else
         sched_kernel<0><<<grid, SCHED_THREADS, kSchedSmem, st>>>(P);
     return cudaGetLastError();

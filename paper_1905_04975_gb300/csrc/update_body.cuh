@@ -33,6 +33,13 @@ constexpr size_t kUpdateSmem = sizeof(double) * ((size_t)WMAX * LDU +
                                                   (size_t)(BM * LDY > WMAX * (BM + 2)
                                                                ? BM * LDY
                                                                : WMAX * (BM + 2)));
+// Wide windows (WMAX < w <= WMAX_WIDE): U stays in global memory (read via
+// L2; the FP64 work per U element read hides its latency) and only the Y
+// tile is staged.
+constexpr int LDY_WIDE = WMAX_WIDE + 4;
+constexpr size_t kUpdateSmemWide = sizeof(double) * (size_t)(BM * LDY_WIDE > WMAX_WIDE * (BM + 2)
+                                                                 ? BM * LDY_WIDE
+                                                                 : WMAX_WIDE * (BM + 2));
 
 enum Panel { PANEL_L = 0, PANEL_R = 1, PANEL_Q = 2 };
 
@@ -69,23 +76,38 @@ __device__ __forceinline__ void panel_geom(int panel, int n, int s, int e, doubl
 // two groups of 8 output columns, the rows [klo, khi) where they have
 // nonzeros, and the products of a group run over those rows only.  If
 // issued is not null, the flops issued by the tile are added to it.
+//
+// WIDE (w up to WMAX_WIDE, 16 column warps: nthreads >= 512): U is read from
+// global memory where the window task formed it, instead of a shared copy.
+template <bool WIDE = false>
 __device__ __forceinline__ void update_tile(double* base, long long rs, long long ks, int r0,
                                             int rows, int w, const double* __restrict__ Ug,
                                             bool load_u, unsigned char* smem_raw,
                                             unsigned long long* issued = nullptr) {
-    double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU
-    double* Ys = Us + WMAX * LDU;                        // BM x LDY
-    __shared__ int k_lo[UPD_THREADS / 32][2], k_hi[UPD_THREADS / 32][2];
+    constexpr int LY = WIDE ? LDY_WIDE : LDY;
+    constexpr int NWC = WIDE ? WMAX_WIDE / 16 : UPD_THREADS / 32;  // warps of 16 output columns
+    double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU (not with WIDE)
+    double* Ys = WIDE ? Us : Us + WMAX * LDU;          // BM x LY
+    __shared__ int k_lo[NWC][2], k_hi[NWC][2];
     const int wp = (w + 15) & ~15;  // padded to the warp column width
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
+    // U(k, c), zero outside w x w
+    auto uat = [&](int k, int c) -> double {
+        if constexpr (WIDE)
+            return (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+        else
+            return Us[k * LDU + c];
+    };
     if (load_u) {
-        for (int i = tid; i < wp * wp; i += nth) {
-            int k = i / wp, c = i % wp;
-            Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+        if constexpr (!WIDE) {
+            for (int i = tid; i < wp * wp; i += nth) {
+                int k = i / wp, c = i % wp;
+                Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (warp < UPD_THREADS / 32) {
+        if (warp < NWC) {
             const int c0 = warp * 16;
 #pragma unroll
             for (int ct = 0; ct < 2; ++ct) {
@@ -94,7 +116,7 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
                     for (int k = lane; k < wp; k += 32) {
                         bool nz = false;
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) nz |= Us[k * LDU + c0 + 8 * ct + c] != 0.0;
+                        for (int c = 0; c < 8; ++c) nz |= uat(k, c0 + 8 * ct + c) != 0.0;
                         if (nz) {
                             lo = min(lo, k);
                             hi = max(hi, k + 1);
@@ -114,12 +136,12 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
     if (rs == 1) {
         for (int i = tid; i < BM * wp; i += nth) {
             int r = i % BM, k = i / BM;
-            Ys[r * LDY + k] = (r < rows && k < w) ? __ldcg(&base[(r0 + r) + (long long)k * ks]) : 0.0;
+            Ys[r * LY + k] = (r < rows && k < w) ? __ldcg(&base[(r0 + r) + (long long)k * ks]) : 0.0;
         }
     } else {
         for (int i = tid; i < BM * wp; i += nth) {
             int k = i % wp, r = i / wp;
-            Ys[r * LDY + k] = (r < rows && k < w) ? __ldcg(&base[(long long)(r0 + r) * rs + k]) : 0.0;
+            Ys[r * LY + k] = (r < rows && k < w) ? __ldcg(&base[(long long)(r0 + r) * rs + k]) : 0.0;
         }
     }
     __syncthreads();
@@ -127,13 +149,13 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
     const int c0 = warp * 16;
     if (issued && tid == 0) {
         unsigned long long f = 0;
-        for (int v = 0; v < UPD_THREADS / 32 && v * 16 < w; ++v)
+        for (int v = 0; v < NWC && v * 16 < w; ++v)
             for (int ct = 0; ct < 2 && v * 16 + 8 * ct < w; ++ct)
                 f += 2ull * rows * (unsigned long long)min(8, w - v * 16 - 8 * ct) *
                      (k_hi[v][ct] - k_lo[v][ct]);
         atomicAdd(issued, f);
     }
-    if (warp < UPD_THREADS / 32 && c0 < wp) {
+    if (warp < NWC && c0 < wp) {
         const int lo0 = k_lo[warp][0], hi0 = k_hi[warp][0];
         const int lo1 = k_lo[warp][1], hi1 = k_hi[warp][1];
         double acc[8][2][2];
@@ -147,9 +169,9 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
         for (int kk = blo; kk < bhi; kk += 4) {
             double a[8], bb[2];
 #pragma unroll
-            for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LDY + kk + tig];
+            for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LY + kk + tig];
 #pragma unroll
-            for (int ct = 0; ct < 2; ++ct) bb[ct] = Us[(kk + tig) * LDU + c0 + ct * 8 + gid];
+            for (int ct = 0; ct < 2; ++ct) bb[ct] = uat(kk + tig, c0 + ct * 8 + gid);
 #pragma unroll
             for (int rt = 0; rt < 8; ++rt)
 #pragma unroll
@@ -165,8 +187,8 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
                 for (int kk = a0; kk < a1; kk += 4) {
                     double a[8];
 #pragma unroll
-                    for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LDY + kk + tig];
-                    const double bv = Us[(kk + tig) * LDU + c0 + ct * 8 + gid];
+                    for (int rt = 0; rt < 8; ++rt) a[rt] = Ys[(rt * 8 + gid) * LY + kk + tig];
+                    const double bv = uat(kk + tig, c0 + ct * 8 + gid);
 #pragma unroll
                     for (int rt = 0; rt < 8; ++rt) dmma(acc[rt][ct][0], acc[rt][ct][1], a[rt], bv);
                 }
@@ -204,33 +226,43 @@ __device__ __forceinline__ void update_tile(double* base, long long rs, long lon
 // a product of adjacent swaps).  Every output is one FMA chain over k in
 // increasing order, starting from 0.
 constexpr int LDK = BM + 2;   // padded pitch of the k-major Y tile (16-byte rows)
-constexpr int FMA_GROUPS = WMAX / 8;
 
+// WIDE: w up to WMAX_WIDE, U read from global memory (see update_tile).
+template <bool WIDE = false>
 __device__ __forceinline__ void update_tile_fma(double* base, long long rs, long long ks, int r0,
                                                 int rows, int w, const double* __restrict__ Ug,
                                                 bool load_u, unsigned char* smem_raw,
                                                 unsigned long long* issued = nullptr) {
     static_assert(BM == 64, "one lane owns two rows of the 64-row tile");
-    double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU
-    double* Yk = Us + WMAX * LDU;                        // WMAX x LDK (k-major)
-    __shared__ int g_lo[FMA_GROUPS], g_hi[FMA_GROUPS];
+    constexpr int NG = (WIDE ? WMAX_WIDE : WMAX) / 8;  // groups of 8 output columns
+    double* Us = reinterpret_cast<double*>(smem_raw);  // WMAX x LDU (not with WIDE)
+    double* Yk = WIDE ? Us : Us + WMAX * LDU;          // wp x LDK (k-major)
+    __shared__ int g_lo[NG], g_hi[NG];
     const int wp = (w + 7) & ~7;  // padded to the group width
     const int ng = wp >> 3;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
     if (load_u) {
-        for (int i = tid; i < wp * wp; i += nth) {
-            int k = i / wp, c = i % wp;
-            Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+        if constexpr (!WIDE) {
+            for (int i = tid; i < wp * wp; i += nth) {
+                int k = i / wp, c = i % wp;
+                Us[k * LDU + c] = (k < w && c < w) ? __ldcg(&Ug[(size_t)c * w + k]) : 0.0;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         // rows of U where each group of 8 columns has nonzeros
         for (int g = warp; g < ng; g += nw) {
             int lo = wp, hi = 0;
             for (int k = lane; k < wp; k += 32) {
                 bool nz = false;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) nz |= Us[k * LDU + 8 * g + c] != 0.0;
+                for (int c = 0; c < 8; ++c) {
+                    if constexpr (WIDE)
+                        nz |= (k < w && 8 * g + c < w) &&
+                              __ldcg(&Ug[(size_t)(8 * g + c) * w + k]) != 0.0;
+                    else
+                        nz |= Us[k * LDU + 8 * g + c] != 0.0;
+                }
                 if (nz) {
                     lo = min(lo, k);
                     hi = max(hi, k + 1);
@@ -272,17 +304,23 @@ __device__ __forceinline__ void update_tile_fma(double* base, long long rs, long
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
-        const double* up = Us + 8 * g;
 #pragma unroll 2
         for (int k = lo; k < hi; ++k) {
             const double2 y = *reinterpret_cast<const double2*>(&Yk[k * LDK + ra]);
-            const double2* u2 = reinterpret_cast<const double2*>(up + k * LDU);
             double u[8];
+            if constexpr (WIDE) {
+                // k < hi <= w: the rows beyond w of U are zero, never in [lo, hi)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const double2 t = u2[j];
-                u[2 * j] = t.x;
-                u[2 * j + 1] = t.y;
+                for (int j = 0; j < 8; ++j)
+                    u[j] = (8 * g + j < w) ? __ldcg(&Ug[(size_t)(8 * g + j) * w + k]) : 0.0;
+            } else {
+                const double2* u2 = reinterpret_cast<const double2*>(Us + 8 * g + k * LDU);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const double2 t = u2[j];
+                    u[2 * j] = t.x;
+                    u[2 * j + 1] = t.y;
+                }
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {

@@ -2,9 +2,12 @@
 // S and accumulates the window's orthogonal transformation U (Section 3.2,
 // Fig. 1b; the "window task" that outputs updated tiles and an accumulator).
 //
-// One CTA owns one window [s, e) of width w <= WMAX.  The window of S lives
-// in shared memory in packed upper-Hessenberg column order (column c keeps
-// rows 0..c+1), U (w x w, starting at the identity) in dense column order.
+// One CTA owns one window [s, e) of width w.  For w <= WMAX the window of S
+// lives in shared memory in packed upper-Hessenberg column order (column c
+// keeps rows 0..c+1), U (w x w, starting at the identity) in dense column
+// order.  Wider windows (up to WMAX_WIDE) do not fit there: the same packed
+// window sits in a global scratch area of the CTA and U is formed in place
+// in global memory, both served by the SM's L1 and L2.
 //
 // The swaps are organised in parallel steps instead of one at a time: in a
 // step, every selected block whose upper neighbour is an unselected block
@@ -312,6 +315,9 @@ constexpr size_t kWindowSmem = sizeof(double) * ((size_t)WMAX * WMAX +
                                                  (size_t)((WMAX * (WMAX + 3)) / 2) +
                                                  (size_t)2 * MAXSW * 16) +
                                sizeof(int) * 2 * 3 * MAXSW + 2 * WMAX;
+// A wide window task keeps only the transforms, swap lists and flags here.
+constexpr size_t kWindowSmemWide = sizeof(double) * (size_t)2 * (WMAX_WIDE / 2) * 16 +
+                                   sizeof(int) * 2 * 3 * (WMAX_WIDE / 2) + 2 * WMAX_WIDE;
 
 // Row r of U, columns [j, j + K) <- (those columns) Z (the right
 // transformation of one swap, applied to U).
@@ -336,35 +342,46 @@ __device__ __forceinline__ void right_u_row(double* __restrict__ U, int w, int j
 // after it was set does nothing (U = I, *skip_out = 1); a window task that
 // rejects a swap sets it, finishes the step it is in, restores the standard
 // form of its 2x2 blocks and stops.  skip_out (nullable) receives 0 or 1.
-__device__ __forceinline__ void window_body(int n, double* __restrict__ S, int ldS, int s0, int w,
-                                            uint8_t* __restrict__ gsel, double* __restrict__ Ug,
-                                            int strong, DevCounters* __restrict__ ctr,
-                                            unsigned char* smem_raw,
-                                            unsigned char* __restrict__ uslices = nullptr,
-                                            int* abort_word = nullptr, int* skip_out = nullptr) {
+//
+// WM is the largest window of the instance: WMAX keeps S and U in shared
+// memory; WMAX_WIDE keeps the packed S window in gsp (this CTA's global
+// scratch, WIDE_SP_STRIDE doubles) and forms U in place in Ug (no split-
+// precision slices).  The steps are the same; only where the two arrays live
+// differs.
+template <int WM>
+__device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int ldS, int s0, int w,
+                                              uint8_t* __restrict__ gsel, double* __restrict__ Ug,
+                                              int strong, DevCounters* __restrict__ ctr,
+                                              unsigned char* smem_raw,
+                                              unsigned char* __restrict__ uslices,
+                                              int* abort_word, int* skip_out,
+                                              double* __restrict__ gsp) {
+    static_assert(WM == WMAX || WM == WMAX_WIDE, "window kernel instances");
+    constexpr bool WIDE = WM > WMAX;
+    constexpr int MSW = WM / 2;  // at most one swap per two positions
     // The state of a step (its swaps, their transforms and the prefix sums
     // of their work) is kept for two steps, by the step's parity: the part
     // of a step's right transformations that acts on U (rows of U, which no
     // swap reads) is applied during the next step's transform phase, by the
     // warps that have no transform of their own to compute.
-    double* U = reinterpret_cast<double*>(smem_raw);           // w*w
-    double* Sp = U + WMAX * WMAX;                               // packed window
-    double* Zbuf = Sp + poff(WMAX);                             // [2][MAXSW * 16]
-    int* swbuf = reinterpret_cast<int*>(Zbuf + 2 * MAXSW * 16); // [2][3][MAXSW]: j, k, p
-    uint8_t* bst = reinterpret_cast<uint8_t*>(swbuf + 2 * 3 * MAXSW);
-    uint8_t* sel = bst + WMAX;
+    double* U = WIDE ? Ug : reinterpret_cast<double*>(smem_raw);        // w*w
+    double* Sp = WIDE ? gsp : U + WM * WM;                               // packed window
+    double* Zbuf = WIDE ? reinterpret_cast<double*>(smem_raw) : Sp + poff(WM);  // [2][MSW * 16]
+    int* swbuf = reinterpret_cast<int*>(Zbuf + 2 * MSW * 16);  // [2][3][MSW]: j, k, p
+    uint8_t* bst = reinterpret_cast<uint8_t*>(swbuf + 2 * 3 * MSW);
+    uint8_t* sel = bst + WM;
     __shared__ int nsw, nrej, nacc;
     unsigned long long wflops = 0;   // per thread (phase D), summed at the end
     __shared__ int tcnt2[2][3];
-    __shared__ int tlist2[2][3][MAXSW];   // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
-    __shared__ int kpre_l[3][MAXSW + 1];  // prefix sums of left-apply columns per k group
-    __shared__ int kpre_s[3][MAXSW + 1];  // prefix sums of right-apply rows of S
-    __shared__ int kpre_u2[2][3][MAXSW + 1];  // prefix sums of right-apply rows of U
+    __shared__ int tlist2[2][3][MSW];   // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
+    __shared__ int kpre_l[3][MSW + 1];  // prefix sums of left-apply columns per k group
+    __shared__ int kpre_s[3][MSW + 1];  // prefix sums of right-apply rows of S
+    __shared__ int kpre_u2[2][3][MSW + 1];  // prefix sums of right-apply rows of U
     // Rows [urlo[c], urhi[c]] hold every nonzero of column c of U: U starts as
     // I and a swap on columns [j, j+k) mixes only those columns, so the rows
     // outside the union of their ranges stay exactly zero and are skipped.
-    __shared__ short urlo[WMAX], urhi[WMAX];
-    __shared__ short slo2[2][MAXSW], shi2[2][MAXSW];  // per slot: U rows its right transform touches
+    __shared__ short urlo[WM], urhi[WM];
+    __shared__ short slo2[2][MSW], shi2[2][MSW];  // per slot: U rows its right transform touches
     __shared__ int pu_par;    // parity of the step whose U rows are pending, or -1
     __shared__ int pu_next;   // next pending U row item to claim
 
@@ -415,8 +432,8 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     // of U for one swap, the swaps' items grouped by k and counted by the
     // prefix sums kpre_u2[pp].
     auto pending_u = [&](int pp) {
-        const int* pj = swbuf + pp * 3 * MAXSW;
-        const int* pk = pj + MAXSW;
+        const int* pj = swbuf + pp * 3 * MSW;
+        const int* pk = pj + MSW;
         const int T0 = kpre_u2[pp][0][tcnt2[pp][0]], T1 = kpre_u2[pp][1][tcnt2[pp][1]];
         const int total = T0 + T1 + kpre_u2[pp][2][tcnt2[pp][2]];
         for (;;) {
@@ -438,7 +455,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
             if (pk[slot] == 0) continue;  // rejected
             const int j = pj[slot];
             const int r = slo2[pp][slot] + (itg - pre[lo]);
-            const double* Z = Zbuf + pp * MAXSW * 16 + slot * 16;
+            const double* Z = Zbuf + pp * MSW * 16 + slot * 16;
             if (g == 0) right_u_row<2>(U, w, j, r, Z);
             else if (g == 1) right_u_row<3>(U, w, j, r, Z);
             else right_u_row<4>(U, w, j, r, Z);
@@ -451,15 +468,15 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     bool final_pass = false;
     for (int iter = 0;; ++iter) {
         const int par = iter & 1;
-        double* Zs = Zbuf + par * MAXSW * 16;
-        int* swj = swbuf + par * 3 * MAXSW;
-        int* swk = swj + MAXSW;
-        int* swp = swk + MAXSW;
-        int (*tlist)[MAXSW] = tlist2[par];
+        double* Zs = Zbuf + par * MSW * 16;
+        int* swj = swbuf + par * 3 * MSW;
+        int* swk = swj + MSW;
+        int* swp = swk + MSW;
+        int (*tlist)[MSW] = tlist2[par];
         int* tcnt = tcnt2[par];
         short* slo = slo2[par];
         short* shi = shi2[par];
-        int (*kpre_u)[MAXSW + 1] = kpre_u2[par];
+        int (*kpre_u)[MSW + 1] = kpre_u2[par];
         __syncthreads();
         if (abort_word && !final_pass && nrej > 0) {
             // ABORT: the first rejection stops the reordering; this window
@@ -467,7 +484,7 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
             final_pass = true;
             if (tid == 0) atomicExch(abort_word, 1);
         }
-        if (iter > 4 * WMAX * WMAX) {
+        if (iter > 4 * WM * WM) {
             if (tid == 0) atomicAdd(&ctr->step_overflow, 1);
             break;
         }
@@ -786,13 +803,27 @@ __device__ __forceinline__ void window_body(int n, double* __restrict__ S, int l
     }
     for (int i = tid; i < w; i += nth)
         if (sel[i] != SEL_WALL) gsel[s0 + i] = sel[i];
-    for (int i = tid; i < w * w; i += nth) Ug[i] = U[i];
-    if (uslices) write_u_slices(U, w, uslices);
+    if constexpr (!WIDE) {
+        for (int i = tid; i < w * w; i += nth) Ug[i] = U[i];
+        if (uslices) write_u_slices(U, w, uslices);
+    }
     if (tid == 0) {
         atomicAdd(&ctr->swaps, (unsigned long long)nacc);
         atomicAdd(&ctr->rejected, (unsigned long long)nrej);
         atomicAdd(&ctr->win_flops, wflops);
     }
+}
+
+
+// The shared-memory window task (w <= WMAX).
+__device__ __forceinline__ void window_body(int n, double* __restrict__ S, int ldS, int s0, int w,
+                                            uint8_t* __restrict__ gsel, double* __restrict__ Ug,
+                                            int strong, DevCounters* __restrict__ ctr,
+                                            unsigned char* smem_raw,
+                                            unsigned char* __restrict__ uslices = nullptr,
+                                            int* abort_word = nullptr, int* skip_out = nullptr) {
+    window_body_t<WMAX>(n, S, ldS, s0, w, gsel, Ug, strong, ctr, smem_raw, uslices, abort_word,
+                        skip_out, nullptr);
 }
 
 }  // namespace win

@@ -67,7 +67,7 @@ def test_argument_errors_before_gpu(lib):
     assert call(lib, 8, dummy, 8, dummy, 4, sel)[0] == -5
     assert call(lib, 8, dummy, 8, None, 8, None)[0] == -6
     bad = g.default_opts()
-    bad.window = 200
+    bad.window = 300
     assert call(lib, 0, None, 1, None, 1, sel, bad)[0] == -10
     bad = g.default_opts()
     bad.chain = 127
@@ -78,6 +78,17 @@ def test_argument_errors_before_gpu(lib):
     # n = 0 is a no-op that succeeds without a GPU
     rc, m = call(lib, 0, None, 1, None, 1, sel)
     assert rc == 0 and m == 0
+    # windows above 128: persistent schedule with FP64 updates only
+    for prec in (g.PREC_FMA, g.PREC_DMMA):
+        wide = g.make_opts(window=256, chain=128, precision=prec)
+        assert call(lib, 0, None, 1, None, 1, sel, wide)[0] == 0
+    wide = g.make_opts(window=256, chain=128, precision="ozaki")
+    assert call(lib, 0, None, 1, None, 1, sel, wide)[0] == g.ERR_UNSUPPORTED
+    wide = g.make_opts(window=200, chain=100, sched="sequential")
+    assert call(lib, 0, None, 1, None, 1, sel, wide)[0] == g.ERR_UNSUPPORTED
+    bad = g.default_opts()
+    bad.window, bad.chain = 257, 64
+    assert call(lib, 0, None, 1, None, 1, sel, bad)[0] == -10
 
 
 def test_update_panel_argument_checks(lib):

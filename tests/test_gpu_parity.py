@@ -362,6 +362,64 @@ def test_split_precision_n4000(gbr):
     check(S, Q, sel, r, Sg, Qg, ref)
 
 
+@pytest.mark.parametrize("prec", ["fma", "dmma"])
+@pytest.mark.parametrize("name,w,m", [("n400", 256, 128), ("ragged", 200, 150),
+                                      ("ragged", 256, 254), ("tiny", 160, 40), ("odd", 129, 64)])
+def test_wide_windows(gbr, prec, name, w, m):
+    """Windows wider than 128 (the packed S window and U in global memory,
+    update tiles reading U from global memory): the same parity bar, on
+    the persistent schedule with FP64 updates."""
+    if name == "n400":
+        S, Q, sel = si.config("n400")
+    elif name == "tiny":
+        S, Q, sel = si.reorder_problem(37, 4, select_frac=0.5, q="householder", reflectors=8)
+    elif name == "odd":
+        S, Q, sel = si.reorder_problem(700, 7, select_frac=0.45, q="householder")
+    else:
+        S, Q, sel = si.reorder_problem(515, 6, select_frac=0.6, q="householder")
+    ref = oracle.reorder(S, Q, sel)
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=w, chain=m, precision=prec)
+    assert r.status == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
+    assert r.stats.windows > 0 or r.m == 0
+    # the task graph orders every overlapping access: a second run is bitwise equal
+    r2, Sg2, Qg2 = run_gpu(gbr, S, Q, sel, window=w, chain=m, precision=prec)
+    assert np.array_equal(Sg, Sg2) and np.array_equal(Qg, Qg2)
+
+
+def test_wide_window_n4000(gbr):
+    """The n = 4000 workload with windows of 256 and chains of 128, against
+    the full oracle run, through the device and the host-buffer entries."""
+    (S, Q, sel), ref = n4000_oracle()
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=256, chain=128, precision="fma")
+    assert r.status == 0
+    check(S, Q, sel, r, Sg, Qg, ref)
+    Sh, Qh = np.asfortranarray(S.copy()), np.asfortranarray(Q.copy())
+    r3 = gbr.reorder_host(Sh, Qh, sel, window=256, chain=128, precision="fma")
+    assert r3.status == 0
+    assert np.array_equal(Sh, Sg) and np.array_equal(Qh, Qg)
+
+
+def test_wide_window_rejections(gbr):
+    """Swap rejections inside wide windows (clustered kappa = 1e6 law):
+    stuck blocks, re-planning, a valid similarity in standard form."""
+    n = 1200
+    S, Q, sel = si.reorder_problem(n, 11, select_frac=0.5, clusters=True, spread=1e-6,
+                                   kappa=1e6)
+    A = Q @ S @ Q.T
+    want, m = expected_order(S, sel)
+    r, Sg, Qg = run_gpu(gbr, S, Q, sel, window=256, chain=200, precision="fma")
+    assert r.status >= 0 and r.m == m
+    assert is_standard(Sg)
+    assert residual(A, Sg, Qg) <= 50 * n * EPS
+    assert orth_err(Qg) <= 50 * n * EPS
+    got = block_eigs(Sg)
+    k = 0
+    while k < m and abs(got[k] - want[k]) <= 1e-6 * max(1, abs(want[k])):
+        k += 1
+    assert k > 0
+
+
 @pytest.mark.parametrize("sched", ["sequential", "persistent"])
 def test_abort_on_first_rejection(gbr, sched):
     """on_reject = ABORT on the clustered kappa = 1e6 input (the rejection

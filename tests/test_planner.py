@@ -53,7 +53,8 @@ def problem(n, seed, frac):
 @pytest.mark.parametrize("n,seed,frac,w,m", [
     (400, 0, 0.3, 128, 64), (4000, 0, 0.35, 128, 64), (1000, 1, 0.5, 64, 30),
     (257, 2, 0.2, 16, 6), (130, 3, 0.9, 32, 10), (50, 4, 0.05, 8, 3), (3, 5, 0.5, 4, 2),
-    (1, 6, 1.0, 4, 1)])
+    (1, 6, 1.0, 4, 1), (4000, 0, 0.35, 256, 128), (1000, 1, 0.5, 200, 150),
+    (600, 2, 0.6, 256, 254)])
 def test_plan_is_the_stable_partition(n, seed, frac, w, m):
     sizes, sel, sub, selb = problem(n, seed, frac)
     W, chains, flops = g.plan(sub, sel, w, m)
@@ -77,4 +78,6 @@ def test_plan_edge_cases():
     W = g.plan(sub, np.array([0, 0, 0, 0, 0, 1], np.int32), 4, 2)[0]
     assert len(W) >= 2 and W[-1, 0] == 0
     with pytest.raises(g.GbrError):
-        g.plan(sub, np.zeros(6, np.int32), 200, 64)
+        g.plan(sub, np.zeros(6, np.int32), 257, 64)
+    with pytest.raises(g.GbrError):
+        g.plan(sub, np.zeros(6, np.int32), 256, 255)
