@@ -1585,9 +1585,18 @@ def main():
                     help="n16000c: skip the accuracy report")
     ap.add_argument("--loads", type=lambda v: [float(x) for x in v.split(",")],
                     default=[0.7, 0.95], help="serve: arrival rates as fractions of saturation")
+    ap.add_argument("--window", type=int, default=None,
+                    help="single-reordering workloads: window size w (4..256)")
+    ap.add_argument("--chain", type=int, default=None,
+                    help="with --window: chain length m (default w / 2)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.window is not None and wl.get("kind") is None:
+        wl["window"] = args.window
+        wl["chain"] = args.chain if args.chain is not None else args.window // 2
+        if args.window > 128 and args.precision in (None, "both"):
+            args.precision = "fma"   # wider windows: FP64 updates only
     if args.cpu_leg:
         return cpu_leg(wl)
     if args.precision is None:

@@ -316,6 +316,49 @@ __device__ __forceinline__ bool slice_step(const long long (&G)[4][8], unsigned 
     return true;
 }
 
+// Staging of 128 rows x 64 columns of Y in shared memory for panels whose
+// rows are contiguous in memory (ks == 1): element (r, c) at r * 64 +
+// (c ^ (r & 15)), so that a half-warp touches 16 different bank pairs both
+// when its lanes run along a row (global side) and down a column (one lane
+// per row: digit generation and the accumulator read-out).
+static_assert(2 * A_BYTES == (size_t)TC_M * 64 * sizeof(double), "staging = both slice buffers");
+__device__ __forceinline__ int stg_idx(int r, int c) { return r * 64 + (c ^ (r & 15)); }
+
+// Columns [k0, k0 + 64) of rows [row0, row0 + pr) into the staging area
+// (zeros beyond w and beyond pr), coalesced along each row.
+// Eight loads per thread are issued before the first store, so that their
+// latencies overlap.
+__device__ __forceinline__ void stage_rows_in(const double* base, long long rs, int row0, int pr,
+                                              int k0, int w, double* stg) {
+    constexpr int PER = (int)TC_M * 64 / TILE_THREADS;  // elements per thread
+    static_assert(PER % 8 == 0, "whole batches of eight");
+#pragma unroll 1
+    for (int u0 = 0; u0 < PER; u0 += 8) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = threadIdx.x + (u0 + u) * TILE_THREADS;
+            const int r = i >> 6, k = k0 + (i & 63);
+            x[u] = (r < pr && k < w) ? __ldcg(&base[(long long)(row0 + r) * rs + k]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = threadIdx.x + (u0 + u) * TILE_THREADS;
+            stg[stg_idx(i >> 6, i & 63)] = x[u];
+        }
+    }
+}
+
+// The staged outputs (columns [n0, n0 + 64) of rows [row0, row0 + pr)) back
+// to Y, coalesced along each row.
+__device__ __forceinline__ void stage_rows_out(double* base, long long rs, int row0, int pr, int n0,
+                                               int w, const double* stg) {
+    for (int i = threadIdx.x; i < pr * 64; i += TILE_THREADS) {
+        const int r = i >> 6, c = i & 63, n = n0 + c;
+        if (n < w) __stcg(&base[(long long)(row0 + r) * rs + n], stg[stg_idx(r, c)]);
+    }
+}
+
 // Rows [y0, y0 + rows) of Y <- (Y U) rows, emulated FP64, in place.
 // uslices: the window's U digits (written by its window task) and column
 // exponents; tmem: the CTA's TMEM_COLS columns of tensor memory; smem_raw:
@@ -332,6 +375,9 @@ static __device__ __noinline__ bool update_tile_tc(double* base, long long rs, l
     int* red = reinterpret_cast<int*>(sm + OFF_RED);
     int* cexp = reinterpret_cast<int*>(sm + OFF_CEXP);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // A0, A1, B
+    // left-panel staging (rows of Y contiguous): both slice buffers, free
+    // while rows are read and after a block's products have completed
+    double* stg = reinterpret_cast<double*>(sm + OFF_A);
     const int* ucexp = reinterpret_cast<const int*>(uslices + OZ_UDIG_ELEMS * 2);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -367,20 +413,50 @@ static __device__ __noinline__ bool update_tile_tc(double* base, long long rs, l
         // 1. the thread's 32 entries (row m, 4 chunks of 8 K) and the row's
         // largest exponent field (4 threads per row, combined in shared memory)
         long long G[4][8];
+        if (ks == 1) {
+            // rows of Y are contiguous (left panel): read them coalesced into
+            // the free slice buffers, 64 columns at a time, then take the
+            // thread's entries from there
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh) {
+#pragma unroll
+                for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) G[2 * kh + ii][j] = 0;
+                if (kh * 64 < w) {
+                    stage_rows_in(base, rs, y0 + p0, pr, kh * 64, w, stg);
+                    __syncthreads();
+#pragma unroll
+                    for (int ii = 0; ii < 2; ++ii) {
+                        const int c0 = 8 * cq + 32 * ii;   // K columns 64 kh + c0 .. + 7
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            G[2 * kh + ii][j] = __double_as_longlong(stg[stg_idx(m, c0 + j)]);
+                    }
+                    __syncthreads();
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k0 = 8 * (cq + 4 * i);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    double x = 0.0;
+                    if (m < pr && k0 + j < w)
+                        x = __ldcg(&base[(long long)(y0 + p0 + m) * rs + (long long)(k0 + j) * ks]);
+                    G[i][j] = __double_as_longlong(x);
+                }
+            }
+        }
         int em = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k0 = 8 * (cq + 4 * i);
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                double x = 0.0;
-                if (m < pr && k0 + j < w)
-                    x = __ldcg(&base[(long long)(y0 + p0 + m) * rs + (long long)(k0 + j) * ks]);
-                G[i][j] = __double_as_longlong(x);
                 const int e = (int)(((unsigned long long)G[i][j] >> 52) & 0x7ff);
                 em = e > em ? e : em;
             }
-        }
         red[cq * 128 + m] = em;
         __syncthreads();
         const int er_gen = max(max(red[m], red[128 + m]), max(red[256 + m], red[384 + m]));
@@ -457,11 +533,20 @@ static __device__ __noinline__ bool update_tile_tc(double* base, long long rs, l
                             unsigned a[NACC];
 #pragma unroll
                             for (int j = 0; j < NACC; ++j) a[j] = v[j][c];
-                            __stcg(&base[(long long)(y0 + p0 + r_out) * rs + (long long)n * ks],
-                                   oz_combine(a, er, cexp[hc * TC_N + col0 + c]));
+                            const double y = oz_combine(a, er, cexp[hc * TC_N + col0 + c]);
+                            if (ks == 1)
+                                stg[stg_idx(r_out, col0 + c)] = y;
+                            else
+                                __stcg(&base[(long long)(y0 + p0 + r_out) * rs + (long long)n * ks],
+                                       y);
                         }
                     }
                 }
+            }
+            if (ks == 1) {
+                // left panel: the staged outputs go out as contiguous row segments
+                if (__syncthreads_or(!ok)) return false;
+                stage_rows_out(base, rs, y0 + p0, pr, h * (int)TC_N, w, stg);
             }
             tc_fence_before();
             if (__syncthreads_or(!ok)) return false;
