@@ -22,7 +22,8 @@ static std::vector<long long> g_trace;  // last traced persistent launch, 8 word
 enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED = 3, POOL_PANEL = 4,
                 POOL_EIGVEC = 5 };
 static_assert(POOL_GEN_SCRATCH == 6 && POOL_GEN_HOST == 7 && POOL_GEN_SCHED == 8 &&
-                  POOL_SWEEP == 9 && POOL_SWEEP_SCHED == 10 && POOL_NSLOTS == 11,
+                  POOL_SWEEP == 9 && POOL_SWEEP_SCHED == 10 && POOL_SCHED_ALT == 11 &&
+                  POOL_NSLOTS == 12,
               "pool slots of the generalized entry points");
 struct DevPool {
     void* ptr[POOL_NSLOTS] = {};
@@ -83,49 +84,135 @@ static CostModel cost_model(const gbr_opts& o) {
     return c;
 }
 
+// A non-blocking stream per device for uploading the launch images of later
+// chunks while an earlier chunk runs (created on first use, destroyed by
+// gbr_release).
+static cudaStream_t g_side[64];
+
+static int side_stream(cudaStream_t* out) {
+    int dev = 0;
+    GBR_CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return GBR_ERR_CUDA;
+    if (!g_side[dev])
+        GBR_CK(cudaStreamCreateWithFlags(&g_side[dev], cudaStreamNonBlocking), "side stream");
+    *out = g_side[dev];
+    return 0;
+}
+
+// Cuts of one pass's window list (in pipeline order) into chunks that run as
+// consecutive persistent launches.  Ordering the task graph of a large pass
+// takes the host tens of milliseconds, during which the device would idle;
+// with chunks, the first launch starts after the host has ordered only its
+// first sixteenth, and each later chunk is planned, ordered and uploaded
+// while the previous one runs.  Small passes, traced launches (one timeline)
+// and ABORT (one abort word per launch) take one launch.
+static std::vector<size_t> chunk_cuts(size_t nw, const gbr_opts& o) {
+    std::vector<size_t> cuts{0};
+    if (nw >= 1024 && o.timing < 2 && o.on_reject != GBR_ON_REJECT_ABORT) {
+        cuts.push_back(nw / 16);
+        cuts.push_back(nw / 4);
+    }
+    cuts.push_back(nw);
+    return cuts;
+}
+
+static int read_err(const SchedLaunch& L, cudaStream_t s, int* acc) {
+    int h = 0;
+    GBR_CK(cudaMemcpyAsync(&h, L.P.err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H err");
+    GBR_CK(cudaStreamSynchronize(s), "sync");
+    *acc |= h;
+    return 0;
+}
+
+// One planned pass through the persistent scheduler.  The windows are put in
+// pipeline order and cut into chunks (chunk_cuts); a chunk is a prefix-closed
+// part of that order (every window that overlaps one of its windows and
+// comes earlier is in it or in an earlier chunk), so running the chunks one
+// after another on the stream keeps every dependence.  Two launch images
+// alternate between the pool slots POOL_SCHED and POOL_SCHED_ALT.
 static int run_persistent(int n, const std::vector<Window>& wins, double* S, int ldS, double* Q,
                           int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
                           long long* ntasks_out, double* ms_out, cudaStream_t st) {
-    std::vector<InstPlan> plans(1);
-    plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
-    plans[0].wins = wins;
-    SchedLaunch L;
-    SchedInfo inf;
-    int rc = sched_prepare(
-        plans, o, cost_model(o), num_sms(),
-        [](size_t b) -> void* {
-            void* p = nullptr;
-            return pool_get(POOL_SCHED, b, &p) ? nullptr : p;
-        },
-        &L, &inf, st);
-    if (rc) return rc;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (o.timing) {
-        GBR_CK(cudaEventCreate(&e0), "event");
-        GBR_CK(cudaEventCreate(&e1), "event");
-        GBR_CK(cudaEventRecord(e0, st), "event");
+    std::vector<Window> all = wins;
+    pipeline_order(n, all);
+    const std::vector<size_t> cuts = chunk_cuts(all.size(), o);
+    const int nch = (int)cuts.size() - 1;
+    cudaStream_t up = st;
+    if (nch > 1) {
+        int rcs = side_stream(&up);
+        if (rcs) return rcs;
     }
-    rc = sched_enqueue(L, st);
-    if (rc) return rc;
-    if (o.timing) GBR_CK(cudaEventRecord(e1, st), "event");
+    // events: timing (e0, e1) and the end of the last chunk of each image
+    struct Events {
+        cudaEvent_t e[4] = {};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    if (o.timing) {
+        GBR_CK(cudaEventCreate(&ev.e[0]), "event");
+        GBR_CK(cudaEventCreate(&ev.e[1]), "event");
+    }
+    if (nch > 1) {
+        GBR_CK(cudaEventCreateWithFlags(&ev.e[2], cudaEventDisableTiming), "event");
+        GBR_CK(cudaEventCreateWithFlags(&ev.e[3], cudaEventDisableTiming), "event");
+    }
+    SchedLaunch L[2];
+    SchedInfo tot;
     int h_err = 0;
-    GBR_CK(cudaMemcpyAsync(&h_err, L.P.err, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H err");
-    GBR_CK(cudaStreamSynchronize(st), "sync");
+    const CostModel cm = cost_model(o);
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        if (c >= 2) {
+            // image b held chunk c - 2: wait until it has run, then reuse it
+            GBR_CK(cudaEventSynchronize(ev.e[2 + b]), "sync chunk");
+            int rce = read_err(L[b], up, &h_err);
+            if (rce) return rce;
+        }
+        std::vector<InstPlan> plans(1);
+        plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
+        plans[0].wins.assign(all.begin() + (long)cuts[c], all.begin() + (long)cuts[c + 1]);
+        // the global pipeline order, so that the chunks together make the
+        // same program order (and the same result) as one launch
+        plans[0].in_pipeline_order = true;
+        const int slot = b ? POOL_SCHED_ALT : POOL_SCHED;
+        SchedInfo inf;
+        int rc = sched_prepare(
+            plans, o, cm, num_sms(),
+            [slot](size_t bytes) -> void* {
+                void* p = nullptr;
+                return pool_get(slot, bytes, &p) ? nullptr : p;
+            },
+            &L[b], &inf, up);
+        if (rc) return rc;
+        tot.tasks += inf.tasks;
+        tot.cp_us += inf.cp_us;
+        tot.sim_us += inf.sim_us;
+        tot.graph_ms += inf.graph_ms;
+        tot.order_ms += inf.order_ms;
+        if (c == 0 && o.timing) GBR_CK(cudaEventRecord(ev.e[0], st), "event");
+        rc = sched_enqueue(L[b], st);
+        if (rc) return rc;
+        if (nch > 1) GBR_CK(cudaEventRecord(ev.e[2 + b], st), "event");
+        *ntasks_out += L[b].P.ntasks;
+    }
+    if (o.timing) GBR_CK(cudaEventRecord(ev.e[1], st), "event");
+    for (int c = std::max(0, nch - 2); c < nch; ++c) {
+        int rce = read_err(L[c & 1], st, &h_err);
+        if (rce) return rce;
+    }
     if (o.timing) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]) != cudaSuccess) {
             ms = 0.f;
             (void)cudaGetLastError();
         }
         *ms_out += ms;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
     }
-    const int nt = L.P.ntasks;
-    *ntasks_out += nt;
-    g_last_sched = inf;
-    if (L.trace_bytes) {
-        int rct = store_trace(L);
+    g_last_sched = tot;
+    if (nch == 1 && L[0].trace_bytes) {
+        int rct = store_trace(L[0]);
         if (rct) return rct;
     }
     if (h_err) {
@@ -751,6 +838,10 @@ void gbr_release(void) {
         if (g_pool[dev].ptr[s]) cudaFree(g_pool[dev].ptr[s]);
         g_pool[dev].ptr[s] = nullptr;
         g_pool[dev].bytes[s] = 0;
+    }
+    if (g_side[dev]) {
+        cudaStreamDestroy(g_side[dev]);
+        g_side[dev] = nullptr;
     }
 }
 

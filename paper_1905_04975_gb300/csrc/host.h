@@ -31,7 +31,7 @@ int num_sms();
 // Device scratch pool (api.cu): one grow-only allocation per device and slot;
 // callers hold api_mutex() while they use it.
 constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_SWEEP = 9,
-              POOL_SWEEP_SCHED = 10, POOL_NSLOTS = 11;
+              POOL_SWEEP_SCHED = 10, POOL_SCHED_ALT = 11, POOL_NSLOTS = 12;
 int pool_get(int slot, size_t bytes, void** out);
 std::mutex& api_mutex();
 
@@ -130,6 +130,7 @@ struct InstPlan {
     Inst d;                    // device pointers and sizes
     std::vector<Window> wins;  // planner order (pipeline order is applied here)
     int far = 0;               // far update-tile rows (0: far_rows(n))
+    bool in_pipeline_order = false;  // wins is already a part of a pipeline order
 };
 
 struct SchedInfo {

@@ -526,7 +526,7 @@ int sched_prepare(std::vector<InstPlan>& plans, const gbr_opts& o, const CostMod
     std::vector<TaskGraph> Gs(ni);
     const unsigned nth = std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()));
     auto work = [&](size_t i) {
-        pipeline_order(plans[i].d.n, plans[i].wins);
+        if (!plans[i].in_pipeline_order) pipeline_order(plans[i].d.n, plans[i].wins);
         build_graph(plans[i].d.n, plans[i].wins, plans[i].d.Q != nullptr, cm, Gs[i], plans[i].far,
                     ni >= 64 ? 1 : (int)nth, plans[i].d.T != nullptr && plans[i].d.Z != nullptr);
     };

@@ -420,6 +420,26 @@ def test_wide_window_rejections(gbr):
     assert k > 0
 
 
+@pytest.mark.parametrize("prec", ["fma", "ozaki"])
+def test_chunked_launches_match_one_launch(gbr, prec):
+    """A pass of more than 1024 windows runs as three consecutive persistent
+    launches whose task graphs are planned while the previous launch runs;
+    the chunks keep the program order of one launch, so the result is
+    bitwise the one of a single (traced, hence unchunked) launch, and it
+    matches the oracle."""
+    n = 1200
+    S, Q, sel = si.reorder_problem(n, 21, select_frac=0.5, q="householder", reflectors=8)
+    sub = np.append(np.diag(S, -1) != 0, False).astype(np.uint8)
+    assert len(gbr.plan(sub, sel, 16, 6)[0]) >= 1024
+    ref = oracle.reorder(S, Q, sel)
+    r1, S1, Q1 = run_gpu(gbr, S, Q, sel, window=16, chain=6, precision=prec)
+    assert r1.status == 0
+    check(S, Q, sel, r1, S1, Q1, ref)
+    r2, S2, Q2 = run_gpu(gbr, S, Q, sel, window=16, chain=6, precision=prec, timing=2)
+    assert len(gbr.last_trace()) == r2.stats.tasks == r1.stats.tasks
+    assert np.array_equal(S1, S2) and np.array_equal(Q1, Q2)
+
+
 @pytest.mark.parametrize("sched", ["sequential", "persistent"])
 def test_abort_on_first_rejection(gbr, sched):
     """on_reject = ABORT on the clustered kappa = 1e6 input (the rejection
