@@ -132,7 +132,8 @@ static int read_err(const SchedLaunch& L, cudaStream_t s, int* acc) {
 // alternate between the pool slots POOL_SCHED and POOL_SCHED_ALT.
 static int run_persistent(int n, const std::vector<Window>& wins, double* S, int ldS, double* Q,
                           int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
-                          long long* ntasks_out, double* ms_out, cudaStream_t st) {
+                          long long* ntasks_out, double* ms_out, long long* launches_out,
+                          cudaStream_t st) {
     std::vector<Window> all = wins;
     pipeline_order(n, all);
     const std::vector<size_t> cuts = chunk_cuts(all.size(), o);
@@ -196,6 +197,7 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
         if (rc) return rc;
         if (nch > 1) GBR_CK(cudaEventRecord(ev.e[2 + b], st), "event");
         *ntasks_out += L[b].P.ntasks;
+        if (L[b].P.ntasks > 0) *launches_out += 1;
     }
     if (o.timing) GBR_CK(cudaEventRecord(ev.e[1], st), "event");
     for (int c = std::max(0, nch - 2); c < nch; ++c) {
@@ -332,9 +334,9 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
         plan_pass(ps, o.window, o.chain, win, nchains);
         if (win.empty()) break;
         if (o.sched == GBR_SCHED_PERSISTENT) {
-            int rcs = run_persistent(n, win, S, ldS, Q, ldQ, d_sel, d_ctr, o, &ntasks, &ms_sched, st);
+            int rcs = run_persistent(n, win, S, ldS, Q, ldQ, d_sel, d_ctr, o, &ntasks, &ms_sched,
+                                     &launches, st);
             if (rcs) return rcs;
-            launches += 1;
             flops += update_flops(n, win, Q != nullptr);
         } else
         {
