@@ -35,6 +35,10 @@ namespace gbr {
 namespace win {
 
 constexpr int WIN_THREADS = 512;
+// Warps of a window task that compute the swap transforms while the others
+// apply the previous step's products (a multiple of 4: the same number on
+// each SM sub-partition).
+constexpr int WIN_TWARPS = 4;
 constexpr int MAXSW = WMAX / 2;  // at most one swap per two positions
 
 __device__ __forceinline__ int poff(int c) { return (c * (c + 3)) >> 1; }
@@ -246,19 +250,6 @@ __device__ __forceinline__ bool swap22_halfwarp(const double* __restrict__ Sp, i
 //   T_11: 1x1|1x1 (Givens), T_3: 1x2 or 2x1 (k = 3), T_22: 2x2|2x2 (k = 4).
 constexpr int T_11 = 0, T_3 = 1, T_22 = 2;
 
-// Warps of a CTA are spread over the SM's four sub-partitions by id % 4; the
-// types go to different sub-partitions so their FP64 streams do not queue
-// behind each other: 2x2|2x2 on partitions 0 and 1, k = 3 on 2, 1x1 on 3.
-__device__ __forceinline__ int type_of_warp(int warp) {
-    int part = warp & 3;
-    return part <= 1 ? T_22 : (part == 2 ? T_3 : T_11);
-}
-// rank of this warp among the warps serving its type
-__device__ __forceinline__ int rank_of_warp(int warp) {
-    int part = warp & 3;
-    return part <= 1 ? (warp >> 2) * 2 + part : (warp >> 2);
-}
-
 // Writes U's digit slices for the split-precision updates (ozaki.cuh): the
 // balanced base-256 digits of every entry relative to the largest exponent of
 // its column, as bf16, in the tensor cores' 128-byte-swizzled K-major layout
@@ -338,6 +329,79 @@ __device__ __forceinline__ void right_u_row(double* __restrict__ U, int w, int j
     for (int c = 0; c < K; ++c) U[(j + c) * w + r] = y[c];
 }
 
+// Left transformation of one swap on one column c of the packed window:
+// rows [j, j + K) of column c <- Z^T (those rows).
+template <int K>
+__device__ __forceinline__ void left_col(double* __restrict__ Sp, int j, int c,
+                                         const double* __restrict__ Z) {
+    double x[K], y[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) x[r] = Sp[poff(c) + j + r];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc = fma(Z[r * 4 + i], x[i], acc);
+        y[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) Sp[poff(c) + j + r] = y[r];
+}
+
+// Right transformation of one swap on one row r (< j) of the packed window:
+// columns [j, j + K) of row r <- (those columns) Z.
+template <int K>
+__device__ __forceinline__ void right_row(double* __restrict__ Sp, int j, int r,
+                                          const double* __restrict__ Z) {
+    double x[K], y[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) x[i] = Sp[poff(j + i) + r];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc = fma(x[i], Z[c * 4 + i], acc);
+        y[c] = acc;
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) Sp[poff(j + c) + r] = y[c];
+}
+
+// Last i in [0, cnt) with pre[i] <= it (pre is nondecreasing, pre[0] = 0).
+__device__ __forceinline__ int prefix_slot(const int* pre, int cnt, int it) {
+    int lo = 0, hi = cnt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Named barriers of the window task's two warp groups (barrier 0 is
+// __syncthreads): PRODUCTS among the product warps, CRIT from the product
+// warps (arrive) to the transform warps (wait).
+__device__ __forceinline__ void bar_products() {
+    asm volatile("bar.sync 1, %0;" ::"n"(WIN_THREADS - 32 * WIN_TWARPS) : "memory");
+}
+__device__ __forceinline__ void bar_crit_arrive() {
+    asm volatile("bar.arrive 2, %0;" ::"n"(WIN_THREADS) : "memory");
+}
+__device__ __forceinline__ void bar_crit_wait() {
+    asm volatile("bar.sync 2, %0;" ::"n"(WIN_THREADS) : "memory");
+}
+
+// Near-diagonal part of a step's products.  The next step's transforms read
+// only diagonal blocks (entries with c - r <= 3).  A left item (swap at j,
+// column c) is critical if c < j + CRIT_L, a right item of S (swap at j of
+// size k, row r) if r >= j + k - CRIT_R.  Every product reaching an entry
+// with c - r <= 3 is critical; no other product reaches one; and a left
+// item that shares an entry with a critical right item is critical itself
+// (c <= j2 + k2 - 1 <= r + 7 <= j1 + 10), so that applying all critical left
+// items, then all critical right items, then the other left items and the
+// other right items applies every entry's left transformation before its
+// right one, as the unsplit phases do.
+constexpr int CRIT_L = 11, CRIT_R = 8;
+
 // abort_word (ABORT on rejection, else null): a window task that starts
 // after it was set does nothing (U = I, *skip_out = 1); a window task that
 // rejects a swap sets it, finishes the step it is in, restores the standard
@@ -348,6 +412,19 @@ __device__ __forceinline__ void right_u_row(double* __restrict__ U, int w, int j
 // scratch, WIDE_SP_STRIDE doubles) and forms U in place in Ug (no split-
 // precision slices).  The steps are the same; only where the two arrays live
 // differs.
+//
+// The steps run as a two-stage pipeline over two groups of warps (blockDim
+// must be WIN_THREADS): while the product warps apply step q's left and
+// right transformations (to S and to U), the WIN_TWARPS transform warps,
+// the same number on each SM sub-partition, compute the transforms of
+// step q + 1.  Those read only the
+// diagonal blocks of step q + 1, so the product warps first apply the part
+// of step q that reaches near the diagonal (CRIT_L, CRIT_R), signal the
+// transform warps, and then the rest; the two groups touch disjoint entries
+// from there on.  Every entry receives the same operations in the same order
+// as in a step-by-step execution, so the result does not change.  The state
+// of a step (swap lists, transforms, prefix sums of the product work) is kept
+// for two steps, by the step's parity.
 template <int WM>
 __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int ldS, int s0, int w,
                                               uint8_t* __restrict__ gsel, double* __restrict__ Ug,
@@ -359,11 +436,9 @@ __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int
     static_assert(WM == WMAX || WM == WMAX_WIDE, "window kernel instances");
     constexpr bool WIDE = WM > WMAX;
     constexpr int MSW = WM / 2;  // at most one swap per two positions
-    // The state of a step (its swaps, their transforms and the prefix sums
-    // of their work) is kept for two steps, by the step's parity: the part
-    // of a step's right transformations that acts on U (rows of U, which no
-    // swap reads) is applied during the next step's transform phase, by the
-    // warps that have no transform of their own to compute.
+    constexpr int NTW = WIN_TWARPS;
+    static_assert(NTW % 4 == 0 && NTW < WIN_THREADS / 32, "transform warps per sub-partition");
+    constexpr int PTHREADS = WIN_THREADS - 32 * NTW;
     double* U = WIDE ? Ug : reinterpret_cast<double*>(smem_raw);        // w*w
     double* Sp = WIDE ? gsp : U + WM * WM;                               // packed window
     double* Zbuf = WIDE ? reinterpret_cast<double*>(smem_raw) : Sp + poff(WM);  // [2][MSW * 16]
@@ -373,17 +448,15 @@ __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int
     __shared__ int nsw, nrej, nacc;
     unsigned long long wflops = 0;   // per thread (phase D), summed at the end
     __shared__ int tcnt2[2][3];
-    __shared__ int tlist2[2][3][MSW];   // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
-    __shared__ int kpre_l[3][MSW + 1];  // prefix sums of left-apply columns per k group
-    __shared__ int kpre_s[3][MSW + 1];  // prefix sums of right-apply rows of S
-    __shared__ int kpre_u2[2][3][MSW + 1];  // prefix sums of right-apply rows of U
+    __shared__ int tlist2[2][3][MSW];     // slots per type (T_11, T_3, T_22: k = 2, 3, 4)
+    __shared__ int kpre_l2[2][3][MSW + 1];  // prefix sums of the far left-apply columns
+    __shared__ int kpre_s2[2][3][MSW + 1];  // prefix sums of the far right-apply rows of S
+    __shared__ int kpre_u2[2][3][MSW + 1];  // prefix sums of the right-apply rows of U
     // Rows [urlo[c], urhi[c]] hold every nonzero of column c of U: U starts as
     // I and a swap on columns [j, j+k) mixes only those columns, so the rows
     // outside the union of their ranges stay exactly zero and are skipped.
     __shared__ short urlo[WM], urhi[WM];
     __shared__ short slo2[2][MSW], shi2[2][MSW];  // per slot: U rows its right transform touches
-    __shared__ int pu_par;    // parity of the step whose U rows are pending, or -1
-    __shared__ int pu_next;   // next pending U row item to claim
 
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
@@ -419,7 +492,6 @@ __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int
     if (tid == 0) {
         nrej = 0;
         nacc = 0;
-        pu_par = -1;
         wall_top = s0 > 0 && __ldcg(&S[cm(s0, s0 - 1, ldS)]) != 0.0;
         wall_bot = s0 + w < n && __ldcg(&S[cm(s0 + w, s0 + w - 1, ldS)]) != 0.0;
     }
@@ -427,76 +499,17 @@ __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int
     if (tid == 0 && wall_top) sel[0] = SEL_WALL;
     if (tid == 0 && wall_bot) sel[w - 1] = SEL_WALL;
 
-    // The U rows of the right transformations of the step of parity pp,
-    // claimed by whole warps in chunks of 32 (pu_next): each item is one row
-    // of U for one swap, the swaps' items grouped by k and counted by the
-    // prefix sums kpre_u2[pp].
-    auto pending_u = [&](int pp) {
-        const int* pj = swbuf + pp * 3 * MSW;
-        const int* pk = pj + MSW;
-        const int T0 = kpre_u2[pp][0][tcnt2[pp][0]], T1 = kpre_u2[pp][1][tcnt2[pp][1]];
-        const int total = T0 + T1 + kpre_u2[pp][2][tcnt2[pp][2]];
-        for (;;) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&pu_next, 32);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base >= total) break;
-            const int it = base + lane;
-            if (it >= total) continue;
-            const int g = it < T0 ? 0 : (it < T0 + T1 ? 1 : 2);
-            const int itg = it - (g == 0 ? 0 : (g == 1 ? T0 : T0 + T1));
-            const int* pre = kpre_u2[pp][g];
-            int lo = 0, hi = tcnt2[pp][g] - 1;   // last i with pre[i] <= itg
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (pre[mid] <= itg) lo = mid; else hi = mid - 1;
-            }
-            const int slot = tlist2[pp][g][lo];
-            if (pk[slot] == 0) continue;  // rejected
-            const int j = pj[slot];
-            const int r = slo2[pp][slot] + (itg - pre[lo]);
-            const double* Z = Zbuf + pp * MSW * 16 + slot * 16;
-            if (g == 0) right_u_row<2>(U, w, j, r, Z);
-            else if (g == 1) right_u_row<3>(U, w, j, r, Z);
-            else right_u_row<4>(U, w, j, r, Z);
-        }
-    };
-
-    // Every accepted swap moves a selected block up and every rejected one
-    // retires a block, so the loop ends within w * w steps; the cap only
-    // guards against a logic error (reported through the counters).
-    bool final_pass = false;
-    for (int iter = 0;; ++iter) {
-        const int par = iter & 1;
-        double* Zs = Zbuf + par * MSW * 16;
-        int* swj = swbuf + par * 3 * MSW;
+    // --- phase A1 of the step of parity pi (integer work only): every
+    // selected block whose upper neighbour is an unselected block swaps with
+    // it.  In the final pass, the 2x2 blocks whose standard form has to be
+    // restored are listed instead (the fast swap paths leave it to this pass).
+    auto list_swaps = [&](int pi, bool fin) {
+        int* swj = swbuf + pi * 3 * MSW;
         int* swk = swj + MSW;
         int* swp = swk + MSW;
-        int (*tlist)[MSW] = tlist2[par];
-        int* tcnt = tcnt2[par];
-        short* slo = slo2[par];
-        short* shi = shi2[par];
-        int (*kpre_u)[MSW + 1] = kpre_u2[par];
-        __syncthreads();
-        if (abort_word && !final_pass && nrej > 0) {
-            // ABORT: the first rejection stops the reordering; this window
-            // only restores the standard form of its 2x2 blocks
-            final_pass = true;
-            if (tid == 0) atomicExch(abort_word, 1);
-        }
-        if (iter > 4 * WM * WM) {
-            if (tid == 0) atomicAdd(&ctr->step_overflow, 1);
-            break;
-        }
-        for (int i = tid; i < w; i += nth)
-            bst[i] = (i == 0) || (Sp[poff(i - 1) + i] == 0.0);
-        if (tid < 3) tcnt[tid] = 0;
-        if (tid == 0) nsw = 0;
-        __syncthreads();
-        // --- phase A1: find the swaps of this step (integer work only).  After the
-        // last swap, one more pass lists the 2x2 blocks whose standard form
-        // has to be restored (the fast swap paths leave it to this pass).
-        if (!final_pass) {
+        int (*tlist)[MSW] = tlist2[pi];
+        int* tcnt = tcnt2[pi];
+        if (!fin) {
             for (int t = tid; t < w; t += nth) {
                 if (t == 0 || !bst[t] || sel[t] != SEL_YES) continue;
                 int ja = bst[t - 1] ? t - 1 : t - 2;
@@ -523,246 +536,67 @@ __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int
                 tlist[T_11][atomicAdd(&tcnt[T_11], 1)] = slot;
             }
         }
-        __syncthreads();
-        const int ns = nsw;
-        if (ns == 0) {
-            // the previous step's U rows now, before its state is reused
-            if (pu_par >= 0) {
-                pending_u(pu_par);
-                __syncthreads();
-                if (tid == 0) pu_par = -1;
-            }
-            if (final_pass) break;
-            final_pass = true;
-            continue;
-        }
-        // --- phase A2: transforms, type-uniform warps
-        {
-            const int ty = type_of_warp(warp);
-            const int rank = rank_of_warp(warp);
-            if (ty == T_22) {
-                // two 2|2 swaps per warp, one per half-warp
-                const int h = lane >> 4, l = lane & 15;
-                const unsigned hmask = h ? 0xffff0000u : 0x0000ffffu;
-                const int nw = (WIN_THREADS / 32) / 2;
-                for (int i = rank * 2 + h; i < tcnt[T_22]; i += nw * 2) {
-                    const int slot = tlist[T_22][i];
-                    const int ja = swj[slot];
-                    double zrc = 0.0, dnrc = 0.0;
-                    bool fb = false;
-                    bool ok = swap22_halfwarp(Sp, ja, l, hmask, h * 16, strong != 0, &zrc, &dnrc, &fb);
-                    const int r = l & 3, c = l >> 2;
-                    if (ok) {
-                        Zs[slot * 16 + c * 4 + r] = zrc;
-                        if (r <= c + 1) Sp[poff(ja + c) + ja + r] = dnrc;
-                        if (l == 0) atomicAdd(&nacc, 1);
-                    } else if (l == 0) {
-                        double D[16], Zl[16], Dn[16];
-                        for (int cc = 0; cc < 4; ++cc)
-                            for (int rr = 0; rr < 4; ++rr)
-                                D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
-                        if (swap_transform(D, 2, 2, strong != 0, Zl, Dn)) {
-                            for (int cc = 0; cc < 4; ++cc)
-                                for (int rr = 0; rr <= min(cc + 1, 3); ++rr)
-                                    Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
-                            for (int e = 0; e < 16; ++e) Zs[slot * 16 + e] = Zl[e];
-                            atomicAdd(&nacc, 1);
-                        } else {
-                            swk[slot] = 0;
-                            swp[slot] = ja + 2;
-                            atomicAdd(&nrej, 1);
-                        }
-                    }
-                    __syncwarp(hmask);
-                }
-            } else {
-                const int nwarps_ty = (WIN_THREADS / 32) / 4;
-                for (int i = rank * 32 + lane; i < tcnt[ty]; i += nwarps_ty * 32) {
-                    const int slot = tlist[ty][i];
-                    const int ja = swj[slot], p = swp[slot], k = swk[slot], q = k - p;
-                    double* Z = &Zs[slot * 16];
-                    bool ok;
-                    if (ty == T_11 && p < 0) {
-                        // restore the standard form of the 2x2 block at ja
-                        double m[16];
-                        m[0] = Sp[poff(ja) + ja];
-                        m[1] = Sp[poff(ja) + ja + 1];
-                        m[4] = Sp[poff(ja + 1) + ja];
-                        m[5] = Sp[poff(ja + 1) + ja + 1];
-                        double cs, sn;
-                        standardize2(m, &cs, &sn);
-                        Sp[poff(ja) + ja] = m[0];
-                        Sp[poff(ja) + ja + 1] = m[1];
-                        Sp[poff(ja + 1) + ja] = m[4];
-                        Sp[poff(ja + 1) + ja + 1] = m[5];
-                        Z[0] = cs; Z[1] = sn; Z[4] = -sn; Z[5] = cs;
-                        ok = true;
-                    } else if (ty == T_11) {
-                        // Givens rotation from (t12, t22 - t11); always accepted
-                        double t11 = Sp[poff(ja) + ja], t12 = Sp[poff(ja + 1) + ja];
-                        double t22 = Sp[poff(ja + 1) + ja + 1];
-                        double c = 1.0, sn = 0.0, n12 = t12;
-                        if (t11 != t22) {
-                            double d = t22 - t11;
-                            double rh = 1.0 / sqrt(fma(t12, t12, d * d));
-                            c = t12 * rh;
-                            sn = d * rh;
-                            double r12 = fma(c, t12, sn * t22);
-                            n12 = fma(r12, c, -(c * t11) * sn);
-                        }
-                        Z[0] = c; Z[1] = sn; Z[4] = -sn; Z[5] = c;
-                        Sp[poff(ja) + ja] = t22;
-                        Sp[poff(ja) + ja + 1] = 0.0;
-                        Sp[poff(ja + 1) + ja] = n12;
-                        Sp[poff(ja + 1) + ja + 1] = t11;
-                        ok = true;
-                    } else {
-                        double D[16], Zl[16], Dn[16];
-                        for (int cc = 0; cc < 3; ++cc)
-                            for (int rr = 0; rr < 3; ++rr)
-                                D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
-                        ok = swap3_fast(D, p, strong != 0, Zl, Dn) ||
-                             swap_transform(D, p, q, strong != 0, Zl, Dn);
-                        if (ok) {
-                            for (int cc = 0; cc < 3; ++cc)
-                                for (int rr = 0; rr <= min(cc + 1, 2); ++rr)
-                                    Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
-                            for (int e = 0; e < 16; ++e) Z[e] = Zl[e];
-                        }
-                    }
-                    if (ok) {
-                        if (p >= 0) atomicAdd(&nacc, 1);
-                    } else {
-                        swk[slot] = 0;
-                        swp[slot] = ja + p;   // the stuck (selected) block
-                        atomicAdd(&nrej, 1);
-                    }
-                }
-            }
-            // Prefix sums of the apply work per k group, one warp per group:
-            // the T_11 warps of rank 1..3 (the Givens rotations of a step fit
-            // in rank 0's 32 lanes, so these are otherwise idle), integer
-            // work that overlaps the FP64 transforms of the other warps.  All
-            // listed swaps are counted; a rejected one is skipped when
-            // applied.  k comes from the group (A2 zeroes swk of a rejection).
-            if (ty == T_11 && rank >= 1) {
-                const int g = rank - 1, k = g + 2, cnt = tcnt[g];
-                int runl = 0, runr = 0, runu = 0;
-                for (int base = 0; base < cnt; base += 32) {
-                    int i = base + lane;
-                    int nl = 0, nr = 0, nu = 0;
-                    if (i < cnt) {
-                        const int slot = tlist[g][i], j = swj[slot];
-                        int lo = urlo[j], hi = urhi[j];
-                        for (int c = 1; c < k; ++c) {
-                            lo = min(lo, (int)urlo[j + c]);
-                            hi = max(hi, (int)urhi[j + c]);
-                        }
-                        slo[slot] = (short)lo;
-                        shi[slot] = (short)hi;
-                        nl = w - j - k;
-                        nr = j;
-                        nu = hi - lo + 1;
-                    }
-                    int il = nl, ir = nr, iu = nu;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        int a = __shfl_up_sync(0xffffffffu, il, o);
-                        int b2 = __shfl_up_sync(0xffffffffu, ir, o);
-                        int c2 = __shfl_up_sync(0xffffffffu, iu, o);
-                        if (lane >= o) { il += a; ir += b2; iu += c2; }
-                    }
-                    if (i < cnt) {
-                        kpre_l[g][i + 1] = runl + il;
-                        kpre_s[g][i + 1] = runr + ir;
-                        kpre_u[g][i + 1] = runu + iu;
-                    }
-                    runl += __shfl_sync(0xffffffffu, il, 31);
-                    runr += __shfl_sync(0xffffffffu, ir, 31);
-                    runu += __shfl_sync(0xffffffffu, iu, 31);
-                }
-                if (lane == 0) {
-                    kpre_l[g][0] = 0;
-                    kpre_s[g][0] = 0;
-                    kpre_u[g][0] = 0;
-                }
-            }
-            // the previous step's U rows, by each warp once its own
-            // transforms are done; while 2|2 swaps are computed (on
-            // sub-partitions 0 and 1) only the warps of sub-partitions 2 and
-            // 3 take them, so that those latency chains keep their FP64 pipes
-            if (pu_par >= 0 && ((warp & 3) >= 2 || tcnt[T_22] == 0)) pending_u(pu_par);
-        }
-        __syncthreads();
-        // --- phase B: left transformations, rows [j, j+k) x columns [j+k, w),
-        // compacted per k so that every lane of a warp runs the same k
-#pragma unroll
+    };
+
+    // Prefix sums of the product work of the step of parity pi, per k group,
+    // by one warp: far left columns, far right rows of S, right rows of U
+    // (whose range per swap, from urlo/urhi, it also records).  All listed
+    // swaps are counted; a rejected one is skipped when applied.
+    auto prefix_sums = [&](int pi) {
+        const int* swj = swbuf + pi * 3 * MSW;
+#pragma unroll 1
         for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = tcnt[g], total = kpre_l[g][cnt];
-            for (int it = tid; it < total; it += nth) {
-                int lo = 0, hi = cnt - 1;   // last i with kpre_l[g][i] <= it
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (kpre_l[g][mid] <= it) lo = mid; else hi = mid - 1;
+            const int k = g + 2, cnt = tcnt2[pi][g];
+            int runl = 0, runr = 0, runu = 0;
+            for (int base = 0; base < cnt; base += 32) {
+                const int i = base + lane;
+                int nl = 0, nr = 0, nu = 0;
+                if (i < cnt) {
+                    const int slot = tlist2[pi][g][i], j = swj[slot];
+                    int lo = urlo[j], hi = urhi[j];
+                    for (int c = 1; c < k; ++c) {
+                        lo = min(lo, (int)urlo[j + c]);
+                        hi = max(hi, (int)urhi[j + c]);
+                    }
+                    slo2[pi][slot] = (short)lo;
+                    shi2[pi][slot] = (short)hi;
+                    nl = max(0, w - j - CRIT_L);
+                    nr = max(0, j + k - CRIT_R);
+                    nu = hi - lo + 1;
                 }
-                const int slot = tlist[g][lo];
-                if (swk[slot] == 0) continue;  // rejected
-                const int j = swj[slot];
-                const int c = j + k + (it - kpre_l[g][lo]);
-                const double* Z = &Zs[slot * 16];
-                double x[4], y[4];
-#pragma unroll
-                for (int r = 0; r < k; ++r) x[r] = Sp[poff(c) + j + r];
-#pragma unroll
-                for (int r = 0; r < k; ++r) {
-                    double acc = 0.0;
-#pragma unroll
-                    for (int i = 0; i < k; ++i) acc = fma(Z[r * 4 + i], x[i], acc);
-                    y[r] = acc;
+                int il = nl, ir = nr, iu = nu;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int a = __shfl_up_sync(0xffffffffu, il, o);
+                    int b2 = __shfl_up_sync(0xffffffffu, ir, o);
+                    int c2 = __shfl_up_sync(0xffffffffu, iu, o);
+                    if (lane >= o) { il += a; ir += b2; iu += c2; }
                 }
-#pragma unroll
-                for (int r = 0; r < k; ++r) Sp[poff(c) + j + r] = y[r];
+                if (i < cnt) {
+                    kpre_l2[pi][g][i + 1] = runl + il;
+                    kpre_s2[pi][g][i + 1] = runr + ir;
+                    kpre_u2[pi][g][i + 1] = runu + iu;
+                }
+                runl += __shfl_sync(0xffffffffu, il, 31);
+                runr += __shfl_sync(0xffffffffu, ir, 31);
+                runu += __shfl_sync(0xffffffffu, iu, 31);
+            }
+            if (lane == 0) {
+                kpre_l2[pi][g][0] = 0;
+                kpre_s2[pi][g][0] = 0;
+                kpre_u2[pi][g][0] = 0;
             }
         }
-        __syncthreads();
-        // --- phase C: right transformations, columns [j, j+k) of S rows [0, j)
-        // (their rows of U follow during the next step's transforms)
-#pragma unroll
-        for (int g = 0; g < 3; ++g) {
-            const int k = g + 2, cnt = tcnt[g], total = kpre_s[g][cnt];
-            for (int it = tid; it < total; it += nth) {
-                int lo = 0, hi = cnt - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (kpre_s[g][mid] <= it) lo = mid; else hi = mid - 1;
-                }
-                const int slot = tlist[g][lo];
-                if (swk[slot] == 0) continue;  // rejected
-                const int j = swj[slot];
-                const int r = it - kpre_s[g][lo];
-                const double* Z = &Zs[slot * 16];
-                double x[4], y[4];
-#pragma unroll
-                for (int i = 0; i < k; ++i) x[i] = Sp[poff(j + i) + r];
-#pragma unroll
-                for (int c = 0; c < k; ++c) {
-                    double acc = 0.0;
-#pragma unroll
-                    for (int i = 0; i < k; ++i) acc = fma(x[i], Z[c * 4 + i], acc);
-                    y[c] = acc;
-                }
-#pragma unroll
-                for (int c = 0; c < k; ++c) Sp[poff(j + c) + r] = y[c];
-            }
-        }
-        __syncthreads();
-        // this step's U rows are pending now
-        if (tid == 0) {
-            pu_par = par;
-            pu_next = 0;
-        }
-        // --- phase D: move the selection flags with the blocks; widen the U
-        // row ranges of the columns each accepted transform mixed
-        for (int sw = tid; sw < ns; sw += nth) {
+    };
+
+    // --- phase D of the step of parity pp with nsq swaps: move the
+    // selection flags with the blocks; widen the U row ranges of the columns
+    // each accepted transform mixed; a stuck 2x2 block is flagged on both of
+    // its rows.  Needs the step's transforms only (not its products).
+    auto phase_d = [&](int pp, int nsq) {
+        const int* swj = swbuf + pp * 3 * MSW;
+        const int* swk = swj + MSW;
+        const int* swp = swk + MSW;
+        for (int sw = tid; sw < nsq; sw += nth) {
             int j = swj[sw], k = swk[sw];
             if (k == 0) {
                 sel[swp[sw]] = SEL_STUCK;
@@ -770,24 +604,307 @@ __device__ __forceinline__ void window_body_t(int n, double* __restrict__ S, int
             }
             // in-window flops of this accepted transform: k x k applied to
             // w - j - k columns (left) and j rows of S + its U rows (right)
-            wflops += 2ull * k * k * (unsigned long long)((w - j - k) + j + (shi[sw] - slo[sw] + 1));
+            wflops += 2ull * k * k *
+                      (unsigned long long)((w - j - k) + j + (shi2[pp][sw] - slo2[pp][sw] + 1));
             for (int c = 0; c < k; ++c) {
-                urlo[j + c] = slo[sw];
-                urhi[j + c] = shi[sw];
+                urlo[j + c] = slo2[pp][sw];
+                urhi[j + c] = shi2[pp][sw];
             }
             int p = swp[sw], q = k - p;
             if (p < 0) continue;   // standardization: blocks do not move
             for (int i = 0; i < q; ++i) sel[j + i] = SEL_YES;
             for (int i = q; i < k; ++i) sel[j + i] = SEL_NO;
         }
-        // a stuck 2x2 block is flagged on both of its rows
         __syncthreads();
         for (int t = tid; t + 1 < w; t += nth)
             if (sel[t] == SEL_STUCK && Sp[poff(t) + t + 1] != 0.0) sel[t + 1] = SEL_STUCK;
+    };
+
+    // --- phase A2 of the step of parity pi, by the transform warps (warps
+    // 0 .. NTW - 1, NTW / 4 per sub-partition; type-uniform, since an FP64
+    // issue costs the same for 1 or 32 active lanes): 2|2 swaps on
+    // sub-partitions 0 and 1 (one per half-warp), k = 3 on 2, 1|1 rotations
+    // on 3.
+    auto transforms = [&](int pi) {
+        double* Zs = Zbuf + pi * MSW * 16;
+        int* swj = swbuf + pi * 3 * MSW;
+        int* swk = swj + MSW;
+        int* swp = swk + MSW;
+        const int (*tlist)[MSW] = tlist2[pi];
+        const int* tcnt = tcnt2[pi];
+        const int part = warp & 3, rank = warp >> 2;
+        constexpr int NRANK = NTW / 4;
+        const int ty = part <= 1 ? T_22 : (part == 2 ? T_3 : T_11);
+        if (ty == T_22) {
+            // two 2|2 swaps per warp, one per half-warp
+            const int h = lane >> 4, l = lane & 15;
+            const unsigned hmask = h ? 0xffff0000u : 0x0000ffffu;
+            for (int i = (rank * 2 + part) * 2 + h; i < tcnt[T_22]; i += 4 * NRANK) {
+                const int slot = tlist[T_22][i];
+                const int ja = swj[slot];
+                double zrc = 0.0, dnrc = 0.0;
+                bool fb = false;
+                bool ok = swap22_halfwarp(Sp, ja, l, hmask, h * 16, strong != 0, &zrc, &dnrc, &fb);
+                const int r = l & 3, c = l >> 2;
+                if (ok) {
+                    Zs[slot * 16 + c * 4 + r] = zrc;
+                    if (r <= c + 1) Sp[poff(ja + c) + ja + r] = dnrc;
+                    if (l == 0) atomicAdd(&nacc, 1);
+                } else if (l == 0) {
+                    double D[16], Zl[16], Dn[16];
+                    for (int cc = 0; cc < 4; ++cc)
+                        for (int rr = 0; rr < 4; ++rr)
+                            D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
+                    if (swap_transform(D, 2, 2, strong != 0, Zl, Dn)) {
+                        for (int cc = 0; cc < 4; ++cc)
+                            for (int rr = 0; rr <= min(cc + 1, 3); ++rr)
+                                Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
+                        for (int e = 0; e < 16; ++e) Zs[slot * 16 + e] = Zl[e];
+                        atomicAdd(&nacc, 1);
+                    } else {
+                        swk[slot] = 0;
+                        swp[slot] = ja + 2;
+                        atomicAdd(&nrej, 1);
+                    }
+                }
+                __syncwarp(hmask);
+            }
+            return;
+        }
+        for (int i = rank * 32 + lane; i < tcnt[ty]; i += 32 * NRANK) {
+            const int slot = tlist[ty][i];
+            const int ja = swj[slot], p = swp[slot], k = swk[slot], q = k - p;
+            double* Z = &Zs[slot * 16];
+            bool ok;
+            if (ty == T_11 && p < 0) {
+                // restore the standard form of the 2x2 block at ja
+                double m[16];
+                m[0] = Sp[poff(ja) + ja];
+                m[1] = Sp[poff(ja) + ja + 1];
+                m[4] = Sp[poff(ja + 1) + ja];
+                m[5] = Sp[poff(ja + 1) + ja + 1];
+                double cs, sn;
+                standardize2(m, &cs, &sn);
+                Sp[poff(ja) + ja] = m[0];
+                Sp[poff(ja) + ja + 1] = m[1];
+                Sp[poff(ja + 1) + ja] = m[4];
+                Sp[poff(ja + 1) + ja + 1] = m[5];
+                Z[0] = cs; Z[1] = sn; Z[4] = -sn; Z[5] = cs;
+                ok = true;
+            } else if (ty == T_11) {
+                // Givens rotation from (t12, t22 - t11); always accepted
+                double t11 = Sp[poff(ja) + ja], t12 = Sp[poff(ja + 1) + ja];
+                double t22 = Sp[poff(ja + 1) + ja + 1];
+                double c = 1.0, sn = 0.0, n12 = t12;
+                if (t11 != t22) {
+                    double d = t22 - t11;
+                    double rh = 1.0 / sqrt(fma(t12, t12, d * d));
+                    c = t12 * rh;
+                    sn = d * rh;
+                    double r12 = fma(c, t12, sn * t22);
+                    n12 = fma(r12, c, -(c * t11) * sn);
+                }
+                Z[0] = c; Z[1] = sn; Z[4] = -sn; Z[5] = c;
+                Sp[poff(ja) + ja] = t22;
+                Sp[poff(ja) + ja + 1] = 0.0;
+                Sp[poff(ja + 1) + ja] = n12;
+                Sp[poff(ja + 1) + ja + 1] = t11;
+                ok = true;
+            } else {
+                double D[16], Zl[16], Dn[16];
+                for (int cc = 0; cc < 3; ++cc)
+                    for (int rr = 0; rr < 3; ++rr)
+                        D[cc * 4 + rr] = (rr <= cc + 1) ? Sp[poff(ja + cc) + ja + rr] : 0.0;
+                ok = swap3_fast(D, p, strong != 0, Zl, Dn) ||
+                     swap_transform(D, p, q, strong != 0, Zl, Dn);
+                if (ok) {
+                    for (int cc = 0; cc < 3; ++cc)
+                        for (int rr = 0; rr <= min(cc + 1, 2); ++rr)
+                            Sp[poff(ja + cc) + ja + rr] = Dn[cc * 4 + rr];
+                    for (int e = 0; e < 16; ++e) Z[e] = Zl[e];
+                }
+            }
+            if (ok) {
+                if (p >= 0) atomicAdd(&nacc, 1);
+            } else {
+                swk[slot] = 0;
+                swp[slot] = ja + p;   // the stuck (selected) block
+                atomicAdd(&nrej, 1);
+            }
+        }
+    };
+
+    // --- phases B and C of the step of parity pp, by the product warps:
+    // critical left items, critical right items of S (then the transform
+    // warps may start), far left items, far right items of S and the right
+    // items of U.  Within each part the items are grouped by k so that the
+    // lanes of a warp run the same k, and whole warps claim 32 items at a
+    // time (claim counters pclaim): an FP64 instruction holds its
+    // sub-partition's pipe for the same time with 1 or 32 lanes, and the
+    // transform warps load some sub-partitions' pipes more than others, so
+    // the warps of the less loaded sub-partitions take more items.
+    // has = the step had swaps; the barriers run either way.
+    __shared__ int pclaim[5][3];
+    auto products = [&](int pp, bool has) {
+        const double* Zs = Zbuf + pp * MSW * 16;
+        const int* swj = swbuf + pp * 3 * MSW;
+        const int* swk = swj + MSW;
+        const int (*tlist)[MSW] = tlist2[pp];
+        const int* tcnt = tcnt2[pp];
+        constexpr int NCL = CRIT_L - 2, NCR = CRIT_R - 2;  // item slots per swap
+        // next item of part `ph`, group g for this lane (or >= total: done)
+        auto claim = [&](int ph, int g) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&pclaim[ph][g], 32);
+            return __shfl_sync(0xffffffffu, base, 0) + lane;
+        };
+        if (has) {
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const int k = g + 2, total = tcnt[g] * NCL;
+                for (int it = claim(0, g); it - lane < total; it = claim(0, g)) {
+                    if (it >= total) continue;
+                    const int slot = tlist[g][it / NCL];
+                    if (swk[slot] == 0) continue;  // rejected
+                    const int j = swj[slot], c = j + k + it % NCL;
+                    if (c >= min(w, j + CRIT_L)) continue;
+                    const double* Z = Zs + slot * 16;
+                    if (g == 0) left_col<2>(Sp, j, c, Z);
+                    else if (g == 1) left_col<3>(Sp, j, c, Z);
+                    else left_col<4>(Sp, j, c, Z);
+                }
+            }
+        }
+        bar_products();
+        if (has) {
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const int k = g + 2, total = tcnt[g] * NCR;
+                for (int it = claim(1, g); it - lane < total; it = claim(1, g)) {
+                    if (it >= total) continue;
+                    const int slot = tlist[g][it / NCR];
+                    if (swk[slot] == 0) continue;
+                    const int j = swj[slot], r = j - 1 - it % NCR;
+                    if (r < max(0, j + k - CRIT_R)) continue;
+                    const double* Z = Zs + slot * 16;
+                    if (g == 0) right_row<2>(Sp, j, r, Z);
+                    else if (g == 1) right_row<3>(Sp, j, r, Z);
+                    else right_row<4>(Sp, j, r, Z);
+                }
+            }
+        }
+        __threadfence_block();
+        bar_crit_arrive();
+        if (has) {
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const int cnt = tcnt[g];
+                const int* pre = kpre_l2[pp][g];
+                const int total = pre[cnt];
+                for (int it = claim(2, g); it - lane < total; it = claim(2, g)) {
+                    if (it >= total) continue;
+                    const int lo = prefix_slot(pre, cnt, it);
+                    const int slot = tlist[g][lo];
+                    if (swk[slot] == 0) continue;
+                    const int j = swj[slot], c = j + CRIT_L + (it - pre[lo]);
+                    const double* Z = Zs + slot * 16;
+                    if (g == 0) left_col<2>(Sp, j, c, Z);
+                    else if (g == 1) left_col<3>(Sp, j, c, Z);
+                    else left_col<4>(Sp, j, c, Z);
+                }
+            }
+        }
+        bar_products();
+        if (has) {
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const int cnt = tcnt[g];
+                const int* pre = kpre_s2[pp][g];
+                const int total = pre[cnt];
+                for (int it = claim(3, g); it - lane < total; it = claim(3, g)) {
+                    if (it >= total) continue;
+                    const int lo = prefix_slot(pre, cnt, it);
+                    const int slot = tlist[g][lo];
+                    if (swk[slot] == 0) continue;
+                    const int j = swj[slot], r = it - pre[lo];
+                    const double* Z = Zs + slot * 16;
+                    if (g == 0) right_row<2>(Sp, j, r, Z);
+                    else if (g == 1) right_row<3>(Sp, j, r, Z);
+                    else right_row<4>(Sp, j, r, Z);
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const int cnt = tcnt[g];
+                const int* pre = kpre_u2[pp][g];
+                const int total = pre[cnt];
+                for (int it = claim(4, g); it - lane < total; it = claim(4, g)) {
+                    if (it >= total) continue;
+                    const int lo = prefix_slot(pre, cnt, it);
+                    const int slot = tlist[g][lo];
+                    if (swk[slot] == 0) continue;
+                    const int j = swj[slot], r = slo2[pp][slot] + (it - pre[lo]);
+                    const double* Z = Zs + slot * 16;
+                    if (g == 0) right_u_row<2>(U, w, j, r, Z);
+                    else if (g == 1) right_u_row<3>(U, w, j, r, Z);
+                    else right_u_row<4>(U, w, j, r, Z);
+                }
+            }
+        }
+    };
+
+    // Step pipeline.  Iteration i: the selection flags of step i - 1 move
+    // (phase D), step i's swaps are listed (phase A1), then the product warps
+    // apply step i - 1 while the transform warps compute step i.  Every
+    // accepted swap moves a selected block up and every rejected one retires
+    // a block, so the steps end within w * w; the cap only guards against a
+    // logic error (reported through the counters).
+    bool final_pass = false, overflow = false;
+    int ns_prev = 0;
+    for (int iter = 0;; ++iter) {
+        const int pi = iter & 1, pp = pi ^ 1;
+        if (ns_prev > 0) phase_d(pp, ns_prev);
+        __syncthreads();
+        if (abort_word && !final_pass && nrej > 0) {
+            // ABORT: the first rejection stops the reordering; this window
+            // only restores the standard form of its 2x2 blocks
+            final_pass = true;
+            if (tid == 0) atomicExch(abort_word, 1);
+        }
+        if (iter > 4 * WM * WM && !overflow) {
+            if (tid == 0) atomicAdd(&ctr->step_overflow, 1);
+            overflow = true;
+        }
+        for (int i = tid; i < w; i += nth) bst[i] = (i == 0) || (Sp[poff(i - 1) + i] == 0.0);
+        if (tid < 3) tcnt2[pi][tid] = 0;
+        if (tid < 15) pclaim[tid / 3][tid % 3] = 0;
+        if (tid == 0) nsw = 0;
+        __syncthreads();
+        if (!overflow) list_swaps(pi, final_pass);
+        __syncthreads();
+        int ns = nsw;
+        if (ns == 0 && !final_pass && !overflow) {
+            // after the last swap: the pass that restores standard forms
+            final_pass = true;
+            __syncthreads();
+            if (tid < 3) tcnt2[pi][tid] = 0;
+            if (tid == 0) nsw = 0;
+            __syncthreads();
+            list_swaps(pi, true);
+            __syncthreads();
+            ns = nsw;
+        }
+        if (warp < NTW) {
+            if (warp == NTW - 1 && ns > 0) prefix_sums(pi);
+            bar_crit_wait();
+            if (ns > 0) transforms(pi);
+        } else {
+            products(pp, ns_prev > 0);
+        }
+        __syncthreads();
+        ns_prev = ns;
+        if (ns == 0) break;
     }
-    // the last step's U rows
-    __syncthreads();
-    if (pu_par >= 0) pending_u(pu_par);
     __shared__ unsigned long long wfl_sum;
     if (tid == 0) wfl_sum = 0;
     __syncthreads();
