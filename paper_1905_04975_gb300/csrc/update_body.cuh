@@ -290,15 +290,45 @@ __device__ __forceinline__ void update_tile_fma(double* base, long long rs, long
         }
     }
     __syncthreads();
+    // A short tile (the last rows of a task) packs q column groups into a
+    // warp, 32 / q lanes each, so that its FMA instructions carry as many
+    // active lanes as a full tile's.  The q groups of a warp run over the
+    // union of their row ranges; outside its own range a group's entries of
+    // U are zero, and adding their products (+-0) leaves each sum unchanged.
+    const int q = rows > 32 ? 1 : (rows > 16 ? 2 : 4);
+    const int lpg = 32 / q, sub = lane / lpg;
+    const int nunits = (ng + q - 1) / q;
+    auto unit_range = [&](int gu, int* lo, int* hi) {
+        int a = wp, b = 0;
+        for (int t = 0; t < q; ++t) {
+            const int gg = gu * q + t;
+            if (gg < ng && g_lo[gg] < g_hi[gg]) {
+                a = min(a, g_lo[gg]);
+                b = max(b, g_hi[gg]);
+            }
+        }
+        *lo = a < b ? a : 0;
+        *hi = a < b ? b : 0;
+    };
     if (issued && tid == 0) {
         unsigned long long f = 0;
-        for (int g = 0; g < ng; ++g)
-            f += 2ull * rows * (unsigned long long)min(8, w - 8 * g) * (g_hi[g] - g_lo[g]);
+        for (int gu = 0; gu < nunits; ++gu) {
+            int lo, hi;
+            unit_range(gu, &lo, &hi);
+            for (int t = 0; t < q; ++t) {
+                const int gg = gu * q + t;
+                if (gg < ng) f += 2ull * rows * (unsigned long long)min(8, w - 8 * gg) * (hi - lo);
+            }
+        }
         atomicAdd(issued, f);
     }
-    const int ra = 2 * lane;
-    for (int g = warp; g < ng; g += nw) {
-        const int lo = g_lo[g], hi = g_hi[g];
+    const int ra = 2 * (lane % lpg);
+    for (int gu = warp; gu < nunits; gu += nw) {
+        int lo, hi;
+        unit_range(gu, &lo, &hi);
+        const int g = gu * q + sub;
+        const bool gv = g < ng;
+        const int gl = gv ? g : 0;  // lanes past the last group read a valid one
         double acc[2][8];
 #pragma unroll
         for (int i = 0; i < 2; ++i)
@@ -312,9 +342,9 @@ __device__ __forceinline__ void update_tile_fma(double* base, long long rs, long
                 // k < hi <= w: the rows beyond w of U are zero, never in [lo, hi)
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
-                    u[j] = (8 * g + j < w) ? __ldcg(&Ug[(size_t)(8 * g + j) * w + k]) : 0.0;
+                    u[j] = (8 * gl + j < w) ? __ldcg(&Ug[(size_t)(8 * gl + j) * w + k]) : 0.0;
             } else {
-                const double2* u2 = reinterpret_cast<const double2*>(Us + 8 * g + k * LDU);
+                const double2* u2 = reinterpret_cast<const double2*>(Us + 8 * gl + k * LDU);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const double2 t = u2[j];
@@ -329,14 +359,16 @@ __device__ __forceinline__ void update_tile_fma(double* base, long long rs, long
             }
         }
         // write back (in place: the tile's rows were all read before)
+        if (gv) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int r = ra + i;
-            if (r >= rows) continue;
+            for (int i = 0; i < 2; ++i) {
+                const int r = ra + i;
+                if (r >= rows) continue;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int k = 8 * g + j;
-                if (k < w) __stcg(&base[(long long)(r0 + r) * rs + (long long)k * ks], acc[i][j]);
+                for (int j = 0; j < 8; ++j) {
+                    const int k = 8 * g + j;
+                    if (k < w) __stcg(&base[(long long)(r0 + r) * rs + (long long)k * ks], acc[i][j]);
+                }
             }
         }
     }
