@@ -76,9 +76,9 @@ METRIC = "selected eigenvalues reordered per second"
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the current kernels (the sched_kernel captures under profiles/);
 # a workload has no entry while no capture of the current build exists.
-NCU_TRAFFIC = {("n4000", "dmma"): 1.909980e9 + 2.635823e9,
-               ("n4000", "fma"): 1.267562e9 + 2.714466e9,
-               ("n4000", "ozaki"): 2.875677e9 + 4.349368e9,
+NCU_TRAFFIC = {("n4000", "dmma"): 1.937360e9 + 2.652817e9,
+               ("n4000", "fma"): 1.299070e9 + 2.728422e9,
+               ("n4000", "ozaki"): 2.886808e9 + 4.348523e9,
                ("eigvec4000", "evgemm"): 1.052943e9 + 0.125283e9,
                ("g4000", "persistent-dmma"): 11.265847e9 + 13.376260e9,
                ("h4000", "persistent-dmma"): 0.220709e9 + 0.187885e9}
