@@ -440,6 +440,23 @@ def test_chunked_launches_match_one_launch(gbr, prec):
     assert np.array_equal(S1, S2) and np.array_equal(Q1, Q2)
 
 
+def test_chunked_launches_with_rejections(gbr):
+    """Chunked passes that reject swaps (clustered kappa = 1e6 law, 3080
+    windows in the first pass): the re-planned passes run chunked too, and
+    the whole result is bitwise that of single traced launches."""
+    n = 1200
+    S, Q, sel = si.reorder_problem(n, 11, select_frac=0.5, clusters=True, spread=1e-6,
+                                   kappa=1e6)
+    r1, S1, Q1 = run_gpu(gbr, S, Q, sel, window=16, chain=6)
+    assert r1.status > 0 and r1.m == expected_order(S, sel)[1]
+    assert is_standard(S1)
+    assert residual(Q @ S @ Q.T, S1, Q1) <= 50 * n * EPS
+    assert orth_err(Q1) <= 50 * n * EPS
+    r2, S2, Q2 = run_gpu(gbr, S, Q, sel, window=16, chain=6, timing=2)
+    assert r2.status == r1.status and r2.stats.swaps == r1.stats.swaps
+    assert np.array_equal(S1, S2) and np.array_equal(Q1, Q2)
+
+
 @pytest.mark.parametrize("sched", ["sequential", "persistent"])
 def test_abort_on_first_rejection(gbr, sched):
     """on_reject = ABORT on the clustered kappa = 1e6 input (the rejection
