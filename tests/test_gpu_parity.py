@@ -440,6 +440,22 @@ def test_chunked_launches_match_one_launch(gbr, prec):
     assert np.array_equal(S1, S2) and np.array_equal(Q1, Q2)
 
 
+def test_chunked_wide_windows(gbr):
+    """Wide windows (130) in a pass of more than 1024 windows: the wide
+    scheduler instance in three chunked launches, against the oracle and
+    bitwise against a single traced launch."""
+    n = 1500
+    S, Q, sel = si.reorder_problem(n, 21, select_frac=0.5, q="householder", reflectors=8)
+    sub = np.append(np.diag(S, -1) != 0, False).astype(np.uint8)
+    assert len(gbr.plan(sub, sel, 130, 2)[0]) >= 1024
+    ref = oracle.reorder(S, Q, sel)
+    r1, S1, Q1 = run_gpu(gbr, S, Q, sel, window=130, chain=2, precision="fma")
+    assert r1.status == 0
+    check(S, Q, sel, r1, S1, Q1, ref)
+    r2, S2, Q2 = run_gpu(gbr, S, Q, sel, window=130, chain=2, precision="fma", timing=2)
+    assert np.array_equal(S1, S2) and np.array_equal(Q1, Q2)
+
+
 def test_chunked_launches_with_rejections(gbr):
     """Chunked passes that reject swaps (clustered kappa = 1e6 law, 3080
     windows in the first pass): the re-planned passes run chunked too, and
