@@ -50,7 +50,10 @@ import schur_inputs as si  # noqa: E402
 WORKLOADS = {
     "n4000": dict(name="n4000", n=4000, select=0.35, q="64 Householder reflectors", window=128,
                   chain=64),
-    "n400": dict(name="n400", n=400, select=0.30, q="identity", window=128, chain=64),
+    # n = 400 is latency bound (a few chains of window tasks): the smaller
+    # window measured fastest for it (window sweep on the GPU: 6.26 ms per
+    # step at w = 32, m = 16 against 8.09 ms at 128, 64)
+    "n400": dict(name="n400", n=400, select=0.30, q="identity", window=32, chain=16),
     "n16000c": dict(name="n16000c", n=16000, select=0.50, q="64 Householder reflectors",
                     window=128, chain=64, clusters="20 clusters, spread 1e-6"),
     "batch4096": dict(name="batch4096", kind="batch", count=4096, nmin=32, nmax=512,
