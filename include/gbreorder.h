@@ -590,7 +590,10 @@ int gbr_plan(int n, const unsigned char *sub, const int *select, int window, int
 
 /*
  * Timeline of the last persistent-scheduler launch made with opts.timing = 2
- * (tracing; no counterpart in the paper).  Writes up to max_tasks records of
+ * by gbr_reorder, gbr_reorder_host (a pass of a single launch: traced calls
+ * are not cut into chunks) or gbr_batch_run (the batch's scheduler launch;
+ * window indices run over all instances in their order) (tracing; no
+ * counterpart in the paper).  Writes up to max_tasks records of
  * 8 long longs each, in queue order: task kind (0 window, 1 left tile,
  * 2 right tile, 3 Q tile), window index, first panel row, panel rows, SM id,
  * time the CTA took the task, time it started executing (its predecessors

@@ -156,3 +156,20 @@ def test_autotuner_table_and_auto_options(gbr):
         ri = R()
         ri.status, ri.m, ri.eigs = int(r.status[i]), int(r.m[i]), r.eigs[i]
         check(S, Q, sel, ri, Sg, Qg, ref)
+
+
+def test_batched_trace(gbr):
+    """opts.timing = 2 on a batch: the scheduler launch of the batch's graph
+    records one timeline entry per task (all instances), readable with
+    gbr_last_trace; every predecessor-free start is ordered sensibly."""
+    probs = instances(12, 5, 40, 200)
+    Sd, Qd = to_dev(gbr, probs)
+    b = gbr.Batch(Sd, Qd, [s for _, _, s in probs], window=64, chain=30, timing=2)
+    r = b.run()
+    assert r.rc == 0
+    tr = gbr.last_trace()
+    assert len(tr) == r.stats.tasks > 0
+    kind, win, _, _, _, take, start, end = tr.T
+    assert set(np.unique(kind)) <= {0, 1, 2, 3}
+    assert np.all(take <= start) and np.all(start <= end)
+    assert int(np.sum(kind == 0)) == r.stats.windows
