@@ -617,7 +617,7 @@ int gbr_batch_create(int count, const int* n, double* const* S, const int* ldS, 
     if (opts) o = *opts; else gbr_default_opts(&o);
     rc = check_batch_opts(o);
     if (rc) return rc;
-    o.timing = o.timing ? 1 : 0;  // kernel events only; no per-task trace in batches
+    o.timing = o.timing >= 2 ? 2 : (o.timing ? 1 : 0);  // 2: per-task timeline of each run
     return batch_create(count, n, S, ldS, Q, ldQ, select, o, 0, status, out,
                         (cudaStream_t)cuda_stream);
 }
