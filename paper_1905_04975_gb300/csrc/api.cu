@@ -163,41 +163,51 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
     SchedInfo tot;
     int h_err = 0;
     const CostModel cm = cost_model(o);
-    for (int c = 0; c < nch; ++c) {
-        const int b = c & 1;
-        if (c >= 2) {
-            // image b held chunk c - 2: wait until it has run, then reuse it
-            GBR_CK(cudaEventSynchronize(ev.e[2 + b]), "sync chunk");
-            int rce = read_err(L[b], up, &h_err);
-            if (rce) return rce;
+    // On an error, launches of earlier chunks may still be running on the
+    // stream with images from the pool: the stream is drained before the
+    // error returns, so that no later call reuses an image in flight.
+    const int rc_loop = [&]() -> int {
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1;
+            if (c >= 2) {
+                // image b held chunk c - 2: wait until it has run, then reuse it
+                GBR_CK(cudaEventSynchronize(ev.e[2 + b]), "sync chunk");
+                int rce = read_err(L[b], up, &h_err);
+                if (rce) return rce;
+            }
+            std::vector<InstPlan> plans(1);
+            plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
+            plans[0].wins.assign(all.begin() + (long)cuts[c], all.begin() + (long)cuts[c + 1]);
+            // the global pipeline order, so that the chunks together make the
+            // same program order (and the same result) as one launch
+            plans[0].in_pipeline_order = true;
+            const int slot = b ? POOL_SCHED_ALT : POOL_SCHED;
+            SchedInfo inf;
+            int rc = sched_prepare(
+                plans, o, cm, num_sms(),
+                [slot](size_t bytes) -> void* {
+                    void* p = nullptr;
+                    return pool_get(slot, bytes, &p) ? nullptr : p;
+                },
+                &L[b], &inf, up);
+            if (rc) return rc;
+            tot.tasks += inf.tasks;
+            tot.cp_us += inf.cp_us;
+            tot.sim_us += inf.sim_us;
+            tot.graph_ms += inf.graph_ms;
+            tot.order_ms += inf.order_ms;
+            if (c == 0 && o.timing) GBR_CK(cudaEventRecord(ev.e[0], st), "event");
+            rc = sched_enqueue(L[b], st);
+            if (rc) return rc;
+            if (nch > 1) GBR_CK(cudaEventRecord(ev.e[2 + b], st), "event");
+            *ntasks_out += L[b].P.ntasks;
+            if (L[b].P.ntasks > 0) *launches_out += 1;
         }
-        std::vector<InstPlan> plans(1);
-        plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
-        plans[0].wins.assign(all.begin() + (long)cuts[c], all.begin() + (long)cuts[c + 1]);
-        // the global pipeline order, so that the chunks together make the
-        // same program order (and the same result) as one launch
-        plans[0].in_pipeline_order = true;
-        const int slot = b ? POOL_SCHED_ALT : POOL_SCHED;
-        SchedInfo inf;
-        int rc = sched_prepare(
-            plans, o, cm, num_sms(),
-            [slot](size_t bytes) -> void* {
-                void* p = nullptr;
-                return pool_get(slot, bytes, &p) ? nullptr : p;
-            },
-            &L[b], &inf, up);
-        if (rc) return rc;
-        tot.tasks += inf.tasks;
-        tot.cp_us += inf.cp_us;
-        tot.sim_us += inf.sim_us;
-        tot.graph_ms += inf.graph_ms;
-        tot.order_ms += inf.order_ms;
-        if (c == 0 && o.timing) GBR_CK(cudaEventRecord(ev.e[0], st), "event");
-        rc = sched_enqueue(L[b], st);
-        if (rc) return rc;
-        if (nch > 1) GBR_CK(cudaEventRecord(ev.e[2 + b], st), "event");
-        *ntasks_out += L[b].P.ntasks;
-        if (L[b].P.ntasks > 0) *launches_out += 1;
+        return 0;
+    }();
+    if (rc_loop) {
+        (void)cudaStreamSynchronize(st);
+        return rc_loop;
     }
     if (o.timing) GBR_CK(cudaEventRecord(ev.e[1], st), "event");
     for (int c = std::max(0, nch - 2); c < nch; ++c) {
