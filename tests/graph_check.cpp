@@ -8,7 +8,12 @@
 //     ordered: the later one is reachable from the earlier one;
 //   * every tile depends on its window task;
 //   * the queue order is a topological order of the graph.
-// Prints "OK tasks edges" or "FAIL <reason>" and exits 0 / 1.
+// For a reordering it also checks the cuts of the chunked launches: every
+// pair of overlapping windows keeps its planner order in the pipeline order
+// (so every prefix of the pipeline order holds all earlier windows that
+// overlap its windows), and the graph of each chunk (first 1/16, next 3/16,
+// last 3/4) passes the same checks on its own.
+// Prints "OK <edges>" or "FAIL <reason>" and exits 0 / 1.
 #include "../paper_1905_04975_gb300/csrc/host.h"
 
 #include <cstdio>
@@ -32,6 +37,53 @@ static int mat_of(const HostTask& t) { return t.kind == TASK_Q ? 1 : (t.kind == 
 
 static bool overlap(const Rect& a, const Rect& b) {
     return a.r0 < b.r1 && b.r0 < a.r1 && a.c0 < b.c1 && b.c0 < a.c1;
+}
+
+// The checks of one task graph over windows in program order; *edges gets
+// the edge count.  Prints the first failure.
+static bool check_graph(int n, const std::vector<Window>& wins, bool withQ, bool withZ,
+                        const CostModel& cm, long long* edges) {
+    TaskGraph G;
+    build_graph(n, wins, withQ, cm, G, 0, 3, withZ);
+    const int nt = (int)G.t.size();
+    // forward edges; reachability by bitsets in reverse program order
+    const int W64 = (nt + 63) / 64;
+    std::vector<unsigned long long> R((size_t)nt * W64, 0ull);
+    for (int u = nt - 1; u >= 0; --u)
+        for (int i = G.soff[u]; i < G.soff[u + 1]; ++i) {
+            const int v = G.succ[i];
+            if (v <= u) { printf("FAIL backward edge %d -> %d\n", u, v); return false; }
+            R[(size_t)u * W64 + v / 64] |= 1ull << (v % 64);
+            for (int k = 0; k < W64; ++k) R[(size_t)u * W64 + k] |= R[(size_t)v * W64 + k];
+        }
+    auto reach = [&](int a, int b) { return (R[(size_t)a * W64 + b / 64] >> (b % 64)) & 1ull; };
+    std::vector<int> wtask(wins.size(), -1);
+    for (int t = 0; t < nt; ++t)
+        if (G.t[t].kind == TASK_W) wtask[G.t[t].win] = t;
+    for (int t = 0; t < nt; ++t) {
+        const HostTask& b = G.t[t];
+        if (b.kind != TASK_W && !reach(wtask[b.win], t)) {
+            printf("FAIL tile %d not after its window task\n", t);
+            return false;
+        }
+        for (int a = 0; a < t; ++a) {
+            const HostTask& x = G.t[a];
+            if (mat_of(x) == mat_of(b) && overlap(x.rc, b.rc) && !reach(a, t)) {
+                printf("FAIL overlapping tasks %d, %d unordered\n", a, t);
+                return false;
+            }
+        }
+    }
+    std::vector<int> order;
+    queue_order(G, 152, order);
+    if ((int)order.size() != nt) { printf("FAIL order size\n"); return false; }
+    std::vector<int> pos(nt, -1);
+    for (int q = 0; q < nt; ++q) pos[order[q]] = q;
+    for (int u = 0; u < nt; ++u)
+        for (int i = G.soff[u]; i < G.soff[u + 1]; ++i)
+            if (pos[G.succ[i]] <= pos[u]) { printf("FAIL queue order\n"); return false; }
+    *edges = (long long)G.succ.size();
+    return true;
 }
 
 int main(int argc, char** argv) {
@@ -60,48 +112,39 @@ int main(int argc, char** argv) {
         int nch = 0;
         plan_pass(ps, w, m, wins, nch);
     }
+    std::vector<Window> planner = wins;
     pipeline_order(n, wins);
     CostModel cm;
     if (withZ) cm.lr_mats = 2.0;
-    TaskGraph G;
-    build_graph(n, wins, withQ, cm, G, 0, 3, withZ);
-    const int nt = (int)G.t.size();
-    // forward edges; reachability by bitsets in reverse program order
-    const int W64 = (nt + 63) / 64;
-    std::vector<unsigned long long> R((size_t)nt * W64, 0ull);
-    for (int u = nt - 1; u >= 0; --u)
-        for (int i = G.soff[u]; i < G.soff[u + 1]; ++i) {
-            const int v = G.succ[i];
-            if (v <= u) { printf("FAIL backward edge %d -> %d\n", u, v); return 1; }
-            R[(size_t)u * W64 + v / 64] |= 1ull << (v % 64);
-            for (int k = 0; k < W64; ++k) R[(size_t)u * W64 + k] |= R[(size_t)v * W64 + k];
+    if (!sweep) {
+        // overlapping windows keep their planner order in the pipeline order
+        auto key = [](const Window& x) { return ((long long)x.chain << 40) | ((long long)x.s << 20) | x.e; };
+        std::vector<long long> kp(wins.size());
+        for (size_t i = 0; i < wins.size(); ++i) kp[i] = key(wins[i]);
+        std::vector<int> ppos(planner.size(), -1);
+        for (size_t i = 0; i < planner.size(); ++i)
+            for (size_t k = 0; k < wins.size(); ++k)
+                if (kp[k] == key(planner[i])) { ppos[i] = (int)k; break; }
+        for (size_t i = 0; i < planner.size(); ++i) {
+            if (ppos[i] < 0) { printf("FAIL window lost by the pipeline order\n"); return 1; }
+            for (size_t k = i + 1; k < planner.size(); ++k)
+                if (planner[i].s < planner[k].e && planner[k].s < planner[i].e && ppos[i] > ppos[k]) {
+                    printf("FAIL overlapping windows %zu, %zu reordered\n", i, k);
+                    return 1;
+                }
         }
-    auto reach = [&](int a, int b) { return (R[(size_t)a * W64 + b / 64] >> (b % 64)) & 1ull; };
-    std::vector<int> wtask(wins.size(), -1);
-    for (int t = 0; t < nt; ++t)
-        if (G.t[t].kind == TASK_W) wtask[G.t[t].win] = t;
-    for (int t = 0; t < nt; ++t) {
-        const HostTask& b = G.t[t];
-        if (b.kind != TASK_W && !reach(wtask[b.win], t)) {
-            printf("FAIL tile %d not after its window task\n", t);
-            return 1;
-        }
-        for (int a = 0; a < t; ++a) {
-            const HostTask& x = G.t[a];
-            if (mat_of(x) == mat_of(b) && overlap(x.rc, b.rc) && !reach(a, t)) {
-                printf("FAIL overlapping tasks %d, %d unordered\n", a, t);
-                return 1;
-            }
+        // each chunk of the pipeline order on its own
+        const size_t nw = wins.size();
+        const size_t cuts[4] = {0, nw / 16, nw / 4, nw};
+        for (int c = 0; c < 3; ++c) {
+            std::vector<Window> part(wins.begin() + (long)cuts[c], wins.begin() + (long)cuts[c + 1]);
+            long long te = 0;
+            if (!check_graph(n, part, withQ, withZ, cm, &te)) return 1;
         }
     }
-    std::vector<int> order;
-    queue_order(G, 152, order);
-    if ((int)order.size() != nt) { printf("FAIL order size\n"); return 1; }
-    std::vector<int> pos(nt, -1);
-    for (int q = 0; q < nt; ++q) pos[order[q]] = q;
-    for (int u = 0; u < nt; ++u)
-        for (int i = G.soff[u]; i < G.soff[u + 1]; ++i)
-            if (pos[G.succ[i]] <= pos[u]) { printf("FAIL queue order\n"); return 1; }
-    printf("OK %d %zu\n", nt, G.succ.size());
+    long long edges = 0;
+    if (!check_graph(n, wins, withQ, withZ, cm, &edges)) return 1;
+    printf("OK %lld\n", edges);
     return 0;
 }
+

@@ -4,7 +4,9 @@ on the host: tests/graph_check.cpp is compiled with the library's planner
 source and run on seeded block structures and sweep plans.  Every
 dependence goes forward, every pair of overlapping tasks (same matrix) is
 ordered, every tile follows its window task, and the queue order is
-topological."""
+topological; for reorderings, the cuts of the chunked launches keep every
+pair of overlapping windows in planner order and each chunk's graph passes
+the same checks."""
 import os
 import shutil
 import subprocess
@@ -35,7 +37,8 @@ def run(checker, *args):
 
 
 @pytest.mark.parametrize("n,w,m,q,z", [(40, 8, 3, 1, 0), (120, 16, 6, 1, 0), (300, 64, 30, 1, 0),
-                                       (300, 32, 12, 0, 0), (200, 24, 10, 1, 1), (257, 64, 32, 1, 1)])
+                                       (300, 32, 12, 0, 0), (200, 24, 10, 1, 1), (257, 64, 32, 1, 1),
+                                       (600, 256, 128, 1, 0), (500, 200, 40, 1, 0)])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_reordering_graph(checker, n, w, m, q, z, seed):
     run(checker, n, w, m, q, z, seed, 0)
