@@ -474,6 +474,27 @@ int gbr_autotune(int n_max, int per_class, void *cuda_stream);
 int gbr_tune_get(int n, int *window, int *chain, int *tile);
 
 /*
+ * Saves the current device's autotuner table to a JSON file, one object per
+ * tuned size class:
+ *   {"tune": [{"n_max": 32, "window": 32, "chain": 24, "tile": 64}, ...]}
+ * (n_max: the largest n of the class, a power of two >= 32; tile 0 means the
+ * built-in far tile height).  Returns the number of classes written, -1 (NULL
+ * path) or -2 (the file cannot be written).
+ */
+int gbr_tune_save(const char *path);
+
+/*
+ * Loads a table written by gbr_tune_save into the current device's table
+ * (the classes it lists replace the tuned or default ones), so that a tuning
+ * can be reused across processes.  Every class is checked first (n_max a
+ * power of two >= 32, window 4..128, chain 1..window-2, tile 0, 64 or 256);
+ * on any error nothing is changed.  Returns the number of classes loaded, -1
+ * (NULL path), -2 (the file cannot be read) or -3 (malformed or invalid
+ * content).  Host only: no GPU work.
+ */
+int gbr_tune_load(const char *path);
+
+/*
  * Reordering server: continuous batching of requests on one GPU.  No
  * counterpart in the paper; each request is the reordering of Eq. 7 with
  * the tasks of Section 3.2.

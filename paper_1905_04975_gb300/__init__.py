@@ -127,6 +127,8 @@ SYMBOLS = {
                                            ctypes.POINTER(GbrStats), ctypes.c_void_p]),
     "gbr_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "gbr_tune_get": (ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip]),
+    "gbr_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "gbr_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "gbr_server_default_cfg": (None, [ctypes.POINTER(GbrServerCfg)]),
     "gbr_server_create": (ctypes.c_int, [ctypes.POINTER(GbrServerCfg),
                                          ctypes.POINTER(ctypes.c_void_p)]),
@@ -676,6 +678,24 @@ def tune_get(n: int):
     w, m, t = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     tuned = load().gbr_tune_get(int(n), ctypes.byref(w), ctypes.byref(m), ctypes.byref(t))
     return w.value, m.value, t.value, bool(tuned)
+
+
+def tune_save(path) -> int:
+    """Write the current device's autotuner table to a JSON file (gbr_tune_save);
+    returns the number of size classes written."""
+    rc = load().gbr_tune_save(os.fsencode(path))
+    if rc < 0:
+        raise GbrError(rc, "tune_save: cannot write " + str(path))
+    return rc
+
+
+def tune_load(path) -> int:
+    """Load a table written by tune_save into the current device's autotuner
+    table (gbr_tune_load); returns the number of size classes loaded."""
+    rc = load().gbr_tune_load(os.fsencode(path))
+    if rc < 0:
+        raise GbrError(rc, "tune_load: cannot read or invalid " + str(path))
+    return rc
 
 
 # ---------------------------------------------------------------------------

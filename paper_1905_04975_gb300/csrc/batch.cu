@@ -12,10 +12,13 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <random>
+#include <string>
 
 struct gbr_batch {
     int count = 0;
@@ -657,6 +660,83 @@ int gbr_tune_get(int n, int* window, int* chain, int* tile) {
     if (chain) *chain = c.m;
     if (tile) *tile = c.far ? c.far : far_rows(std::max(1, n));
     return tuned ? 1 : 0;
+}
+
+int gbr_tune_save(const char* path) {
+    if (!path) return -1;
+    std::map<int, TuneChoice> t;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        t = g_tune[current_device()];
+    }
+    FILE* f = fopen(path, "w");
+    if (!f) return -2;
+    int k = 0;
+    fprintf(f, "{\"tune\": [");
+    for (const auto& kv : t) {
+        fprintf(f, "%s\n  {\"n_max\": %d, \"window\": %d, \"chain\": %d, \"tile\": %d}",
+                k ? "," : "", 1 << kv.first, kv.second.w, kv.second.m, kv.second.far);
+        ++k;
+    }
+    fprintf(f, "%s]}\n", k ? "\n" : "");
+    if (fclose(f) != 0) return -2;
+    return k;
+}
+
+// Reads the integer after "key": in [p, end); false if absent or malformed.
+static bool json_int(const char* p, const char* end, const char* key, long* out) {
+    const size_t kl = strlen(key);
+    for (const char* q = p; q + kl + 2 <= end; ++q) {
+        if (q[0] != '"' || strncmp(q + 1, key, kl) != 0 || q[kl + 1] != '"') continue;
+        const char* r = q + kl + 2;
+        while (r < end && (*r == ' ' || *r == '\t' || *r == '\n' || *r == '\r')) ++r;
+        if (r >= end || *r != ':') return false;
+        ++r;
+        char* e = nullptr;
+        const long v = strtol(r, &e, 10);
+        if (e == r || e > end) return false;
+        *out = v;
+        return true;
+    }
+    return false;
+}
+
+int gbr_tune_load(const char* path) {
+    if (!path) return -1;
+    FILE* f = fopen(path, "r");
+    if (!f) return -2;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof buf, f)) > 0) {
+        text.append(buf, got);
+        if (text.size() > (1u << 20)) break;  // a table is a few hundred bytes
+    }
+    fclose(f);
+    if (text.size() > (1u << 20)) return -3;
+    // every {...} object holds one class; all are checked before any is kept
+    std::map<int, TuneChoice> in;
+    const char* s0 = text.c_str();
+    const char* endp = s0 + text.size();
+    const char* arr = strstr(s0, "\"tune\"");
+    if (!arr) return -3;
+    for (const char* p = strchr(arr, '{'); p && p < endp; p = strchr(p + 1, '{')) {
+        const char* q = strchr(p, '}');
+        if (!q) return -3;
+        long nm, w, m, far;
+        if (!json_int(p, q, "n_max", &nm) || !json_int(p, q, "window", &w) ||
+            !json_int(p, q, "chain", &m) || !json_int(p, q, "tile", &far))
+            return -3;
+        if (nm < 32 || nm > (1L << 30) || (nm & (nm - 1)) != 0) return -3;
+        if (w < 4 || w > WMAX || m < 1 || m > w - 2) return -3;
+        if (far != 0 && far != UPD_BM && far != UPD_FAR) return -3;
+        in[size_class((int)nm)] = TuneChoice{(int)w, (int)m, (int)far};
+        p = q;
+    }
+    std::lock_guard<std::mutex> lk(g_tmu);
+    auto& t = g_tune[current_device()];
+    for (const auto& kv : in) t[kv.first] = kv.second;
+    return (int)in.size();
 }
 
 }  // extern "C"

@@ -281,3 +281,38 @@ def test_struct_layouts_match_header(tmp_path):
         assert seen[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert seen[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_tune_table_json_round_trip(lib, tmp_path):
+    """The autotuner table persists as JSON (host only, no GPU): a loaded
+    table answers gbr_tune_get, saves back to the same classes, and invalid
+    or malformed files change nothing."""
+    src = tmp_path / "tune.json"
+    src.write_text('{"tune": [\n  {"n_max": 32, "window": 32, "chain": 24, "tile": 64},\n'
+                   '  {"n_max": 512, "window": 128, "chain": 64, "tile": 256}\n]}\n')
+    assert g.tune_load(src) == 2
+    assert g.tune_get(20)[:2] == (32, 24) and g.tune_get(20)[3]
+    assert g.tune_get(300) == (128, 64, 256, True)
+    out = tmp_path / "saved.json"
+    assert g.tune_save(out) >= 2
+    text = out.read_text()
+    assert '"n_max": 32, "window": 32, "chain": 24, "tile": 64' in text
+    assert '"n_max": 512, "window": 128, "chain": 64, "tile": 256' in text
+    # reload what was saved: same answers
+    assert g.tune_load(out) >= 2
+    assert g.tune_get(300) == (128, 64, 256, True)
+    for bad in ['{"tune": [{"n_max": 64, "window": 200, "chain": 64, "tile": 64}]}',
+                '{"tune": [{"n_max": 64, "window": 64, "chain": 63, "tile": 64}]}',
+                '{"tune": [{"n_max": 48, "window": 32, "chain": 16, "tile": 64}]}',
+                '{"tune": [{"n_max": 64, "window": 32, "chain": 16, "tile": 100}]}',
+                '{"tune": [{"n_max": 64, "window": 32, "tile": 64}]}',
+                '{"other": 1}']:
+        f = tmp_path / "bad.json"
+        f.write_text(bad)
+        with pytest.raises(g.GbrError) as ei:
+            g.tune_load(f)
+        assert ei.value.status == -3
+    assert g.tune_get(300) == (128, 64, 256, True)  # unchanged
+    with pytest.raises(g.GbrError):
+        g.tune_load(tmp_path / "missing.json")
+    assert lib.gbr_tune_load(None) == -1 and lib.gbr_tune_save(None) == -1
