@@ -175,6 +175,7 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
                 int rce = read_err(L[b], up, &h_err);
                 if (rce) return rce;
             }
+            NvtxRange nv_chunk("gbr task graph, order and launch of a chunk");
             std::vector<InstPlan> plans(1);
             plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
             plans[0].wins.assign(all.begin() + (long)cuts[c], all.begin() + (long)cuts[c + 1]);
@@ -300,6 +301,7 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
 
     DevCounters h_ctr{0, 0, INT_MAX, 0, 0};
     GBR_CK(cudaMemcpyAsync(d_ctr, &h_ctr, sizeof h_ctr, cudaMemcpyHostToDevice, st), "H2D counters");
+    NvtxRange nv_call("gbr_reorder");
     if (o.validate) GBR_CK(launch_validate(n, S, ldS, d_ctr, st), "validate kernel");
     GBR_CK(launch_subdiag(n, S, ldS, d_sub, st), "subdiag kernel");
     std::vector<uint8_t> sub(n), sel(n);
@@ -341,7 +343,10 @@ static int reorder_device_at(char* b, int n, double* S, int ldS, double* Q, int 
     long long ntasks = 0;
     for (int pass = 0; pass < 1 + 2 * n; ++pass) {
         std::vector<Window> win;
-        plan_pass(ps, o.window, o.chain, win, nchains);
+        {
+            NvtxRange nv_plan("gbr window plan");
+            plan_pass(ps, o.window, o.chain, win, nchains);
+        }
         if (win.empty()) break;
         if (o.sched == GBR_SCHED_PERSISTENT) {
             int rcs = run_persistent(n, win, S, ldS, Q, ldQ, d_sel, d_ctr, o, &ntasks, &ms_sched,
@@ -507,6 +512,7 @@ int gbr_reorder_host(int n, double* S, int ldS, double* Q, int ldQ, const int* s
         rc = pool_get(POOL_HOST_Q, mat, &dQ);
         if (rc) return rc;
     }
+    NvtxRange nv_host("gbr_reorder_host");
     CopyTimer ct(o.timing != 0 && stats != nullptr);
     ct.mark(0, st);
     GBR_CK(cudaMemcpy2DAsync(dS, n * sizeof(double), S, (size_t)ldS * sizeof(double),

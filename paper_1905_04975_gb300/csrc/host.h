@@ -6,6 +6,8 @@
 #include "../../include/gbreorder.h"
 #include "common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <functional>
 #include <mutex>
 #include <string>
@@ -34,6 +36,15 @@ constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_
               POOL_SWEEP_SCHED = 10, POOL_SCHED_ALT = 11, POOL_NSLOTS = 12;
 int pool_get(int slot, size_t bytes, void** out);
 std::mutex& api_mutex();
+
+// A named range of the call's host timeline for profilers (NVTX; costs
+// nothing when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // CUDA events around the copies of the host-buffer entry points when
 // opts.timing is set: [0, 1] bracket the host-to-device copies, [2, 3] the
