@@ -27,6 +27,9 @@
  *   - a non-NULL `cuda_stream` is a cudaStream_t; NULL means the legacy
  *     default stream;
  *   - calls are synchronous: they return after all GPU work has finished;
+ *     so a call on a stream that is being captured into a CUDA graph is
+ *     refused with GBR_ERR_CAPTURING before anything is enqueued (the
+ *     capture stays valid);
  *   - the library never frees caller memory.  Its own scratch (window
  *     accumulators, block plan, counters) comes from a per-device pool the
  *     library owns, grown on demand and kept until gbr_release().
@@ -58,6 +61,13 @@ extern "C" {
 #define GBR_ERR_PLAN_MISMATCH (-1006) /* gbr_batch_run: an S no longer has the block
                                          structure it was planned for; nothing was
                                          modified */
+#define GBR_ERR_CAPTURING (-1007) /* cuda_stream is being captured into a CUDA graph
+                                     (or is the legacy stream while another stream
+                                     captures): the call synchronizes its stream and
+                                     reads results back, which a capture refuses.
+                                     Checked with cudaStreamIsCapturing before
+                                     anything is enqueued: nothing was modified and
+                                     the capture stays valid */
 
 #define GBR_PREC_DMMA   0  /* off-diagonal updates on FP64 tensor cores (DMMA) */
 #define GBR_PREC_OZAKI  1  /* off-diagonal updates as split-precision emulated FP64:

@@ -37,6 +37,7 @@ ERR_TIMEOUT = -1003
 ERR_UNSUPPORTED = -1004
 ERR_NOALLOC_LIMIT = -1005
 ERR_PLAN_MISMATCH = -1006
+ERR_CAPTURING = -1007
 NOALLOC_MAX_N = 16384
 AUTO = 0
 

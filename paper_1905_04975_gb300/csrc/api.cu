@@ -478,6 +478,8 @@ int gbr_reorder(int n, double* S, int ldS, double* Q, int ldQ, const int* select
         if (m_out) *m_out = 0;
         return 0;
     }
+    rc = refuse_capture((cudaStream_t)cuda_stream);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_mu);
     rc = reorder_device(n, S, ldS, Q, ldQ, select, eig_re, eig_im, m_out, o, stats,
                         (cudaStream_t)cuda_stream);
@@ -503,6 +505,8 @@ int gbr_reorder_host(int n, double* S, int ldS, double* Q, int ldQ, const int* s
         return 0;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    rc = refuse_capture(st);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_mu);
     size_t mat = (size_t)n * n * sizeof(double);
     void *dS = nullptr, *dQ = nullptr;
@@ -623,6 +627,8 @@ int gbr_reorder_noalloc(int n, double* S, int ldS, double* Q, int ldQ, const int
         if (m_out) *m_out = 0;
         return 0;
     }
+    rc = refuse_capture((cudaStream_t)cuda_stream);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_mu);
     char* base = nullptr;
     rc = noalloc_scratch(&base);
@@ -647,6 +653,8 @@ int gbr_update_panel(int rows, int w, double* Y, long long rs, long long ks, con
         return -8;
     if (rows == 0) return 0;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int rcc = refuse_capture(st);
+    if (rcc) return rcc;
     std::lock_guard<std::mutex> lock(g_mu);
     // scratch: U contiguous (w x w), then the digit slices, then an error word
     const size_t b_u = align256((size_t)w * w * sizeof(double));
@@ -690,6 +698,8 @@ int gbr_eigenvectors(int n, const double* S, int ldS, const double* Q, int ldQ,
     if (m_out) *m_out = 0;
     if (n == 0) return 0;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int rcc = refuse_capture(st);
+    if (rcc) return rcc;
     std::lock_guard<std::mutex> lock(g_mu);
     // structure: validation and the 2x2 pattern
     char* b = nullptr;
@@ -833,6 +843,8 @@ const char* gbr_status_string(int s) {
             return "n exceeds GBR_NOALLOC_MAX_N, the size the no-allocation entry point supports";
         case GBR_ERR_PLAN_MISMATCH:
             return "the block structure of an S differs from the one its batch was planned for";
+        case GBR_ERR_CAPTURING:
+            return "the stream is being captured into a CUDA graph; the call synchronizes it";
         default: return "invalid argument";
     }
 }

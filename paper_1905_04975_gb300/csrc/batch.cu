@@ -521,6 +521,8 @@ static void synth_schur(int n, std::mt19937_64& rng, double* S, int* sel) {
 static int autotune(int n_max, int per_class, cudaStream_t st) {
     if (n_max < 1) return -1;
     if (per_class < 1) return -2;
+    const int rcc = refuse_capture(st);
+    if (rcc) return rcc;
     const int dev = current_device();
     int tuned = 0;
     for (int cls = 5; (1 << (cls - 1)) < n_max; ++cls) {
@@ -621,6 +623,8 @@ int gbr_batch_create(int count, const int* n, double* const* S, const int* ldS, 
     rc = check_batch_opts(o);
     if (rc) return rc;
     o.timing = o.timing >= 2 ? 2 : (o.timing ? 1 : 0);  // 2: per-task timeline of each run
+    rc = refuse_capture((cudaStream_t)cuda_stream);
+    if (rc) return rc;
     return batch_create(count, n, S, ldS, Q, ldQ, select, o, 0, status, out,
                         (cudaStream_t)cuda_stream);
 }
@@ -628,6 +632,8 @@ int gbr_batch_create(int count, const int* n, double* const* S, const int* ldS, 
 int gbr_batch_run(gbr_batch* batch, double* eig_re, double* eig_im, int* m_out, int* status,
                   gbr_stats* stats, void* cuda_stream) {
     if (!batch) return -1;
+    const int rc = refuse_capture((cudaStream_t)cuda_stream);
+    if (rc) return rc;
     return batch_run(batch, eig_re, eig_im, m_out, status, stats, (cudaStream_t)cuda_stream);
 }
 

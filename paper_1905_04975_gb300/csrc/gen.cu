@@ -454,6 +454,8 @@ int gbr_reorder_gen(int n, double* S, int ldS, double* T, int ldT, double* Q, in
         if (m_out) *m_out = 0;
         return 0;
     }
+    rc = refuse_capture((cudaStream_t)cuda_stream);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(api_mutex());
     rc = reorder_gen_device(n, S, ldS, T, ldT, Q, ldQ, Z, ldZ, select, eig_re, eig_im, m_out, o,
                             stats, (cudaStream_t)cuda_stream);
@@ -477,6 +479,8 @@ int gbr_reorder_gen_host(int n, double* S, int ldS, double* T, int ldT, double* 
         return 0;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    rc = refuse_capture(st);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(api_mutex());
     const size_t mat = (size_t)n * n * sizeof(double);
     double* d = nullptr;

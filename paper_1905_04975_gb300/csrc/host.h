@@ -21,6 +21,10 @@ namespace gbr {
 void set_last_error(const std::string& s);
 const char* last_error_cstr();
 int cuda_fail(cudaError_t e, const char* what);
+// GBR_ERR_CAPTURING if st is being captured into a CUDA graph (or is the
+// legacy stream while another stream captures), else 0.  Touches nothing on
+// st; the error a refused query leaves behind is cleared.
+int refuse_capture(cudaStream_t st);
 
 #define GBR_CK(call, what)                                   \
     do {                                                     \

@@ -35,6 +35,18 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? GBR_ERR_NOMEM : GBR_ERR_CUDA;
 }
 
+int refuse_capture(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e == cudaErrorStreamCaptureImplicit || (e == cudaSuccess && cs != cudaStreamCaptureStatusNone)) {
+        if (e != cudaSuccess) (void)cudaGetLastError();
+        set_last_error("the stream is being captured into a CUDA graph; this call synchronizes it");
+        return GBR_ERR_CAPTURING;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    return 0;
+}
+
 int num_sms() {
     static int sms[64] = {};
     int dev = 0;

@@ -294,8 +294,10 @@ int gbr_qr_sweep(int n, double* H, int ldH, double* Q, int ldQ, int nshifts, con
     if (o.sched != GBR_SCHED_PERSISTENT && o.sched != GBR_SCHED_SEQUENTIAL) return -10;
     if (stats) memset(stats, 0, sizeof *stats);
     if (n < 3 || nshifts == 0) return 0;
+    int rc = refuse_capture((cudaStream_t)cuda_stream);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lock(api_mutex());
-    int rc = sweep_device(n, H, ldH, Q, ldQ, nshifts, shift_re, shift_im, o, stats,
+    rc = sweep_device(n, H, ldH, Q, ldQ, nshifts, shift_re, shift_im, o, stats,
                           (cudaStream_t)cuda_stream);
     if (stats)
         stats->ms_total =

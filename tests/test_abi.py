@@ -44,6 +44,22 @@ def test_defaults_and_strings(lib):
         assert lib.gbr_status_string(code)
 
 
+def test_error_codes_match_header(lib):
+    """Every GBR_ERR_* of the header has the same value in the binding and a
+    status string of its own."""
+    with open(os.path.join(ROOT, "include", "gbreorder.h")) as f:
+        codes = dict(re.findall(r"#define GBR_ERR_(\w+)\s+\((-\d+)\)", f.read()))
+    assert "CAPTURING" in codes and len(codes) >= 7
+    fallback = lib.gbr_status_string(-999)
+    strings = set()
+    for name, value in codes.items():
+        assert getattr(g, "ERR_" + name) == int(value), name
+        s = lib.gbr_status_string(int(value))
+        assert s and s != fallback, name
+        strings.add(s)
+    assert len(strings) == len(codes)
+
+
 def call(lib, n, S, ldS, Q, ldQ, sel, opts=None):
     wr = np.zeros(max(n, 1))
     wi = np.zeros(max(n, 1))

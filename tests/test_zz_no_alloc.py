@@ -69,6 +69,35 @@ def test_noalloc_matches_reorder_twice(g, case):
         assert r.stats.windows == ref.stats.windows
 
 
+def test_capturing_stream_is_refused(g):
+    """The entry points synchronize their stream, which a CUDA graph capture
+    refuses: on a capturing stream they return ERR_CAPTURING before they
+    enqueue anything.  S and Q stay untouched and the capture stays valid
+    (the graph captured around the calls replays and computes its own
+    work)."""
+    S, Q, sel = si.reorder_problem(96, 5, select_frac=0.4, q="householder")
+    Sd, Qd = g.to_device(S), g.to_device(Q)
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    codes = []
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="relaxed"):
+        x.add_(1.0)
+        for fn in (g.reorder_noalloc, g.reorder):
+            try:
+                fn(Sd, Qd, sel)
+                codes.append(0)
+            except g.GbrError as e:
+                codes.append(e.status)
+        x.mul_(3.0)
+    assert codes == [g.ERR_CAPTURING, g.ERR_CAPTURING]
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x, torch.full_like(x, 3.0))
+    assert np.array_equal(g.to_host(Sd), S) and np.array_equal(g.to_host(Qd), Q)
+
+
 def test_noalloc_rejects_oversized(g):
     lib = g.load()
     n = g.NOALLOC_MAX_N + 1
