@@ -23,7 +23,7 @@ enum PoolSlot { POOL_SCRATCH = 0, POOL_HOST_S = 1, POOL_HOST_Q = 2, POOL_SCHED =
                 POOL_EIGVEC = 5 };
 static_assert(POOL_GEN_SCRATCH == 6 && POOL_GEN_HOST == 7 && POOL_GEN_SCHED == 8 &&
                   POOL_SWEEP == 9 && POOL_SWEEP_SCHED == 10 && POOL_SCHED_ALT == 11 &&
-                  POOL_NSLOTS == 12,
+                  POOL_GEN_SCHED_ALT == 12 && POOL_NSLOTS == 13,
               "pool slots of the generalized entry points");
 struct DevPool {
     void* ptr[POOL_NSLOTS] = {};
@@ -129,13 +129,12 @@ static int read_err(const SchedLaunch& L, cudaStream_t s, int* acc) {
 // part of that order (every window that overlaps one of its windows and
 // comes earlier is in it or in an earlier chunk), so running the chunks one
 // after another on the stream keeps every dependence.  Two launch images
-// alternate between the pool slots POOL_SCHED and POOL_SCHED_ALT.
-static int run_persistent(int n, const std::vector<Window>& wins, double* S, int ldS, double* Q,
-                          int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
-                          long long* ntasks_out, double* ms_out, long long* launches_out,
-                          cudaStream_t st) {
+// alternate between the pool slots pl.slot[0] and pl.slot[1].
+int run_pass_persistent(const std::vector<Window>& wins, const PassLaunch& pl, const gbr_opts& o,
+                        long long* ntasks_out, double* ms_out, long long* launches_out,
+                        SchedInfo* info, cudaStream_t st) {
     std::vector<Window> all = wins;
-    pipeline_order(n, all);
+    pipeline_order(pl.inst.n, all);
     const std::vector<size_t> cuts = chunk_cuts(all.size(), o);
     const int nch = (int)cuts.size() - 1;
     cudaStream_t up = st;
@@ -162,7 +161,6 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
     SchedLaunch L[2];
     SchedInfo tot;
     int h_err = 0;
-    const CostModel cm = cost_model(o);
     // On an error, launches of earlier chunks may still be running on the
     // stream with images from the pool: the stream is drained before the
     // error returns, so that no later call reuses an image in flight.
@@ -177,21 +175,22 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
             }
             NvtxRange nv_chunk("gbr task graph, order and launch of a chunk");
             std::vector<InstPlan> plans(1);
-            plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
+            plans[0].d = pl.inst;
             plans[0].wins.assign(all.begin() + (long)cuts[c], all.begin() + (long)cuts[c + 1]);
             // the global pipeline order, so that the chunks together make the
             // same program order (and the same result) as one launch
             plans[0].in_pipeline_order = true;
-            const int slot = b ? POOL_SCHED_ALT : POOL_SCHED;
+            const int slot = pl.slot[b];
             SchedInfo inf;
             int rc = sched_prepare(
-                plans, o, cm, num_sms(),
+                plans, o, pl.cm, num_sms(),
                 [slot](size_t bytes) -> void* {
                     void* p = nullptr;
                     return pool_get(slot, bytes, &p) ? nullptr : p;
                 },
                 &L[b], &inf, up);
             if (rc) return rc;
+            if (pl.mode >= 0) L[b].P.mode = pl.mode;
             tot.tasks += inf.tasks;
             tot.cp_us += inf.cp_us;
             tot.sim_us += inf.sim_us;
@@ -223,16 +222,30 @@ static int run_persistent(int n, const std::vector<Window>& wins, double* S, int
         }
         *ms_out += ms;
     }
-    g_last_sched = tot;
+    if (info) *info = tot;
     if (nch == 1 && L[0].trace_bytes) {
         int rct = store_trace(L[0]);
         if (rct) return rct;
     }
     if (h_err) {
-        set_last_error("persistent scheduler: a task waited longer than wait_limit_ms");
+        set_last_error(pl.timeout_msg);
         return GBR_ERR_TIMEOUT;
     }
     return 0;
+}
+
+// A pass of a standard form (S, Q).
+static int run_persistent(int n, const std::vector<Window>& wins, double* S, int ldS, double* Q,
+                          int ldQ, uint8_t* d_sel, DevCounters* d_ctr, const gbr_opts& o,
+                          long long* ntasks_out, double* ms_out, long long* launches_out,
+                          cudaStream_t st) {
+    PassLaunch pl{};
+    pl.inst = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0};
+    pl.cm = cost_model(o);
+    pl.slot[0] = POOL_SCHED;
+    pl.slot[1] = POOL_SCHED_ALT;
+    pl.timeout_msg = "persistent scheduler: a task waited longer than wait_limit_ms";
+    return run_pass_persistent(wins, pl, o, ntasks_out, ms_out, launches_out, &g_last_sched, st);
 }
 
 // ---------------------------------------------------------------------------

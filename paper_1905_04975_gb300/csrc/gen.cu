@@ -208,61 +208,23 @@ void gen_window(const gbr_opts& o, int* w, int* m) {
 
 // One planned pass through the persistent scheduler: the generalized
 // instance's window tasks run window_gen_body, its tiles update S and T
-// (left by UQ, right by UZ), Q (UQ) and Z (UZ).
+// (left by UQ, right by UZ), Q (UQ) and Z (UZ).  A large pass runs as
+// chunked launches like a pass of a standard form.
 int run_persistent_gen(int n, const std::vector<Window>& wins, double* S, int ldS, double* T,
                        int ldT, double* Q, int ldQ, double* Z, int ldZ, uint8_t* d_sel,
                        DevCounters* d_ctr, const gbr_opts& o, long long* ntasks_out,
-                       double* ms_out, SchedInfo* info, cudaStream_t st) {
-    std::vector<InstPlan> plans(1);
-    plans[0].d = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0, T, Z, ldT, ldZ};
-    plans[0].wins = wins;
-    CostModel cm;
-    cm.lr_mats = 2.0;
-    cm.win_us_128 = kGenWinUs128;
-    if (o.precision == GBR_PREC_OZAKI) cm.tile_rate = 100000.0;
-    if (o.precision == GBR_PREC_FMA) cm.tile_rate = 7600.0;
-    SchedLaunch L;
-    int rc = sched_prepare(
-        plans, o, cm, num_sms(),
-        [](size_t b) -> void* {
-            void* p = nullptr;
-            return pool_get(POOL_GEN_SCHED, b, &p) ? nullptr : p;
-        },
-        &L, info, st);
-    if (rc) return rc;
-    L.P.mode = 1;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (o.timing) {
-        GBR_CK(cudaEventCreate(&e0), "event");
-        GBR_CK(cudaEventCreate(&e1), "event");
-        GBR_CK(cudaEventRecord(e0, st), "event");
-    }
-    rc = sched_enqueue(L, st);
-    if (rc) return rc;
-    if (o.timing) GBR_CK(cudaEventRecord(e1, st), "event");
-    int h_err = 0;
-    GBR_CK(cudaMemcpyAsync(&h_err, L.P.err, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H err");
-    GBR_CK(cudaStreamSynchronize(st), "sync");
-    if (o.timing) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            ms = 0.f;
-            (void)cudaGetLastError();
-        }
-        *ms_out += ms;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
-    if (L.trace_bytes) {
-        const int rct = store_trace(L);
-        if (rct) return rct;
-    }
-    *ntasks_out += L.P.ntasks;
-    if (h_err) {
-        set_last_error("persistent scheduler (pair): a task waited longer than wait_limit_ms");
-        return GBR_ERR_TIMEOUT;
-    }
-    return 0;
+                       double* ms_out, long long* launches_out, SchedInfo* info, cudaStream_t st) {
+    PassLaunch pl{};
+    pl.inst = Inst{S, Q, d_sel, d_ctr, n, ldS, ldQ, 0, T, Z, ldT, ldZ};
+    pl.cm.lr_mats = 2.0;
+    pl.cm.win_us_128 = kGenWinUs128;
+    if (o.precision == GBR_PREC_OZAKI) pl.cm.tile_rate = 100000.0;
+    if (o.precision == GBR_PREC_FMA) pl.cm.tile_rate = 7600.0;
+    pl.slot[0] = POOL_GEN_SCHED;
+    pl.slot[1] = POOL_GEN_SCHED_ALT;
+    pl.mode = 1;
+    pl.timeout_msg = "persistent scheduler (pair): a task waited longer than wait_limit_ms";
+    return run_pass_persistent(wins, pl, o, ntasks_out, ms_out, launches_out, info, st);
 }
 
 int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q, int ldQ, double* Z,
@@ -332,13 +294,12 @@ int reorder_gen_device(int n, double* S, int ldS, double* T, int ldT, double* Q,
         if (o.sched == GBR_SCHED_PERSISTENT) {
             SchedInfo inf;
             rc = run_persistent_gen(n, win, S, ldS, T, ldT, Q, ldQ, Z, ldZ, d_sel, d_ctr, o, &ntasks,
-                                    &ms_sched, &inf, st);
+                                    &ms_sched, &launches, &inf, st);
             if (rc) return rc;
             info_all.cp_us = inf.cp_us;
             info_all.sim_us = inf.sim_us;
             info_all.graph_ms += inf.graph_ms;
             info_all.order_ms += inf.order_ms;
-            launches += 1;
         } else
         for (const Window& wd : win) {
             if (o.timing) GBR_CK(mark(evw), "event");

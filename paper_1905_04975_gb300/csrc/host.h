@@ -37,7 +37,8 @@ int num_sms();
 // Device scratch pool (api.cu): one grow-only allocation per device and slot;
 // callers hold api_mutex() while they use it.
 constexpr int POOL_GEN_SCRATCH = 6, POOL_GEN_HOST = 7, POOL_GEN_SCHED = 8, POOL_SWEEP = 9,
-              POOL_SWEEP_SCHED = 10, POOL_SCHED_ALT = 11, POOL_NSLOTS = 12;
+              POOL_SWEEP_SCHED = 10, POOL_SCHED_ALT = 11, POOL_GEN_SCHED_ALT = 12,
+              POOL_NSLOTS = 13;
 int pool_get(int slot, size_t bytes, void** out);
 std::mutex& api_mutex();
 
@@ -178,5 +179,23 @@ int sched_enqueue(const SchedLaunch& L, cudaStream_t st,
 // Keeps the per-task timeline of a finished traced launch (opts.timing = 2)
 // for gbr_last_trace.
 int store_trace(const SchedLaunch& L);
+
+// One planned pass of one instance through the persistent scheduler (api.cu).
+// The windows are put in pipeline order; a large pass is cut into chunks
+// that run as consecutive launches, each planned and uploaded while the
+// previous one runs, from two launch images that alternate between the pool
+// slots slot[0] and slot[1].
+struct PassLaunch {
+    Inst inst;                 // the instance (T and Z set for a pair)
+    CostModel cm;              // duration model of the queue order
+    int slot[2];               // pool slots of the two launch images
+    int mode = -1;             // scheduler instance forced after planning (-1: as planned)
+    const char* timeout_msg;   // message of GBR_ERR_TIMEOUT
+};
+// Adds the tasks, the launches and (with opts.timing) the launches' device
+// time to the outputs; *info receives the chunks' planning figures summed.
+int run_pass_persistent(const std::vector<Window>& wins, const PassLaunch& pl, const gbr_opts& o,
+                        long long* ntasks_out, double* ms_out, long long* launches_out,
+                        SchedInfo* info, cudaStream_t st);
 
 }  // namespace gbr

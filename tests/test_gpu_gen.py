@@ -193,6 +193,27 @@ def test_persistent_matches_sequential(gbr, n, w, m):
     check(S, T, Q, Z, sel, rp, Sp, Tp, Qp, Zp)
 
 
+@pytest.mark.parametrize("prec", ["fma", "ozaki"])
+def test_chunked_launches_match_one_launch(gbr, prec):
+    """A pass of more than 1024 pair windows runs as three consecutive
+    persistent launches, each planned while the previous one runs; together
+    they keep the program order of one launch, so (S, T, Q, Z) come out
+    bitwise as from a single traced (hence unchunked) launch."""
+    n = 1200
+    S, T, Q, Z, sel = si.gen_problem(n, 21, select_frac=0.5, reflectors=8)
+    sub = np.append(np.diag(S, -1) != 0, False).astype(np.uint8)
+    assert len(gbr.plan(sub, sel, 16, 6)[0]) >= 1024
+    r1, S1, T1, Q1, Z1 = run_gpu(gbr, S, T, Q, Z, sel, window=16, chain=6, precision=prec)
+    assert r1.status == 0
+    check(S, T, Q, Z, sel, r1, S1, T1, Q1, Z1)
+    r2, S2, T2, Q2, Z2 = run_gpu(gbr, S, T, Q, Z, sel, window=16, chain=6, precision=prec,
+                                 timing=2)
+    assert r2.status == 0 and r2.stats.tasks == r1.stats.tasks
+    assert r1.stats.launches == r2.stats.launches + 2   # one pass, three launches
+    for a, b in ((S1, S2), (T1, T2), (Q1, Q2), (Z1, Z2)):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("name,n,w,m", [("n200", 200, 64, 32), ("ragged515", 515, 32, 12),
                                         ("g400", 400, 64, 32)])
 def test_split_precision_updates(gbr, name, n, w, m):
