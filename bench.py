@@ -87,6 +87,14 @@ NCU_TRAFFIC = {("n4000", "dmma"): 1.937360e9 + 2.652817e9,
                ("h4000", "persistent-dmma"): 0.220709e9 + 0.187885e9}
 
 
+def f_min_flops(n, swaps):
+    """The unblocked scalar floor of a reordering: every adjacent swap applied
+    as a rotation to two rows and two columns of S and two columns of Q, 6
+    flops per element pair over about 2n elements, i.e. 12 n flops per swap
+    (about 6 p (1 - p) n^3 in all for a fraction p selected)."""
+    return 12.0 * n * swaps
+
+
 def whole_job_rate(units, local_ms, dist=None, device="cpu"):
     """Replicas: every rank processed `units` in `local_ms`; the job's time is
     the slowest rank's (max over ranks), and its rate is all ranks' units over
@@ -1546,7 +1554,12 @@ def run_reorder(args, wl):
                            "upd_flops": st0.upd_flops, "upd_flops_issued": st0.upd_flops_issued,
                            "win_flops": st0.win_flops,
                            "fp64_tflops_of_step": m["fp64_tflops_of_step"],
-                           "host_graph_ms": st0.ms_graph, "host_order_ms": st0.ms_order}}
+                           "host_graph_ms": st0.ms_graph, "host_order_ms": st0.ms_order,
+                           # unblocked scalar floor: 12 n flops per adjacent swap (a
+                           # rotation on two rows and two columns of S and two of Q)
+                           "f_min_flops": f_min_flops(n, int(st0.swaps)),
+                           "f_min_tflops_of_step": f_min_flops(n, int(st0.swaps))
+                           / (m["ms"] / 1e3) / 1e12}}
         if len(precs) > 1:
             o = res[precs[1]]
             line["split_precision"] = {
