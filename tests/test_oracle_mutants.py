@@ -46,6 +46,9 @@ MUTANTS = [
     ("block above assumed 1x1", "int pa = (here - 2 >= ks && EL(S, ldS, here - 1, here - 2) != 0.0) ? 2 : 1;",
      "int pa = 1;"),
     ("2x2 selection not merged", "sel[j] = sel[j + 1] = s2;", "(void)s2;"),
+    ("abort ignored", "if (!ok && abort_on_reject) break;", "if (!ok && abort_on_reject < 0) break;"),
+    ("selection flags left behind", "for (int i = j; i < j + q; ++i) sel[i] = 1;\n",
+     "for (int i = j; i < j; ++i) sel[i] = 1;\n"),
     ("eigenvalue imaginary part", "double im = sqrt(fabs(EL(S, ldS, j, j + 1))) * sqrt(fabs(EL(S, ldS, j + 1, j)));",
      "double im = sqrt(fabs(EL(S, ldS, j, j + 1)));"),
 ]
@@ -73,6 +76,7 @@ checks = [
     lambda: P.test_swap_decision_matches_dtrsen(),
     lambda: P.test_invariants_n400("n400"),
     lambda: P.test_edge_cases(),
+    lambda: P.test_rejection_semantics(),
 ]
 failed = 0
 for c in checks:
