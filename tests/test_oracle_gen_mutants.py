@@ -36,6 +36,12 @@ MUTANTS = [
      "*b = s11 * t22 + s22 * t11 + s21 * t12;"),
     ("second reflector skipped", "house0(k - 1, x, v2, &tau2);", "tau2 = 0.0;"),
     ("weak test dropped", "if (lowa > tha || lowb > thb) return 1;", ";"),
+    ("old flags kept at the moved block", "for (int i = j + q; i < j + q + pa; ++i) sel[i] = 0;",
+     "for (int i = j + q; i < j + q; ++i) sel[i] = 0;"),
+    ("block above taken as 1x1",
+     "const int pa = (here - 2 >= ks && EL(S, ldS, here - 1, here - 2) != 0.0) ? 2 : 1;",
+     "const int pa = 1;"),
+    ("2x2 selection not merged", "sel[j] = sel[j + 1] = s2;", "(void)s2;"),
     ("real pair roots swapped", "wr[j] = m + r; wi[j] = 0.0;\n                wr[j + 1] = m - r;",
      "wr[j] = m - r; wi[j] = 0.0;\n                wr[j + 1] = m + r;"),
 ]
