@@ -28,6 +28,10 @@ MUTANTS = [
     ("reflector sign", "double b = alpha >= 0.0 ? -norm : norm;", "double b = alpha >= 0.0 ? norm : -norm;"),
     ("last bulge stops early", "const int last = (n - 3) + 3 * (nb - 1) + 1;",
      "const int last = (n - 3) + 3 * (nb - 1);"),
+    ("introduction misses row 3", "apply(n, H, ldH, Q, ldQ, 0, 3, v, tau, 0, n < 4 ? n : 4);",
+     "apply(n, H, ldH, Q, ldQ, 0, 3, v, tau, 0, n < 3 ? n : 3);"),
+    ("bulge fill not cleared", "for (int i = 1; i < len; ++i) EL(H, ldH, k + 1 + i, k) = 0.0;",
+     "for (int i = 1; i < 1; ++i) EL(H, ldH, k + 1 + i, k) = 0.0;"),
     ("Q not updated", "            for (int i = 0; i < len; ++i) EL(Q, ldQ, r, r0 + i) -= w * v[i];",
      "            for (int i = 0; i < len; ++i) (void)w;"),
 ]
