@@ -31,6 +31,12 @@ MUTANTS = [
      "for (int it = 0; it < 0 && cabs1(r[b0]) > BIG * cabs1(d); ++it) {"),
     ("no scaling before an update", "for (int it = 0; it < 8 && rb + k * cm * xm > BIG; ++it) {",
      "for (int it = 0; it < 0 && rb + k * cm * xm > BIG; ++it) {"),
+    ("pair selected by its first row only",
+     "int sel = select ? (select[j] != 0 || (nb == 2 && select[j + 1] != 0)) : 1;",
+     "int sel = select ? (select[j] != 0) : 1;"),
+    ("real and imaginary columns exchanged",
+     "for (int i = 0; i < n; ++i) AT(Y, ldY, i, m) = y[i].re;",
+     "for (int i = 0; i < n; ++i) AT(Y, ldY, i, m) = nb == 2 ? y[i].im : y[i].re;"),
     ("normalization norm", "for (int i = 0; i < top; ++i) mx = fmax(mx, cabs1(y[i]));",
      "for (int i = 0; i < top; ++i) mx = fmax(mx, fabs(y[i].re));"),
 ]
